@@ -1,0 +1,380 @@
+"""Throughput benchmark: a brick random circuit on one GPU per process.
+
+Default workload (the precision + fusion configuration): the 30-qubit brick
+random circuit of depth 40 (U3 on every qubit, then CNOT(i, i+1) on
+alternating pairs; the QSB structure of §IV-F), seed 6, complex64 state
+(8 GiB) in the tiled (multi-gate-per-HBM-pass) plan.  The same circuit in
+complex128 (16 GiB) runs beside it and both are reported, with their
+infidelity measured on the GPU.
+
+Metric (§IV-F, Eq. 5 traffic model): effective HBM bandwidth
+    2 * 2^n * bytes_per_amplitude * #gates / time
+(every logical gate counted as one read + write of the whole vector), and
+logical gates per second.  `value` is the whole-job effective GB/s of the
+headline dtype (summed over ranks; one independent replica per GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload brick30|brick28|qft28] [--dtype c64|c128]
+                  [--mode tiled|unfused]
+
+`--impl reference` times the FP64 CPU oracle (a deliberately plain program)
+on the host cores, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "brick30": dict(n=30, make=lambda: W.brick(30, 40, 6), desc="30-qubit brick random circuit, depth 40, seed 6"),
+    "brick28": dict(n=28, make=lambda: W.brick(28, 40, 3), desc="28-qubit brick random circuit, depth 40, seed 3"),
+    "qft28": dict(n=28, make=lambda: W.qft(28), desc="28-qubit QFT"),
+    "brick20": dict(n=20, make=lambda: W.brick(20, 40, 6), desc="20-qubit brick random circuit, depth 40, seed 6"),
+}
+S_BYTES = {"c64": 8, "c128": 16}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(workload, budget_s):
+    """Run the oracle over the first gates of the workload circuit until
+    ``budget_s`` of wall time is spent; returns (gates_done, seconds, n)."""
+    import oracle
+    wl = WORKLOADS[workload]
+    n = wl["n"]
+    circ = wl["make"]()
+    psi = oracle.zero_state(n)
+    oracle.run_circuit(psi, circ[:1])  # touch the pages before timing
+    done, t0 = 0, time.perf_counter()
+    while done < len(circ) and time.perf_counter() - t0 < budget_s:
+        oracle.run_circuit(psi, circ[done:done + 1])
+        done += 1
+    return done, time.perf_counter() - t0, n
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    S = 16  # the oracle computes in FP64 (complex128)
+    per_step = []
+    gates = 0
+    for i in range(args.warmup + args.steps):
+        g, t, _ = oracle_sample(args.workload, args.ref_budget)
+        if i >= args.warmup:
+            per_step.append(t)
+            gates += g
+    T = sum(per_step)
+    gbs = 2.0 * (1 << n) * S * gates / T / 1e9
+    line = {
+        "impl": "reference", "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate)",
+        "value": gbs, "unit": "GB/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * T / len(per_step), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"] + " (oracle, FP64 complex128)", "n": n, "gates_per_step": gates / len(per_step)},
+        "gates_per_s": gates / T,
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"first gates of the circuit, {args.ref_budget:.0f} s of wall time per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def timed_run(qs, torch, state, plan, steps, warmup, world, device, profile=True):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        state.set_basis(0)
+        state.run(plan)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        state.set_basis(0)
+        if profile:
+            step_ms.append(state.run_profiled(plan))
+        else:
+            state.run(plan)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return allreduce_max(ms, world, device), step_ms
+
+
+def kernel_roofline(plan, step_ms, peak):
+    """Per step kind: algorithmic bytes and device time summed over the timed
+    steps; the dominant kind (largest time) gives the roofline object."""
+    info = plan.step_info()
+    tot_t, tot_b, cnt = {}, {}, {}
+    for ms in step_ms:
+        for (kind, b), t in zip(info, ms):
+            tot_t[kind] = tot_t.get(kind, 0.0) + t
+            tot_b[kind] = tot_b.get(kind, 0.0) + b
+            cnt[kind] = cnt.get(kind, 0) + 1
+    if not tot_t:
+        return None, {}
+    dom = max(tot_t, key=tot_t.get)
+    achieved = tot_b[dom] / (tot_t[dom] / 1e3) / 1e9
+    per_kind = {k: {"launches": cnt[k], "ms": tot_t[k], "share": tot_t[k] / sum(tot_t.values()),
+                    "GB/s": tot_b[k] / (tot_t[k] / 1e3) / 1e9} for k in tot_t}
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "bytes_per_launch": tot_b[dom] / cnt[dom],
+            "ms_per_launch": tot_t[dom] / cnt[dom]}, per_kind
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2203_16044_gb300 as qs
+
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    circ = wl["make"]()
+    mode = qs.PLAN_TILED if args.mode == "tiled" else qs.PLAN_UNFUSED
+    peak, peak_kind = measured_peaks()
+    results = {}
+    dtypes = [args.dtype] + ([d for d in ("c64", "c128") if d != args.dtype] if args.both else [])
+    circuit = qs.Circuit(circ)
+    states = {}
+    for dt in dtypes:
+        plan = qs.Plan(circuit, n, dt, mode=mode)
+        st = plan.stats()
+        state = qs.State(n, dt, device=device)
+        with ClockSampler(local) as clk:
+            ms, step_ms = timed_run(qs, torch, state, plan, args.steps, args.warmup, world, device)
+        roof, per_kind = kernel_roofline(plan, step_ms, peak)
+        S = S_BYTES[dt]
+        eff = st["metric_bytes"] / (ms / 1e3) / 1e9
+        results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
+                       "passes": st["passes"], "gates": st["gates"], "hbm_bytes_per_step": st["hbm_bytes"],
+                       "hbm_GBps": st["hbm_bytes"] / (ms / 1e3) / 1e9, "roofline": roof, "kernels": per_kind,
+                       "clocks": clk.summary(), "bytes_per_amp": S,
+                       "gpu_launches": (st["passes"] + 1) * args.steps}
+        states[dt] = state
+        del plan
+    # precision: infidelity of the headline run against complex128 on the GPU
+    infid = None
+    if "c64" in states and "c128" in states:
+        a64 = states["c64"].tensor.to(torch.complex128)
+        ov = torch.vdot(a64, states["c128"].tensor).item()
+        infid = 1.0 - abs(ov) ** 2
+        del a64
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(qs, torch, args, n, circ, mode, device, world)
+    head = results[args.dtype]
+    line = {
+        "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate) & gates/s, 30-qubit brick circuit",
+        "value": head["effective_GBps"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": n, "gates": head["gates"], "dtype": args.dtype,
+                   "plan": args.mode, "passes": head["passes"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (state %.0f GiB)" % (2.0 ** n * S_BYTES[args.dtype] / 2 ** 30)},
+        "gates_per_s": head["gates_per_s"],
+        "hbm_GBps_algorithmic": head["hbm_GBps"],
+        "roofline": dict(head["roofline"], traffic=None, peak_source=peak_kind) if head["roofline"] else None,
+        "kernels": head["kernels"],
+        "clocks": head["clocks"],
+        "gpu_launches": head["gpu_launches"],
+        "e2e": e2e,
+        "precision": {"infidelity_c64_vs_c128": infid},
+        "other_dtypes": {dt: {k: v for k, v in r.items() if k not in ("kernels",)} for dt, r in results.items()
+                         if dt != args.dtype},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, t, n_cpu = oracle_sample(args.workload, args.cpu_budget)
+        line["cpu_baseline"] = {"value": 2.0 * (1 << n_cpu) * 16 * g / t / 1e9, "unit": "GB/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": f"first {g} gates of the same circuit at n={n_cpu}, FP64 complex128 "
+                                          f"(16 B/amplitude), {t:.1f} s wall",
+                                "gates_per_s": g / t}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(qs, torch, args, n, circ, mode, device, world):
+    """Per step: host state -> device (pinned), compile the circuit, run it,
+    device -> host (pinned); timed on the host around the whole call chain."""
+    dt = args.dtype
+    tdt = torch.complex64 if dt == "c64" else torch.complex128
+    host = torch.zeros(1 << n, dtype=tdt, pin_memory=True)
+    host[0] = 1
+    state = qs.State(n, dt, device=device)
+    S = S_BYTES[dt]
+    steps = max(1, min(args.steps, 3))
+    gates = len(circ)
+    times = []
+    for i in range(1 + steps):
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        c = qs.Circuit(circ)
+        p = qs.Plan(c, n, dt, mode=mode)
+        qs.lib().qs_set_stream(state.handle, qs._stream_ptr())
+        assert qs.lib().qs_copy_from_host(state.handle, ctypes_ptr(host)) == 0
+        state.run(p)
+        assert qs.lib().qs_copy_to_host(state.handle, ctypes_ptr(host)) == 0
+        t = time.perf_counter() - t0
+        if i > 0:
+            times.append(t)
+        host.zero_()
+        host[0] = 1
+    T = allreduce_max(sum(times) / len(times), world, device)
+    del state
+    return {"value": 2.0 * (1 << n) * S * gates / T / 1e9 * world, "unit": "GB/s",
+            "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": (1 << n) * S,
+            "ms_per_step": 1000 * T, "gates_per_s": gates / T * world, "steps": steps}
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="brick30", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--mode", default="tiled", choices=["tiled", "unfused"])
+    ap.add_argument("--both", type=int, default=1, help="also run the other dtype")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * qs.h -- C ABI of the GB300 state-vector gate engine (libqs.so).
+ *
+ * The library applies a quantum circuit's gates to a full 2^n-amplitude
+ * complex state vector resident in GPU memory (sm_103a, one GPU per process).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  State layout (§II-A, Eq. 2): amplitude a_x of basis state |x> is element x;
+ *    bit q of x is qubit q (qubit 0 = least significant).  QS_C128 stores
+ *    interleaved (re, im) doubles, 16 bytes per amplitude, 2^(n+4) bytes in
+ *    total (§I); QS_C64 stores interleaved (re, im) floats, 8 bytes per
+ *    amplitude.  These are the numpy/PyTorch complex128 / complex64 layouts.
+ *  Matrices are always passed on the host in FP64: a 2x2 matrix is 8 doubles,
+ *    row-major, (re, im) per entry; a k-qubit matrix over qubits[0..k-1] is
+ *    2^k x 2^k row-major, and bit i of its row/column index r corresponds to
+ *    qubits[i].  QS_C64 states round matrices to FP32 once per call.
+ *  Host arrays passed in are read before the call returns; the caller keeps
+ *    ownership.  Device work is enqueued on the state's stream (qs_set_stream)
+ *    and is asynchronous unless the call returns a host value.
+ *  Errors: every call returns a qs_status.  Argument errors are detected
+ *    synchronously, return QS_EINVAL and leave the state unchanged.  CUDA
+ *    launch errors return QS_ECUDA; asynchronous device errors surface on the
+ *    next call that synchronises (qs_sync, reductions, copies).  The library
+ *    never aborts the process.  qs_last_error() returns a thread-local
+ *    description of the most recent failure.
+ *  Numerics: QS_C64 computes in FP32; QS_C128 computes with at least 48-bit
+ *    significands (FP64, or double-float pairs of FP32 values where the FP64
+ *    pipe would be the bottleneck).  Reductions (norm, inner product,
+ *    expectation values) accumulate in at least FP64-equivalent precision for
+ *    both dtypes and are deterministic (fixed reduction order).
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qs_status;
+enum {
+  QS_OK = 0,
+  QS_EINVAL = -1,        /* bad argument; nothing was enqueued            */
+  QS_ENOMEM = -2,        /* device or host allocation failed              */
+  QS_ECUDA = -3,         /* CUDA runtime / launch error                   */
+  QS_ETIMEOUT = -4,      /* a bounded device wait gave up                 */
+  QS_EUNSUPPORTED = -5   /* valid request this build does not implement   */
+};
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Largest qubit count accepted by qs_alloc / qs_wrap (2^34 amplitudes). */
+#define QS_MAX_QUBITS 34
+
+typedef struct qs_state qs_state;     /* opaque: one state vector        */
+typedef struct qs_circuit qs_circuit; /* opaque: host-side gate list     */
+typedef struct qs_plan qs_plan;       /* opaque: compiled pass schedule  */
+
+/* Thread-local text of the last failure ("" if none).  Never NULL. */
+const char* qs_last_error(void);
+/* Library version string. */
+const char* qs_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* State lifetime                                                         */
+/* ---------------------------------------------------------------------- */
+
+/* Allocate a state of n qubits (1 <= n <= QS_MAX_QUBITS) on the current
+ * device, initialised to |0...0>.  The library owns the memory (freed by
+ * qs_free).  QS_ENOMEM if the device allocation fails. */
+qs_status qs_alloc(int n, qs_dtype dtype, qs_state** out);
+
+/* Wrap caller-owned device memory of 2^n amplitudes of `dtype` (for example
+ * a PyTorch tensor's storage).  dev_ptr must be 16-byte aligned and stay
+ * valid until qs_free; the contents are not touched; qs_free does not free
+ * it. */
+qs_status qs_wrap(int n, qs_dtype dtype, void* dev_ptr, qs_state** out);
+
+/* Release the handle (and its memory if it came from qs_alloc) after
+ * synchronising its stream.  NULL is accepted. */
+qs_status qs_free(qs_state* st);
+
+/* Enqueue all later work of this state on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream). */
+qs_status qs_set_stream(qs_state* st, void* stream);
+
+/* Wait for all work enqueued on the state's stream; reports any pending
+ * asynchronous device error as QS_ECUDA. */
+qs_status qs_sync(qs_state* st);
+
+/* Device pointer and size of the amplitude array. */
+qs_status qs_data(qs_state* st, void** dev_ptr, size_t* bytes);
+
+/* Set the state to the basis state |x>, x < 2^n (§II-A, Eq. 2). */
+qs_status qs_set_basis(qs_state* st, uint64_t x);
+
+/* Copy the whole amplitude array to / from host memory of 2^n amplitudes in
+ * the state's dtype layout.  Synchronous with respect to the host.  Pinned
+ * host memory gives full link bandwidth; pageable memory also works. */
+qs_status qs_copy_to_host(qs_state* st, void* dst);
+qs_status qs_copy_from_host(qs_state* st, const void* src);
+
+/* ---------------------------------------------------------------------- */
+/* Gate application (one HBM pass each)                                   */
+/* ---------------------------------------------------------------------- */
+
+/* One-qubit gate U on qubit q, Eq. (4) of §II-A: for every x with bit q
+ * clear and y = x | 2^q, (a_x, a_y) <- U (a_x, a_y).  U: 8 doubles. */
+qs_status qs_apply_1q(qs_state* st, int q, const double U[8]);
+
+/* Controlled one-qubit gate: Eq. (4) applied only where every control bit
+ * of x is 1 (CNOT = controlled X, as in the CNOT layers of §IV-F).
+ * 0 <= nc <= 8 distinct controls, all different from target. */
+qs_status qs_apply_controlled(qs_state* st, const int* controls, int nc, int target,
+                              const double U[8]);
+
+/* Diagonal gate on k distinct qubits (1 <= k <= 8): a_x <- d[r(x)] a_x with
+ * bit i of r(x) = bit qubits[i] of x.  d: 2^k complex values (2^(k+1)
+ * doubles).  RZ, CZ and the controlled phases of the QFT are diagonal. */
+qs_status qs_apply_diag(qs_state* st, const int* qubits, int k, const double* d);
+
+/* Dense k-qubit gate (1 <= k <= 6) on distinct qubits: for every base x with
+ * the k bits clear, the 2^k amplitudes a[x | spread(r)] are multiplied by
+ * the 2^k x 2^k matrix M (2^(2k+1) doubles, row-major, (re, im)). */
+qs_status qs_apply_fused(qs_state* st, const int* qubits, int k, const double* M);
+
+/* Qubit permutation: out[pi(x)] = in[x] where pi moves bit j of x to bit
+ * perm[j]; perm is a permutation of 0..n-1.  In place.  The fused swap of
+ * §III-D (Listing 1) is the permutation exchanging the disjoint bit fields
+ * [p, p+s) and [q, q+s); any permutation runs as at most two in-place passes
+ * of disjoint bit-field exchanges. */
+qs_status qs_permute_qubits(qs_state* st, const int* perm);
+
+/* fused_swap(p, q, s) of §III-D: swap(p+i, q+i) for i = 0..s-1; the ranges
+ * [p, p+s) and [q, q+s) must not overlap.  One in-place pass that moves the
+ * 2^n (1 - 2^-s) amplitudes whose two fields differ. */
+qs_status qs_fused_swap(qs_state* st, int p, int q, int s);
+
+/* ---------------------------------------------------------------------- */
+/* Reductions (return host values; synchronise the state's stream)       */
+/* ---------------------------------------------------------------------- */
+
+/* out = sum_x |a_x|^2. */
+qs_status qs_norm2(qs_state* st, double* out);
+
+/* out[0] + i out[1] = <a|b> = sum_x conj(a_x) b_x.  Same n and dtype. */
+qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
+
+/* out = sum_t coeff[t] <psi|P_t|psi> for Pauli strings P_t with X on the
+ * qubits set only in xmask[t], Z on those set only in zmask[t], Y on those
+ * set in both.  1 <= nterms <= 65536. */
+qs_status qs_expect_pauli(qs_state* st, int nterms, const uint64_t* xmask,
+                          const uint64_t* zmask, const double* coeff, double* out);
+
+/* ---------------------------------------------------------------------- */
+/* Circuits and compiled plans                                            */
+/* ---------------------------------------------------------------------- */
+
+/* Gate kinds for qs_circuit_add.  Angles in radians.
+ *   H, X, Y, Z, S = diag(1, i), T = diag(1, e^{i pi/4})
+ *   RX/RY/RZ(t) = exp(-i t P / 2),  P(l) = diag(1, e^{il})
+ *   U3(t, p, l) = [[cos t/2, -e^{il} sin t/2], [e^{ip} sin t/2, e^{i(p+l)} cos t/2]]
+ *   CNOT(control, target), CZ(a, b), CP(a, b; l) = diag(1,1,1,e^{il}), SWAP(a, b)
+ */
+typedef enum {
+  QS_GATE_H = 0, QS_GATE_X, QS_GATE_Y, QS_GATE_Z, QS_GATE_S, QS_GATE_T,
+  QS_GATE_RX, QS_GATE_RY, QS_GATE_RZ, QS_GATE_P, QS_GATE_U3,
+  QS_GATE_CNOT = 16, QS_GATE_CZ, QS_GATE_CP, QS_GATE_SWAP
+} qs_gate_kind;
+
+qs_status qs_circuit_create(qs_circuit** out);
+qs_status qs_circuit_destroy(qs_circuit* c);
+/* Append one gate.  qubits: 1 or 2 entries by kind; params: 0, 1 or 3 angles
+ * by kind (NULL when none).  param_index >= 0 marks the (single) angle of an
+ * RX/RY/RZ gate as trainable parameter number param_index (used by
+ * qs_adjoint_grad); -1 otherwise. */
+qs_status qs_circuit_add(qs_circuit* c, int kind, const int* qubits, int nq,
+                         const double* params, int param_index);
+/* Number of gates appended so far. */
+qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
+
+/* Plan options.  mode: QS_PLAN_UNFUSED applies every gate with its own pass
+ * (one kernel per gate); QS_PLAN_TILED groups gates into shared-memory tile
+ * passes.  tile_qubits: qubits resident per tile pass (0 = library default
+ * for the dtype); low_qubits: qubits 0..low_qubits-1 kept in every tile for
+ * coalesced access (0 = default). */
+enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1 };
+typedef struct {
+  int mode;
+  int tile_qubits;
+  int low_qubits;
+  int reserved[5];
+} qs_plan_opts;
+
+typedef struct {
+  int n;              /* qubits                                          */
+  int dtype;          /* qs_dtype                                        */
+  int gates;          /* logical gates of the circuit                    */
+  int passes;         /* HBM passes of the plan (kernel launches)        */
+  double hbm_bytes;   /* algorithmic HBM bytes of one run of the plan    */
+  double metric_bytes;/* 2 * 2^n * bytes_per_amp * gates (Eq. 5 traffic) */
+} qs_plan_stats;
+
+/* Compile circuit `c` for n qubits and `dtype`.  opts may be NULL
+ * (QS_PLAN_TILED with defaults).  The plan keeps its own copy of the gates;
+ * device-side gate tables are uploaded on the first qs_run_plan. */
+qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_plan_opts* opts,
+                        qs_plan** out);
+qs_status qs_plan_stats_get(const qs_plan* p, qs_plan_stats* out);
+qs_status qs_plan_destroy(qs_plan* p);
+
+/* Apply the whole plan to the state (n and dtype must match). */
+qs_status qs_run_plan(qs_state* st, qs_plan* p);
+
+/* Step kinds reported by qs_plan_step_info. */
+enum { QS_STEP_1Q = 0, QS_STEP_CTRL = 1, QS_STEP_DIAG = 2, QS_STEP_SWAP = 3, QS_STEP_TILE = 4 };
+
+/* Kind and algorithmic HBM bytes (read + write of the amplitudes it
+ * touches) of plan step i, 0 <= i < passes. */
+qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_bytes);
+
+/* As qs_run_plan, and also times every step with CUDA events recorded on the
+ * state's stream between launches: step_ms[i] receives the device time of
+ * step i (nsteps must equal the plan's pass count).  Synchronises the
+ * stream before returning.  Event recording adds a few microseconds per
+ * step; use qs_run_plan for throughput. */
+qs_status qs_run_plan_profiled(qs_state* st, qs_plan* p, float* step_ms, int nsteps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_H */

@@ -1,0 +1,256 @@
+// Circuits and compiled plans.
+//
+// A circuit is an ordered gate sequence (§II-A).  qs_plan_build compiles it
+// for a qubit count and dtype into a list of HBM passes:
+//   QS_PLAN_UNFUSED  one pass per gate, the per-gate traffic model of Eq. (5):
+//                    dense one-qubit gates as pair updates (Eq. 4), CNOT as a
+//                    controlled update, diagonal gates (RZ, CZ, CP, ...) as
+//                    diagonal passes, SWAP as an in-place bit exchange.
+//   QS_PLAN_TILED    gates grouped into shared-memory tile passes (tile.cu):
+//                    the single-GPU form of applying gates on local qubits
+//                    (§III-B) -- a tile of 2^m amplitudes spanning a chosen
+//                    qubit set is read once, every gate on those qubits is
+//                    applied in shared memory, and the tile is written back.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qs_internal.h"
+#include "planner.h"
+
+using namespace qs;
+
+namespace qs {
+
+// Algorithmic HBM bytes of one unfused step (read + write of what it touches).
+double step_bytes(const qs_step& st, int n, int S) {
+  const double N = std::ldexp(1.0, n);
+  switch (st.type) {
+    case qs_step::GATE_1Q: return 2.0 * N * S;
+    case qs_step::GATE_CTRL: return 2.0 * N * S / std::ldexp(1.0, st.nq - 1);
+    case qs_step::GATE_DIAG: {
+      const int k = st.nq, D = 1 << k;
+      bool sparse = true;
+      for (int r = 0; r < D - 1 && sparse; ++r) sparse = (st.m[2 * r] == 1.0 && st.m[2 * r + 1] == 0.0);
+      return sparse ? 2.0 * N * S / D : 2.0 * N * S;
+    }
+    case qs_step::GATE_SWAP: return N * S;  // half the amplitudes move
+    case qs_step::TILE: return 2.0 * N * S;
+  }
+  return 0.0;
+}
+
+qs_step unfused_step(const qs_gate_rec& g) {
+  qs_step st{};
+  double m[32];
+  gate_matrix(g.kind, g.p, m);
+  const int arity = gate_arity(g.kind);
+  if (arity == 1) {
+    st.q[0] = g.q[0];
+    if (gate_is_diagonal(g.kind)) {
+      st.type = qs_step::GATE_DIAG;
+      st.nq = 1;
+      st.m[0] = m[0]; st.m[1] = m[1];   // d0 = m00
+      st.m[2] = m[6]; st.m[3] = m[7];   // d1 = m11
+    } else {
+      st.type = qs_step::GATE_1Q;
+      st.nq = 1;
+      std::memcpy(st.m, m, sizeof(double) * 8);
+    }
+  } else if (g.kind == QS_GATE_CNOT) {
+    st.type = qs_step::GATE_CTRL;
+    st.nq = 2;
+    st.q[0] = g.q[0];  // control
+    st.q[1] = g.q[1];  // target
+    double x[8];
+    gate_matrix(QS_GATE_X, nullptr, x);
+    std::memcpy(st.m, x, sizeof(x));
+  } else if (g.kind == QS_GATE_SWAP) {
+    st.type = qs_step::GATE_SWAP;
+    st.nq = 2;
+    st.q[0] = g.q[0];
+    st.q[1] = g.q[1];
+  } else {  // CZ, CP: diagonal of the 4x4 matrix
+    st.type = qs_step::GATE_DIAG;
+    st.nq = 2;
+    st.q[0] = g.q[0];
+    st.q[1] = g.q[1];
+    for (int r = 0; r < 4; ++r) {
+      st.m[2 * r] = m[2 * (r * 4 + r)];
+      st.m[2 * r + 1] = m[2 * (r * 4 + r) + 1];
+    }
+  }
+  return st;
+}
+
+qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
+  switch (st.type) {
+    case qs_step::GATE_1Q: return run_1q(s, st.q[0], st.m);
+    case qs_step::GATE_CTRL: return run_controlled(s, &st.q[0], st.nq - 1, st.q[st.nq - 1], st.m);
+    case qs_step::GATE_DIAG: return run_diag(s, st.q, st.nq, st.m);
+    case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
+    case qs_step::TILE: return run_tile(s, p, st.tile_index);
+  }
+  return fail(QS_EINVAL, "bad plan step");
+}
+
+}  // namespace qs
+
+extern "C" {
+
+qs_status qs_circuit_create(qs_circuit** out) {
+  if (!out) return fail(QS_EINVAL, "qs_circuit_create: out is NULL");
+  *out = new (std::nothrow) qs_circuit();
+  return *out ? QS_OK : fail(QS_ENOMEM, "qs_circuit_create");
+}
+
+qs_status qs_circuit_destroy(qs_circuit* c) {
+  delete c;
+  return QS_OK;
+}
+
+qs_status qs_circuit_add(qs_circuit* c, int kind, const int* qubits, int nq, const double* params,
+                         int param_index) {
+  if (!c) return fail(QS_EINVAL, "qs_circuit_add: circuit is NULL");
+  const int arity = gate_arity(kind);
+  if (arity < 0) return fail(QS_EINVAL, "qs_circuit_add: unknown gate kind %d", kind);
+  if (nq != arity || !qubits) return fail(QS_EINVAL, "qs_circuit_add: kind %d takes %d qubits", kind, arity);
+  if (qubits[0] < 0 || (arity == 2 && (qubits[1] < 0 || qubits[1] == qubits[0])))
+    return fail(QS_EINVAL, "qs_circuit_add: qubits must be distinct and non-negative");
+  const int np = gate_nparams(kind);
+  if (np > 0 && !params) return fail(QS_EINVAL, "qs_circuit_add: kind %d needs %d params", kind, np);
+  if (param_index >= 0 && !(kind == QS_GATE_RX || kind == QS_GATE_RY || kind == QS_GATE_RZ))
+    return fail(QS_EINVAL, "qs_circuit_add: only RX/RY/RZ angles can be trainable");
+  qs_gate_rec g{};
+  g.kind = kind;
+  g.q[0] = qubits[0];
+  g.q[1] = arity == 2 ? qubits[1] : -1;
+  for (int i = 0; i < np; ++i) g.p[i] = params[i];
+  g.param_index = param_index < 0 ? -1 : param_index;
+  c->gates.push_back(g);
+  return QS_OK;
+}
+
+qs_status qs_circuit_size(const qs_circuit* c, int* ngates) {
+  if (!c || !ngates) return fail(QS_EINVAL, "qs_circuit_size: NULL argument");
+  *ngates = (int)c->gates.size();
+  return QS_OK;
+}
+
+qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_plan_opts* opts, qs_plan** out) {
+  if (!c || !out) return fail(QS_EINVAL, "qs_plan_build: NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qs_plan_build: n=%d outside [1, %d]", n, QS_MAX_QUBITS);
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "qs_plan_build: bad dtype");
+  for (size_t i = 0; i < c->gates.size(); ++i) {
+    const qs_gate_rec& g = c->gates[i];
+    if (g.q[0] >= n || g.q[1] >= n)
+      return fail(QS_EINVAL, "qs_plan_build: gate %zu acts on a qubit >= n=%d", i, n);
+  }
+  qs_plan* p = new (std::nothrow) qs_plan();
+  if (!p) return fail(QS_ENOMEM, "qs_plan_build");
+  p->n = n;
+  p->dtype = dtype;
+  if (opts) p->opts = *opts;
+  else {
+    std::memset(&p->opts, 0, sizeof(p->opts));
+    p->opts.mode = QS_PLAN_TILED;
+  }
+  p->gates = c->gates;
+  qs_status st;
+  if (p->opts.mode == QS_PLAN_UNFUSED) {
+    for (const qs_gate_rec& g : p->gates) p->steps.push_back(unfused_step(g));
+    st = QS_OK;
+  } else if (p->opts.mode == QS_PLAN_TILED) {
+    st = plan_tiled(p);
+  } else {
+    st = fail(QS_EINVAL, "qs_plan_build: unknown mode %d", p->opts.mode);
+  }
+  if (st != QS_OK) {
+    qs_plan_destroy(p);
+    return st;
+  }
+  const int S = amp_bytes(dtype);
+  p->stats.n = n;
+  p->stats.dtype = dtype;
+  p->stats.gates = (int)p->gates.size();
+  p->stats.passes = (int)p->steps.size();
+  p->stats.hbm_bytes = 0.0;
+  for (const qs_step& s : p->steps) p->stats.hbm_bytes += step_bytes(s, n, S);
+  p->stats.metric_bytes = 2.0 * std::ldexp(1.0, n) * S * (double)p->gates.size();
+  *out = p;
+  return QS_OK;
+}
+
+qs_status qs_plan_stats_get(const qs_plan* p, qs_plan_stats* out) {
+  if (!p || !out) return fail(QS_EINVAL, "qs_plan_stats_get: NULL argument");
+  *out = p->stats;
+  return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan* p) {
+  if (!p) return QS_OK;
+  for (qs_tile_pass* t : p->tiles) tile_free(t);
+  if (p->dev_tables) cudaFree(p->dev_tables);
+  delete p;
+  return QS_OK;
+}
+
+qs_status qs_run_plan(qs_state* s, qs_plan* p) {
+  if (!s || !p) return fail(QS_EINVAL, "qs_run_plan: NULL argument");
+  if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan: plan built for another n/dtype");
+  if (!p->tiles.empty()) {
+    qs_status st = plan_tiles_upload(p, s->stream);
+    if (st != QS_OK) return st;
+  }
+  for (const qs_step& st : p->steps) {
+    qs_status r = run_step(s, p, st);
+    if (r != QS_OK) return r;
+  }
+  return QS_OK;
+}
+
+qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_bytes) {
+  if (!p || !kind || !hbm_bytes) return fail(QS_EINVAL, "qs_plan_step_info: NULL argument");
+  if (i < 0 || i >= (int)p->steps.size()) return fail(QS_EINVAL, "qs_plan_step_info: step %d out of range", i);
+  const qs_step& st = p->steps[i];
+  switch (st.type) {
+    case qs_step::GATE_1Q: *kind = QS_STEP_1Q; break;
+    case qs_step::GATE_CTRL: *kind = QS_STEP_CTRL; break;
+    case qs_step::GATE_DIAG: *kind = QS_STEP_DIAG; break;
+    case qs_step::GATE_SWAP: *kind = QS_STEP_SWAP; break;
+    case qs_step::TILE: *kind = QS_STEP_TILE; break;
+  }
+  *hbm_bytes = step_bytes(st, p->n, amp_bytes(p->dtype));
+  return QS_OK;
+}
+
+qs_status qs_run_plan_profiled(qs_state* s, qs_plan* p, float* step_ms, int nsteps) {
+  if (!s || !p || !step_ms) return fail(QS_EINVAL, "qs_run_plan_profiled: NULL argument");
+  if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan_profiled: plan built for another n/dtype");
+  if (nsteps != (int)p->steps.size()) return fail(QS_EINVAL, "qs_run_plan_profiled: nsteps != %zu", p->steps.size());
+  if (!p->tiles.empty()) {
+    qs_status st = plan_tiles_upload(p, s->stream);
+    if (st != QS_OK) return st;
+  }
+  std::vector<cudaEvent_t> ev(nsteps + 1);
+  for (auto& e : ev) {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return cuda_fail(r, "qs_run_plan_profiled: event");
+  }
+  qs_status result = QS_OK;
+  cudaEventRecord(ev[0], s->stream);
+  for (int i = 0; i < nsteps && result == QS_OK; ++i) {
+    result = run_step(s, p, p->steps[i]);
+    cudaEventRecord(ev[i + 1], s->stream);
+  }
+  cudaError_t r = cudaStreamSynchronize(s->stream);
+  if (result == QS_OK && r != cudaSuccess) result = cuda_fail(r, "qs_run_plan_profiled: sync");
+  if (result == QS_OK)
+    for (int i = 0; i < nsteps; ++i) cudaEventElapsedTime(&step_ms[i], ev[i], ev[i + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,11 @@
+// Planner internals shared by planner.cpp and tile.cu.
+#pragma once
+#include "qs_internal.h"
+
+namespace qs {
+double step_bytes(const qs_step& st, int n, int S);
+qs_step unfused_step(const qs_gate_rec& g);
+qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st);
+// Fills p->steps (and p->tiles) for QS_PLAN_TILED.
+qs_status plan_tiled(qs_plan* p);
+}  // namespace qs

@@ -1,0 +1,109 @@
+// Internal declarations of libqs (not installed; the public ABI is qs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qs.h"
+
+typedef uint64_t u64;
+
+struct qs_state {
+  int n = 0;
+  qs_dtype dtype = QS_C128;
+  void* amp = nullptr;          // 2^n amplitudes, interleaved (re, im)
+  bool owns = false;            // allocated by qs_alloc
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* scratch = nullptr;      // reduction partials, plan tables
+  size_t scratch_bytes = 0;
+  double* pinned = nullptr;     // small pinned host buffer for results
+};
+
+namespace qs {
+
+// ---- errors ---------------------------------------------------------------
+qs_status fail(qs_status code, const char* fmt, ...);
+qs_status cuda_fail(cudaError_t e, const char* what);
+// Check for a launch error after enqueueing kernels.
+qs_status launch_ok(const char* what);
+
+inline int amp_bytes(qs_dtype d) { return d == QS_C64 ? 8 : 16; }
+inline u64 state_bytes(const qs_state* s) { return (u64(1) << s->n) * amp_bytes(s->dtype); }
+
+// Grows the state's device scratch buffer to at least `bytes` (stream-ordered).
+qs_status ensure_scratch(qs_state* s, size_t bytes);
+
+// SM count of the current device (cached).
+int sm_count();
+
+// ---- host-side gate matrices (gatemat.cpp) ---------------------------------
+// Writes the 2x2 (nq = 1) or 4x4 (nq = 2) matrix of a named gate; returns nq
+// or -1 for an unknown kind.  Bit 0 of a 4x4 index = qubits[0].
+int gate_matrix(int kind, const double* params, double* out);
+int gate_arity(int kind);
+int gate_nparams(int kind);
+bool gate_is_diagonal(int kind);
+
+// ---- kernels (gates.cu) ----------------------------------------------------
+qs_status run_1q(qs_state* s, int q, const double U[8]);
+qs_status run_controlled(qs_state* s, const int* ctrl, int nc, int t, const double U[8]);
+qs_status run_diag(qs_state* s, const int* qubits, int k, const double* d);
+qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M);
+// In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
+qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
+qs_status run_set_basis(qs_state* s, u64 x);
+
+// ---- reductions (reduce.cu) ------------------------------------------------
+qs_status run_norm2(qs_state* s, double* out);
+qs_status run_inner(qs_state* a, qs_state* b, double out[2]);
+qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask,
+                     const double* coeff, double* out);
+
+}  // namespace qs
+
+// ---- circuits and plans (planner.cpp / tile.cu) -----------------------------
+struct qs_gate_rec {
+  int kind;
+  int q[2];
+  double p[3];
+  int param_index;
+};
+
+struct qs_circuit {
+  std::vector<qs_gate_rec> gates;
+};
+
+// One step of a compiled plan.
+struct qs_step {
+  enum Type { GATE_1Q, GATE_CTRL, GATE_DIAG, GATE_SWAP, TILE } type;
+  int q[4];
+  int nq;
+  double m[32];         // matrix / diagonal (FP64)
+  int tile_index;       // TILE: index into plan->tiles
+};
+
+struct qs_tile_pass;    // defined in tile.cu
+
+struct qs_plan {
+  int n = 0;
+  qs_dtype dtype = QS_C128;
+  qs_plan_opts opts{};
+  std::vector<qs_gate_rec> gates;
+  std::vector<qs_step> steps;
+  qs_plan_stats stats{};
+  // tile passes (host description + device tables), owned by tile.cu helpers
+  std::vector<qs_tile_pass*> tiles;
+  void* dev_tables = nullptr;
+  size_t dev_tables_bytes = 0;
+  int dev_tables_device = -1;
+};
+
+namespace qs {
+qs_status plan_tiles_upload(qs_plan* p, cudaStream_t stream);
+qs_status run_tile(qs_state* s, qs_plan* p, int tile_index);
+void tile_free(qs_tile_pass* t);
+}  // namespace qs

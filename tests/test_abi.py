@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports every entry point include/qs.h
+declares; host-side argument validation and plan building (no GPU calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*(qs_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_16044_gb300 as qs
+    return qs
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ["qs_alloc", "qs_apply_1q", "qs_apply_diag", "qs_apply_controlled", "qs_apply_fused",
+                 "qs_permute_qubits", "qs_expect_pauli", "qs_run_plan"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(qs):
+    lib = ctypes.CDLL(qs.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", qs.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (qs_[a-z0-9_]+)", out))
+    assert set(declared_functions()) <= exported
+    # the binding wraps every declared entry point
+    assert set(declared_functions()) <= set(qs.EXPORTED)
+
+
+def test_null_and_range_checks_without_gpu(qs):
+    L = qs.lib()
+    U = (ctypes.c_double * 8)(1, 0, 0, 0, 0, 0, 1, 0)
+    assert L.qs_apply_1q(None, 0, U) == qs.QS_EINVAL
+    assert "NULL" in L.qs_last_error().decode()
+    h = ctypes.c_void_p()
+    assert L.qs_alloc(0, qs.C128, ctypes.byref(h)) == qs.QS_EINVAL
+    assert L.qs_alloc(35, qs.C128, ctypes.byref(h)) == qs.QS_EINVAL
+    assert L.qs_alloc(10, 7, ctypes.byref(h)) == qs.QS_EINVAL
+    assert L.qs_wrap(10, qs.C128, ctypes.c_void_p(8), ctypes.byref(h)) == qs.QS_EINVAL  # misaligned
+    assert L.qs_free(None) == qs.QS_OK
+
+
+def test_circuit_and_plan_host_logic(qs):
+    import workloads as W
+    c = qs.Circuit(W.brick(12, 20, 1))
+    assert len(c) == 350
+    p = qs.Plan(c, 12, "c128", mode=qs.PLAN_UNFUSED)
+    s = p.stats()
+    assert s["gates"] == 350 and s["passes"] == 350
+    N, S = 1 << 12, 16
+    assert s["metric_bytes"] == 2 * N * S * 350
+    # U3: full pass; CNOT: half the amplitudes (one control)
+    assert s["hbm_bytes"] == 240 * 2 * N * S + 110 * N * S
+    # QFT: H full, CP touches a quarter, SWAP moves half
+    q = qs.Plan(qs.Circuit(W.qft(12)), 12, "c64", mode=qs.PLAN_UNFUSED).stats()
+    assert q["hbm_bytes"] == 12 * 2 * N * 8 + 66 * 2 * N * 8 / 4 + 6 * N * 8
+    with pytest.raises(qs.QSError):
+        qs.Plan(c, 11, "c128", mode=qs.PLAN_UNFUSED)  # gate on qubit 11 >= n
+    with pytest.raises(qs.QSError):
+        c.add("CNOT", [3, 3])
+    with pytest.raises(qs.QSError):
+        c.add("U3", [1], [0.1, 0.2, 0.3], param_index=0)  # only RX/RY/RZ trainable

@@ -1,0 +1,100 @@
+"""GPU parity of whole circuits against the FP64 oracle.
+
+ * 12-qubit brick random circuit (U3 layer + nearest-neighbour CNOT layer,
+   the QSB shape of §IV-F), depth 20 and 40, and a 12-qubit QFT on a seeded
+   basis state: complex128 element-wise max error <= 1e-12; complex64
+   infidelity 1 - |<psi64|psi128>|^2 <= 1e-5 against the oracle's state.
+ * The paper's own synthetic circuits (QSB structure §IV-F, Hadamard
+   benchmark §IV-D) at small n.
+ * Every plan mode gives the same state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C128_TOL = 1e-12
+C64_INFIDELITY = 1e-5
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2203_16044_gb300 as qs
+    return qs
+
+
+def run_gpu(qs, n, circ, dtype, mode, x0=0):
+    s = qs.State(n, dtype)
+    s.set_basis(x0)
+    stats = qs.run_circuit(s, circ, mode=mode)
+    return s.to_numpy(), stats
+
+
+def infidelity(psi64, ref):
+    ov = np.vdot(psi64.astype(np.complex128), ref)
+    return 1.0 - abs(ov) ** 2
+
+
+def oracle_state(n, circ, x0=0):
+    psi = oracle.zero_state(n, x0)
+    oracle.run_circuit(psi, circ)
+    return psi
+
+
+CASES = [
+    ("brick12_d20", 12, lambda: W.brick(12, 20, 1), 0),
+    ("brick12_d40", 12, lambda: W.brick(12, 40, 1), 0),
+    ("qft12", 12, lambda: W.qft(12), W.basis_index(12, 2)),
+    ("brick9_d40", 9, lambda: W.brick(9, 40, 21), 0),
+    ("qsb10", 10, lambda: W.qsb(10, 22), 0),
+    ("hadamard11x7", 7, lambda: W.hadamard_bench(7), 5),
+    ("ghz16", 16, lambda: W.ghz(16), 0),
+    ("brick3", 3, lambda: W.brick(3, 10, 23), 0),
+    ("brick1", 1, lambda: W.brick(1, 5, 24), 0),
+]
+
+
+@pytest.mark.parametrize("name,n,make,x0", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["unfused", "tiled"])
+def test_circuit_matches_oracle(qs, name, n, make, x0, dtype, mode):
+    circ = make()
+    want = oracle_state(n, circ, x0)
+    got, stats = run_gpu(qs, n, circ, dtype, mode, x0)
+    assert stats["gates"] == len(circ)
+    if dtype == "c128":
+        err = np.max(np.abs(got - want))
+        assert err <= C128_TOL, err
+    else:
+        assert infidelity(got, want) <= C64_INFIDELITY
+        assert abs(np.vdot(got, got).real - 1) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["unfused", "tiled"])
+def test_qft_closed_form_gpu(qs, dtype, mode):
+    n = 14
+    x0 = W.basis_index(n, 9)
+    got, _ = run_gpu(qs, n, W.qft(n), dtype, mode, x0)
+    delta = np.zeros(1 << n, dtype=complex)
+    delta[x0] = 1
+    want = np.fft.ifft(delta) * math.sqrt(1 << n)
+    tol = C128_TOL if dtype == "c128" else 2e-6
+    assert np.max(np.abs(got - want)) <= tol
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["unfused", "tiled"])
+def test_c64_vs_oracle_depth40_16q(qs, mode):
+    # the complex64 tolerance at depth 40 on a size the oracle runs in seconds
+    n = 16
+    circ = W.brick(n, 40, 8)
+    want = oracle_state(n, circ)
+    got, _ = run_gpu(qs, n, circ, "c64", mode)
+    assert infidelity(got, want) <= C64_INFIDELITY

@@ -1,0 +1,225 @@
+"""GPU parity of every gate / reduction entry point against the FP64 oracle.
+
+Same seeded inputs on both sides (workloads module).  Tolerances:
+  complex128: max |a_gpu - a_oracle| <= 1e-12 (absolute, unit-norm states).
+  complex64:  FP32 arithmetic; a 2x2 (or 2^k x 2^k) complex mat-vec with
+              FMA contraction rounds each output with relative error about
+              (k + 2) * 2^-24 of the sum of |terms|, and the inputs (state and
+              matrix) are themselves rounded to FP32: tolerance
+              C64_TOL * max|a| with C64_TOL = 4e-6 for single gates.
+Sizes run from 1 qubit (less than one CTA of work) to 16 qubits (many CTAs
+and grid-stride iterations), so tails and multi-tile cases are covered.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C128_TOL = 1e-12
+C64_TOL = 4e-6
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2203_16044_gb300 as qs
+    return qs
+
+
+def gpu_state(qs, psi, dtype):
+    n = int(psi.size).bit_length() - 1
+    s = qs.State(n, dtype)
+    s.from_numpy(psi.astype(np.complex64 if dtype == "c64" else np.complex128))
+    return s
+
+
+def check(got, want, dtype, scale=None):
+    err = np.max(np.abs(got.astype(np.complex128) - want))
+    if dtype == "c128":
+        assert err <= C128_TOL, err
+    else:
+        ref = scale if scale is not None else max(np.max(np.abs(want)), 1e-30)
+        assert err <= C64_TOL * ref, (err, ref)
+
+
+def start(psi, dtype):
+    """The oracle's input: for c64 the same FP32-rounded values the GPU gets."""
+    if dtype == "c64":
+        return psi.astype(np.complex64).astype(np.complex128)
+    return psi.copy()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 11, 16])
+def test_apply_1q_every_target(qs, dtype, n):
+    psi = W.random_state(n, 1000 + n)
+    for q in range(n):
+        U = W.random_unitary(2, 2000 + 17 * n + q)
+        s = gpu_state(qs, psi, dtype)
+        s.apply_1q(q, U)
+        want = start(psi, dtype)
+        oracle.apply_1q(want, q, U)
+        check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,nc", [(2, 1), (5, 1), (9, 2), (12, 3), (14, 1)])
+def test_apply_controlled(qs, dtype, n, nc):
+    psi = W.random_state(n, 3000 + n)
+    for seed in range(6):
+        qsel = W.random_qubits(n, nc + 1, 3100 + 31 * n + seed)
+        ctrl, t = qsel[:nc], qsel[nc]
+        U = W.random_matrix(2, 3200 + seed)
+        s = gpu_state(qs, psi, dtype)
+        s.apply_controlled(ctrl, t, U)
+        want = start(psi, dtype)
+        oracle.apply_controlled(want, ctrl, t, U)
+        check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_cnot_every_pair(qs, dtype):
+    n = 7
+    X = np.array([[0, 1], [1, 0]])
+    psi = W.random_state(n, 4000)
+    for c in range(n):
+        for t in range(n):
+            if c == t:
+                continue
+            s = gpu_state(qs, psi, dtype)
+            s.apply_controlled([c], t, X)
+            want = start(psi, dtype)
+            oracle.apply_controlled(want, [c], t, X)
+            check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,k", [(1, 1), (4, 1), (6, 2), (10, 3), (13, 5), (15, 8)])
+def test_apply_diag_general(qs, dtype, n, k):
+    psi = W.random_state(n, 5000 + n)
+    for seed in range(3):
+        qsel = W.random_qubits(n, k, 5100 + 7 * n + seed)
+        d = W.random_diag(1 << k, 5200 + seed, unit=(seed != 2))
+        s = gpu_state(qs, psi, dtype)
+        s.apply_diag(qsel, d)
+        want = start(psi, dtype)
+        oracle.apply_diag(want, qsel, d)
+        check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,k", [(1, 1), (3, 2), (8, 2), (12, 3), (16, 1)])
+def test_apply_diag_phase_on_ones(qs, dtype, n, k):
+    # CZ / CP / Z-type: every entry 1 but the last (the sparse kernel)
+    psi = W.random_state(n, 6000 + n)
+    for seed in range(4):
+        qsel = W.random_qubits(n, k, 6100 + 5 * n + seed)
+        d = np.ones(1 << k, dtype=complex)
+        d[-1] = np.exp(1j * (0.3 + seed))
+        s = gpu_state(qs, psi, dtype)
+        s.apply_diag(qsel, d)
+        want = start(psi, dtype)
+        oracle.apply_diag(want, qsel, d)
+        check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,k", [(2, 2), (5, 3), (9, 4), (12, 5), (13, 6), (11, 1)])
+def test_apply_fused(qs, dtype, n, k):
+    psi = W.random_state(n, 7000 + n)
+    for seed in range(2):
+        qsel = W.random_qubits(n, k, 7100 + n + seed)
+        M = W.random_unitary(1 << k, 7200 + seed)
+        s = gpu_state(qs, psi, dtype)
+        s.apply_fused(qsel, M)
+        want = start(psi, dtype)
+        oracle.apply_dense(want, qsel, M)
+        check(s.to_numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [2, 4, 7, 12, 15])
+def test_fused_swap(qs, dtype, n):
+    psi = W.random_state(n, 8000 + n)
+    cases = [(0, n // 2, n // 2), (n // 2, 0, n // 2), (0, 1, 1), (n - 2, 0, 1), (1, n - 1, 1)]
+    for (p, q, sw) in cases:
+        if sw < 1 or p + sw > n or q + sw > n or not (p + sw <= q or q + sw <= p):
+            continue
+        s = gpu_state(qs, psi, dtype)
+        s.fused_swap(p, q, sw)
+        want = start(psi, dtype)
+        oracle.fused_swap(want, p, q, sw)
+        # a permutation moves values exactly
+        assert np.array_equal(s.to_numpy().astype(np.complex128), want)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 3, 6, 10, 14])
+def test_permute_qubits(qs, dtype, n):
+    psi = W.random_state(n, 9000 + n)
+    for seed in range(4):
+        perm = W.random_perm(n, 9100 + seed)
+        s = gpu_state(qs, psi, dtype)
+        s.permute_qubits(perm)
+        want = oracle.permute(start(psi, dtype), perm)
+        assert np.array_equal(s.to_numpy().astype(np.complex128), want)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 5, 12, 17])
+def test_norm_and_inner(qs, dtype, n):
+    a = W.random_state(n, 10000 + n, normalise=False)
+    b = W.random_state(n, 10100 + n, normalise=False)
+    sa, sb = gpu_state(qs, a, dtype), gpu_state(qs, b, dtype)
+    a0, b0 = start(a, dtype), start(b, dtype)
+    want_n = oracle.inner(a0, a0).real
+    want_i = oracle.inner(a0, b0)
+    # FP64 accumulation of the same (FP32-exact for c64) inputs
+    assert abs(sa.norm2() - want_n) <= 1e-12 * want_n
+    assert abs(sa.inner(sb) - want_i) <= 1e-12 * (1 << n)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [2, 6, 11])
+def test_expect_pauli(qs, dtype, n):
+    psi = W.random_state(n, 11000 + n)
+    terms = W.random_paulis(n, 40, 11100 + n) + W.tfim(n)
+    s = gpu_state(qs, psi, dtype)
+    want = oracle.expect_pauli(start(psi, dtype), terms)
+    got = s.expect_pauli(terms)
+    assert abs(got - want) <= 1e-12 * sum(abs(t.coeff) for t in terms)
+
+
+def test_set_basis_and_alloc_via_abi(qs):
+    import ctypes
+    L = qs.lib()
+    h = ctypes.c_void_p()
+    assert L.qs_alloc(9, qs.C128, ctypes.byref(h)) == qs.QS_OK
+    buf = np.zeros(1 << 9, dtype=np.complex128)
+    assert L.qs_copy_to_host(h, buf.ctypes.data_as(ctypes.c_void_p)) == qs.QS_OK
+    assert buf[0] == 1 and np.count_nonzero(buf) == 1
+    assert L.qs_set_basis(h, 300) == qs.QS_OK
+    assert L.qs_copy_to_host(h, buf.ctypes.data_as(ctypes.c_void_p)) == qs.QS_OK
+    assert buf[300] == 1 and np.count_nonzero(buf) == 1
+    assert L.qs_set_basis(h, 512) == qs.QS_EINVAL
+    assert L.qs_free(h) == qs.QS_OK
+
+
+def test_invalid_arguments_leave_state_unchanged(qs):
+    psi = W.random_state(5, 12000)
+    s = gpu_state(qs, psi, "c128")
+    with pytest.raises(qs.QSError):
+        s.apply_1q(5, np.eye(2))
+    with pytest.raises(qs.QSError):
+        s.apply_controlled([2], 2, np.eye(2))
+    with pytest.raises(qs.QSError):
+        s.apply_diag([1, 1], np.ones(4))
+    with pytest.raises(qs.QSError):
+        s.fused_swap(0, 1, 2)
+    with pytest.raises(qs.QSError):
+        s.permute_qubits([0, 0, 1, 2, 3])
+    assert np.array_equal(s.to_numpy(), psi)
