@@ -155,6 +155,26 @@ qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status qs_expect_pauli(qs_state* st, int nterms, const uint64_t* xmask,
                           const uint64_t* zmask, const double* coeff, double* out);
 
+/* Allocation-free inner product, for callers that cannot let the library
+ * allocate device memory (a framework allocator that owns the GPU's memory,
+ * a latency-critical loop where cudaMalloc/cudaFree would synchronise, a
+ * host policy that forbids allocations outside its own allocator).  The
+ * paper has no counterpart; this is an interface convenience.
+ *   a, b:   device pointers to 2^n amplitudes of `dtype` (16-byte aligned),
+ *           caller-owned, read only.
+ *   stream: cudaStream_t to run on (NULL = legacy default stream).
+ *   out:    host array; receives <a|b> = sum_x conj(a_x) b_x (re, im), FP64.
+ * Synchronises `stream` before returning.  Allocates nothing: its partial
+ * sums live in a fixed 16 KiB (1024 x 16-byte partials + result) static
+ * device array that every GPU loading the library keeps until exit.  The
+ * first call on a device looks that array's address up (make it before any
+ * stream capture that should contain the call).  All calls share the array:
+ * calls that overlap on the GPU race and must be serialised.  Returns
+ * QS_EUNSUPPORTED if the reduction would need more than 1024 partials (a
+ * device with more than 256 SMs). */
+qs_status qs_inner_noalloc(const void* a, const void* b, int n, qs_dtype dtype, void* stream,
+                           double out[2]);
+
 /* ---------------------------------------------------------------------- */
 /* Circuits and compiled plans                                            */
 /* ---------------------------------------------------------------------- */

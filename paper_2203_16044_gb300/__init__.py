@@ -73,6 +73,7 @@ _SIGS = {
     "qs_norm2": ([_vp, _dp], _int),
     "qs_inner": ([_vp, _vp, _dp], _int),
     "qs_expect_pauli": ([_vp, _int, _up, _up, _dp, _dp], _int),
+    "qs_inner_noalloc": ([_vp, _vp, _int, _int, _vp, _dp], _int),
     "qs_circuit_create": ([ctypes.POINTER(_vp)], _int),
     "qs_circuit_destroy": ([_vp], _int),
     "qs_circuit_add": ([_vp, _int, _ip, _int, _dp, _int], _int),
