@@ -205,14 +205,20 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
 /* Plan options.  mode: QS_PLAN_UNFUSED applies every gate with its own pass
  * (one kernel per gate); QS_PLAN_TILED groups gates into shared-memory tile
  * passes.  tile_qubits: qubits resident per tile pass (0 = library default
- * for the dtype); low_qubits: qubits 0..low_qubits-1 kept in every tile for
- * coalesced access (0 = default). */
+ * for the dtype; at most 14 for QS_C64, 13 for QS_C128); low_qubits: qubits
+ * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);
+ * slot_qubits: qubits held in registers per stage inside a tile pass, 3 or
+ * 4 (0 = default); groups_per_thread: register groups a thread works on at
+ * once, 1 or 2 (0 = default; QS_C128 with 4 slots always uses 1).  Every
+ * field must be zero or valid. */
 enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1 };
 typedef struct {
   int mode;
   int tile_qubits;
   int low_qubits;
-  int reserved[5];
+  int slot_qubits;
+  int groups_per_thread;
+  int reserved[3];
 } qs_plan_opts;
 
 typedef struct {
@@ -222,6 +228,8 @@ typedef struct {
   int passes;         /* HBM passes of the plan (kernel launches)        */
   double hbm_bytes;   /* algorithmic HBM bytes of one run of the plan    */
   double metric_bytes;/* 2 * 2^n * bytes_per_amp * gates (Eq. 5 traffic) */
+  int stages;         /* register stages summed over all tile passes     */
+  int reserved;
 } qs_plan_stats;
 
 /* Compile circuit `c` for n qubits and `dtype`.  opts may be NULL

@@ -15,9 +15,15 @@
 //    in shared memory and multiplies them by the 2^k x 2^k matrix.
 //  * bit-field exchange (swap / fused swap of §III-D, Listing 1): an
 //    in-place, shared-memory-tiled involution over pairs of 512-byte runs.
+//
+// Arithmetic: complex64 in FP32.  complex128 pair, diagonal and phase
+// updates run in double-float (dfloat.cuh): GB300's FP64 pipe is ~1/64 of
+// FP32, so native FP64 would cap these passes near a third of HBM bandwidth.
+// X-type gates (X, CNOT, Toffoli-like) are pure exchanges with no arithmetic.
 #include <algorithm>
 #include <cstring>
 
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 
 namespace qs {
@@ -28,13 +34,72 @@ constexpr int kUnroll = 2;
 constexpr int kWaves = 8;
 
 // ---------------------------------------------------------------------------
+// Per-amplitude-pair arithmetic: FP32 for complex64, double-float for
+// complex128 (values converted from / to FP64 with integer operations).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_apply(const M2<float>& U, float& ar, float& ai, float& br, float& bi) {
+  mv2(U, ar, ai, br, bi);
+}
+__device__ __forceinline__ void pair_apply(const M2df& U, double& ar, double& ai, double& br, double& bi) {
+  const dfl xr = d2df(ar), xi = d2df(ai), yr = d2df(br), yi = d2df(bi);
+  cdf x{xr.h, xr.l, xi.h, xi.l}, y{yr.h, yr.l, yi.h, yi.l};
+  mv2df(U, x, y);
+  ar = df2d(dfl{x.rh, x.rl});
+  ai = df2d(dfl{x.ih, x.il});
+  br = df2d(dfl{y.rh, y.rl});
+  bi = df2d(dfl{y.ih, y.il});
+}
+
+// Complex scalar in the kernel's arithmetic: FP32, or double-float (h, l).
+struct Zf { float r, i; };
+struct Zdf { float rh, rl, ih, il; };
+
+__device__ __forceinline__ void scal_apply(const Zf& z, float& xr, float& xi) {
+  const float r = z.r * xr - z.i * xi;
+  xi = z.r * xi + z.i * xr;
+  xr = r;
+}
+__device__ __forceinline__ void scal_apply(const Zdf& z, double& xr, double& xi) {
+  const dfl a = d2df(xr), b = d2df(xi);
+  cdf x{a.h, a.l, b.h, b.l};
+  const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
+  cmul_df(zh, zl, x);
+  xr = df2d(dfl{x.rh, x.rl});
+  xi = df2d(dfl{x.ih, x.il});
+}
+
+template <typename R> struct Ar;
+template <> struct Ar<float> { typedef M2<float> Mat; typedef Zf Z; };
+template <> struct Ar<double> { typedef M2df Mat; typedef Zdf Z; };
+
+Ar<float>::Mat to_mat(const double U[8], float) {
+  M2<float> m;
+  for (int i = 0; i < 8; ++i) m.m[i] = (float)U[i];
+  return m;
+}
+Ar<double>::Mat to_mat(const double U[8], double) {
+  M2df m;
+  for (int i = 0; i < 8; ++i) {
+    m.h[i] = (float)U[i];
+    m.l[i] = (float)(U[i] - (double)m.h[i]);
+  }
+  return m;
+}
+Zf to_z(double re, double im, float) { return Zf{(float)re, (float)im}; }
+Zdf to_z(double re, double im, double) {
+  const float rh = (float)re, ih = (float)im;
+  return Zdf{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+}
+
+// ---------------------------------------------------------------------------
 // Pair update over packets: p0 = expand(i), p1 = p0 + 2^tp.
 // jmask selects which amplitudes of a packet take part (complex64 packets
 // hold two; a control on qubit 0 restricts the update to the odd one).
+// XG: the matrix is X -- exchange, no arithmetic.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool XG>
 __global__ void __launch_bounds__(kThreads) k_pairs(R* __restrict__ a, u64 nwork, Ins ins, int tp,
-                                                    int jmask, M2<R> U) {
+                                                    int jmask, typename Ar<R>::Mat U) {
   constexpr int V = PK<R>::V, A = PK<R>::A;
   const u64 step = (u64)gridDim.x * kThreads * kUnroll;
   const u64 dp = u64(1) << tp;
@@ -51,8 +116,18 @@ __global__ void __launch_bounds__(kThreads) k_pairs(R* __restrict__ a, u64 nwork
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-      for (int j = 0; j < A; ++j)
-        if ((jmask >> j) & 1) mv2(U, x0[u][2 * j], x0[u][2 * j + 1], x1[u][2 * j], x1[u][2 * j + 1]);
+      for (int j = 0; j < A; ++j) {
+        if (!((jmask >> j) & 1)) continue;
+        if (XG) {
+          const R tr = x0[u][2 * j], ti = x0[u][2 * j + 1];
+          x0[u][2 * j] = x1[u][2 * j];
+          x0[u][2 * j + 1] = x1[u][2 * j + 1];
+          x1[u][2 * j] = tr;
+          x1[u][2 * j + 1] = ti;
+        } else {
+          pair_apply(U, x0[u][2 * j], x0[u][2 * j + 1], x1[u][2 * j], x1[u][2 * j + 1]);
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -67,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(R* __restrict__ a, u64 nwork
 // ---------------------------------------------------------------------------
 // complex64, target qubit 0: the pair (a_2p, a_2p+1) is one packet.
 // ---------------------------------------------------------------------------
+template <bool XG>
 __global__ void __launch_bounds__(kThreads) k_inpkt(float* __restrict__ a, u64 nwork, Ins ins, M2<float> U) {
   const u64 step = (u64)gridDim.x * kThreads * kUnroll;
   for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < nwork; base += step) {
@@ -79,7 +155,17 @@ __global__ void __launch_bounds__(kThreads) k_inpkt(float* __restrict__ a, u64 n
       ld16(a + p[u] * 4, v[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) mv2(U, v[u][0], v[u][1], v[u][2], v[u][3]);
+    for (int u = 0; u < kUnroll; ++u) {
+      if (XG) {
+        const float r = v[u][0], i = v[u][1];
+        v[u][0] = v[u][2];
+        v[u][1] = v[u][3];
+        v[u][2] = r;
+        v[u][3] = i;
+      } else {
+        mv2(U, v[u][0], v[u][1], v[u][2], v[u][3]);
+      }
+    }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
       if (base + (u64)u * kThreads < nwork) st16(a + p[u] * 4, v[u]);
@@ -94,15 +180,16 @@ template <typename R>
 struct DiagTab {
   int k;
   int q[kMaxDiagK];
-  R d[2 << kMaxDiagK];  // 2^k complex
+  typename Ar<R>::Z d[1 << kMaxDiagK];
 };
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_diag(R* __restrict__ a, u64 npk, const __grid_constant__ DiagTab<R> T) {
+  typedef typename Ar<R>::Z Z;
   constexpr int V = PK<R>::V, A = PK<R>::A, LA = PK<R>::LA;
-  __shared__ R sd[2 << kMaxDiagK];
+  __shared__ Z sd[1 << kMaxDiagK];
   const int D = 1 << T.k;
-  for (int i = threadIdx.x; i < 2 * D; i += kThreads) sd[i] = T.d[i];
+  for (int i = threadIdx.x; i < D; i += kThreads) sd[i] = T.d[i];
   __syncthreads();
   const u64 step = (u64)gridDim.x * kThreads * kUnroll;
   for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < npk; base += step) {
@@ -120,10 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(R* __restrict__ a, u64 npk, c
         const u64 x = (p << LA) | (u64)j;
         int r = 0;
         for (int i = 0; i < T.k; ++i) r |= (int)((x >> T.q[i]) & 1u) << i;
-        const R dr = sd[2 * r], di = sd[2 * r + 1];
-        const R xr = v[u][2 * j], xi = v[u][2 * j + 1];
-        v[u][2 * j] = dr * xr - di * xi;
-        v[u][2 * j + 1] = dr * xi + di * xr;
+        scal_apply(sd[r], v[u][2 * j], v[u][2 * j + 1]);
       }
     }
 #pragma unroll
@@ -139,7 +223,8 @@ __global__ void __launch_bounds__(kThreads) k_diag(R* __restrict__ a, u64 npk, c
 // Packets enumerated by bit insertion; jmask as in k_pairs.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_phase(R* __restrict__ a, u64 nwork, Ins ins, int jmask, R zr, R zi) {
+__global__ void __launch_bounds__(kThreads) k_phase(R* __restrict__ a, u64 nwork, Ins ins, int jmask,
+                                                    typename Ar<R>::Z z) {
   constexpr int V = PK<R>::V, A = PK<R>::A;
   const u64 step = (u64)gridDim.x * kThreads * kUnroll;
   for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < nwork; base += step) {
@@ -154,13 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_phase(R* __restrict__ a, u64 nwork
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
-      for (int j = 0; j < A; ++j) {
-        if ((jmask >> j) & 1) {
-          const R xr = v[u][2 * j], xi = v[u][2 * j + 1];
-          v[u][2 * j] = zr * xr - zi * xi;
-          v[u][2 * j + 1] = zr * xi + zi * xr;
-        }
-      }
+      for (int j = 0; j < A; ++j)
+        if ((jmask >> j) & 1) scal_apply(z, v[u][2 * j], v[u][2 * j + 1]);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
@@ -304,11 +384,8 @@ __global__ void __launch_bounds__(kThreads) k_bitswap(R* __restrict__ a, u64 nti
   }
 }
 
-template <typename R>
-M2<R> to_m2(const double U[8]) {
-  M2<R> m;
-  for (int i = 0; i < 8; ++i) m.m[i] = (R)U[i];
-  return m;
+bool is_x(const double U[8]) {
+  return U[0] == 0 && U[1] == 0 && U[2] == 1 && U[3] == 0 && U[4] == 1 && U[5] == 0 && U[6] == 0 && U[7] == 0;
 }
 
 Ins make_ins(std::vector<std::pair<int, int>> bits) {  // (position, value)
@@ -334,7 +411,9 @@ qs_status pairs_or_inpkt(qs_state* s, const int* ctrl, int nc, int t, const doub
     for (int i = 0; i < nc; ++i) bits.push_back({ctrl[i] - 1, 1});
     const u64 nwork = u64(1) << (nb - nc);
     const unsigned g = grid_for(nwork, (u64)kThreads * kUnroll, kWaves);
-    k_inpkt<<<g, kThreads, 0, s->stream>>>(reinterpret_cast<float*>(a), nwork, make_ins(bits), to_m2<float>(U));
+    const M2<float> m = to_mat(U, 0.0f);
+    if (is_x(U)) k_inpkt<true><<<g, kThreads, 0, s->stream>>>(reinterpret_cast<float*>(a), nwork, make_ins(bits), m);
+    else k_inpkt<false><<<g, kThreads, 0, s->stream>>>(reinterpret_cast<float*>(a), nwork, make_ins(bits), m);
     return launch_ok("k_inpkt");
   }
   std::vector<std::pair<int, int>> bits;
@@ -353,7 +432,9 @@ qs_status pairs_or_inpkt(qs_state* s, const int* ctrl, int nc, int t, const doub
   const u64 nwork = u64(1) << (nb - nins);
   const unsigned g = grid_for(nwork, (u64)kThreads * kUnroll, kWaves);
   (void)n_in;
-  k_pairs<R><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), t - LA, jmask, to_m2<R>(U));
+  const typename Ar<R>::Mat m = to_mat(U, R(0));
+  if (is_x(U)) k_pairs<R, true><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), t - LA, jmask, m);
+  else k_pairs<R, false><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), t - LA, jmask, m);
   return launch_ok("k_pairs");
 }
 
@@ -391,13 +472,13 @@ static qs_status diag_impl(qs_state* s, const int* qubits, int k, const double* 
     }
     const u64 nwork = u64(1) << (s->n - LA - (int)bits.size());
     const unsigned g = grid_for(nwork, (u64)kThreads * kUnroll, kWaves);
-    k_phase<R><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), jmask, (R)d[2 * (D - 1)], (R)d[2 * (D - 1) + 1]);
+    k_phase<R><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), jmask, to_z(d[2 * (D - 1)], d[2 * (D - 1) + 1], R(0)));
     return launch_ok("k_phase");
   }
   DiagTab<R> T{};
   T.k = k;
   for (int i = 0; i < k; ++i) T.q[i] = qubits[i];
-  for (int i = 0; i < 2 * D; ++i) T.d[i] = (R)d[i];
+  for (int i = 0; i < D; ++i) T.d[i] = to_z(d[2 * i], d[2 * i + 1], R(0));
   const u64 npk = u64(1) << (s->n - LA);
   const unsigned g = grid_for(npk, (u64)kThreads * kUnroll, kWaves);
   k_diag<R><<<g, kThreads, 0, s->stream>>>(a, npk, T);

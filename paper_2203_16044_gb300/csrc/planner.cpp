@@ -178,6 +178,7 @@ qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_pla
   p->stats.passes = (int)p->steps.size();
   p->stats.hbm_bytes = 0.0;
   for (const qs_step& s : p->steps) p->stats.hbm_bytes += step_bytes(s, n, S);
+  p->stats.stages = tile_stage_count(p);
   p->stats.metric_bytes = 2.0 * std::ldexp(1.0, n) * S * (double)p->gates.size();
   *out = p;
   return QS_OK;
@@ -192,7 +193,6 @@ qs_status qs_plan_stats_get(const qs_plan* p, qs_plan_stats* out) {
 qs_status qs_plan_destroy(qs_plan* p) {
   if (!p) return QS_OK;
   for (qs_tile_pass* t : p->tiles) tile_free(t);
-  if (p->dev_tables) cudaFree(p->dev_tables);
   delete p;
   return QS_OK;
 }
@@ -200,10 +200,6 @@ qs_status qs_plan_destroy(qs_plan* p) {
 qs_status qs_run_plan(qs_state* s, qs_plan* p) {
   if (!s || !p) return fail(QS_EINVAL, "qs_run_plan: NULL argument");
   if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan: plan built for another n/dtype");
-  if (!p->tiles.empty()) {
-    qs_status st = plan_tiles_upload(p, s->stream);
-    if (st != QS_OK) return st;
-  }
   for (const qs_step& st : p->steps) {
     qs_status r = run_step(s, p, st);
     if (r != QS_OK) return r;
@@ -230,10 +226,6 @@ qs_status qs_run_plan_profiled(qs_state* s, qs_plan* p, float* step_ms, int nste
   if (!s || !p || !step_ms) return fail(QS_EINVAL, "qs_run_plan_profiled: NULL argument");
   if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan_profiled: plan built for another n/dtype");
   if (nsteps != (int)p->steps.size()) return fail(QS_EINVAL, "qs_run_plan_profiled: nsteps != %zu", p->steps.size());
-  if (!p->tiles.empty()) {
-    qs_status st = plan_tiles_upload(p, s->stream);
-    if (st != QS_OK) return st;
-  }
   std::vector<cudaEvent_t> ev(nsteps + 1);
   for (auto& e : ev) {
     cudaError_t r = cudaEventCreate(&e);

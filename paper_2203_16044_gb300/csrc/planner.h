@@ -8,4 +8,6 @@ qs_step unfused_step(const qs_gate_rec& g);
 qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st);
 // Fills p->steps (and p->tiles) for QS_PLAN_TILED.
 qs_status plan_tiled(qs_plan* p);
+// Register stages summed over the plan's tile passes.
+int tile_stage_count(const qs_plan* p);
 }  // namespace qs

@@ -95,15 +95,11 @@ struct qs_plan {
   std::vector<qs_gate_rec> gates;
   std::vector<qs_step> steps;
   qs_plan_stats stats{};
-  // tile passes (host description + device tables), owned by tile.cu helpers
+  // tile passes (host description; owned by the plan, freed by tile_free)
   std::vector<qs_tile_pass*> tiles;
-  void* dev_tables = nullptr;
-  size_t dev_tables_bytes = 0;
-  int dev_tables_device = -1;
 };
 
 namespace qs {
-qs_status plan_tiles_upload(qs_plan* p, cudaStream_t stream);
 qs_status run_tile(qs_state* s, qs_plan* p, int tile_index);
 void tile_free(qs_tile_pass* t);
 }  // namespace qs

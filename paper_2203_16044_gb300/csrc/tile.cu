@@ -12,11 +12,15 @@
 // explicit swap / fused-swap insertion of §III-D: no permutation pass is
 // needed, since each pass gathers whichever qubits it works on.
 //
-// Inside a pass the gate list is split into stages.  A stage names three
-// "slot" qubits; each thread loads the 8 amplitudes spanning them (for one
-// assignment of the other tile bits) from shared memory into registers,
-// applies every gate of the stage whose target is a slot qubit (controls and
-// phases may be on any qubit), and writes them back.
+// Inside a pass the gate list is split into stages.  A stage names G "slot"
+// qubits (G = 3 or 4); each thread loads the 2^G amplitudes spanning them
+// (for GPT assignments of the other tile bits at once) from shared memory
+// into registers, applies every gate of the stage whose target is a slot
+// qubit (controls and phases may be on any qubit), and writes them back.
+// Each operation is decoded once per stage and thread and applied to all of
+// the thread's register groups.  Shared memory is XOR-swizzled so that the
+// strided accesses of a stage whose slots include low qubits stay free of
+// bank conflicts.
 //
 // Arithmetic: complex64 in FP32; complex128 in double-float (dfloat.cuh),
 // converted from / to the FP64 layout once per pass at load / store.
@@ -34,11 +38,11 @@ namespace qs {
 
 enum : uint8_t { T_U = 0, T_XPERM = 1, T_PHASE = 2, T_DIAG1 = 3, T_SWAP = 4 };
 
-// One operation of a tile pass (device format, 80 bytes).
+// One operation of a tile pass (device format, 80 bytes = 5 x 16).
 struct alignas(16) TOp {
   uint8_t type;
-  uint8_t a;        // slot of the target (T_U, T_XPERM), first slot (T_SWAP), qubit (T_DIAG1)
-  uint8_t b;        // second slot (T_SWAP)
+  uint8_t a;        // slot of the target (T_U, T_XPERM), lower slot (T_SWAP), qubit (T_DIAG1)
+  uint8_t b;        // upper slot (T_SWAP)
   uint8_t dglobal;  // T_DIAG1: a is a global qubit (constant over the tile)
   uint32_t lmask;   // local bits that must all be 1 (controls, phase bits)
   uint64_t gmask;   // global bits that must all be 1
@@ -47,20 +51,19 @@ struct alignas(16) TOp {
 static_assert(sizeof(TOp) == 80, "TOp layout");
 
 struct TStage {
-  uint8_t sq[3];    // local qubit of slot 0, 1, 2
-  uint8_t srt[3];   // the same, ascending (for index insertion)
+  uint8_t sq[4];    // local qubit of slot 0..3 (unused slots: 0)
+  uint8_t srt[4];   // the slot qubits ascending (for index insertion)
   uint16_t op_begin, op_end;
 };
-static_assert(sizeof(TStage) == 10, "TStage layout");
+static_assert(sizeof(TStage) == 12, "TStage layout");
 
 }  // namespace qs
 
 struct qs_tile_pass {
-  int L = 0, r = 0, m = 0;
+  int L = 0, r = 0, m = 0, G = 3;
   int H[24] = {0};
   std::vector<qs::TOp> ops;
   std::vector<qs::TStage> stages;
-  size_t ops_off = 0, stages_off = 0;  // byte offsets into the plan's device table
 };
 
 namespace qs {
@@ -69,15 +72,20 @@ namespace {
 constexpr int kTT = 256;         // threads per CTA
 constexpr int kTabBits = 6;      // spread tables: 2 x 64 entries
 constexpr int kMaxR = 2 * kTabBits;
+// A pass's ops and stages travel in the kernel parameter block (constant
+// bank: uniform, short-latency reads); the planner keeps passes within it.
+constexpr int kMaxOps = 288;
+constexpr int kMaxStages = 96;
 
 struct TileArgs {
   int L, m, r, nstages;
   u64 ntiles;
   Ins tins;            // zero insertion at the high tile qubits
   int H[kMaxR];
-  const TOp* ops;
-  const TStage* stages;
+  TStage stages[kMaxStages];
+  TOp ops[kMaxOps];
 };
+static_assert(sizeof(TileArgs) < 32000, "kernel parameter block limit");
 
 template <int MODE> struct Elem;
 template <> struct Elem<0> { typedef float2 T; };
@@ -88,182 +96,179 @@ __device__ __forceinline__ int ins1(int x, int p) {
   return ((x ^ lo) << 1) | lo;
 }
 
-// ---- per-op application on the 8 register amplitudes ----------------------
-
-template <int A>
-__device__ __forceinline__ void op_u(float2 (&v)[8], const int (&li)[8], uint32_t lmask, const M2<float>& U) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k & (1 << A)) continue;
-    if ((li[k] & lmask) == lmask) mv2(U, v[k].x, v[k].y, v[k | (1 << A)].x, v[k | (1 << A)].y);
-  }
-}
-template <int A>
-__device__ __forceinline__ void op_u(cdf (&v)[8], const int (&li)[8], uint32_t lmask, const M2df& U) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k & (1 << A)) continue;
-    if ((li[k] & lmask) == lmask) mv2df(U, v[k], v[k | (1 << A)]);
-  }
-}
-template <int A, typename T>
-__device__ __forceinline__ void op_x(T (&v)[8], const int (&li)[8], uint32_t lmask) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k & (1 << A)) continue;
-    if ((li[k] & lmask) == lmask) {
-      const T t = v[k];
-      v[k] = v[k | (1 << A)];
-      v[k | (1 << A)] = t;
-    }
-  }
-}
-template <int A, int B, typename T>
-__device__ __forceinline__ void op_swap(T (&v)[8]) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if ((k & (1 << A)) && !(k & (1 << B))) {
-      const int k2 = (k ^ (1 << A)) | (1 << B);
-      const T t = v[k];
-      v[k] = v[k2];
-      v[k2] = t;
-    }
-  }
+// amplitudes per 128-byte shared-memory row: 16 (complex64) or 8 (complex128)
+template <int MODE>
+__device__ __forceinline__ int swz(int x) {
+  constexpr int SW = MODE == 0 ? 4 : 3;
+  return x ^ ((x >> SW) & ((1 << SW) - 1));
 }
 
-__device__ __forceinline__ void cmul(float2& x, float zr, float zi) {
+// ---- arithmetic on one pair / one amplitude --------------------------------
+
+struct OpData {
+  uint32_t lmask;
+  float f[16];
+};
+
+__device__ __forceinline__ void pair_u(const OpData& d, float2& x, float2& y) {
+  M2<float> U;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) U.m[i] = d.f[i];
+  mv2(U, x.x, x.y, y.x, y.y);
+}
+__device__ __forceinline__ void pair_u(const OpData& d, cdf& x, cdf& y) {
+  M2df U;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    U.h[i] = d.f[i];
+    U.l[i] = d.f[8 + i];
+  }
+  mv2df(U, x, y);
+}
+__device__ __forceinline__ void amp_mul(float2& x, float zr, float zi, float, float) {
   const float r = zr * x.x - zi * x.y;
   x.y = zr * x.y + zi * x.x;
   x.x = r;
 }
+__device__ __forceinline__ void amp_mul(cdf& x, float zr, float zi, float zrl, float zil) {
+  const float zh[2] = {zr, zi}, zl[2] = {zrl, zil};
+  cmul_df(zh, zl, x);
+}
 
-__device__ __forceinline__ void apply_op(const TOp& op, float2 (&v)[8], const int (&li)[8], u64 F) {
-  if ((F & op.gmask) != op.gmask) return;
-  switch (op.type) {
-    case T_U: {
-      M2<float> U;
+// ---- per-op application on the register groups ------------------------------
+
+template <int G, int GPT, int A, bool CTRL, typename E>
+__device__ __forceinline__ void apply_u(E (&v)[GPT][1 << G], const int (&base)[GPT], const int (&sk)[1 << G],
+                                       const OpData& d) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) U.m[i] = op.f[i];
-      if (op.a == 0) op_u<0>(v, li, op.lmask, U);
-      else if (op.a == 1) op_u<1>(v, li, op.lmask, U);
-      else op_u<2>(v, li, op.lmask, U);
-    } break;
-    case T_XPERM:
-      if (op.a == 0) op_x<0>(v, li, op.lmask);
-      else if (op.a == 1) op_x<1>(v, li, op.lmask);
-      else op_x<2>(v, li, op.lmask);
-      break;
-    case T_PHASE:
+  for (int j = 0; j < GPT; ++j) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if ((li[k] & op.lmask) == op.lmask) cmul(v[k], op.f[0], op.f[1]);
-      break;
-    case T_DIAG1:
-      if (op.dglobal) {
-        const int hi = (int)((F >> op.a) & 1u);
-        const float zr = op.f[2 * hi], zi = op.f[2 * hi + 1];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) cmul(v[k], zr, zi);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int hi = (li[k] >> op.a) & 1;
-          cmul(v[k], hi ? op.f[2] : op.f[0], hi ? op.f[3] : op.f[1]);
-        }
-      }
-      break;
-    case T_SWAP:
-      if (op.a == 0 && op.b == 1) op_swap<0, 1>(v);
-      else if (op.a == 1 && op.b == 0) op_swap<1, 0>(v);
-      else if (op.a == 0 && op.b == 2) op_swap<0, 2>(v);
-      else if (op.a == 2 && op.b == 0) op_swap<2, 0>(v);
-      else if (op.a == 1 && op.b == 2) op_swap<1, 2>(v);
-      else op_swap<2, 1>(v);
-      break;
+    for (int k = 0; k < (1 << G); ++k) {
+      if (k & (1 << A)) continue;
+      if (!CTRL || (((base[j] | sk[k]) & d.lmask) == d.lmask)) pair_u(d, v[j][k], v[j][k | (1 << A)]);
+    }
   }
 }
 
-__device__ __forceinline__ void apply_op(const TOp& op, cdf (&v)[8], const int (&li)[8], u64 F) {
-  if ((F & op.gmask) != op.gmask) return;
-  switch (op.type) {
-    case T_U: {
-      M2df U;
+template <int G, int GPT, int A, bool CTRL, typename E>
+__device__ __forceinline__ void apply_x(E (&v)[GPT][1 << G], const int (&base)[GPT], const int (&sk)[1 << G],
+                                       uint32_t lmask) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        U.h[i] = op.f[i];
-        U.l[i] = op.f[8 + i];
+  for (int j = 0; j < GPT; ++j) {
+#pragma unroll
+    for (int k = 0; k < (1 << G); ++k) {
+      if (k & (1 << A)) continue;
+      if (!CTRL || (((base[j] | sk[k]) & lmask) == lmask)) {
+        const E t = v[j][k];
+        v[j][k] = v[j][k | (1 << A)];
+        v[j][k | (1 << A)] = t;
       }
-      if (op.a == 0) op_u<0>(v, li, op.lmask, U);
-      else if (op.a == 1) op_u<1>(v, li, op.lmask, U);
-      else op_u<2>(v, li, op.lmask, U);
-    } break;
-    case T_XPERM:
-      if (op.a == 0) op_x<0>(v, li, op.lmask);
-      else if (op.a == 1) op_x<1>(v, li, op.lmask);
-      else op_x<2>(v, li, op.lmask);
-      break;
-    case T_PHASE: {
-      const float zh[2] = {op.f[0], op.f[1]}, zl[2] = {op.f[8], op.f[9]};
+    }
+  }
+}
+
+template <int G, int GPT, int A, int B, typename E>
+__device__ __forceinline__ void apply_swap(E (&v)[GPT][1 << G]) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if ((li[k] & op.lmask) == op.lmask) cmul_df(zh, zl, v[k]);
-    } break;
-    case T_DIAG1:
+  for (int j = 0; j < GPT; ++j) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int hi = op.dglobal ? (int)((F >> op.a) & 1u) : (li[k] >> op.a) & 1;
-        const float zh[2] = {op.f[2 * hi], op.f[2 * hi + 1]}, zl[2] = {op.f[8 + 2 * hi], op.f[9 + 2 * hi]};
-        cmul_df(zh, zl, v[k]);
+    for (int k = 0; k < (1 << G); ++k) {
+      if ((k & (1 << A)) && !(k & (1 << B))) {
+        const int k2 = (k ^ (1 << A)) | (1 << B);
+        const E t = v[j][k];
+        v[j][k] = v[j][k2];
+        v[j][k2] = t;
       }
-      break;
-    case T_SWAP:
-      if (op.a == 0 && op.b == 1) op_swap<0, 1>(v);
-      else if (op.a == 1 && op.b == 0) op_swap<1, 0>(v);
-      else if (op.a == 0 && op.b == 2) op_swap<0, 2>(v);
-      else if (op.a == 2 && op.b == 0) op_swap<2, 0>(v);
-      else if (op.a == 1 && op.b == 2) op_swap<1, 2>(v);
-      else op_swap<2, 1>(v);
-      break;
+    }
+  }
+}
+
+template <int G, int GPT, typename E>
+__device__ __forceinline__ void dispatch_u(int a, bool ctrl, E (&v)[GPT][1 << G], const int (&base)[GPT],
+                                           const int (&sk)[1 << G], const OpData& d) {
+#define QS_U(A)                                                   \
+  if (a == A) {                                                   \
+    if (ctrl) apply_u<G, GPT, A, true>(v, base, sk, d);           \
+    else apply_u<G, GPT, A, false>(v, base, sk, d);               \
+    return;                                                       \
+  }
+  QS_U(0) QS_U(1) QS_U(2)
+  if (G > 3) { QS_U((G > 3 ? 3 : 0)) }
+#undef QS_U
+}
+
+template <int G, int GPT, typename E>
+__device__ __forceinline__ void dispatch_x(int a, bool ctrl, E (&v)[GPT][1 << G], const int (&base)[GPT],
+                                           const int (&sk)[1 << G], uint32_t lmask) {
+#define QS_X(A)                                                   \
+  if (a == A) {                                                   \
+    if (ctrl) apply_x<G, GPT, A, true>(v, base, sk, lmask);       \
+    else apply_x<G, GPT, A, false>(v, base, sk, lmask);           \
+    return;                                                       \
+  }
+  QS_X(0) QS_X(1) QS_X(2)
+  if (G > 3) { QS_X((G > 3 ? 3 : 0)) }
+#undef QS_X
+}
+
+template <int G, int GPT, typename E>
+__device__ __forceinline__ void dispatch_swap(int a, int b, E (&v)[GPT][1 << G]) {
+  // a < b (the planner orders them)
+  if (a == 0 && b == 1) apply_swap<G, GPT, 0, 1>(v);
+  else if (a == 0 && b == 2) apply_swap<G, GPT, 0, 2>(v);
+  else if (a == 1 && b == 2) apply_swap<G, GPT, 1, 2>(v);
+  else if (G > 3) {
+    constexpr int S3 = G > 3 ? 3 : 2;
+    if (a == 0) apply_swap<G, GPT, 0, S3>(v);
+    else if (a == 1) apply_swap<G, GPT, 1, S3>(v);
+    else apply_swap<G, GPT, 2, S3>(v);
   }
 }
 
 // ---- HBM <-> shared memory ------------------------------------------------
 
+template <int MODE>
 __device__ __forceinline__ void load_pk(const float* a, u64 p, float2* t, int la) {
   float v[4];
   ld16(a + p * 4, v);
-  t[la] = make_float2(v[0], v[1]);
-  t[la + 1] = make_float2(v[2], v[3]);
+  t[swz<MODE>(la)] = make_float2(v[0], v[1]);
+  t[swz<MODE>(la + 1)] = make_float2(v[2], v[3]);
 }
+template <int MODE>
 __device__ __forceinline__ void store_pk(float* a, u64 p, const float2* t, int la) {
-  const float2 x = t[la], y = t[la + 1];
+  const float2 x = t[swz<MODE>(la)], y = t[swz<MODE>(la + 1)];
   const float v[4] = {x.x, x.y, y.x, y.y};
   st16(a + p * 4, v);
 }
+template <int MODE>
 __device__ __forceinline__ void load_pk(const double* a, u64 p, cdf* t, int la) {
   double v[2];
   ld16(a + p * 2, v);
   const dfl r = d2df(v[0]), i = d2df(v[1]);
-  t[la] = cdf{r.h, r.l, i.h, i.l};
+  t[swz<MODE>(la)] = cdf{r.h, r.l, i.h, i.l};
 }
+template <int MODE>
 __device__ __forceinline__ void store_pk(double* a, u64 p, const cdf* t, int la) {
-  const cdf x = t[la];
+  const cdf x = t[swz<MODE>(la)];
   const double v[2] = {df2d(dfl{x.rh, x.rl}), df2d(dfl{x.ih, x.il})};
   st16(a + p * 2, v);
 }
 
-template <int MODE>
+template <int MODE, int G, int GPT>
 __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__ TileArgs A) {
   typedef typename Elem<MODE>::T E;
   typedef typename std::conditional<MODE == 0, float, double>::type R;
   constexpr int APP = MODE == 0 ? 2 : 1;  // amplitudes per 16-byte packet
+  constexpr int NK = 1 << G;
+  constexpr int NF = MODE == 0 ? 8 : 16;  // matrix floats an op carries
   extern __shared__ __align__(16) unsigned char smem[];
-  u64* tab = reinterpret_cast<u64*>(smem);            // [2][64] spread tables
+  u64* tab = reinterpret_cast<u64*>(smem);  // [2][64] spread tables
   E* t = reinterpret_cast<E*>(smem + 2 * 64 * sizeof(u64));
   R* a = static_cast<R*>(amp);
   const int L = A.L, m = A.m;
   const int tile = 1 << m;
   const int lmask = (1 << L) - 1;
+  const int ngroups = tile >> G;
   // spread tables: j -> OR of 2^H[b] over the set bits b of j
   for (int i = threadIdx.x; i < 128; i += kTT) {
     const int part = i >> 6, j = i & 63;
@@ -277,29 +282,78 @@ __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__
   __syncthreads();
   for (u64 ti = blockIdx.x; ti < A.ntiles; ti += gridDim.x) {
     const u64 F = expand(ti << L, A.tins);
-    // load the tile: run j = la >> L, offset la & lmask
     for (int e = threadIdx.x; e < tile / APP; e += kTT) {
       const int la = e * APP;
       const int j = la >> L;
       const u64 g = F | tab[j & 63] | tab[64 + (j >> kTabBits)] | (u64)(la & lmask);
-      load_pk(a, g / APP, t, la);
+      load_pk<MODE>(a, g / APP, t, la);
     }
     __syncthreads();
     for (int s = 0; s < A.nstages; ++s) {
-      const TStage st = A.stages[s];
-      const int q0 = st.sq[0], q1 = st.sq[1], q2 = st.sq[2];
-      for (int gi = threadIdx.x; gi < (tile >> 3); gi += kTT) {
-        const int base = ins1(ins1(ins1(gi, st.srt[0]), st.srt[1]), st.srt[2]);
-        int li[8];
-        E v[8];
+      const TStage& st = A.stages[s];
+      int sk[NK];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          li[k] = base | ((k & 1) << q0) | (((k >> 1) & 1) << q1) | (((k >> 2) & 1) << q2);
-          v[k] = t[li[k]];
+      for (int k = 0; k < NK; ++k) {
+        int x = 0;
+#pragma unroll
+        for (int i = 0; i < G; ++i) x |= ((k >> i) & 1) << st.sq[i];
+        sk[k] = x;
+      }
+      for (int g0 = threadIdx.x; g0 < ngroups; g0 += kTT * GPT) {
+        int base[GPT];
+        E v[GPT][NK];
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+          const int gi = g0 + j * kTT;
+          int b = gi < ngroups ? gi : 0;
+#pragma unroll
+          for (int i = 0; i < G; ++i) b = ins1(b, st.srt[i]);
+          base[j] = b;
+#pragma unroll
+          for (int k = 0; k < NK; ++k) v[j][k] = t[swz<MODE>(b | sk[k])];
         }
-        for (int o = st.op_begin; o < st.op_end; ++o) apply_op(A.ops[o], v, li, F);
+        for (int o = st.op_begin; o < st.op_end; ++o) {
+          const TOp& op = A.ops[o];
+          const int type = op.type, oa = op.a;
+          const u64 gmask = op.gmask;
+          if ((F & gmask) != gmask) continue;
+          OpData d;
+          d.lmask = op.lmask;
+          if (type == T_U || type == T_PHASE || type == T_DIAG1) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) t[li[k]] = v[k];
+            for (int q = 0; q < NF; ++q) d.f[q] = op.f[q];
+          }
+          if (type == T_U) {
+            dispatch_u<G, GPT>(oa, d.lmask != 0, v, base, sk, d);
+          } else if (type == T_XPERM) {
+            dispatch_x<G, GPT>(oa, d.lmask != 0, v, base, sk, d.lmask);
+          } else if (type == T_PHASE) {
+#pragma unroll
+            for (int j = 0; j < GPT; ++j)
+#pragma unroll
+              for (int k = 0; k < NK; ++k)
+                if (((base[j] | sk[k]) & d.lmask) == d.lmask) amp_mul(v[j][k], d.f[0], d.f[1], d.f[8 % NF], d.f[9 % NF]);
+          } else if (type == T_DIAG1) {
+            const bool dglobal = op.dglobal != 0;
+#pragma unroll
+            for (int j = 0; j < GPT; ++j)
+#pragma unroll
+              for (int k = 0; k < NK; ++k) {
+                const int hi = dglobal ? (int)((F >> oa) & 1u) : (((base[j] | sk[k]) >> oa) & 1);
+                if (hi) amp_mul(v[j][k], d.f[2], d.f[3], d.f[10 % NF], d.f[11 % NF]);
+                else amp_mul(v[j][k], d.f[0], d.f[1], d.f[8 % NF], d.f[9 % NF]);
+              }
+          } else {  // T_SWAP
+            dispatch_swap<G, GPT>(oa, (int)op.b, v);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+          if (g0 + j * kTT < ngroups) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) t[swz<MODE>(base[j] | sk[k])] = v[j][k];
+          }
+        }
       }
       __syncthreads();
     }
@@ -307,7 +361,7 @@ __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__
       const int la = e * APP;
       const int j = la >> L;
       const u64 g = F | tab[j & 63] | tab[64 + (j >> kTabBits)] | (u64)(la & lmask);
-      store_pk(a, g / APP, t, la);
+      store_pk<MODE>(a, g / APP, t, la);
     }
     __syncthreads();
   }
@@ -354,8 +408,11 @@ void set_matrix(TOp& op, const double* m, int count, qs_dtype dt) {
   }
 }
 
-// Build the stages and device ops of one pass from its gate list.
+// Build the stages and device ops of one pass from its gate list: greedy
+// list scheduling; a gate joins the current stage when no earlier gate left
+// for a later stage touches its tile qubits and its targets fit the G slots.
 void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gates, qs_dtype dt, int n) {
+  const int G = tp.G;
   std::vector<int> loc(n, -1);
   for (int q = 0; q < tp.L; ++q) loc[q] = q;
   for (int i = 0; i < tp.r; ++i) loc[tp.H[i]] = tp.L + i;
@@ -363,8 +420,7 @@ void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gat
   while (!rest.empty()) {
     std::vector<int> S;  // slot -> local qubit
     uint64_t blocked = 0;
-    std::vector<const qs_gate_rec*> later;
-    std::vector<std::pair<const qs_gate_rec*, std::vector<int>>> taken;
+    std::vector<const qs_gate_rec*> later, taken;
     for (const qs_gate_rec* g : rest) {
       int gq[2];
       const int ng = gate_qubits(*g, gq);
@@ -383,32 +439,30 @@ void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gat
         const int l = loc[nq[i]];
         if (std::find(S.begin(), S.end(), l) == S.end()) need.push_back(l);
       }
-      if (S.size() + need.size() <= 3) {
+      if ((int)(S.size() + need.size()) <= G) {
         for (int l : need) S.push_back(l);
-        taken.push_back({g, {}});
+        taken.push_back(g);
       } else {
         blocked |= lq;
         later.push_back(g);
       }
     }
-    // complete the slot set with unused local qubits, highest first (keeps
-    // the low qubits out of the slots: consecutive threads then touch
-    // consecutive shared-memory words)
-    for (int l = tp.m - 1; l >= 0 && S.size() < 3; --l)
+    // complete the slot set with unused local qubits, highest first
+    for (int l = tp.m - 1; l >= 0 && (int)S.size() < G; --l)
       if (std::find(S.begin(), S.end(), l) == S.end()) S.push_back(l);
     TStage st{};
-    for (int i = 0; i < 3; ++i) st.sq[i] = (uint8_t)S[i];
+    for (int i = 0; i < G; ++i) st.sq[i] = (uint8_t)S[i];
     std::vector<int> srt = S;
     std::sort(srt.begin(), srt.end());
-    for (int i = 0; i < 3; ++i) st.srt[i] = (uint8_t)srt[i];
+    for (int i = 0; i < G; ++i) st.srt[i] = (uint8_t)srt[i];
     st.op_begin = (uint16_t)tp.ops.size();
     auto slot_of = [&](int q) { return (int)(std::find(S.begin(), S.end(), loc[q]) - S.begin()); };
     auto bit_masks = [&](int q, TOp& op) {
       if (loc[q] >= 0) op.lmask |= 1u << loc[q];
       else op.gmask |= uint64_t(1) << q;
     };
-    for (auto& tk : taken) {
-      const qs_gate_rec& g = *tk.first;
+    for (const qs_gate_rec* gp : taken) {
+      const qs_gate_rec& g = *gp;
       TOp op{};
       double m[32];
       gate_matrix(g.kind, g.p, m);
@@ -447,11 +501,12 @@ void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gat
           const double d[4] = {m[0], m[1], m[6], m[7]};
           set_matrix(op, d, 4, dt);
         } break;
-        case G_SWAP:
+        case G_SWAP: {
           op.type = T_SWAP;
-          op.a = (uint8_t)slot_of(g.q[0]);
-          op.b = (uint8_t)slot_of(g.q[1]);
-          break;
+          const int s0 = slot_of(g.q[0]), s1 = slot_of(g.q[1]);
+          op.a = (uint8_t)std::min(s0, s1);
+          op.b = (uint8_t)std::max(s0, s1);
+        } break;
       }
       tp.ops.push_back(op);
     }
@@ -461,27 +516,53 @@ void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gat
   }
 }
 
+// Defaults from a sweep on GB300 (30- and 26-qubit brick circuits).
 int default_tile_qubits(qs_dtype dt) { return dt == QS_C64 ? 13 : 12; }
-int default_low_qubits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
+int default_low_qubits(qs_dtype dt) { return dt == QS_C64 ? 4 : 4; }
+int default_slots(qs_dtype dt) { return dt == QS_C64 ? 3 : 3; }
+int default_gpt(qs_dtype dt) { return dt == QS_C64 ? 1 : 1; }
+
+template <int MODE, int G, int GPT>
+qs_status launch_tile(qs_state* s, const TileArgs& A, size_t smem, unsigned grid) {
+  auto kern = k_tile<MODE, G, GPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "tile: smem attribute");
+  kern<<<grid, kTT, smem, s->stream>>>(s->amp, A);
+  return launch_ok("k_tile");
+}
 
 }  // namespace
 
+int tile_stage_count(const qs_plan* p) {
+  int n = 0;
+  for (const qs_tile_pass* t : p->tiles) n += (int)t->stages.size();
+  return n;
+}
+
 qs_status plan_tiled(qs_plan* p) {
   const int n = p->n;
-  if (n < 3) {  // a tile needs three slot qubits: per-gate passes instead
+  if (n < 4) {  // a tile needs its slot qubits: per-gate passes instead
     for (const qs_gate_rec& g : p->gates) p->steps.push_back(unfused_step(g));
     return QS_OK;
   }
-  int m = p->opts.tile_qubits > 0 ? p->opts.tile_qubits : default_tile_qubits(p->dtype);
-  int L = p->opts.low_qubits > 0 ? p->opts.low_qubits : default_low_qubits(p->dtype);
+  const qs_plan_opts& o = p->opts;
+  int m = o.tile_qubits > 0 ? o.tile_qubits : default_tile_qubits(p->dtype);
+  int L = o.low_qubits > 0 ? o.low_qubits : default_low_qubits(p->dtype);
+  const int G = o.slot_qubits > 0 ? o.slot_qubits : default_slots(p->dtype);
+  const int gpt = o.groups_per_thread > 0 ? o.groups_per_thread : default_gpt(p->dtype);
   const int maxm = p->dtype == QS_C64 ? 14 : 13;
-  if (m < 3 || m > maxm) return fail(QS_EINVAL, "qs_plan_build: tile_qubits=%d outside [3, %d]", m, maxm);
+  if (m < 4 || m > maxm) return fail(QS_EINVAL, "qs_plan_build: tile_qubits=%d outside [4, %d]", m, maxm);
   if (L < 1 || L > m) return fail(QS_EINVAL, "qs_plan_build: low_qubits=%d outside [1, tile_qubits]", L);
+  if (G != 3 && G != 4) return fail(QS_EINVAL, "qs_plan_build: slot_qubits must be 3 or 4");
+  if (gpt != 1 && gpt != 2) return fail(QS_EINVAL, "qs_plan_build: groups_per_thread must be 1 or 2");
   if (m > n) m = n;
   if (L > m) L = m;
-  int r = m - L;
+  const int r = m - L;
   if (r > kMaxR) return fail(QS_EINVAL, "qs_plan_build: at most %d high tile qubits", kMaxR);
-  if (p->dtype == QS_C64 && L < 1) L = 1;
+  p->opts.slot_qubits = G;
+  // complex128 with four slots holds 64 floats per group: one group per
+  // thread (two would spill registers)
+  p->opts.groups_per_thread = (p->dtype == QS_C128 && G == 4) ? 1 : gpt;
 
   std::vector<const qs_gate_rec*> remaining;
   for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
@@ -501,7 +582,7 @@ qs_status plan_tiled(qs_plan* p) {
         std::vector<int> add;
         for (int i = 0; i < nn; ++i)
           if (!inT[nq[i]]) add.push_back(nq[i]);
-        if ((int)(H.size() + add.size()) <= r) {
+        if ((int)(H.size() + add.size()) <= r && (int)absorbed.size() < kMaxOps) {
           for (int q : add) { inT[q] = 1; H.push_back(q); }
           absorbed.push_back(g);
           continue;
@@ -520,11 +601,26 @@ qs_status plan_tiled(qs_plan* p) {
     tp->L = L;
     tp->r = r;
     tp->m = m;
+    tp->G = G;
     for (int i = 0; i < r; ++i) tp->H[i] = H[i];
     build_pass_ops(*tp, absorbed, p->dtype, n);
-    if (tp->ops.size() > 65535 || tp->stages.size() > 65535) {
+    if ((int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
+      // too many stages for one parameter block: split the pass's gates
       delete tp;
-      return fail(QS_EUNSUPPORTED, "qs_plan_build: tile pass too large");
+      const size_t half = absorbed.size() / 2;
+      std::vector<const qs_gate_rec*> again(absorbed.begin() + half, absorbed.end());
+      again.insert(again.end(), rest.begin(), rest.end());
+      // the first half stays absorbed by a smaller pass over the same tile set
+      std::vector<const qs_gate_rec*> first(absorbed.begin(), absorbed.begin() + half);
+      tp = new qs_tile_pass();
+      tp->L = L; tp->r = r; tp->m = m; tp->G = G;
+      for (int i = 0; i < r; ++i) tp->H[i] = H[i];
+      build_pass_ops(*tp, first, p->dtype, n);
+      if (half == 0 || (int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
+        delete tp;
+        return fail(QS_EUNSUPPORTED, "qs_plan_build: tile pass too large");
+      }
+      rest.swap(again);
     }
     p->tiles.push_back(tp);
     qs_step st{};
@@ -536,51 +632,14 @@ qs_status plan_tiled(qs_plan* p) {
   return QS_OK;
 }
 
-qs_status plan_tiles_upload(qs_plan* p, cudaStream_t stream) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (p->dev_tables && p->dev_tables_device == dev) return QS_OK;
-  if (p->dev_tables) {
-    cudaFree(p->dev_tables);
-    p->dev_tables = nullptr;
-  }
-  size_t bytes = 0;
-  for (qs_tile_pass* t : p->tiles) {
-    t->ops_off = bytes;
-    bytes += t->ops.size() * sizeof(TOp);
-    bytes = (bytes + 15) & ~size_t(15);
-    t->stages_off = bytes;
-    bytes += t->stages.size() * sizeof(TStage);
-    bytes = (bytes + 15) & ~size_t(15);
-  }
-  std::vector<unsigned char> host(bytes ? bytes : 16);
-  for (qs_tile_pass* t : p->tiles) {
-    if (!t->ops.empty()) std::memcpy(host.data() + t->ops_off, t->ops.data(), t->ops.size() * sizeof(TOp));
-    if (!t->stages.empty())
-      std::memcpy(host.data() + t->stages_off, t->stages.data(), t->stages.size() * sizeof(TStage));
-  }
-  cudaError_t e = cudaMalloc(&p->dev_tables, host.size());
-  if (e != cudaSuccess) {
-    p->dev_tables = nullptr;
-    return fail(QS_ENOMEM, "plan tables: %s", cudaGetErrorString(e));
-  }
-  e = cudaMemcpyAsync(p->dev_tables, host.data(), host.size(), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return cuda_fail(e, "plan tables upload");
-  p->dev_tables_bytes = host.size();
-  p->dev_tables_device = dev;
-  return QS_OK;
-}
-
 qs_status run_tile(qs_state* s, qs_plan* p, int tile_index) {
   const qs_tile_pass& tp = *p->tiles[tile_index];
-  TileArgs A{};
+  static thread_local TileArgs A;
   A.L = tp.L;
   A.m = tp.m;
   A.r = tp.r;
   A.nstages = (int)tp.stages.size();
   A.ntiles = u64(1) << (s->n - tp.m);
-  std::vector<std::pair<int, int>> bits;
   Ins ins{};
   ins.k = tp.r;
   ins.set = 0;
@@ -589,24 +648,19 @@ qs_status run_tile(qs_state* s, qs_plan* p, int tile_index) {
     A.H[i] = tp.H[i];
   }
   A.tins = ins;
-  const unsigned char* base = static_cast<const unsigned char*>(p->dev_tables);
-  A.ops = reinterpret_cast<const TOp*>(base + tp.ops_off);
-  A.stages = reinterpret_cast<const TStage*>(base + tp.stages_off);
+  std::memcpy(A.stages, tp.stages.data(), tp.stages.size() * sizeof(TStage));
+  std::memcpy(A.ops, tp.ops.data(), tp.ops.size() * sizeof(TOp));
   const size_t esize = s->dtype == QS_C64 ? sizeof(float2) : sizeof(cdf);
   const size_t smem = 2 * 64 * sizeof(u64) + (size_t(1) << tp.m) * esize;
   const int per_sm = (int)std::max<size_t>(1, (227 * 1024) / (smem + 1024));
   const unsigned grid = grid_for(A.ntiles, 1, std::min(per_sm, 8));
-  cudaError_t e;
+  const int gpt = p->opts.groups_per_thread;
   if (s->dtype == QS_C64) {
-    e = cudaFuncSetAttribute(k_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "tile: smem attribute");
-    k_tile<0><<<grid, kTT, smem, s->stream>>>(s->amp, A);
-  } else {
-    e = cudaFuncSetAttribute(k_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "tile: smem attribute");
-    k_tile<1><<<grid, kTT, smem, s->stream>>>(s->amp, A);
+    if (tp.G == 4) return gpt == 2 ? launch_tile<0, 4, 2>(s, A, smem, grid) : launch_tile<0, 4, 1>(s, A, smem, grid);
+    return gpt == 2 ? launch_tile<0, 3, 2>(s, A, smem, grid) : launch_tile<0, 3, 1>(s, A, smem, grid);
   }
-  return launch_ok("k_tile");
+  if (tp.G == 4) return launch_tile<1, 4, 1>(s, A, smem, grid);
+  return gpt == 2 ? launch_tile<1, 3, 2>(s, A, smem, grid) : launch_tile<1, 3, 1>(s, A, smem, grid);
 }
 
 void tile_free(qs_tile_pass* t) { delete t; }

@@ -98,3 +98,24 @@ def test_c64_vs_oracle_depth40_16q(qs, mode):
     want = oracle_state(n, circ)
     got, _ = run_gpu(qs, n, circ, "c64", mode)
     assert infidelity(got, want) <= C64_INFIDELITY
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("slots,gpt", [(3, 1), (3, 2), (4, 1), (4, 2)])
+@pytest.mark.parametrize("tile,low", [(0, 0), (6, 2), (9, 1)])
+def test_tile_variants_match_oracle(qs, dtype, slots, gpt, tile, low):
+    # every tile-kernel instantiation and a few tile shapes (many tiles per
+    # pass, ragged stage counts) against the oracle
+    n = 13
+    circ = W.brick(n, 12, 31) + W.qft(n) + W.qsb(n, 32, sets=2)
+    want = oracle_state(n, circ)
+    s = qs.State(n, dtype)
+    c = qs.Circuit(circ)
+    p = qs.Plan(c, n, dtype, mode=qs.PLAN_TILED, tile_qubits=tile, low_qubits=low, slot_qubits=slots,
+                groups_per_thread=gpt)
+    s.run(p)
+    got = s.to_numpy()
+    if dtype == "c128":
+        assert np.max(np.abs(got - want)) <= C128_TOL
+    else:
+        assert infidelity(got, want) <= C64_INFIDELITY
