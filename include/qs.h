@@ -257,6 +257,29 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
  * step; use qs_run_plan for throughput. */
 qs_status qs_run_plan_profiled(qs_state* st, qs_plan* p, float* step_ms, int nsteps);
 
+/* ---------------------------------------------------------------------- */
+/* Differentiation                                                        */
+/* ---------------------------------------------------------------------- */
+
+/* Energies and gradients of E(theta) = <psi(theta)|H|psi(theta)> for `batch`
+ * parameter sets, psi(theta) = circuit applied to |0...0>.  The paper has no
+ * differentiation; this is the standard adjoint (reverse-sweep) method: one
+ * forward run, lambda = H psi, then for each gate from last to first the
+ * gradient term Im <lambda|P|psi> of a trainable R_P(theta_j) =
+ * exp(-i theta_j P / 2) followed by un-applying the gate to psi and lambda.
+ *   st:      state fixing n and dtype; its contents are overwritten.
+ *   c:       the circuit; RX/RY/RZ gates added with param_index j >= 0 take
+ *            their angle from theta (the stored angle is ignored).
+ *   theta:   batch x nparam angles (row-major).
+ *   H:       sum_t coeff[t] P_t with Pauli strings as in qs_expect_pauli.
+ *   energy:  batch values; grad: batch x nparam, dE/dtheta (row-major).
+ * Gradients accumulate in FP64 for both dtypes.  Synchronises the state's
+ * stream.  Allocates one extra state vector and the gradient partials for
+ * the duration of the call. */
+qs_status qs_adjoint_grad(qs_state* st, const qs_circuit* c, const double* theta, int nparam, int batch,
+                          int nterms, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                          double* energy, double* grad);
+
 #ifdef __cplusplus
 }
 #endif

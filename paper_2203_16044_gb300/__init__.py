@@ -85,6 +85,7 @@ _SIGS = {
     "qs_run_plan": ([_vp, _vp], _int),
     "qs_plan_step_info": ([_vp, _int, _ip, _dp], _int),
     "qs_run_plan_profiled": ([_vp, _vp, ctypes.POINTER(ctypes.c_float), _int], _int),
+    "qs_adjoint_grad": ([_vp, _vp, _dp, _int, _int, _int, _up, _up, _dp, _dp, _dp], _int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -365,3 +366,56 @@ def run_circuit(state: State, gates, mode: int = PLAN_TILED, **kw) -> dict:
     p = Plan(c, state.n, state.dtype, mode=mode, **kw)
     state.run(p)
     return p.stats()
+
+
+def _terms(terms):
+    xm = np.ascontiguousarray([t.xmask for t in terms], dtype=np.uint64)
+    zm = np.ascontiguousarray([t.zmask for t in terms], dtype=np.uint64)
+    cf = np.ascontiguousarray([t.coeff for t in terms], dtype=np.float64)
+    return xm, zm, cf
+
+
+def adjoint_grad(state: State, circuit: Circuit, theta, terms):
+    """Energies and adjoint gradients for a batch of parameter sets.
+
+    theta: (batch, nparam) or (nparam,) array of angles.  Returns
+    (energy[batch], grad[batch, nparam]) as float64 numpy arrays (squeezed to
+    match a 1-D theta).  The state's contents are overwritten."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    single = th.ndim == 1
+    th2 = th.reshape(1, -1) if single else th
+    batch, nparam = th2.shape
+    xm, zm, cf = _terms(terms)
+    energy = np.zeros(batch, dtype=np.float64)
+    grad = np.zeros((batch, max(nparam, 1)), dtype=np.float64)
+    _check(_lib.qs_adjoint_grad(state._bind(), circuit.handle, _dptr(th2), nparam, batch, len(terms),
+                                xm.ctypes.data_as(_up), zm.ctypes.data_as(_up), _dptr(cf), _dptr(energy),
+                                _dptr(grad)), "qs_adjoint_grad")
+    grad = grad[:, :nparam]
+    return (energy[0], grad[0]) if single else (energy, grad)
+
+
+def expectation_fn():
+    """torch.autograd.Function computing E(theta) with the adjoint gradient.
+
+    Usage: E = expectation_fn().apply(theta, state, circuit, terms) with theta
+    a float64 tensor of shape (nparam,) or (batch, nparam); E.backward()
+    fills theta.grad.  Forward runs the adjoint sweep once (energy and
+    gradient together, on the GPU) and keeps the gradient for backward."""
+    torch = _torch()
+
+    class _Expectation(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, state, circuit, terms):
+            e, g = adjoint_grad(state, circuit, theta.detach().cpu().numpy(), terms)
+            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+            return torch.as_tensor(e, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            if g.dim() == 1:
+                return grad_out * g, None, None, None
+            return grad_out[:, None] * g, None, None, None
+
+    return _Expectation

@@ -13,9 +13,9 @@
 // For m != 0 the pairs {x, x^m} are visited once (x with bit h of m clear,
 // h = highest set bit of m), each amplitude read once.
 #include <algorithm>
-#include <map>
 
 #include "kcommon.cuh"
+#include "pauli.cuh"
 
 namespace qs {
 namespace {
@@ -99,24 +99,6 @@ __global__ void __launch_bounds__(kThreads) k_final(const double2* part, int n, 
   if (threadIdx.x == 0) {
     if (accumulate) { out->x += sr; out->y += si; }
     else *out = make_double2(sr, si);
-  }
-}
-
-constexpr int kMaxGroupTerms = 64;
-struct PauliGroup {
-  u64 m;           // X/Y mask shared by the group
-  int h;           // highest bit of m (-1 if m == 0)
-  int nt;          // terms in this launch
-  u64 z[kMaxGroupTerms];
-  double wr[kMaxGroupTerms], wi[kMaxGroupTerms];  // c_t * i^{nY_t}
-};
-
-__device__ __forceinline__ void fval(const PauliGroup& g, u64 x, double& fr, double& fi) {
-  fr = 0.0; fi = 0.0;
-  for (int t = 0; t < g.nt; ++t) {
-    const double sgn = (__popcll(x & g.z[t]) & 1) ? -1.0 : 1.0;
-    fr += sgn * g.wr[t];
-    fi += sgn * g.wi[t];
   }
 }
 
@@ -219,32 +201,7 @@ qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
 
 qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask, const double* coeff,
                      double* out) {
-  // group by X/Y mask, in order of first appearance (deterministic)
-  std::vector<PauliGroup> groups;
-  std::map<u64, int> idx;
-  for (int t = 0; t < nterms; ++t) {
-    const u64 m = xmask[t], z = zmask[t];
-    auto it = idx.find(m);
-    int gi;
-    if (it == idx.end() || groups[it->second].nt == kMaxGroupTerms) {
-      PauliGroup g{};
-      g.m = m;
-      g.h = m ? 63 - __builtin_clzll(m) : -1;
-      g.nt = 0;
-      groups.push_back(g);
-      gi = (int)groups.size() - 1;
-      idx[m] = gi;
-    } else {
-      gi = it->second;
-    }
-    PauliGroup& g = groups[gi];
-    const int ny = __builtin_popcountll(m & z) & 3;  // i^{nY}
-    const double pr[4] = {1, 0, -1, 0}, pim[4] = {0, 1, 0, -1};
-    g.z[g.nt] = z;
-    g.wr[g.nt] = coeff[t] * pr[ny];
-    g.wi[g.nt] = coeff[t] * pim[ny];
-    ++g.nt;
-  }
+  const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
   const u64 N = u64(1) << s->n;
   const unsigned gsz = red_grid(N / 2);
   const size_t ng = groups.size();
