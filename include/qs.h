@@ -258,6 +258,60 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
 qs_status qs_run_plan_profiled(qs_state* st, qs_plan* p, float* step_ms, int nsteps);
 
 /* ---------------------------------------------------------------------- */
+/* Batched execution                                                      */
+/* ---------------------------------------------------------------------- */
+
+typedef struct qs_batch qs_batch;  /* opaque: many circuits, one launch */
+
+typedef struct {
+  int circuits;       /* circuits in the batch                           */
+  int units;          /* work units in the queue                         */
+  int passes;         /* tile passes summed over circuits                */
+  int grid;           /* persistent CTAs (0 before the first run)        */
+  int graph;          /* 1 when runs replay a captured CUDA graph        */
+  int reserved;
+  double hbm_bytes;   /* algorithmic HBM bytes of one run                */
+  double metric_bytes;/* 2 * 2^n_i * bytes_per_amp * gates_i, summed     */
+} qs_batch_stats;
+
+/* Compile `count` independent circuits (circuit i on n[i] >= 4 qubits,
+ * state i at dev_states[i]: 2^n[i] amplitudes of `dtype`, 16-byte aligned,
+ * caller-owned) into one batch run on `stream`.  Every circuit becomes tile
+ * passes (opts as for qs_plan_build, mode ignored; NULL = defaults); the
+ * batch is a work queue of (circuit, pass, tiles) units executed by one
+ * persistent cooperative launch.  The paper runs circuits one at a time; this
+ * is the library's own scheduling.  The first qs_batch_run captures the
+ * launch in a CUDA graph (unless `stream` is the legacy default stream).
+ * opts->reserved[0] is a test hook and must be 0 in normal use: a positive
+ * value makes every wait for a previous pass demand that many tiles more
+ * than exist, so the bounded wait runs out (QS_ETIMEOUT from
+ * qs_batch_sync, after about 2 s). */
+qs_status qs_batch_create(int count, const int* n, qs_dtype dtype, void* const* dev_states,
+                          const qs_circuit* const* circuits, const qs_plan_opts* opts, void* stream,
+                          qs_batch** out);
+
+/* Enqueue one run of every circuit of the batch (asynchronous).  init_zero:
+ * start every circuit from |0...0> (the vectors are not read); otherwise the
+ * circuits act on the current contents. */
+qs_status qs_batch_run(qs_batch* b, int init_zero);
+
+/* Wait for the batch's stream and check the run: QS_ETIMEOUT if a bounded
+ * pass-dependency wait gave up (the states are then incomplete). */
+qs_status qs_batch_sync(qs_batch* b);
+
+qs_status qs_batch_stats_get(const qs_batch* b, qs_batch_stats* out);
+qs_status qs_batch_destroy(qs_batch* b);
+
+/* Autotuner: builds and times the batch for candidate tile sizes and
+ * register slot counts (two runs each, starting from |0...0>, so the states
+ * are overwritten) and returns the fastest options in *best (and its time
+ * in *best_ms if non-NULL).  Cached per process for the same dtype, count,
+ * total qubits and total gates. */
+qs_status qs_batch_autotune(int count, const int* n, qs_dtype dtype, void* const* dev_states,
+                            const qs_circuit* const* circuits, void* stream, qs_plan_opts* best,
+                            double* best_ms);
+
+/* ---------------------------------------------------------------------- */
 /* Differentiation                                                        */
 /* ---------------------------------------------------------------------- */
 

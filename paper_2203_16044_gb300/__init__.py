@@ -86,6 +86,14 @@ _SIGS = {
     "qs_plan_step_info": ([_vp, _int, _ip, _dp], _int),
     "qs_run_plan_profiled": ([_vp, _vp, ctypes.POINTER(ctypes.c_float), _int], _int),
     "qs_adjoint_grad": ([_vp, _vp, _dp, _int, _int, _int, _up, _up, _dp, _dp, _dp], _int),
+    "qs_batch_create": ([_int, _ip, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(PlanOpts), _vp,
+                         ctypes.POINTER(_vp)], _int),
+    "qs_batch_run": ([_vp, _int], _int),
+    "qs_batch_sync": ([_vp], _int),
+    "qs_batch_stats_get": ([_vp, ctypes.c_void_p], _int),
+    "qs_batch_destroy": ([_vp], _int),
+    "qs_batch_autotune": ([_int, _ip, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, ctypes.POINTER(PlanOpts),
+                           _dp], _int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -419,3 +427,89 @@ def expectation_fn():
             return grad_out[:, None] * g, None, None, None
 
     return _Expectation
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("circuits", ctypes.c_int), ("units", ctypes.c_int), ("passes", ctypes.c_int), ("grid", ctypes.c_int),
+                ("graph", ctypes.c_int), ("reserved", ctypes.c_int), ("hbm_bytes", ctypes.c_double),
+                ("metric_bytes", ctypes.c_double)]
+
+
+class Batch:
+    """Many independent circuits run by one persistent launch (qs_batch).
+
+    ``sizes``: qubit count of each circuit; ``gate_lists``: workload Gate
+    lists.  The states live in one torch buffer (``self.buffer``) owned by
+    this object; ``state(i)`` returns circuit i's vector (a view).  opts:
+    PlanOpts fields as keywords (tile_qubits, slot_qubits, ...), or
+    ``autotune=True`` to let the library pick them by timing."""
+
+    def __init__(self, sizes, gate_lists, dtype: str = "c64", autotune: bool = False, **opts):
+        torch = _torch()
+        self.sizes = [int(n) for n in sizes]
+        self.dtype = dtype
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        self.offsets = []
+        off = 0
+        for n in self.sizes:
+            self.offsets.append(off)
+            off += 1 << n
+        self.buffer = torch.zeros(off, dtype=tdt, device="cuda")
+        self.circuits = [Circuit(g) for g in gate_lists]
+        count = len(self.sizes)
+        self._n = (ctypes.c_int * count)(*self.sizes)
+        self._ptrs = (_vp * count)(*[self.buffer[o:].data_ptr() for o in self.offsets])
+        self._circ = (_vp * count)(*[c.handle.value for c in self.circuits])
+        # a stream of its own: the legacy default stream cannot be captured
+        # into a CUDA graph
+        self._tstream = torch.cuda.Stream()
+        self._tstream.wait_stream(torch.cuda.current_stream())
+        self._stream = ctypes.c_void_p(self._tstream.cuda_stream)
+        dt = C64 if dtype == "c64" else C128
+        po = PlanOpts(mode=PLAN_TILED, **opts)
+        self.tuned_ms = None
+        if autotune:
+            best = PlanOpts()
+            ms = ctypes.c_double()
+            _check(_lib.qs_batch_autotune(count, self._n, dt, self._ptrs, self._circ, self._stream, ctypes.byref(best),
+                                          ctypes.byref(ms)), "qs_batch_autotune")
+            po, self.tuned_ms = best, ms.value
+        self.opts = po
+        h = _vp()
+        _check(_lib.qs_batch_create(count, self._n, dt, self._ptrs, self._circ, ctypes.byref(po), self._stream,
+                                    ctypes.byref(h)), "qs_batch_create")
+        self._h = h
+
+    def run(self, init_zero: bool = True) -> "Batch":
+        """Enqueue one run on the batch's stream, after the work already
+        queued on the caller's current stream."""
+        torch = _torch()
+        self._tstream.wait_stream(torch.cuda.current_stream())
+        _check(_lib.qs_batch_run(self._h, 1 if init_zero else 0), "qs_batch_run")
+        return self
+
+    def sync(self) -> None:
+        """Wait for the batch and check it (QSError QS_ETIMEOUT if a bounded
+        wait gave up); later work on the current stream is ordered after it."""
+        torch = _torch()
+        _check(_lib.qs_batch_sync(self._h), "qs_batch_sync")
+        torch.cuda.current_stream().wait_stream(self._tstream)
+
+    def state(self, i: int):
+        return self.buffer[self.offsets[i]:self.offsets[i] + (1 << self.sizes[i])]
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        _check(_lib.qs_batch_stats_get(self._h, ctypes.byref(s)), "qs_batch_stats_get")
+        return {f: getattr(s, f) for f, _ in BatchStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
