@@ -14,7 +14,7 @@ logical gates per second.  `value` is the whole-job effective GB/s of the
 headline dtype (summed over ranks; one independent replica per GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload brick30|brick28|qft28] [--dtype c64|c128]
+                  [--workload brick30|brick28|brick26|qft28] [--dtype c64|c128]
                   [--mode tiled|unfused]
 
 `--impl reference` times the FP64 CPU oracle (a deliberately plain program)
@@ -41,8 +41,15 @@ WORKLOADS = {
     "brick30": dict(n=30, make=lambda: W.brick(30, 40, 6), desc="30-qubit brick random circuit, depth 40, seed 6"),
     "brick28": dict(n=28, make=lambda: W.brick(28, 40, 3), desc="28-qubit brick random circuit, depth 40, seed 3"),
     "qft28": dict(n=28, make=lambda: W.qft(28), desc="28-qubit QFT"),
+    "brick26": dict(n=26, make=lambda: W.brick(26, 40, 6), desc="26-qubit brick random circuit, depth 40, seed 6"),
     "brick20": dict(n=20, make=lambda: W.brick(20, 40, 6), desc="20-qubit brick random circuit, depth 40, seed 6"),
 }
+
+# DRAM bytes (read + write) per launch of the complex64 tile kernel, from one
+# ncu capture on the 26-qubit workload (profiles/tile_c64_brick26.md); per
+# launch traffic grows with the state, so n qubits scale it by 2^(n - 26).
+# Set to None whenever the tile kernel changes until it is re-captured.
+TILE_C64_TRAFFIC_26Q = 537.064704e6 + 475.623168e6
 S_BYTES = {"c64": 8, "c128": 16}
 
 
@@ -136,15 +143,23 @@ def allreduce_max(x, world, device=None):
 # CPU oracle timing (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
 
+_ORACLE_PSI = {}
+
+
 def oracle_sample(workload, budget_s):
     """Run the oracle over the first gates of the workload circuit until
-    ``budget_s`` of wall time is spent; returns (gates_done, seconds, n)."""
+    ``budget_s`` of wall time is spent; returns (gates_done, seconds, n).
+    The state vector is allocated once per size and reused."""
     import oracle
     wl = WORKLOADS[workload]
     n = wl["n"]
     circ = wl["make"]()
-    psi = oracle.zero_state(n)
-    oracle.run_circuit(psi, circ[:1])  # touch the pages before timing
+    if n not in _ORACLE_PSI:
+        _ORACLE_PSI[n] = oracle.zero_state(n)
+        oracle.run_circuit(_ORACLE_PSI[n], circ[:1])  # touch the pages before timing
+    psi = _ORACLE_PSI[n]
+    psi[:] = 0
+    psi[0] = 1
     done, t0 = 0, time.perf_counter()
     while done < len(circ) and time.perf_counter() - t0 < budget_s:
         oracle.run_circuit(psi, circ[done:done + 1])
@@ -177,7 +192,7 @@ def run_reference(args):
     gbs = 2.0 * (1 << n) * S * gates / T / 1e9
     line = {
         "impl": "reference", "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate)",
-        "value": gbs, "unit": "GB/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * T / len(per_step), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["desc"] + " (oracle, FP64 complex128)", "n": n, "gates_per_step": gates / len(per_step)},
@@ -219,6 +234,28 @@ def timed_run(qs, torch, state, plan, steps, warmup, world, device, profile=True
     return allreduce_max(ms, world, device), step_ms
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def circuit_flops(circ, n):
+    """Algorithmic floating-point operations of a circuit on 2^n amplitudes:
+    a dense one-qubit gate costs 4 complex multiplies and 2 complex adds per
+    amplitude pair (14 flops per amplitude); a phase or diagonal gate 6 flops
+    per amplitude it changes; X-type gates and swaps none."""
+    N = float(1 << n)
+    f = 0.0
+    for g in circ:
+        if g.name in ("U3", "H", "RX", "RY", "Y"):
+            f += 14 * N
+        elif g.name in ("RZ",):
+            f += 6 * N
+        elif g.name in ("Z", "S", "T", "P"):
+            f += 6 * N / 2
+        elif g.name in ("CZ", "CP"):
+            f += 6 * N / 4
+    return f
+
+
 def kernel_roofline(plan, step_ms, peak):
     """Per step kind: algorithmic bytes and device time summed over the timed
     steps; the dominant kind (largest time) gives the roofline object."""
@@ -237,7 +274,96 @@ def kernel_roofline(plan, step_ms, peak):
                     "GB/s": tot_b[k] / (tot_t[k] / 1e3) / 1e9} for k in tot_t}
     return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "bytes_per_launch": tot_b[dom] / cnt[dom],
-            "ms_per_launch": tot_t[dom] / cnt[dom]}, per_kind
+            "ms_per_launch": tot_t[dom] / cnt[dom], "traffic": None}, per_kind
+
+
+def unfused_classes(qs, torch, device, n, reps=10):
+    """Per-gate-class unfused passes (the RX-per-qubit sweep of §IV-C widened
+    to four classes): algorithmic HBM GB/s per class and dtype over targets."""
+    out = {}
+    targets = sorted({0, 1, 2, 5, n // 2, n - 2, n - 1})
+    for dt in ("c64", "c128"):
+        s = qs.State(n, dt, device=device)
+        # a dense state (a U3 on every qubit): no amplitude is zero, so no
+        # arithmetic fast path applies
+        s.run(qs.Plan(qs.Circuit(W.brick(n, 1, 4)), n, dt, mode=qs.PLAN_TILED))
+        for cls in ("U3", "RZ", "CNOT", "CZ"):
+            res = []
+            for t in targets:
+                circ = W.microbench(n, cls, t, seed=5, reps=reps)
+                p = qs.Plan(qs.Circuit(circ), n, dt, mode=qs.PLAN_UNFUSED)
+                s.run(p)
+                ms = s.run_profiled(p)
+                b = sum(x[1] for x in p.step_info())
+                res.append(b / (ms.sum() / 1e3) / 1e9)
+            out.setdefault(cls, {})[dt] = {"targets": targets, "GBps": [round(x, 1) for x in res],
+                                           "min": round(min(res), 1), "median": round(float(np.median(res)), 1)}
+        del s
+    return out
+
+
+def batch_workload(qs, torch, device, count=512, layers=8, seed=9):
+    """512 hardware-efficient-ansatz circuits, n uniform in [10, 20], complex64:
+    one persistent launch (graph replay, autotuned tiles) vs one plan per
+    circuit launched one after another."""
+    sizes = W.batch_sizes(count, 10, 20, seed)
+    circs = [W.hea(n, layers, 10 + i)[0] for i, n in enumerate(sizes)]
+    b = qs.Batch(sizes, circs, dtype="c64", autotune=True)
+    b.run(True)
+    b.sync()
+    st = b.stats()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.run(True)
+    b.sync()
+    t_batch = (time.perf_counter() - t0) / reps
+    # one by one: each circuit its own plan and launches, same tiles
+    plans = [qs.Plan(qs.Circuit(c), n, "c64", mode=qs.PLAN_TILED) for n, c in zip(sizes, circs)]
+    views = [qs.State(n, "c64", tensor=b.state(i)) for i, n in enumerate(sizes)]
+    for v, p in zip(views, plans):
+        v.set_basis(0)
+        v.run(p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v, p in zip(views, plans):
+        v.set_basis(0)
+        v.run(p)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    gates = sum(len(c) for c in circs)
+    return {"circuits": count, "n_range": [10, 20], "gates": gates, "passes": st["passes"], "units": st["units"],
+            "grid": st["grid"], "graph": st["graph"], "tuned_opts": {"tile_qubits": b.opts.tile_qubits,
+                                                                     "slot_qubits": b.opts.slot_qubits,
+                                                                     "groups_per_thread": b.opts.groups_per_thread},
+            "batched_ms": 1e3 * t_batch, "circuits_per_s": count / t_batch,
+            "hbm_GBps_batched": st["hbm_bytes"] / t_batch / 1e9,
+            "one_by_one_ms": 1e3 * t_single, "one_by_one_circuits_per_s": count / t_single,
+            "speedup_vs_one_by_one": t_single / t_batch}
+
+
+def adjoint_workload(qs, torch, device, n=20, layers=10, batch=16):
+    """Adjoint gradients: 20-qubit hardware-efficient ansatz, 10 layers of RY
+    and RZ (400 parameters), CZ ladder, transverse-field Ising observable."""
+    circ, _ = W.hea(n, layers, 11)
+    thetas = np.stack([W.hea(n, layers, 11 + b)[1] for b in range(batch)])
+    terms = W.tfim(n)
+    c = qs.Circuit(circ)
+    out = {"n": n, "params": thetas.shape[1], "batch": batch}
+    for dt in ("c128", "c64"):
+        s = qs.State(n, dt, device=device)
+        qs.adjoint_grad(s, c, thetas[:1], terms)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, g = qs.adjoint_grad(s, c, thetas, terms)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out[dt] = {"ms_per_gradient": 1e3 * t / batch, "gradients_per_s": batch / t,
+                   "energy0": float(e[0]), "grad0_norm": float(np.linalg.norm(g[0]))}
+        del s
+    return out
 
 
 def run_ours(args):
@@ -263,6 +389,22 @@ def run_ours(args):
         with ClockSampler(local) as clk:
             ms, step_ms = timed_run(qs, torch, state, plan, args.steps, args.warmup, world, device)
         roof, per_kind = kernel_roofline(plan, step_ms, peak)
+        if roof and roof["kernel"] == "tile":
+            # tile passes run many gates per HBM pass: FP32-issue bound, not HBM
+            flops = circuit_flops(circ, n)
+            tile_ms = per_kind["tile"]["ms"] / len(step_ms)
+            roof_hbm = dict(roof)
+            roof = {"kernel": "tile", "bound": "alu", "traffic": None, "achieved": flops / (tile_ms / 1e3) / 1e12,
+                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": flops / (tile_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                    "flops_per_step": flops, "ms_per_launch": roof_hbm["ms_per_launch"],
+                    "hbm": {"achieved": roof_hbm["achieved"], "peak": peak, "unit": "GB/s",
+                            "frac": roof_hbm["frac"], "bytes_per_launch": roof_hbm["bytes_per_launch"]}}
+            if dt == "c128":
+                roof["note"] = "complex128 in double-float: each FP64-equivalent flop costs ~6 FP32-pipe ops"
+            elif TILE_C64_TRAFFIC_26Q is not None:
+                roof["traffic"] = TILE_C64_TRAFFIC_26Q * 2.0 ** (n - 26)
+                roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 26 qubits, scaled by 2^(n-26)"
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
@@ -283,6 +425,11 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(qs, torch, args, n, circ, mode, device, world)
+    extras = {}
+    if not args.no_extras:
+        extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
+        extras["batch_512_hea"] = batch_workload(qs, torch, device)
+        extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
     head = results[args.dtype]
     line = {
         "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate) & gates/s, 30-qubit brick circuit",
@@ -294,7 +441,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (state %.0f GiB)" % (2.0 ** n * S_BYTES[args.dtype] / 2 ** 30)},
         "gates_per_s": head["gates_per_s"],
         "hbm_GBps_algorithmic": head["hbm_GBps"],
-        "roofline": dict(head["roofline"], traffic=None, peak_source=peak_kind) if head["roofline"] else None,
+        "roofline": dict(head["roofline"], peak_source=peak_kind) if head["roofline"] else None,
         "kernels": head["kernels"],
         "clocks": head["clocks"],
         "gpu_launches": head["gpu_launches"],
@@ -302,6 +449,7 @@ def run_ours(args):
         "precision": {"infidelity_c64_vs_c128": infid},
         "other_dtypes": {dt: {k: v for k, v in r.items() if k not in ("kernels",)} for dt, r in results.items()
                          if dt != args.dtype},
+        "extras": extras,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, t, n_cpu = oracle_sample(args.workload, args.cpu_budget)
@@ -366,6 +514,7 @@ def main():
     ap.add_argument("--both", type=int, default=1, help="also run the other dtype")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the class sweep, batch and adjoint workloads")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     args = ap.parse_args()
