@@ -209,8 +209,10 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);
  * slot_qubits: qubits held in registers per stage inside a tile pass, 3 or
  * 4 (0 = default); groups_per_thread: register groups a thread works on at
- * once, 1 or 2 (0 = default; QS_C128 with 4 slots always uses 1).  Every
- * field must be zero or valid. */
+ * once, 1 or 2 (0 = default; QS_C128 with 4 slots always uses 1); dense:
+ * 0 = a stage whose gates all act within its three slot qubits may be fused
+ * into one 8x8 matrix when the planner estimates that cheaper (complex64,
+ * three slots), -1 = never.  Every field must be zero or valid. */
 enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1 };
 typedef struct {
   int mode;
@@ -218,7 +220,8 @@ typedef struct {
   int low_qubits;
   int slot_qubits;
   int groups_per_thread;
-  int reserved[3];
+  int dense;
+  int reserved[2];
 } qs_plan_opts;
 
 typedef struct {
@@ -229,7 +232,7 @@ typedef struct {
   double hbm_bytes;   /* algorithmic HBM bytes of one run of the plan    */
   double metric_bytes;/* 2 * 2^n * bytes_per_amp * gates (Eq. 5 traffic) */
   int stages;         /* register stages summed over all tile passes     */
-  int reserved;
+  int dense_stages;   /* of which fused into one dense 8x8 matrix        */
 } qs_plan_stats;
 
 /* Compile circuit `c` for n qubits and `dtype`.  opts may be NULL

@@ -44,13 +44,14 @@ _int = ctypes.c_int
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("low_qubits", ctypes.c_int),
-                ("slot_qubits", ctypes.c_int), ("groups_per_thread", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("slot_qubits", ctypes.c_int), ("groups_per_thread", ctypes.c_int), ("dense", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class PlanStats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("dtype", ctypes.c_int), ("gates", ctypes.c_int), ("passes", ctypes.c_int),
                 ("hbm_bytes", ctypes.c_double), ("metric_bytes", ctypes.c_double), ("stages", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("dense_stages", ctypes.c_int)]
 
 
 _SIGS = {
@@ -325,9 +326,10 @@ class Plan:
     """A circuit compiled for (n, dtype) into HBM passes (qs_plan)."""
 
     def __init__(self, circuit: Circuit, n: int, dtype: str = "c128", mode: int = PLAN_TILED,
-                 tile_qubits: int = 0, low_qubits: int = 0, slot_qubits: int = 0, groups_per_thread: int = 0):
+                 tile_qubits: int = 0, low_qubits: int = 0, slot_qubits: int = 0, groups_per_thread: int = 0,
+                 dense: int = 0):
         opts = PlanOpts(mode=mode, tile_qubits=tile_qubits, low_qubits=low_qubits, slot_qubits=slot_qubits,
-                        groups_per_thread=groups_per_thread)
+                        groups_per_thread=groups_per_thread, dense=dense)
         h = _vp()
         _check(_lib.qs_plan_build(circuit.handle, int(n), C64 if dtype == "c64" else C128, ctypes.byref(opts),
                                   ctypes.byref(h)), "qs_plan_build")
@@ -343,7 +345,7 @@ class Plan:
         s = PlanStats()
         _check(_lib.qs_plan_stats_get(self._h, ctypes.byref(s)), "qs_plan_stats_get")
         return {"n": s.n, "dtype": s.dtype, "gates": s.gates, "passes": s.passes, "hbm_bytes": s.hbm_bytes,
-                "metric_bytes": s.metric_bytes, "stages": s.stages}
+                "metric_bytes": s.metric_bytes, "stages": s.stages, "dense_stages": s.dense_stages}
 
     STEP_KINDS = ("1q", "ctrl", "diag", "swap", "tile")
 

@@ -45,7 +45,7 @@ struct BCircuit {   // device
   int pad;
 };
 struct BPass {      // device
-  int nstages, op_off, stage_off, pad;
+  int nstages, op_off, stage_off, mat_off;
   int H[kMaxR];
   Ins tins;
 };
@@ -59,6 +59,7 @@ struct BatchArgs {
   const BPass* passes;
   const TOp* ops;
   const TStage* stages;
+  const float* mats;
   unsigned* counters;   // [0] queue head, [1 + c] tiles done of circuit c
   int* err;
   int init_zero;
@@ -68,8 +69,10 @@ struct BatchArgs {
 struct GlobalSrc {
   const TOp* ops;
   const TStage* st;
+  const float* mats;
   __device__ __forceinline__ const TStage& stage(int s) const { return st[s]; }
   __device__ __forceinline__ const TOp& op(int o) const { return ops[o]; }
+  __device__ __forceinline__ const float* mat(int i) const { return mats + i * kMatFloats; }
 };
 
 __device__ __forceinline__ void ldcg16(const float* p, float (&v)[4]) {
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kTT) k_batch(const __grid_constant__ BatchArgs
     R* a = static_cast<R*>(cd.amp);
     const int tile = 1 << cd.m;
     const bool zero = A.init_zero && unit.p == 0;
-    const GlobalSrc src{A.ops + pd.op_off, A.stages + pd.stage_off};
+    const GlobalSrc src{A.ops + pd.op_off, A.stages + pd.stage_off, A.mats + pd.mat_off};
     for (int ti = unit.tile0; ti < unit.tile0 + unit.ntiles; ++ti) {
       const u64 F = expand((u64)ti << cd.L, pd.tins);
       for (int e = threadIdx.x; e < tile / APP; e += kTT) {
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kTT) k_batch(const __grid_constant__ BatchArgs
         bload<MODE>(a, tile_global(F, tab, la, cd.L) / APP, t, la, zero);
       }
       __syncthreads();
-      run_stages<MODE, G, GPT>(t, cd.m, F, src, pd.nstages);
+      run_stages<MODE, G, GPT, MODE == 0 && G == 3>(t, cd.m, F, src, pd.nstages);
       for (int e = threadIdx.x; e < tile / APP; e += kTT) {
         const int la = e * APP;
         bstore<MODE>(a, tile_global(F, tab, la, cd.L) / APP, t, la);
@@ -265,6 +268,7 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
   std::vector<BPass> hp;
   std::vector<TOp> hops;
   std::vector<TStage> hst;
+  std::vector<float> hmat;
   std::vector<BUnit> hu;
   int maxm = 0, maxpasses = 0;
   double hbm = 0, metric = 0;
@@ -307,6 +311,8 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
       bp.nstages = (int)tp->stages.size();
       bp.op_off = (int)hops.size();
       bp.stage_off = (int)hst.size();
+      bp.mat_off = (int)hmat.size();
+      hmat.insert(hmat.end(), tp->mats.begin(), tp->mats.end());
       for (int k = 0; k < tp->r; ++k) bp.H[k] = tp->H[k];
       bp.tins.k = tp->r;
       bp.tins.set = 0;
@@ -339,14 +345,15 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t ou = 0, oc = al(ou + hu.size() * sizeof(BUnit)), op = al(oc + hc.size() * sizeof(BCircuit)),
                oo = al(op + hp.size() * sizeof(BPass)), os = al(oo + hops.size() * sizeof(TOp)),
-               ocnt = al(os + hst.size() * sizeof(TStage)), oerr = al(ocnt + sizeof(unsigned) * (1 + count)),
-               total = al(oerr + sizeof(int));
+               om = al(os + hst.size() * sizeof(TStage)), ocnt = al(om + hmat.size() * sizeof(float)),
+               oerr = al(ocnt + sizeof(unsigned) * (1 + count)), total = al(oerr + sizeof(int));
   std::vector<unsigned char> host(total, 0);
   std::memcpy(host.data() + ou, hu.data(), hu.size() * sizeof(BUnit));
   std::memcpy(host.data() + oc, hc.data(), hc.size() * sizeof(BCircuit));
   std::memcpy(host.data() + op, hp.data(), hp.size() * sizeof(BPass));
   if (!hops.empty()) std::memcpy(host.data() + oo, hops.data(), hops.size() * sizeof(TOp));
   if (!hst.empty()) std::memcpy(host.data() + os, hst.data(), hst.size() * sizeof(TStage));
+  if (!hmat.empty()) std::memcpy(host.data() + om, hmat.data(), hmat.size() * sizeof(float));
   cudaError_t e = cudaMalloc(&b->dev, total);
   if (e != cudaSuccess) {
     qs_batch_destroy(b);
@@ -364,6 +371,7 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
   b->args.passes = reinterpret_cast<const BPass*>(d + op);
   b->args.ops = reinterpret_cast<const TOp*>(d + oo);
   b->args.stages = reinterpret_cast<const TStage*>(d + os);
+  b->args.mats = reinterpret_cast<const float*>(d + om);
   b->args.counters = reinterpret_cast<unsigned*>(d + ocnt);
   b->args.err = reinterpret_cast<int*>(d + oerr);
   b->args.init_zero = 1;

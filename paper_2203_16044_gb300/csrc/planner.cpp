@@ -178,7 +178,7 @@ qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_pla
   p->stats.passes = (int)p->steps.size();
   p->stats.hbm_bytes = 0.0;
   for (const qs_step& s : p->steps) p->stats.hbm_bytes += step_bytes(s, n, S);
-  p->stats.stages = tile_stage_count(p);
+  p->stats.stages = tile_stage_count(p, &p->stats.dense_stages);
   p->stats.metric_bytes = 2.0 * std::ldexp(1.0, n) * S * (double)p->gates.size();
   *out = p;
   return QS_OK;

@@ -9,5 +9,5 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st);
 // Fills p->steps (and p->tiles) for QS_PLAN_TILED.
 qs_status plan_tiled(qs_plan* p);
 // Register stages summed over the plan's tile passes.
-int tile_stage_count(const qs_plan* p);
+int tile_stage_count(const qs_plan* p, int* dense);
 }  // namespace qs

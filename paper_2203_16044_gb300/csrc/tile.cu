@@ -26,6 +26,7 @@
 // converted from / to the FP64 layout once per pass at load / store.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -42,17 +43,19 @@ struct TileArgs {
   int H[kMaxR];
   TStage stages[kMaxStages];
   TOp ops[kMaxOps];
+  float mats[kMaxMats * kMatFloats];
 };
 static_assert(sizeof(TileArgs) < 32000, "kernel parameter block limit");
 
-// ops and stages read straight from the kernel parameter block
+// ops, stages and dense matrices read straight from the kernel parameter block
 struct ParamSrc {
   const TileArgs& A;
   __device__ __forceinline__ const TStage& stage(int s) const { return A.stages[s]; }
   __device__ __forceinline__ const TOp& op(int o) const { return A.ops[o]; }
+  __device__ __forceinline__ const float* mat(int i) const { return A.mats + i * kMatFloats; }
 };
 
-template <int MODE, int G, int GPT>
+template <int MODE, int G, int GPT, bool DENSE>
 __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__ TileArgs A) {
   typedef typename Elem<MODE>::T E;
   typedef typename std::conditional<MODE == 0, float, double>::type R;
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__
       load_pk<MODE>(a, tile_global(F, tab, la, L) / APP, t, la);
     }
     __syncthreads();
-    run_stages<MODE, G, GPT>(t, m, F, src, A.nstages);
+    run_stages<MODE, G, GPT, DENSE>(t, m, F, src, A.nstages);
     for (int e = threadIdx.x; e < tile / APP; e += kTT) {
       const int la = e * APP;
       store_pk<MODE>(a, tile_global(F, tab, la, L) / APP, t, la);
@@ -123,25 +126,161 @@ void set_matrix(TOp& op, const double* m, int count, qs_dtype dt) {
   }
 }
 
+// Local tile qubits a gate touches (targets, controls, phase bits) and
+// whether it also reads bits outside the tile.
+void gate_locality(const qs_gate_rec& g, const std::vector<int>& loc, uint64_t& lq, bool& global) {
+  int gq[2];
+  const int ng = gate_qubits(g, gq);
+  lq = 0;
+  global = false;
+  for (int i = 0; i < ng; ++i) {
+    if (loc[gq[i]] >= 0) lq |= uint64_t(1) << loc[gq[i]];
+    else global = true;
+  }
+}
+
+// Rough per-amplitude instruction costs, used to pick dense or op stages
+// (measured shape on GB300: a stage's shared-memory round trip ~12, a dense
+// 8x8 stage ~44, a dense one-qubit op ~10, an exchange ~4).
+double op_cost(const qs_gate_rec& g) {
+  switch (classify(g.kind)) {
+    case G_DENSE1: return 10.0;
+    case G_DIAG1: return 8.0;
+    case G_PHASE1: case G_PHASE2: return 6.0;
+    default: return 4.0;
+  }
+}
+constexpr double kStageCost = 12.0, kDenseStageCost = 44.0;
+
+typedef std::complex<double> cd;
+
+// 8x8 matrix of one gate on the slot qubits S (bit i of the index = S[i]).
+void gate_on_slots(const qs_gate_rec& g, const std::vector<int>& loc, const std::vector<int>& S, cd (*G8)[8]) {
+  auto slot = [&](int q) { return (int)(std::find(S.begin(), S.end(), loc[q]) - S.begin()); };
+  for (int r = 0; r < 8; ++r)
+    for (int c = 0; c < 8; ++c) G8[r][c] = 0.0;
+  double m[32];
+  gate_matrix(g.kind, g.p, m);
+  switch (classify(g.kind)) {
+    case G_DENSE1: case G_XGATE: case G_DIAG1: case G_PHASE1: {
+      const int a = slot(g.q[0]);
+      for (int k = 0; k < 8; ++k)
+        for (int k2 = 0; k2 < 8; ++k2)
+          if (((k ^ k2) & ~(1 << a)) == 0) {
+            const int ro = (k2 >> a) & 1, co = (k >> a) & 1;
+            G8[k2][k] = cd(m[2 * (ro * 2 + co)], m[2 * (ro * 2 + co) + 1]);
+          }
+    } break;
+    case G_CNOT: {
+      const int c = slot(g.q[0]), t = slot(g.q[1]);
+      for (int k = 0; k < 8; ++k) G8[((k >> c) & 1) ? (k ^ (1 << t)) : k][k] = 1.0;
+    } break;
+    case G_PHASE2: {
+      const int a = slot(g.q[0]), b = slot(g.q[1]);
+      for (int k = 0; k < 8; ++k) {
+        const int r4 = ((k >> a) & 1) | (((k >> b) & 1) << 1);
+        G8[k][k] = cd(m[2 * (r4 * 4 + r4)], m[2 * (r4 * 4 + r4) + 1]);
+      }
+    } break;
+    case G_SWAP: {
+      const int a = slot(g.q[0]), b = slot(g.q[1]);
+      for (int k = 0; k < 8; ++k) {
+        const int ba = (k >> a) & 1, bb = (k >> b) & 1;
+        const int k2 = (k & ~((1 << a) | (1 << b))) | (ba << b) | (bb << a);
+        G8[k2][k] = 1.0;
+      }
+    } break;
+  }
+}
+
 // Build the stages and device ops of one pass from its gate list: greedy
 // list scheduling; a gate joins the current stage when no earlier gate left
-// for a later stage touches its tile qubits and its targets fit the G slots.
-void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gates, qs_dtype dt, int n) {
+// for a later stage touches its tile qubits and it fits the stage.  For
+// complex64 with three slots a stage may instead be dense: every gate whose
+// tile qubits all lie in the three slots (and that reads nothing outside the
+// tile) is multiplied into one 8x8 matrix, used when cheaper than the ops.
+void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gates, qs_dtype dt, int n,
+                    bool allow_dense) {
   const int G = tp.G;
+  const bool dense_ok = allow_dense && dt == QS_C64 && G == 3;
   std::vector<int> loc(n, -1);
   for (int q = 0; q < tp.L; ++q) loc[q] = q;
   for (int i = 0; i < tp.r; ++i) loc[tp.H[i]] = tp.L + i;
   std::vector<const qs_gate_rec*> rest = gates;
+  auto finish_slots = [&](std::vector<int>& S, TStage& st) {
+    // complete the slot set with unused local qubits, highest first
+    for (int l = tp.m - 1; l >= 0 && (int)S.size() < G; --l)
+      if (std::find(S.begin(), S.end(), l) == S.end()) S.push_back(l);
+    for (int i = 0; i < G; ++i) st.sq[i] = (uint8_t)S[i];
+    std::vector<int> srt = S;
+    std::sort(srt.begin(), srt.end());
+    for (int i = 0; i < G; ++i) st.srt[i] = (uint8_t)srt[i];
+  };
   while (!rest.empty()) {
+    if (dense_ok && (int)(tp.mats.size() / kMatFloats) < kMaxMats) {
+      std::vector<int> S;
+      uint64_t blocked = 0;
+      std::vector<const qs_gate_rec*> later, taken;
+      double cost_ops = kStageCost;
+      for (const qs_gate_rec* g : rest) {
+        uint64_t lq;
+        bool glob;
+        gate_locality(*g, loc, lq, glob);
+        if ((lq & blocked) || glob) {
+          blocked |= lq;
+          later.push_back(g);
+          continue;
+        }
+        std::vector<int> need;
+        for (int l = 0; l < tp.m; ++l)
+          if (((lq >> l) & 1) && std::find(S.begin(), S.end(), l) == S.end()) need.push_back(l);
+        if (S.size() + need.size() <= 3) {
+          for (int l : need) S.push_back(l);
+          taken.push_back(g);
+          cost_ops += op_cost(*g);
+        } else {
+          blocked |= lq;
+          later.push_back(g);
+        }
+      }
+      if (!taken.empty() && cost_ops > kDenseStageCost) {
+        TStage st{};
+        finish_slots(S, st);
+        cd M[8][8], G8[8][8], T[8][8];
+        for (int r = 0; r < 8; ++r)
+          for (int c = 0; c < 8; ++c) M[r][c] = (r == c) ? 1.0 : 0.0;
+        for (const qs_gate_rec* g : taken) {
+          gate_on_slots(*g, loc, S, G8);
+          for (int r = 0; r < 8; ++r)
+            for (int c = 0; c < 8; ++c) {
+              cd acc = 0.0;
+              for (int k = 0; k < 8; ++k) acc += G8[r][k] * M[k][c];
+              T[r][c] = acc;
+            }
+          for (int r = 0; r < 8; ++r)
+            for (int c = 0; c < 8; ++c) M[r][c] = T[r][c];
+        }
+        st.dense = 1;
+        st.op_begin = (uint16_t)(tp.mats.size() / kMatFloats);
+        st.op_end = st.op_begin;
+        for (int r = 0; r < 8; ++r)
+          for (int c = 0; c < 8; ++c) {
+            tp.mats.push_back((float)M[r][c].real());
+            tp.mats.push_back((float)M[r][c].imag());
+          }
+        tp.stages.push_back(st);
+        rest.swap(later);
+        continue;
+      }
+    }
+    // op stage: targets in the G slots, controls and phases anywhere
     std::vector<int> S;  // slot -> local qubit
     uint64_t blocked = 0;
     std::vector<const qs_gate_rec*> later, taken;
     for (const qs_gate_rec* g : rest) {
-      int gq[2];
-      const int ng = gate_qubits(*g, gq);
-      uint64_t lq = 0;
-      for (int i = 0; i < ng; ++i)
-        if (loc[gq[i]] >= 0) lq |= uint64_t(1) << loc[gq[i]];
+      uint64_t lq;
+      bool glob;
+      gate_locality(*g, loc, lq, glob);
       if (lq & blocked) {
         blocked |= lq;
         later.push_back(g);
@@ -162,14 +301,8 @@ void build_pass_ops(qs_tile_pass& tp, const std::vector<const qs_gate_rec*>& gat
         later.push_back(g);
       }
     }
-    // complete the slot set with unused local qubits, highest first
-    for (int l = tp.m - 1; l >= 0 && (int)S.size() < G; --l)
-      if (std::find(S.begin(), S.end(), l) == S.end()) S.push_back(l);
     TStage st{};
-    for (int i = 0; i < G; ++i) st.sq[i] = (uint8_t)S[i];
-    std::vector<int> srt = S;
-    std::sort(srt.begin(), srt.end());
-    for (int i = 0; i < G; ++i) st.srt[i] = (uint8_t)srt[i];
+    finish_slots(S, st);
     st.op_begin = (uint16_t)tp.ops.size();
     auto slot_of = [&](int q) { return (int)(std::find(S.begin(), S.end(), loc[q]) - S.begin()); };
     auto bit_masks = [&](int q, TOp& op) {
@@ -237,9 +370,9 @@ int default_low_qubits(qs_dtype dt) { return dt == QS_C64 ? 4 : 4; }
 int default_slots(qs_dtype dt) { return dt == QS_C64 ? 3 : 3; }
 int default_gpt(qs_dtype dt) { return dt == QS_C64 ? 1 : 1; }
 
-template <int MODE, int G, int GPT>
+template <int MODE, int G, int GPT, bool DENSE>
 qs_status launch_tile(qs_state* s, const TileArgs& A, size_t smem, unsigned grid) {
-  auto kern = k_tile<MODE, G, GPT>;
+  auto kern = k_tile<MODE, G, GPT, DENSE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "tile: smem attribute");
   kern<<<grid, kTT, smem, s->stream>>>(s->amp, A);
@@ -248,9 +381,13 @@ qs_status launch_tile(qs_state* s, const TileArgs& A, size_t smem, unsigned grid
 
 }  // namespace
 
-int tile_stage_count(const qs_plan* p) {
-  int n = 0;
-  for (const qs_tile_pass* t : p->tiles) n += (int)t->stages.size();
+int tile_stage_count(const qs_plan* p, int* dense) {
+  int n = 0, d = 0;
+  for (const qs_tile_pass* t : p->tiles) {
+    n += (int)t->stages.size();
+    for (const TStage& s : t->stages) d += s.dense;
+  }
+  if (dense) *dense = d;
   return n;
 }
 
@@ -270,6 +407,7 @@ qs_status plan_tiled(qs_plan* p) {
   if (L < 1 || L > m) return fail(QS_EINVAL, "qs_plan_build: low_qubits=%d outside [1, tile_qubits]", L);
   if (G != 3 && G != 4) return fail(QS_EINVAL, "qs_plan_build: slot_qubits must be 3 or 4");
   if (gpt != 1 && gpt != 2) return fail(QS_EINVAL, "qs_plan_build: groups_per_thread must be 1 or 2");
+  if (o.dense != 0 && o.dense != -1) return fail(QS_EINVAL, "qs_plan_build: dense must be 0 or -1");
   if (m > n) m = n;
   if (L > m) L = m;
   const int r = m - L;
@@ -318,7 +456,7 @@ qs_status plan_tiled(qs_plan* p) {
     tp->m = m;
     tp->G = G;
     for (int i = 0; i < r; ++i) tp->H[i] = H[i];
-    build_pass_ops(*tp, absorbed, p->dtype, n);
+    build_pass_ops(*tp, absorbed, p->dtype, n, o.dense >= 0);
     if ((int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
       // too many stages for one parameter block: split the pass's gates
       delete tp;
@@ -330,7 +468,7 @@ qs_status plan_tiled(qs_plan* p) {
       tp = new qs_tile_pass();
       tp->L = L; tp->r = r; tp->m = m; tp->G = G;
       for (int i = 0; i < r; ++i) tp->H[i] = H[i];
-      build_pass_ops(*tp, first, p->dtype, n);
+      build_pass_ops(*tp, first, p->dtype, n, o.dense >= 0);
       if (half == 0 || (int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
         delete tp;
         return fail(QS_EUNSUPPORTED, "qs_plan_build: tile pass too large");
@@ -365,17 +503,20 @@ qs_status run_tile(qs_state* s, qs_plan* p, int tile_index) {
   A.tins = ins;
   std::memcpy(A.stages, tp.stages.data(), tp.stages.size() * sizeof(TStage));
   std::memcpy(A.ops, tp.ops.data(), tp.ops.size() * sizeof(TOp));
+  if (!tp.mats.empty()) std::memcpy(A.mats, tp.mats.data(), tp.mats.size() * sizeof(float));
   const size_t esize = s->dtype == QS_C64 ? sizeof(float2) : sizeof(cdf);
   const size_t smem = 2 * 64 * sizeof(u64) + (size_t(1) << tp.m) * esize;
   const int per_sm = (int)std::max<size_t>(1, (227 * 1024) / (smem + 1024));
   const unsigned grid = grid_for(A.ntiles, 1, std::min(per_sm, 8));
   const int gpt = p->opts.groups_per_thread;
   if (s->dtype == QS_C64) {
-    if (tp.G == 4) return gpt == 2 ? launch_tile<0, 4, 2>(s, A, smem, grid) : launch_tile<0, 4, 1>(s, A, smem, grid);
-    return gpt == 2 ? launch_tile<0, 3, 2>(s, A, smem, grid) : launch_tile<0, 3, 1>(s, A, smem, grid);
+    if (tp.G == 4) return gpt == 2 ? launch_tile<0, 4, 2, false>(s, A, smem, grid) : launch_tile<0, 4, 1, false>(s, A, smem, grid);
+    if (!tp.mats.empty())
+      return gpt == 2 ? launch_tile<0, 3, 2, true>(s, A, smem, grid) : launch_tile<0, 3, 1, true>(s, A, smem, grid);
+    return gpt == 2 ? launch_tile<0, 3, 2, false>(s, A, smem, grid) : launch_tile<0, 3, 1, false>(s, A, smem, grid);
   }
-  if (tp.G == 4) return launch_tile<1, 4, 1>(s, A, smem, grid);
-  return gpt == 2 ? launch_tile<1, 3, 2>(s, A, smem, grid) : launch_tile<1, 3, 1>(s, A, smem, grid);
+  if (tp.G == 4) return launch_tile<1, 4, 1, false>(s, A, smem, grid);
+  return gpt == 2 ? launch_tile<1, 3, 2, false>(s, A, smem, grid) : launch_tile<1, 3, 1, false>(s, A, smem, grid);
 }
 
 void tile_free(qs_tile_pass* t) { delete t; }

@@ -29,9 +29,11 @@ static_assert(sizeof(TOp) == 80, "TOp layout");
 struct TStage {
   uint8_t sq[4];    // local qubit of slot 0..3 (unused slots: 0)
   uint8_t srt[4];   // the slot qubits ascending (for index insertion)
-  uint16_t op_begin, op_end;
+  uint16_t op_begin, op_end;  // ops [op_begin, op_end); dense: op_begin = matrix index
+  uint8_t dense;    // 1: the stage is one 8x8 complex64 matrix on its 3 slots
+  uint8_t pad[3];
 };
-static_assert(sizeof(TStage) == 12, "TStage layout");
+static_assert(sizeof(TStage) == 16, "TStage layout");
 
 }  // namespace qs
 
@@ -40,6 +42,7 @@ struct qs_tile_pass {
   int H[24] = {0};
   std::vector<qs::TOp> ops;
   std::vector<qs::TStage> stages;
+  std::vector<float> mats;  // dense stages: 128 floats each, (re, im) row-major 8x8
 };
 
 namespace qs {
@@ -50,8 +53,10 @@ constexpr int kTabBits = 6;      // spread tables: 2 x 64 entries
 constexpr int kMaxR = 2 * kTabBits;
 // A pass's ops and stages travel in the kernel parameter block (constant
 // bank: uniform, short-latency reads); the planner keeps passes within it.
-constexpr int kMaxOps = 288;
-constexpr int kMaxStages = 96;
+constexpr int kMaxOps = 200;
+constexpr int kMaxStages = 64;
+constexpr int kMaxMats = 24;     // dense stage matrices per pass
+constexpr int kMatFloats = 128;  // 8 x 8 complex64
 
 template <int MODE> struct Elem;
 template <> struct Elem<0> { typedef float2 T; };
@@ -221,10 +226,56 @@ __device__ __forceinline__ void store_pk(double* a, u64 p, const cdf* t, int la)
 }
 
 
+// Dense stage (complex64, three slots): out[r] = sum_c M[r][c] v[c] for the
+// 8 amplitudes spanning the slot qubits, GPT groups per thread sharing each
+// matrix element.  M: 8 x 8 complex, (re, im) row-major, uniform over the CTA.
+// Rows are produced one at a time and written straight back to the tile:
+// the group's 8 inputs are already in registers and no other thread reads
+// them during the stage.
+template <int GPT>
+__device__ __forceinline__ void dense_stage(float2* t, const TStage& st, const float* M, int ngroups) {
+  const int q0 = st.sq[0], q1 = st.sq[1], q2 = st.sq[2];
+  for (int g0 = threadIdx.x; g0 < ngroups; g0 += kTT * GPT) {
+    int base[GPT];
+    float2 v[GPT][8];
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int gi = g0 + j * kTT;
+      int b = gi < ngroups ? gi : 0;
+      b = ins1(ins1(ins1(b, st.srt[0]), st.srt[1]), st.srt[2]);
+      base[j] = b;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[j][k] = t[swz<0>(b | ((k & 1) << q0) | (((k >> 1) & 1) << q1) | ((k >> 2) << q2))];
+    }
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) {
+      float ar[GPT], ai[GPT];
+#pragma unroll
+      for (int j = 0; j < GPT; ++j) { ar[j] = 0.f; ai[j] = 0.f; }
+      const float* Mr = M + 16 * r;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float mr = Mr[2 * c], mi = Mr[2 * c + 1];
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+          ar[j] = fmaf(mr, v[j][c].x, ar[j]);
+          ar[j] = fmaf(-mi, v[j][c].y, ar[j]);
+          ai[j] = fmaf(mr, v[j][c].y, ai[j]);
+          ai[j] = fmaf(mi, v[j][c].x, ai[j]);
+        }
+      }
+      const int off = ((r & 1) << q0) | (((r >> 1) & 1) << q1) | ((r >> 2) << q2);
+#pragma unroll
+      for (int j = 0; j < GPT; ++j)
+        if (g0 + j * kTT < ngroups) t[swz<0>(base[j] | off)] = make_float2(ar[j], ai[j]);
+    }
+  }
+}
+
 // Runs the stages of one tile pass on the shared-memory tile t (2^m
 // amplitudes, swizzled).  SRC supplies the pass's stages and ops:
 // stage(s) and op(o).  F: the tile's global bits.
-template <int MODE, int G, int GPT, class SRC>
+template <int MODE, int G, int GPT, bool DENSE, class SRC>
 __device__ __forceinline__ void run_stages(typename Elem<MODE>::T* t, int m, u64 F, const SRC& src, int nstages) {
   typedef typename Elem<MODE>::T E;
   constexpr int NK = 1 << G;
@@ -232,6 +283,13 @@ __device__ __forceinline__ void run_stages(typename Elem<MODE>::T* t, int m, u64
   const int ngroups = (1 << m) >> G;
   for (int s = 0; s < nstages; ++s) {
     const TStage& st = src.stage(s);
+    if constexpr (DENSE && MODE == 0 && G == 3) {
+      if (st.dense) {
+        dense_stage<GPT>(t, st, src.mat(st.op_begin), ngroups);
+        __syncthreads();
+        continue;
+      }
+    }
     int sk[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {

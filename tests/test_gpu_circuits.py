@@ -101,9 +101,9 @@ def test_c64_vs_oracle_depth40_16q(qs, mode):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("slots,gpt", [(3, 1), (3, 2), (4, 1), (4, 2)])
+@pytest.mark.parametrize("slots,gpt,dense", [(3, 1, 0), (3, 2, 0), (3, 1, -1), (3, 2, -1), (4, 1, 0), (4, 2, 0)])
 @pytest.mark.parametrize("tile,low", [(0, 0), (6, 2), (9, 1)])
-def test_tile_variants_match_oracle(qs, dtype, slots, gpt, tile, low):
+def test_tile_variants_match_oracle(qs, dtype, slots, gpt, dense, tile, low):
     # every tile-kernel instantiation and a few tile shapes (many tiles per
     # pass, ragged stage counts) against the oracle
     n = 13
@@ -112,7 +112,7 @@ def test_tile_variants_match_oracle(qs, dtype, slots, gpt, tile, low):
     s = qs.State(n, dtype)
     c = qs.Circuit(circ)
     p = qs.Plan(c, n, dtype, mode=qs.PLAN_TILED, tile_qubits=tile, low_qubits=low, slot_qubits=slots,
-                groups_per_thread=gpt)
+                groups_per_thread=gpt, dense=dense)
     s.run(p)
     got = s.to_numpy()
     if dtype == "c128":
