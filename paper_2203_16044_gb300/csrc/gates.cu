@@ -325,6 +325,86 @@ __global__ void __launch_bounds__(kThreads) k_bitswap(R* __restrict__ a, u64 nti
   }
 }
 
+// ---------------------------------------------------------------------------
+// complex128 in double-float storage: each FP64 value of the vector is held
+// as its (hi, lo) float pair in the same 8 bytes, so an amplitude is one
+// float4 (re_h, re_l, im_h, im_l).  Plans convert a complex128 state to this
+// layout once at the start and back at the end (k_to_dfl / k_from_dfl), so
+// the per-gate kernels below do no conversion work.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_to_dfl(double* a, u64 npk) {
+  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
+    const double2 v = reinterpret_cast<const double2*>(a)[p];
+    const dfl r = d2df(v.x), i = d2df(v.y);
+    reinterpret_cast<float4*>(a)[p] = make_float4(r.h, r.l, i.h, i.l);
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_from_dfl(double* a, u64 npk) {
+  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
+    const float4 v = reinterpret_cast<const float4*>(a)[p];
+    reinterpret_cast<double2*>(a)[p] = make_double2(df2d(dfl{v.x, v.y}), df2d(dfl{v.z, v.w}));
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pairs_dfl(float4* __restrict__ a, u64 nwork, Ins ins, int tp, M2df U) {
+  const u64 step = (u64)gridDim.x * kThreads * kUnroll;
+  const u64 dp = u64(1) << tp;
+  for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < nwork; base += step) {
+    float4 x0[kUnroll], x1[kUnroll];
+    u64 p0[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const u64 i = base + (u64)u * kThreads;
+      p0[u] = expand(i < nwork ? i : 0, ins);
+      x0[u] = a[p0[u]];
+      x1[u] = a[p0[u] + dp];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      cdf A{x0[u].x, x0[u].y, x0[u].z, x0[u].w}, B{x1[u].x, x1[u].y, x1[u].z, x1[u].w};
+      mv2df(U, A, B);
+      x0[u] = make_float4(A.rh, A.rl, A.ih, A.il);
+      x1[u] = make_float4(B.rh, B.rl, B.ih, B.il);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (base + (u64)u * kThreads < nwork) {
+        a[p0[u]] = x0[u];
+        a[p0[u] + dp] = x1[u];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_phase_dfl(float4* __restrict__ a, u64 nwork, Ins ins, Zdf z) {
+  const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
+  for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < nwork; i += (u64)gridDim.x * kThreads) {
+    const u64 p = expand(i, ins);
+    const float4 v = a[p];
+    cdf x{v.x, v.y, v.z, v.w};
+    cmul_df(zh, zl, x);
+    a[p] = make_float4(x.rh, x.rl, x.ih, x.il);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_diag_dfl(float4* __restrict__ a, u64 npk,
+                                                       const __grid_constant__ DiagTab<double> T) {
+  __shared__ Zdf sd[1 << kMaxDiagK];
+  const int D = 1 << T.k;
+  for (int i = threadIdx.x; i < D; i += kThreads) sd[i] = T.d[i];
+  __syncthreads();
+  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
+    int r = 0;
+    for (int i = 0; i < T.k; ++i) r |= (int)((p >> T.q[i]) & 1u) << i;
+    const float4 v = a[p];
+    cdf x{v.x, v.y, v.z, v.w};
+    const Zdf z = sd[r];
+    const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
+    cmul_df(zh, zl, x);
+    a[p] = make_float4(x.rh, x.rl, x.ih, x.il);
+  }
+}
+
 bool is_x(const double U[8]) {
   return U[0] == 0 && U[1] == 0 && U[2] == 1 && U[3] == 0 && U[4] == 1 && U[5] == 0 && U[6] == 0 && U[7] == 0;
 }
@@ -525,6 +605,53 @@ template <typename R>
 __global__ void k_set_one(R* a, u64 x) {
   a[2 * x] = (R)1;
   a[2 * x + 1] = (R)0;
+}
+
+qs_status run_layout_dfl(qs_state* s, bool to_dfl) {
+  if (s->dtype != QS_C128) return QS_OK;
+  const u64 npk = u64(1) << s->n;
+  const unsigned g = grid_for(npk, kThreads, kWaves);
+  if (to_dfl) k_to_dfl<<<g, kThreads, 0, s->stream>>>(static_cast<double*>(s->amp), npk);
+  else k_from_dfl<<<g, kThreads, 0, s->stream>>>(static_cast<double*>(s->amp), npk);
+  return launch_ok(to_dfl ? "k_to_dfl" : "k_from_dfl");
+}
+
+// complex128 gates on a state in double-float storage (see k_to_dfl).
+qs_status run_controlled_dfl(qs_state* s, const int* ctrl, int nc, int t, const double U[8]) {
+  if (is_x(U)) return run_controlled(s, ctrl, nc, t, U);  // exchange: layout-agnostic
+  std::vector<std::pair<int, int>> bits;
+  for (int i = 0; i < nc; ++i) bits.push_back({ctrl[i], 1});
+  bits.push_back({t, 0});
+  const u64 nwork = u64(1) << (s->n - (int)bits.size());
+  const unsigned g = grid_for(nwork, (u64)kThreads * kUnroll, kWaves);
+  k_pairs_dfl<<<g, kThreads, 0, s->stream>>>(static_cast<float4*>(s->amp), nwork, make_ins(bits), t,
+                                             to_mat(U, 0.0));
+  return launch_ok("k_pairs_dfl");
+}
+
+qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d) {
+  if (k > kMaxDiagK) return fail(QS_EINVAL, "diag: k=%d exceeds %d", k, kMaxDiagK);
+  const int D = 1 << k;
+  bool sparse = true;
+  for (int r = 0; r < D - 1 && sparse; ++r) sparse = (d[2 * r] == 1.0 && d[2 * r + 1] == 0.0);
+  float4* a = static_cast<float4*>(s->amp);
+  if (sparse) {
+    if (d[2 * (D - 1)] == 1.0 && d[2 * (D - 1) + 1] == 0.0) return QS_OK;
+    std::vector<std::pair<int, int>> bits;
+    for (int i = 0; i < k; ++i) bits.push_back({qubits[i], 1});
+    const u64 nwork = u64(1) << (s->n - k);
+    const unsigned g = grid_for(nwork, kThreads, kWaves);
+    k_phase_dfl<<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), to_z(d[2 * (D - 1)], d[2 * (D - 1) + 1], 0.0));
+    return launch_ok("k_phase_dfl");
+  }
+  DiagTab<double> T{};
+  T.k = k;
+  for (int i = 0; i < k; ++i) T.q[i] = qubits[i];
+  for (int i = 0; i < D; ++i) T.d[i] = to_z(d[2 * i], d[2 * i + 1], 0.0);
+  const u64 npk = u64(1) << s->n;
+  const unsigned g = grid_for(npk, kThreads, kWaves);
+  k_diag_dfl<<<g, kThreads, 0, s->stream>>>(a, npk, T);
+  return launch_ok("k_diag_dfl");
 }
 
 qs_status run_set_basis(qs_state* s, u64 x) {

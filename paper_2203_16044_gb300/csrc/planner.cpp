@@ -90,9 +90,39 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::GATE_CTRL: return run_controlled(s, &st.q[0], st.nq - 1, st.q[st.nq - 1], st.m);
     case qs_step::GATE_DIAG: return run_diag(s, st.q, st.nq, st.m);
     case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
-    case qs_step::TILE: return run_tile(s, p, st.tile_index);
+    case qs_step::TILE: return run_tile(s, p, st.tile_index, false);
   }
   return fail(QS_EINVAL, "bad plan step");
+}
+
+// The same step on a complex128 state held in double-float storage.
+qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
+  switch (st.type) {
+    case qs_step::GATE_1Q: return run_controlled_dfl(s, nullptr, 0, st.q[0], st.m);
+    case qs_step::GATE_CTRL: return run_controlled_dfl(s, &st.q[0], st.nq - 1, st.q[st.nq - 1], st.m);
+    case qs_step::GATE_DIAG: return run_diag_dfl(s, st.q, st.nq, st.m);
+    case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
+    case qs_step::TILE: return run_tile(s, p, st.tile_index, true);
+  }
+  return fail(QS_EINVAL, "bad plan step");
+}
+
+// Runs every step (optionally recording an event before the first step and
+// after each one).  A complex128 state is switched to double-float storage
+// for the duration of the plan and switched back even if a step fails.
+qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
+  const bool dfl = s->dtype == QS_C128;
+  qs_status r = dfl ? run_layout_dfl(s, true) : QS_OK;
+  if (ev) cudaEventRecord(ev[0], s->stream);
+  for (size_t i = 0; i < p->steps.size() && r == QS_OK; ++i) {
+    r = dfl ? run_step_dfl(s, p, p->steps[i]) : run_step(s, p, p->steps[i]);
+    if (ev) cudaEventRecord(ev[i + 1], s->stream);
+  }
+  if (dfl) {
+    const qs_status r2 = run_layout_dfl(s, false);
+    if (r == QS_OK) r = r2;
+  }
+  return r;
 }
 
 }  // namespace qs
@@ -200,11 +230,7 @@ qs_status qs_plan_destroy(qs_plan* p) {
 qs_status qs_run_plan(qs_state* s, qs_plan* p) {
   if (!s || !p) return fail(QS_EINVAL, "qs_run_plan: NULL argument");
   if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan: plan built for another n/dtype");
-  for (const qs_step& st : p->steps) {
-    qs_status r = run_step(s, p, st);
-    if (r != QS_OK) return r;
-  }
-  return QS_OK;
+  return run_all_steps(s, p, nullptr);
 }
 
 qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_bytes) {
@@ -231,12 +257,7 @@ qs_status qs_run_plan_profiled(qs_state* s, qs_plan* p, float* step_ms, int nste
     cudaError_t r = cudaEventCreate(&e);
     if (r != cudaSuccess) return cuda_fail(r, "qs_run_plan_profiled: event");
   }
-  qs_status result = QS_OK;
-  cudaEventRecord(ev[0], s->stream);
-  for (int i = 0; i < nsteps && result == QS_OK; ++i) {
-    result = run_step(s, p, p->steps[i]);
-    cudaEventRecord(ev[i + 1], s->stream);
-  }
+  qs_status result = run_all_steps(s, p, ev.data());
   cudaError_t r = cudaStreamSynchronize(s->stream);
   if (result == QS_OK && r != cudaSuccess) result = cuda_fail(r, "qs_run_plan_profiled: sync");
   if (result == QS_OK)

@@ -6,6 +6,8 @@ namespace qs {
 double step_bytes(const qs_step& st, int n, int S);
 qs_step unfused_step(const qs_gate_rec& g);
 qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st);
+qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st);
+qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev);
 // Fills p->steps (and p->tiles) for QS_PLAN_TILED.
 qs_status plan_tiled(qs_plan* p);
 // Register stages summed over the plan's tile passes.

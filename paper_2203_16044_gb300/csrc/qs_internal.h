@@ -56,6 +56,10 @@ qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M);
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
 qs_status run_set_basis(qs_state* s, u64 x);
+// complex128 double-float storage: in-place layout change and the gates on it
+qs_status run_layout_dfl(qs_state* s, bool to_dfl);
+qs_status run_controlled_dfl(qs_state* s, const int* ctrl, int nc, int t, const double U[8]);
+qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d);
 
 // ---- reductions (reduce.cu) ------------------------------------------------
 qs_status run_norm2(qs_state* s, double* out);
@@ -100,6 +104,6 @@ struct qs_plan {
 };
 
 namespace qs {
-qs_status run_tile(qs_state* s, qs_plan* p, int tile_index);
+qs_status run_tile(qs_state* s, qs_plan* p, int tile_index, bool dfl);
 void tile_free(qs_tile_pass* t);
 }  // namespace qs

@@ -58,7 +58,7 @@ struct ParamSrc {
 template <int MODE, int G, int GPT, bool DENSE>
 __global__ void __launch_bounds__(kTT) k_tile(void* amp, const __grid_constant__ TileArgs A) {
   typedef typename Elem<MODE>::T E;
-  typedef typename std::conditional<MODE == 0, float, double>::type R;
+  typedef typename std::conditional<MODE == 1, double, float>::type R;  // MODE 2: double-float storage
   constexpr int APP = MODE == 0 ? 2 : 1;  // amplitudes per 16-byte packet
   extern __shared__ __align__(16) unsigned char smem[];
   u64* tab = reinterpret_cast<u64*>(smem);  // [2][64] spread tables
@@ -485,7 +485,7 @@ qs_status plan_tiled(qs_plan* p) {
   return QS_OK;
 }
 
-qs_status run_tile(qs_state* s, qs_plan* p, int tile_index) {
+qs_status run_tile(qs_state* s, qs_plan* p, int tile_index, bool dfl) {
   const qs_tile_pass& tp = *p->tiles[tile_index];
   static thread_local TileArgs A;
   A.L = tp.L;
@@ -514,6 +514,10 @@ qs_status run_tile(qs_state* s, qs_plan* p, int tile_index) {
     if (!tp.mats.empty())
       return gpt == 2 ? launch_tile<0, 3, 2, true>(s, A, smem, grid) : launch_tile<0, 3, 1, true>(s, A, smem, grid);
     return gpt == 2 ? launch_tile<0, 3, 2, false>(s, A, smem, grid) : launch_tile<0, 3, 1, false>(s, A, smem, grid);
+  }
+  if (dfl) {
+    if (tp.G == 4) return launch_tile<2, 4, 1, false>(s, A, smem, grid);
+    return gpt == 2 ? launch_tile<2, 3, 2, false>(s, A, smem, grid) : launch_tile<2, 3, 1, false>(s, A, smem, grid);
   }
   if (tp.G == 4) return launch_tile<1, 4, 1, false>(s, A, smem, grid);
   return gpt == 2 ? launch_tile<1, 3, 2, false>(s, A, smem, grid) : launch_tile<1, 3, 1, false>(s, A, smem, grid);

@@ -61,6 +61,7 @@ constexpr int kMatFloats = 128;  // 8 x 8 complex64
 template <int MODE> struct Elem;
 template <> struct Elem<0> { typedef float2 T; };
 template <> struct Elem<1> { typedef cdf T; };
+template <> struct Elem<2> { typedef cdf T; };  // complex128 held in double-float storage
 
 __device__ __forceinline__ int ins1(int x, int p) {
   const int lo = x & ((1 << p) - 1);
@@ -217,6 +218,17 @@ __device__ __forceinline__ void load_pk(const double* a, u64 p, cdf* t, int la) 
   ld16(a + p * 2, v);
   const dfl r = d2df(v[0]), i = d2df(v[1]);
   t[swz<MODE>(la)] = cdf{r.h, r.l, i.h, i.l};
+}
+// complex128 in double-float storage: an amplitude is one float4 (re_h, re_l, im_h, im_l)
+template <int MODE>
+__device__ __forceinline__ void load_pk(const float* a, u64 p, cdf* t, int la) {
+  const float4 v = *reinterpret_cast<const float4*>(a + p * 4);
+  t[swz<MODE>(la)] = cdf{v.x, v.y, v.z, v.w};
+}
+template <int MODE>
+__device__ __forceinline__ void store_pk(float* a, u64 p, const cdf* t, int la) {
+  const cdf x = t[swz<MODE>(la)];
+  *reinterpret_cast<float4*>(a + p * 4) = make_float4(x.rh, x.rl, x.ih, x.il);
 }
 template <int MODE>
 __device__ __forceinline__ void store_pk(double* a, u64 p, const cdf* t, int la) {
