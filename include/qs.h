@@ -204,7 +204,9 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
 
 /* Plan options.  mode: QS_PLAN_UNFUSED applies every gate with its own pass
  * (one kernel per gate); QS_PLAN_TILED groups gates into shared-memory tile
- * passes.  tile_qubits: qubits resident per tile pass (0 = library default
+ * passes; QS_PLAN_FUSED multiplies gates into dense blocks of at most
+ * fuse_qubits qubits, each applied as one pass (complex64 blocks of 4 to 6
+ * qubits run on the tensor cores, as qs_apply_fused).  tile_qubits: qubits resident per tile pass (0 = library default
  * for the dtype; at most 14 for QS_C64, 13 for QS_C128); low_qubits: qubits
  * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);
  * slot_qubits: qubits held in registers per stage inside a tile pass, 3 or
@@ -213,7 +215,7 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * 0 = a stage whose gates all act within its three slot qubits may be fused
  * into one 8x8 matrix when the planner estimates that cheaper (complex64,
  * three slots), -1 = never.  Every field must be zero or valid. */
-enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1 };
+enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1, QS_PLAN_FUSED = 2 };
 typedef struct {
   int mode;
   int tile_qubits;
@@ -221,7 +223,8 @@ typedef struct {
   int slot_qubits;
   int groups_per_thread;
   int dense;
-  int reserved[2];
+  int fuse_qubits;    /* QS_PLAN_FUSED: qubits per dense block, 2..6 (0 = 5) */
+  int reserved[1];
 } qs_plan_opts;
 
 typedef struct {
@@ -247,7 +250,7 @@ qs_status qs_plan_destroy(qs_plan* p);
 qs_status qs_run_plan(qs_state* st, qs_plan* p);
 
 /* Step kinds reported by qs_plan_step_info. */
-enum { QS_STEP_1Q = 0, QS_STEP_CTRL = 1, QS_STEP_DIAG = 2, QS_STEP_SWAP = 3, QS_STEP_TILE = 4 };
+enum { QS_STEP_1Q = 0, QS_STEP_CTRL = 1, QS_STEP_DIAG = 2, QS_STEP_SWAP = 3, QS_STEP_TILE = 4, QS_STEP_BLOCK = 5 };
 
 /* Kind and algorithmic HBM bytes (read + write of the amplitudes it
  * touches) of plan step i, 0 <= i < passes. */

@@ -30,7 +30,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 C64, C128 = 0, 1
-PLAN_UNFUSED, PLAN_TILED = 0, 1
+PLAN_UNFUSED, PLAN_TILED, PLAN_FUSED = 0, 1, 2
 
 GATE_KIND = {"H": 0, "X": 1, "Y": 2, "Z": 3, "S": 4, "T": 5, "RX": 6, "RY": 7, "RZ": 8, "P": 9,
              "U3": 10, "CNOT": 16, "CZ": 17, "CP": 18, "SWAP": 19}
@@ -45,7 +45,7 @@ _int = ctypes.c_int
 class PlanOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("low_qubits", ctypes.c_int),
                 ("slot_qubits", ctypes.c_int), ("groups_per_thread", ctypes.c_int), ("dense", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("fuse_qubits", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class PlanStats(ctypes.Structure):
@@ -327,9 +327,9 @@ class Plan:
 
     def __init__(self, circuit: Circuit, n: int, dtype: str = "c128", mode: int = PLAN_TILED,
                  tile_qubits: int = 0, low_qubits: int = 0, slot_qubits: int = 0, groups_per_thread: int = 0,
-                 dense: int = 0):
+                 dense: int = 0, fuse_qubits: int = 0):
         opts = PlanOpts(mode=mode, tile_qubits=tile_qubits, low_qubits=low_qubits, slot_qubits=slot_qubits,
-                        groups_per_thread=groups_per_thread, dense=dense)
+                        groups_per_thread=groups_per_thread, dense=dense, fuse_qubits=fuse_qubits)
         h = _vp()
         _check(_lib.qs_plan_build(circuit.handle, int(n), C64 if dtype == "c64" else C128, ctypes.byref(opts),
                                   ctypes.byref(h)), "qs_plan_build")
@@ -347,7 +347,7 @@ class Plan:
         return {"n": s.n, "dtype": s.dtype, "gates": s.gates, "passes": s.passes, "hbm_bytes": s.hbm_bytes,
                 "metric_bytes": s.metric_bytes, "stages": s.stages, "dense_stages": s.dense_stages}
 
-    STEP_KINDS = ("1q", "ctrl", "diag", "swap", "tile")
+    STEP_KINDS = ("1q", "ctrl", "diag", "swap", "tile", "block")
 
     def step_info(self):
         """[(kind, algorithmic HBM bytes)] for every pass of the plan."""

@@ -11,7 +11,9 @@
 //                    (§III-B) -- a tile of 2^m amplitudes spanning a chosen
 //                    qubit set is read once, every gate on those qubits is
 //                    applied in shared memory, and the tile is written back.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -37,6 +39,7 @@ double step_bytes(const qs_step& st, int n, int S) {
     }
     case qs_step::GATE_SWAP: return N * S;  // half the amplitudes move
     case qs_step::TILE: return 2.0 * N * S;
+    case qs_step::BLOCK: return 2.0 * N * S;
   }
   return 0.0;
 }
@@ -91,6 +94,10 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::GATE_DIAG: return run_diag(s, st.q, st.nq, st.m);
     case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
     case qs_step::TILE: return run_tile(s, p, st.tile_index, false);
+    case qs_step::BLOCK: {
+      const qs_block& b = p->blocks[st.tile_index];
+      return run_dense(s, b.q, b.k, b.M.data(), 1);  // a product of unitary gates
+    }
   }
   return fail(QS_EINVAL, "bad plan step");
 }
@@ -103,6 +110,7 @@ qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::GATE_DIAG: return run_diag_dfl(s, st.q, st.nq, st.m);
     case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
     case qs_step::TILE: return run_tile(s, p, st.tile_index, true);
+    case qs_step::BLOCK: return fail(QS_EINVAL, "dense blocks do not run in double-float storage");
   }
   return fail(QS_EINVAL, "bad plan step");
 }
@@ -111,7 +119,9 @@ qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
 // after each one).  A complex128 state is switched to double-float storage
 // for the duration of the plan and switched back even if a step fails.
 qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
-  const bool dfl = s->dtype == QS_C128;
+  // complex128 plans switch to double-float storage unless they hold dense
+  // blocks (those run on the FP64 layout)
+  const bool dfl = s->dtype == QS_C128 && p->blocks.empty();
   qs_status r = dfl ? run_layout_dfl(s, true) : QS_OK;
   if (ev) cudaEventRecord(ev[0], s->stream);
   for (size_t i = 0; i < p->steps.size() && r == QS_OK; ++i) {
@@ -122,7 +132,119 @@ qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
     const qs_status r2 = run_layout_dfl(s, false);
     if (r == QS_OK) r = r2;
   }
+  // complex64 tensor-core blocks: their FP32 accumulation truncates (rounds
+  // toward zero), a small systematic norm loss per block; the exact circuit
+  // is unitary, so the state is rescaled to its input norm (unit) at the end
+  if (r == QS_OK && s->dtype == QS_C64) {
+    bool tc = false;
+    for (const qs_block& b : p->blocks) tc |= b.k >= 4;
+    if (tc) r = run_normalize(s);
+  }
   return r;
+}
+
+// ---------------------------------------------------------------------------
+// QS_PLAN_FUSED: gates multiplied into dense blocks of at most k qubits.
+// Greedy over the circuit in order: a gate joins the current block when no
+// earlier gate left out of the block touches its qubits and the block's
+// qubit set, with the gate's, stays within k; otherwise its qubits are
+// blocked for the rest of the scan.  The block matrix is built by applying
+// each gate's 2x2 / 4x4 matrix to the rows of the running product.
+// ---------------------------------------------------------------------------
+namespace {
+typedef std::complex<double> cd;
+
+void left_apply(std::vector<cd>& M, int k, const qs_gate_rec& g, const std::vector<int>& bq) {
+  const int D = 1 << k;
+  auto slot = [&](int q) { return (int)(std::find(bq.begin(), bq.end(), q) - bq.begin()); };
+  double m[32];
+  const int nq = gate_matrix(g.kind, g.p, m);
+  if (nq == 1) {
+    const int a = slot(g.q[0]);
+    const cd u00(m[0], m[1]), u01(m[2], m[3]), u10(m[4], m[5]), u11(m[6], m[7]);
+    for (int r0 = 0; r0 < D; ++r0) {
+      if ((r0 >> a) & 1) continue;
+      const int r1 = r0 | (1 << a);
+      for (int c = 0; c < D; ++c) {
+        const cd x = M[r0 * D + c], y = M[r1 * D + c];
+        M[r0 * D + c] = u00 * x + u01 * y;
+        M[r1 * D + c] = u10 * x + u11 * y;
+      }
+    }
+  } else {
+    const int a = slot(g.q[0]), b = slot(g.q[1]);
+    cd G[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) G[i][j] = cd(m[2 * (i * 4 + j)], m[2 * (i * 4 + j) + 1]);
+    for (int base = 0; base < D; ++base) {
+      if (((base >> a) & 1) || ((base >> b) & 1)) continue;
+      const int idx[4] = {base, base | (1 << a), base | (1 << b), base | (1 << a) | (1 << b)};
+      for (int c = 0; c < D; ++c) {
+        cd v[4], w[4];
+        for (int j = 0; j < 4; ++j) v[j] = M[idx[j] * D + c];
+        for (int i = 0; i < 4; ++i) {
+          w[i] = 0.0;
+          for (int j = 0; j < 4; ++j) w[i] += G[i][j] * v[j];
+        }
+        for (int i = 0; i < 4; ++i) M[idx[i] * D + c] = w[i];
+      }
+    }
+  }
+}
+}  // namespace
+
+qs_status plan_fused(qs_plan* p) {
+  const int n = p->n;
+  int kmax = p->opts.fuse_qubits > 0 ? p->opts.fuse_qubits : 5;
+  if (kmax < 2 || kmax > 6) return fail(QS_EINVAL, "qs_plan_build: fuse_qubits=%d outside [2, 6]", kmax);
+  if (kmax > n) kmax = n;
+  std::vector<const qs_gate_rec*> remaining;
+  for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
+  while (!remaining.empty()) {
+    std::vector<char> inB(n, 0), blocked(n, 0);
+    std::vector<int> bq;
+    std::vector<const qs_gate_rec*> absorbed, rest;
+    for (const qs_gate_rec* g : remaining) {
+      int gq[2];
+      gq[0] = g->q[0];
+      const int ng = gate_arity(g->kind);
+      if (ng == 2) gq[1] = g->q[1];
+      bool blk = false;
+      int add = 0;
+      for (int i = 0; i < ng; ++i) {
+        blk |= blocked[gq[i]] != 0;
+        add += inB[gq[i]] ? 0 : 1;
+      }
+      if (!blk && (int)bq.size() + add <= kmax) {
+        for (int i = 0; i < ng; ++i)
+          if (!inB[gq[i]]) { inB[gq[i]] = 1; bq.push_back(gq[i]); }
+        absorbed.push_back(g);
+        continue;
+      }
+      for (int i = 0; i < ng; ++i) blocked[gq[i]] = 1;
+      rest.push_back(g);
+    }
+    std::sort(bq.begin(), bq.end());
+    qs_block b;
+    b.k = (int)bq.size();
+    for (int i = 0; i < b.k; ++i) b.q[i] = bq[i];
+    const int D = 1 << b.k;
+    std::vector<cd> M((size_t)D * D, 0.0);
+    for (int r = 0; r < D; ++r) M[(size_t)r * D + r] = 1.0;
+    for (const qs_gate_rec* g : absorbed) left_apply(M, b.k, *g, bq);
+    b.M.resize((size_t)2 * D * D);
+    for (size_t i = 0; i < M.size(); ++i) {
+      b.M[2 * i] = M[i].real();
+      b.M[2 * i + 1] = M[i].imag();
+    }
+    p->blocks.push_back(std::move(b));
+    qs_step st{};
+    st.type = qs_step::BLOCK;
+    st.tile_index = (int)p->blocks.size() - 1;
+    p->steps.push_back(st);
+    remaining.swap(rest);
+  }
+  return QS_OK;
 }
 
 }  // namespace qs
@@ -194,6 +316,8 @@ qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_pla
     st = QS_OK;
   } else if (p->opts.mode == QS_PLAN_TILED) {
     st = plan_tiled(p);
+  } else if (p->opts.mode == QS_PLAN_FUSED) {
+    st = plan_fused(p);
   } else {
     st = fail(QS_EINVAL, "qs_plan_build: unknown mode %d", p->opts.mode);
   }
@@ -243,6 +367,7 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
     case qs_step::GATE_DIAG: *kind = QS_STEP_DIAG; break;
     case qs_step::GATE_SWAP: *kind = QS_STEP_SWAP; break;
     case qs_step::TILE: *kind = QS_STEP_TILE; break;
+    case qs_step::BLOCK: *kind = QS_STEP_BLOCK; break;
   }
   *hbm_bytes = step_bytes(st, p->n, amp_bytes(p->dtype));
   return QS_OK;

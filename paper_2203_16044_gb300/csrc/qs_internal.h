@@ -52,7 +52,10 @@ bool gate_is_diagonal(int kind);
 qs_status run_1q(qs_state* s, int q, const double U[8]);
 qs_status run_controlled(qs_state* s, const int* ctrl, int nc, int t, const double U[8]);
 qs_status run_diag(qs_state* s, const int* qubits, int k, const double* d);
-qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M);
+// unitary: 1 known unitary, 0 not, -1 check (tensor-core path restores group norms)
+qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M, int unitary = -1);
+// complex64 dense block, 4 <= k <= 6, on the tensor cores (fused_tc.cu)
+qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, int unitary);
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
 qs_status run_set_basis(qs_state* s, u64 x);
@@ -63,6 +66,7 @@ qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d);
 
 // ---- reductions (reduce.cu) ------------------------------------------------
 qs_status run_norm2(qs_state* s, double* out);
+qs_status run_normalize(qs_state* s);
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask,
                      const double* coeff, double* out);
@@ -83,11 +87,18 @@ struct qs_circuit {
 
 // One step of a compiled plan.
 struct qs_step {
-  enum Type { GATE_1Q, GATE_CTRL, GATE_DIAG, GATE_SWAP, TILE } type;
+  enum Type { GATE_1Q, GATE_CTRL, GATE_DIAG, GATE_SWAP, TILE, BLOCK } type;
   int q[4];
   int nq;
   double m[32];         // matrix / diagonal (FP64)
-  int tile_index;       // TILE: index into plan->tiles
+  int tile_index;       // TILE: index into plan->tiles; BLOCK: into plan->blocks
+};
+
+// A dense block of a QS_PLAN_FUSED plan: 2^k x 2^k complex matrix over qubits.
+struct qs_block {
+  int k;
+  int q[6];
+  std::vector<double> M;  // row-major (re, im)
 };
 
 struct qs_tile_pass;    // defined in tile.cu
@@ -101,6 +112,7 @@ struct qs_plan {
   qs_plan_stats stats{};
   // tile passes (host description; owned by the plan, freed by tile_free)
   std::vector<qs_tile_pass*> tiles;
+  std::vector<qs_block> blocks;
 };
 
 namespace qs {

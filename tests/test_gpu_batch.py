@@ -104,7 +104,7 @@ def test_batch_tile_options_and_autotune(qs):
 def test_batch_wait_times_out_cleanly(qs):
     sizes = [15, 16]  # multi-pass circuits: second passes wait on the first
     circs = circuits_for(sizes, 400)
-    b = qs.Batch(sizes, circs, dtype="c64", reserved=(1, 0))
+    b = qs.Batch(sizes, circs, dtype="c64", reserved=(1,))
     b.run(True)
     with pytest.raises(qs.QSError) as ei:
         b.sync()

@@ -63,11 +63,16 @@ CASES = [
 
 @pytest.mark.parametrize("name,n,make,x0", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("mode", [0, 1], ids=["unfused", "tiled"])
-def test_circuit_matches_oracle(qs, name, n, make, x0, dtype, mode):
+@pytest.mark.parametrize("mode,fuse", [(0, 0), (1, 0), (2, 4), (2, 5), (2, 6), (2, 3)],
+                         ids=["unfused", "tiled", "fused4", "fused5", "fused6", "fused3"])
+def test_circuit_matches_oracle(qs, name, n, make, x0, dtype, mode, fuse):
     circ = make()
     want = oracle_state(n, circ, x0)
-    got, stats = run_gpu(qs, n, circ, dtype, mode, x0)
+    s = qs.State(n, dtype)
+    s.set_basis(x0)
+    p = qs.Plan(qs.Circuit(circ), n, dtype, mode=mode, fuse_qubits=fuse)
+    s.run(p)
+    got, stats = s.to_numpy(), p.stats()
     assert stats["gates"] == len(circ)
     if dtype == "c128":
         err = np.max(np.abs(got - want))
@@ -90,7 +95,7 @@ def test_qft_closed_form_gpu(qs, dtype, mode):
     assert np.max(np.abs(got - want)) <= tol
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["unfused", "tiled"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["unfused", "tiled", "fused"])
 def test_c64_vs_oracle_depth40_16q(qs, mode):
     # the complex64 tolerance at depth 40 on a size the oracle runs in seconds
     n = 16

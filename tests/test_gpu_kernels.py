@@ -128,8 +128,11 @@ def test_apply_diag_phase_on_ones(qs, dtype, n, k):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,k", [(2, 2), (5, 3), (9, 4), (12, 5), (13, 6), (11, 1)])
+@pytest.mark.parametrize("n,k", [(2, 2), (5, 3), (9, 4), (12, 5), (13, 6), (11, 1), (4, 4), (6, 6), (16, 4), (15, 6),
+                                 (20, 5)])
 def test_apply_fused(qs, dtype, n, k):
+    # complex64 with k >= 4 runs on the tensor cores (3xTF32 split products):
+    # ~2^-21 relative per product, inside C64_TOL for 2^k-term sums
     psi = W.random_state(n, 7000 + n)
     for seed in range(2):
         qsel = W.random_qubits(n, k, 7100 + n + seed)
