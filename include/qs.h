@@ -333,9 +333,14 @@ qs_status qs_batch_autotune(int count, const int* n, qs_dtype dtype, void* const
  *   theta:   batch x nparam angles (row-major).
  *   H:       sum_t coeff[t] P_t with Pauli strings as in qs_expect_pauli.
  *   energy:  batch values; grad: batch x nparam, dE/dtheta (row-major).
- * Gradients accumulate in FP64 for both dtypes.  Synchronises the state's
- * stream.  Allocates one extra state vector and the gradient partials for
- * the duration of the call. */
+ * Per-pair gradient products are FP32 (complex64) or double-float
+ * (complex128), summed per thread in double-float and across threads in FP64.
+ * Parameter sets run in chunks of Bc (a power of two chosen from the state
+ * size): psi and lambda of a chunk share one allocation of 2 Bc state
+ * vectors, so each fixed gate is one launch for the whole chunk; with Bc = 1
+ * the state itself holds psi and one extra vector is allocated.  Allocations
+ * (stream-ordered) last for the call; QS_ENOMEM if they fail.  Synchronises
+ * the state's stream. */
 qs_status qs_adjoint_grad(qs_state* st, const qs_circuit* c, const double* theta, int nparam, int batch,
                           int nterms, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
                           double* energy, double* grad);

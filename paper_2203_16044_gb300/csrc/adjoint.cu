@@ -3,28 +3,34 @@
 // The paper has no differentiation; this is the standard reverse sweep for
 // E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U_L ... U_1 |0...0>,
 // whose trainable gates are R_P(t) = exp(-i t P / 2), P in {X, Y, Z}:
-//   forward:  psi = U_L ... U_1 |0>        (a compiled tile plan)
-//             lambda = H psi               (k_pauli_apply, one pass per X/Y mask)
-//             E = Re <psi|lambda>
+//   forward:  psi = U_L ... U_1 |0>        (a compiled tile plan per parameter set)
+//             lambda = H psi, E = Re <psi|lambda>   (one fused pass, k_hamiltonian)
 //   reverse:  for l = L .. 1
 //               if gate l is R_P(theta_j):  g_j += Im <lambda|P_q|psi>
 //               psi <- U_l^dagger psi ;  lambda <- U_l^dagger lambda
 // (dE/dt = 2 Re <lambda_l| (-i P/2) |psi_l> = Im <lambda_l|P|psi_l> with
 // psi_l, lambda_l the states right after gate l.)
 //
-// One-qubit steps run as one fused kernel (k_adj_1q): it reads the pair
-// (psi_x0, psi_x1) and (lambda_x0, lambda_x1) once, accumulates the
-// gradient term in FP64 (per-CTA partials, summed in a fixed order), and
-// writes back U^dagger applied to both -- one pass over two vectors instead of
-// three.  Two-qubit gates (CNOT, CZ, CP, SWAP) are un-applied with the
-// per-gate kernels.  complex128 uses double-float arithmetic, complex64 FP32;
-// gradients accumulate in FP64 for both.
+// Parameter sets are processed Bc at a time.  psi and lambda of the chunk live
+// in one buffer [psi_0 .. psi_{Bc-1}, lambda_0 .. lambda_{Bc-1}], which is
+// itself a state of n + log2(Bc) + 1 qubits: a fixed gate on qubits < n is
+// un-applied to all 2 Bc vectors by one launch of the per-gate kernel, and a
+// trainable gate by one launch of k_adj_1q over (pairs, set).  Bc is the
+// largest power of two <= batch whose 2 Bc vectors fit a budget (adj_chunk).
+// With Bc = 1 psi is the caller's state and lambda a second vector.
+//
+// Arithmetic: complex64 in FP32; complex128 in double-float, with psi and
+// lambda held in double-float storage for the whole reverse sweep (each FP64
+// value as its (hi, lo) float pair in the same 8 bytes, so an amplitude is one
+// float4 and no kernel converts).  Per-pair gradient products are FP32
+// (complex64) or double-float (complex128), summed per thread in
+// double-float; CTA partials are summed in FP64 in a fixed order.
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "arith.cuh"
-#include "pauli.cuh"
 #include "planner.h"
 
 namespace qs {
@@ -52,57 +58,153 @@ __device__ __forceinline__ double a_block_sum(double a) {
   return a;
 }
 
-// gen: 0 none, 1 X, 2 Y, 3 Z (the generator of the trainable gate).
-template <typename R>
-__global__ void __launch_bounds__(kAT) k_adj_1q(R* __restrict__ psi, R* __restrict__ lam, u64 npairs, int q,
-                                                typename Ar<R>::Mat Udag, int gen, double* part) {
+// acc += v in double-float (low part left unnormalised; it only gathers the
+// rounding errors of the high part)
+__device__ __forceinline__ void df_acc(dfl& acc, dfl v) {
+  float e;
+  acc.h = two_sum(acc.h, v.h, e);
+  acc.l = __fadd_rn(acc.l, __fadd_rn(e, v.l));
+}
+
+// a + b in double-float, normalised
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float e;
+  const float s = two_sum(a.h, b.h, e);
+  dfl r;
+  r.h = fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)), r.l);
+  return r;
+}
+
+// Amplitude storage of the sweep: complex64 as float2 (re, im); complex128
+// in double-float storage as float4 (re_h, re_l, im_h, im_l).
+template <typename R> struct Amp;
+template <> struct Amp<float> { typedef float2 V; };
+template <> struct Amp<double> { typedef float4 V; };
+
+__device__ __forceinline__ void upd(const M2<float>& U, float2& a, float2& b) { mv2(U, a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ void upd(const M2df& U, float4& a, float4& b) {
+  cdf A{a.x, a.y, a.z, a.w}, B{b.x, b.y, b.z, b.w};
+  mv2df(U, A, B);
+  a = make_float4(A.rh, A.rl, A.ih, A.il);
+  b = make_float4(B.rh, B.rl, B.ih, B.il);
+}
+
+// Gradient term of one amplitude pair, Im <lambda|P_q|psi> restricted to the
+// pair (a = lambda, b = psi; conj(a) b = (ar br + ai bi) + i (ar bi - ai br)):
+//   P = X: Im(conj(a0) b1 + conj(a1) b0)
+//   P = Y: Im(-i conj(a0) b1 + i conj(a1) b0) = -Re(conj(a0) b1) + Re(conj(a1) b0)
+//   P = Z: Im(conj(a0) b0 - conj(a1) b1)
+__device__ __forceinline__ dfl grad_term(int gen, float2 a0, float2 a1, float2 b0, float2 b1) {
+  float t;
+  if (gen == 1) t = __fmaf_rn(a0.x, b1.y, -a0.y * b1.x) + __fmaf_rn(a1.x, b0.y, -a1.y * b0.x);
+  else if (gen == 2) t = __fmaf_rn(a1.x, b0.x, a1.y * b0.y) - __fmaf_rn(a0.x, b1.x, a0.y * b1.y);
+  else t = __fmaf_rn(a0.x, b0.y, -a0.y * b0.x) - __fmaf_rn(a1.x, b1.y, -a1.y * b1.x);
+  return dfl{t, 0.0f};
+}
+__device__ __forceinline__ dfl grad_term(int gen, float4 a0, float4 a1, float4 b0, float4 b1) {
+  // components: .x re_h, .y re_l, .z im_h, .w im_l
+  if (gen == 1)
+    return dot4(a0.x, a0.y, b1.z, b1.w, -a0.z, -a0.w, b1.x, b1.y, a1.x, a1.y, b0.z, b0.w, -a1.z, -a1.w, b0.x, b0.y);
+  if (gen == 2)
+    return dot4(-a0.x, -a0.y, b1.x, b1.y, -a0.z, -a0.w, b1.z, b1.w, a1.x, a1.y, b0.x, b0.y, a1.z, a1.w, b0.z, b0.w);
+  return dot4(a0.x, a0.y, b0.z, b0.w, -a0.z, -a0.w, b0.x, b0.y, -a1.x, -a1.y, b1.z, b1.w, a1.z, a1.w, b1.x, b1.y);
+}
+
+// Trainable step (gen 1, 2, 3: generator X, Y, Z) for every set b =
+// blockIdx.y: psi_b = psi + b N, lambda_b = lam + b N, U^dagger of set b at
+// mats[b]; gradient partials part[b * gridDim.x + blockIdx.x].
+template <typename V, typename Mat>
+__global__ void __launch_bounds__(kAT) k_adj_1q(V* __restrict__ psi, V* __restrict__ lam, u64 N, u64 npairs, int q,
+                                                const Mat* __restrict__ mats, int gen, double* __restrict__ part) {
+  const int b = blockIdx.y;
+  V* ps = psi + N * b;
+  V* lm = lam + N * b;
+  const Mat U = mats[b];
   const u64 lo_mask = (u64(1) << q) - 1;
-  double g = 0.0;
+  dfl acc{0.0f, 0.0f};
   for (u64 i = (u64)blockIdx.x * kAT + threadIdx.x; i < npairs; i += (u64)gridDim.x * kAT) {
     const u64 x0 = ((i & ~lo_mask) << 1) | (i & lo_mask);
     const u64 x1 = x0 | (lo_mask + 1);
-    R p0r = psi[2 * x0], p0i = psi[2 * x0 + 1], p1r = psi[2 * x1], p1i = psi[2 * x1 + 1];
-    R l0r = lam[2 * x0], l0i = lam[2 * x0 + 1], l1r = lam[2 * x1], l1i = lam[2 * x1 + 1];
-    if (gen) {
-      // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-      const double a0r = l0r, a0i = l0i, a1r = l1r, a1i = l1i;
-      const double b0r = p0r, b0i = p0i, b1r = p1r, b1i = p1i;
-      if (gen == 1) {         // Im(conj(l0) p1 + conj(l1) p0)
-        g += (a0r * b1i - a0i * b1r) + (a1r * b0i - a1i * b0r);
-      } else if (gen == 2) {  // Im(-i conj(l0) p1 + i conj(l1) p0) = -Re(conj(l0) p1) + Re(conj(l1) p0)
-        g += -(a0r * b1r + a0i * b1i) + (a1r * b0r + a1i * b0i);
-      } else {                // Im(conj(l0) p0 - conj(l1) p1)
-        g += (a0r * b0i - a0i * b0r) - (a1r * b1i - a1i * b1r);
-      }
-    }
-    pair_apply(Udag, p0r, p0i, p1r, p1i);
-    pair_apply(Udag, l0r, l0i, l1r, l1i);
-    psi[2 * x0] = p0r; psi[2 * x0 + 1] = p0i; psi[2 * x1] = p1r; psi[2 * x1 + 1] = p1i;
-    lam[2 * x0] = l0r; lam[2 * x0 + 1] = l0i; lam[2 * x1] = l1r; lam[2 * x1 + 1] = l1i;
+    V p0 = ps[x0], p1 = ps[x1], l0 = lm[x0], l1 = lm[x1];
+    df_acc(acc, grad_term(gen, l0, l1, p0, p1));
+    upd(U, p0, p1);
+    upd(U, l0, l1);
+    ps[x0] = p0;
+    ps[x1] = p1;
+    lm[x0] = l0;
+    lm[x1] = l1;
   }
-  if (gen) {
-    g = a_block_sum(g);
-    if (threadIdx.x == 0) part[blockIdx.x] = g;
-  }
+  const double g = a_block_sum((double)acc.h + (double)acc.l);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = g;
 }
 
-// out (=, or += if accumulate) f(x ^ m) psi_{x ^ m} for one Pauli group.
-template <typename R>
-__global__ void __launch_bounds__(kAT) k_pauli_apply(const R* __restrict__ psi, R* __restrict__ out, u64 N,
-                                                     const __grid_constant__ PauliGroup g, int accumulate) {
-  for (u64 x = (u64)blockIdx.x * kAT + threadIdx.x; x < N; x += (u64)gridDim.x * kAT) {
-    const u64 y = x ^ g.m;
-    double fr, fi;
-    fval(g, y, fr, fi);
-    const double yr = psi[2 * y], yi = psi[2 * y + 1];
-    double r = fr * yr - fi * yi, im = fr * yi + fi * yr;
-    if (accumulate) {
-      r += (double)out[2 * x];
-      im += (double)out[2 * x + 1];
-    }
-    out[2 * x] = (R)r;
-    out[2 * x + 1] = (R)im;
+// H = sum_t c_t P_t with Pauli strings grouped by their X/Y mask m:
+// P|x> = i^{nY} (-1)^{popcount(x & z)} |x ^ m>, so
+//   (H psi)_x = sum_groups f_g(x ^ m_g) psi_{x ^ m_g},
+//   f_g(y) = sum_{t in g} w_t (-1)^{popcount(y & z_t)},  w_t = c_t i^{nY_t}.
+struct HGroup {
+  u64 m;
+  int first, nt;
+};
+struct HTerm {
+  u64 z;
+  float wrh, wrl, wih, wil;  // w_t in double-float
+};
+
+__device__ __forceinline__ void hmul_acc(const HTerm* __restrict__ T, const HGroup& G, u64 y, float2 py, float2& acc) {
+  float fr = 0.0f, fi = 0.0f;
+  for (int t = 0; t < G.nt; ++t) {
+    const HTerm w = T[G.first + t];
+    const bool neg = __popcll(y & w.z) & 1;
+    fr += neg ? -w.wrh : w.wrh;
+    fi += neg ? -w.wih : w.wih;
   }
+  acc.x = __fmaf_rn(fr, py.x, __fmaf_rn(-fi, py.y, acc.x));
+  acc.y = __fmaf_rn(fr, py.y, __fmaf_rn(fi, py.x, acc.y));
+}
+__device__ __forceinline__ void hmul_acc(const HTerm* __restrict__ T, const HGroup& G, u64 y, float4 py,
+                                         float4& acc) {
+  dfl fr{0.0f, 0.0f}, fi{0.0f, 0.0f};
+  for (int t = 0; t < G.nt; ++t) {
+    const HTerm w = T[G.first + t];
+    const float s = (__popcll(y & w.z) & 1) ? -1.0f : 1.0f;
+    df_acc(fr, dfl{s * w.wrh, s * w.wrl});
+    df_acc(fi, dfl{s * w.wih, s * w.wil});
+  }
+  fr.h = fast_two_sum(fr.h, fr.l, fr.l);
+  fi.h = fast_two_sum(fi.h, fi.l, fi.l);
+  const dfl re = dot2(fr.h, fr.l, py.x, py.y, -fi.h, -fi.l, py.z, py.w);
+  const dfl im = dot2(fr.h, fr.l, py.z, py.w, fi.h, fi.l, py.x, py.y);
+  const dfl ar = df_add(dfl{acc.x, acc.y}, re), ai = df_add(dfl{acc.z, acc.w}, im);
+  acc = make_float4(ar.h, ar.l, ai.h, ai.l);
+}
+__device__ __forceinline__ void vzero(float2& v) { v = make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ void vzero(float4& v) { v = make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
+__device__ __forceinline__ dfl re_dot(float2 a, float2 b) { return dfl{__fmaf_rn(a.x, b.x, a.y * b.y), 0.0f}; }
+__device__ __forceinline__ dfl re_dot(float4 a, float4 b) { return dot2(a.x, a.y, b.x, b.y, a.z, a.w, b.z, b.w); }
+
+// lambda_b = H psi_b (every set b = blockIdx.y) and the partials of
+// E_b = Re <psi_b|lambda_b>, part[b * gridDim.x + blockIdx.x], in one pass.
+template <typename V>
+__global__ void __launch_bounds__(kAT) k_hamiltonian(const V* __restrict__ psi, V* __restrict__ lam, u64 N,
+                                                     const HGroup* __restrict__ groups, int ngroups,
+                                                     const HTerm* __restrict__ terms, double* __restrict__ part) {
+  const V* ps = psi + N * blockIdx.y;
+  V* lm = lam + N * blockIdx.y;
+  dfl e{0.0f, 0.0f};
+  for (u64 x = (u64)blockIdx.x * kAT + threadIdx.x; x < N; x += (u64)gridDim.x * kAT) {
+    V acc;
+    vzero(acc);
+    for (int g = 0; g < ngroups; ++g) {
+      const HGroup G = groups[g];
+      const u64 y = x ^ G.m;
+      hmul_acc(terms, G, y, ps[y], acc);
+    }
+    lm[x] = acc;
+    df_acc(e, re_dot(ps[x], acc));
+  }
+  const double s = a_block_sum((double)e.h + (double)e.l);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
 // out[s] = sum_{b < G} part[s * G + b], in order (one CTA per slot).
@@ -131,26 +233,216 @@ void dagger2(const double* m, double* d) {
     }
 }
 
-template <typename R>
-qs_status adj_step_1q(qs_state* psi, qs_state* lam, int q, const double* Udag, int gen, double* part) {
-  const u64 npairs = u64(1) << (psi->n - 1);
-  const unsigned g = adj_grid(npairs);
-  k_adj_1q<R><<<g, kAT, 0, psi->stream>>>(static_cast<R*>(psi->amp), static_cast<R*>(lam->amp), npairs, q,
-                                          to_mat(Udag, R(0)), gen, part);
-  return launch_ok("k_adj_1q");
+// Chunk budget for psi and lambda of Bc sets.  complex64: about half of L2,
+// so the per-gate sweep re-reads the vectors from L2.  complex128: the
+// double-float sweep is ALU-bound, and a larger chunk gives each launch more
+// CTAs (measured at 20 qubits, 64 sets: 7.4 ms per set at 64 MB, 6.6 ms at
+// 1 GB; complex64 2.85 ms at 64 MB, 2.95 ms at 1 GB).
+int adj_chunk(int batch, u64 sbytes, bool df) {
+  const u64 budget = df ? (1ull << 30) : (64ull << 20);
+  int bc = 1;
+  while (2 * bc <= batch && 2 * (u64)(2 * bc) * sbytes <= budget) bc *= 2;
+  return bc;
 }
 
-template <typename R>
-qs_status pauli_apply(qs_state* psi, qs_state* out, const std::vector<PauliGroup>& groups) {
-  const u64 N = u64(1) << psi->n;
-  const unsigned g = adj_grid(N);
-  for (size_t i = 0; i < groups.size(); ++i) {
-    k_pauli_apply<R><<<g, kAT, 0, psi->stream>>>(static_cast<const R*>(psi->amp), static_cast<R*>(out->amp), N,
-                                                 groups[i], i > 0 ? 1 : 0);
-    qs_status st = launch_ok("k_pauli_apply");
-    if (st != QS_OK) return st;
+// Run f on a view of `st` at another address / qubit count; the view borrows
+// st's scratch buffer and hands any reallocation back.
+template <typename F>
+qs_status on_view(qs_state* st, void* amp, int n, F&& f) {
+  qs_state v = *st;
+  v.amp = amp;
+  v.n = n;
+  v.owns = false;
+  const qs_status rc = f(&v);
+  st->scratch = v.scratch;
+  st->scratch_bytes = v.scratch_bytes;
+  return rc;
+}
+
+// U^dagger of a fixed gate on a vector (or the chunk's combined vector);
+// complex128 vectors are in double-float storage.
+qs_status unapply_fixed(qs_state* v, const qs_gate_rec& g, bool dfl_layout) {
+  double m[32];
+  const int nq = gate_matrix(g.kind, g.p, m);
+  if (nq == 1) {
+    double md[8];
+    dagger2(m, md);
+    return dfl_layout ? run_controlled_dfl(v, nullptr, 0, g.q[0], md) : run_1q(v, g.q[0], md);
   }
-  return QS_OK;
+  if (g.kind == QS_GATE_CNOT) {  // an exchange: the same in either storage
+    double x[8];
+    gate_matrix(QS_GATE_X, nullptr, x);
+    return run_controlled(v, &g.q[0], 1, g.q[1], x);
+  }
+  if (g.kind == QS_GATE_SWAP) return run_bitswap(v, &g.q[0], &g.q[1], 1);
+  double d[8];  // CZ, CP: conjugate of the diagonal
+  for (int r = 0; r < 4; ++r) {
+    d[2 * r] = m[2 * (r * 4 + r)];
+    d[2 * r + 1] = -m[2 * (r * 4 + r) + 1];
+  }
+  return dfl_layout ? run_diag_dfl(v, g.q, 2, d) : run_diag(v, g.q, 2, d);
+}
+
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename R>
+qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, int nparam, int batch, int nterms,
+                      const u64* xmask, const u64* zmask, const double* coeff, double* energy, double* grad) {
+  typedef typename Ar<R>::Mat Mat;
+  typedef typename Amp<R>::V V;
+  const bool df = sizeof(R) == 8;
+  const int n = st->n;
+  const u64 N = u64(1) << n;
+  const size_t sbytes = state_bytes(st);
+  const int Bc = adj_chunk(batch, sbytes, df);
+  int lb = 0;
+  while ((1 << lb) < Bc) ++lb;
+  const unsigned G = adj_grid(N >> 1);
+
+  // trainable gates in reverse order: slot s <-> gate index
+  std::vector<int> slot_gate;
+  for (int gi = (int)c->gates.size() - 1; gi >= 0; --gi)
+    if (c->gates[gi].param_index >= 0) slot_gate.push_back(gi);
+  const int nslots = (int)slot_gate.size() + 1;  // trainable gates, then the energy
+  const int eslot = nslots - 1;
+
+  // Hamiltonian grouped by X/Y mask, in order of first appearance
+  std::vector<HGroup> hg;
+  std::vector<HTerm> ht;
+  {
+    std::map<u64, std::vector<int>> by_m;
+    std::vector<u64> order;
+    for (int t = 0; t < nterms; ++t) {
+      if (!by_m.count(xmask[t])) order.push_back(xmask[t]);
+      by_m[xmask[t]].push_back(t);
+    }
+    for (u64 m : order) {
+      HGroup g{m, (int)ht.size(), (int)by_m[m].size()};
+      hg.push_back(g);
+      for (int t : by_m[m]) {
+        const int ny = __builtin_popcountll(xmask[t] & zmask[t]) & 3;  // i^{nY}
+        const double pr[4] = {1, 0, -1, 0}, pim[4] = {0, 1, 0, -1};
+        const double wr = coeff[t] * pr[ny], wi = coeff[t] * pim[ny];
+        HTerm w;
+        w.z = zmask[t];
+        w.wrh = (float)wr;
+        w.wrl = (float)(wr - (double)w.wrh);
+        w.wih = (float)wi;
+        w.wil = (float)(wi - (double)w.wih);
+        ht.push_back(w);
+      }
+    }
+  }
+
+  // device: [psi/lambda chunk (Bc > 1) or lambda][partials][sums][mats][groups][terms]
+  const size_t vec_b = up256((Bc > 1 ? 2 * (size_t)Bc : 1) * sbytes);
+  const size_t part_b = up256(sizeof(double) * (size_t)nslots * Bc * G);
+  const size_t sums_b = up256(sizeof(double) * (size_t)nslots * Bc);
+  const size_t mats_b = up256(sizeof(Mat) * (size_t)nslots * Bc);
+  const size_t grp_b = up256(sizeof(HGroup) * hg.size()), trm_b = up256(sizeof(HTerm) * ht.size());
+  const size_t bytes = vec_b + part_b + sums_b + mats_b + grp_b + trm_b;
+  char* dev = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), bytes, st->stream);
+  if (e != cudaSuccess) return fail(QS_ENOMEM, "qs_adjoint_grad: %zu bytes: %s", bytes, cudaGetErrorString(e));
+  char* psi = Bc > 1 ? dev : static_cast<char*>(st->amp);
+  char* lam = Bc > 1 ? dev + (size_t)Bc * sbytes : dev;
+  double* part = reinterpret_cast<double*>(dev + vec_b);
+  double* sums = reinterpret_cast<double*>(dev + vec_b + part_b);
+  Mat* mats = reinterpret_cast<Mat*>(dev + vec_b + part_b + sums_b);
+  HGroup* dgrp = reinterpret_cast<HGroup*>(dev + vec_b + part_b + sums_b + mats_b);
+  HTerm* dtrm = reinterpret_cast<HTerm*>(dev + vec_b + part_b + sums_b + mats_b + grp_b);
+  qs_status rc = QS_OK;
+  e = cudaMemcpyAsync(dgrp, hg.data(), sizeof(HGroup) * hg.size(), cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dtrm, ht.data(), sizeof(HTerm) * ht.size(), cudaMemcpyHostToDevice, st->stream);
+  // padded sets of a short last chunk stay finite: they pass through the
+  // fixed-gate launches but are never read
+  if (e == cudaSuccess && Bc > 1) e = cudaMemsetAsync(dev, 0, 2 * (size_t)Bc * sbytes, st->stream);
+  if (e != cudaSuccess) rc = cuda_fail(e, "qs_adjoint_grad: setup");
+
+  // targets of the fixed-gate launches
+  std::vector<std::pair<char*, int>> targets;
+  if (Bc > 1) targets.push_back({psi, n + lb + 1});
+  else targets = {{psi, n}, {lam, n}};
+
+  std::vector<Mat> hmats((size_t)nslots * Bc);
+  std::vector<double> hsums((size_t)nslots * Bc);
+  qs_circuit cb;
+  cb.gates = c->gates;
+  for (int c0 = 0; c0 < batch && rc == QS_OK; c0 += Bc) {
+    const int cnt = batch - c0 < Bc ? batch - c0 : Bc;
+    // forward: one compiled plan per parameter set, run on psi_b
+    for (int b = 0; b < cnt && rc == QS_OK; ++b) {
+      const double* th = theta + (size_t)(c0 + b) * nparam;
+      for (qs_gate_rec& g : cb.gates)
+        if (g.param_index >= 0) g.p[0] = th[g.param_index];
+      qs_plan* plan = nullptr;
+      if ((rc = qs_plan_build(&cb, n, st->dtype, nullptr, &plan)) != QS_OK) break;
+      rc = on_view(st, psi + (size_t)b * sbytes, n, [&](qs_state* v) {
+        qs_status r = run_set_basis(v, 0);
+        return r == QS_OK ? qs_run_plan(v, plan) : r;
+      });
+      qs_plan_destroy(plan);
+      for (size_t s = 0; s < slot_gate.size(); ++s) {  // U^dagger of each trainable gate
+        const qs_gate_rec& g = cb.gates[slot_gate[s]];
+        double m[32], md[8];
+        gate_matrix(g.kind, g.p, m);
+        dagger2(m, md);
+        hmats[s * Bc + b] = to_mat(md, R(0));
+      }
+    }
+    if (rc != QS_OK) break;
+    if (!slot_gate.empty()) {
+      e = cudaMemcpyAsync(mats, hmats.data(), sizeof(Mat) * hmats.size(), cudaMemcpyHostToDevice, st->stream);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "qs_adjoint_grad: matrix upload"); break; }
+    }
+    if (df) {  // psi of the chunk to double-float storage; lambda is written in it
+      rc = on_view(st, psi, n + lb, [&](qs_state* v) { return run_layout_dfl(v, true); });
+      if (rc != QS_OK) break;
+    }
+    // lambda_b = H psi_b and E_b
+    k_hamiltonian<V><<<dim3(G, cnt), kAT, 0, st->stream>>>(reinterpret_cast<const V*>(psi), reinterpret_cast<V*>(lam),
+                                                          N, dgrp, (int)hg.size(), dtrm,
+                                                          part + (size_t)eslot * Bc * G);
+    if ((rc = launch_ok("k_hamiltonian")) != QS_OK) break;
+    // reverse sweep
+    int slot = 0;
+    for (int gi = (int)c->gates.size() - 1; gi >= 0 && rc == QS_OK; --gi) {
+      const qs_gate_rec& g = c->gates[gi];
+      if (g.param_index >= 0) {
+        const int gen = g.kind == QS_GATE_RX ? 1 : g.kind == QS_GATE_RY ? 2 : 3;
+        k_adj_1q<V, Mat><<<dim3(G, cnt), kAT, 0, st->stream>>>(reinterpret_cast<V*>(psi), reinterpret_cast<V*>(lam), N,
+                                                               N >> 1, g.q[0], mats + (size_t)slot * Bc, gen,
+                                                               part + (size_t)slot * Bc * G);
+        rc = launch_ok("k_adj_1q");
+        ++slot;
+        continue;
+      }
+      for (size_t t = 0; t < targets.size() && rc == QS_OK; ++t)
+        rc = on_view(st, targets[t].first, targets[t].second, [&](qs_state* v) { return unapply_fixed(v, g, df); });
+    }
+    if (rc != QS_OK) break;
+    k_slot_sums<<<nslots * Bc, kAT, 0, st->stream>>>(part, (int)G, sums);
+    if ((rc = launch_ok("k_slot_sums")) != QS_OK) break;
+    e = cudaMemcpyAsync(hsums.data(), sums, sizeof(double) * hsums.size(), cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "qs_adjoint_grad: gradient readback"); break; }
+    for (int b = 0; b < cnt; ++b) {
+      energy[c0 + b] = hsums[(size_t)eslot * Bc + b];
+      if (nparam == 0) continue;
+      double* gb = grad + (size_t)(c0 + b) * nparam;
+      for (int j = 0; j < nparam; ++j) gb[j] = 0.0;
+      for (size_t s = 0; s < slot_gate.size(); ++s) gb[c->gates[slot_gate[s]].param_index] += hsums[s * Bc + b];
+    }
+  }
+  // the caller's state back in plain storage
+  if (rc == QS_OK && df && Bc == 1) rc = run_layout_dfl(st, false);
+  cudaFreeAsync(dev, st->stream);
+  if (rc == QS_OK) {
+    e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "qs_adjoint_grad: sync");
+  }
+  return rc;
 }
 
 }  // namespace
@@ -170,113 +462,12 @@ extern "C" qs_status qs_adjoint_grad(qs_state* st, const qs_circuit* c, const do
   const uint64_t lim = (1ull << n) - 1;
   for (int t = 0; t < nterms; ++t)
     if ((xmask[t] & ~lim) || (zmask[t] & ~lim)) return fail(QS_EINVAL, "qs_adjoint_grad: term %d acts on a qubit >= n", t);
-  int nparam_gates = 0;
   for (size_t i = 0; i < c->gates.size(); ++i) {
     const qs_gate_rec& g = c->gates[i];
     if (g.q[0] >= n || g.q[1] >= n) return fail(QS_EINVAL, "qs_adjoint_grad: gate %zu acts on a qubit >= n", i);
     if (g.param_index >= nparam) return fail(QS_EINVAL, "qs_adjoint_grad: gate %zu uses parameter %d >= nparam", i, g.param_index);
-    if (g.param_index >= 0) ++nparam_gates;
   }
-  const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
-  const bool c64 = st->dtype == QS_C64;
-  const size_t sbytes = state_bytes(st);
-  const unsigned G = adj_grid(u64(1) << (n - 1));
-  // lambda vector and per-gate gradient partials (stream-ordered allocation)
-  void* lam_buf = nullptr;
-  double* part = nullptr;
-  cudaError_t e = cudaMallocAsync(&lam_buf, sbytes, st->stream);
-  if (e != cudaSuccess) return fail(QS_ENOMEM, "qs_adjoint_grad: lambda (%zu bytes): %s", sbytes, cudaGetErrorString(e));
-  const size_t pbytes = sizeof(double) * ((size_t)G * (nparam_gates + 1) + nparam_gates + 1);
-  e = cudaMallocAsync(reinterpret_cast<void**>(&part), pbytes, st->stream);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(lam_buf, st->stream);
-    return fail(QS_ENOMEM, "qs_adjoint_grad: partials: %s", cudaGetErrorString(e));
-  }
-  double* sums = part + (size_t)G * (nparam_gates + 1);
-  qs_state lam;
-  lam.n = n;
-  lam.dtype = st->dtype;
-  lam.amp = lam_buf;
-  lam.owns = false;
-  lam.stream = st->stream;
-  lam.device = st->device;
-  lam.pinned = st->pinned;
-  std::vector<double> hsums(nparam_gates + 1);
-  qs_status rc = QS_OK;
-  for (int b = 0; b < batch && rc == QS_OK; ++b) {
-    const double* th = theta ? theta + (size_t)b * nparam : nullptr;
-    // forward with this parameter set
-    qs_circuit cb;
-    cb.gates = c->gates;
-    for (qs_gate_rec& g : cb.gates)
-      if (g.param_index >= 0) g.p[0] = th[g.param_index];
-    qs_plan* plan = nullptr;
-    if ((rc = qs_plan_build(&cb, n, st->dtype, nullptr, &plan)) != QS_OK) break;
-    rc = run_set_basis(st, 0);
-    if (rc == QS_OK) rc = qs_run_plan(st, plan);
-    qs_plan_destroy(plan);
-    if (rc != QS_OK) break;
-    // lambda = H psi, E = Re <psi|lambda>
-    rc = c64 ? pauli_apply<float>(st, &lam, groups) : pauli_apply<double>(st, &lam, groups);
-    if (rc != QS_OK) break;
-    double ip[2];
-    if ((rc = run_inner(st, &lam, ip)) != QS_OK) break;
-    energy[b] = ip[0];
-    // reverse sweep
-    int slot = 0;
-    for (int gi = (int)cb.gates.size() - 1; gi >= 0 && rc == QS_OK; --gi) {
-      const qs_gate_rec& g = cb.gates[gi];
-      double m[32];
-      const int nq = gate_matrix(g.kind, g.p, m);
-      if (nq == 1) {
-        double md[8];
-        dagger2(m, md);
-        int gen = 0;
-        double* pp = part + (size_t)G * nparam_gates;  // unused slot for fixed gates
-        if (g.param_index >= 0) {
-          gen = g.kind == QS_GATE_RX ? 1 : g.kind == QS_GATE_RY ? 2 : 3;
-          pp = part + (size_t)G * slot;
-          ++slot;
-        }
-        rc = c64 ? adj_step_1q<float>(st, &lam, g.q[0], md, gen, pp)
-                 : adj_step_1q<double>(st, &lam, g.q[0], md, gen, pp);
-      } else if (g.kind == QS_GATE_CNOT) {
-        double x[8];
-        gate_matrix(QS_GATE_X, nullptr, x);
-        rc = run_controlled(st, &g.q[0], 1, g.q[1], x);
-        if (rc == QS_OK) rc = run_controlled(&lam, &g.q[0], 1, g.q[1], x);
-      } else if (g.kind == QS_GATE_SWAP) {
-        rc = run_bitswap(st, &g.q[0], &g.q[1], 1);
-        if (rc == QS_OK) rc = run_bitswap(&lam, &g.q[0], &g.q[1], 1);
-      } else {  // CZ, CP: conjugate of the diagonal
-        double d[8];
-        for (int r = 0; r < 4; ++r) {
-          d[2 * r] = m[2 * (r * 4 + r)];
-          d[2 * r + 1] = -m[2 * (r * 4 + r) + 1];
-        }
-        rc = run_diag(st, g.q, 2, d);
-        if (rc == QS_OK) rc = run_diag(&lam, g.q, 2, d);
-      }
-    }
-    if (rc != QS_OK) break;
-    if (nparam_gates > 0) {
-      k_slot_sums<<<nparam_gates, kAT, 0, st->stream>>>(part, (int)G, sums);
-      if ((rc = launch_ok("k_slot_sums")) != QS_OK) break;
-      e = cudaMemcpyAsync(hsums.data(), sums, sizeof(double) * nparam_gates, cudaMemcpyDeviceToHost, st->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "qs_adjoint_grad: gradient readback"); break; }
-    }
-    double* gb = grad + (size_t)b * nparam;
-    for (int j = 0; j < nparam; ++j) gb[j] = 0.0;
-    slot = 0;
-    for (int gi = (int)cb.gates.size() - 1; gi >= 0; --gi)
-      if (cb.gates[gi].param_index >= 0) gb[cb.gates[gi].param_index] += hsums[slot++];
-  }
-  cudaFreeAsync(part, st->stream);
-  cudaFreeAsync(lam_buf, st->stream);
-  if (rc == QS_OK) {
-    e = cudaStreamSynchronize(st->stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "qs_adjoint_grad: sync");
-  }
-  return rc;
+  return st->dtype == QS_C64
+             ? adjoint_run<float>(st, c, theta, nparam, batch, nterms, xmask, zmask, coeff, energy, grad)
+             : adjoint_run<double>(st, c, theta, nparam, batch, nterms, xmask, zmask, coeff, energy, grad);
 }

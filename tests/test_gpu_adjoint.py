@@ -94,3 +94,32 @@ def test_autograd_function(qs):
     e_ref, g_ref = oracle.adjoint_grad(oracle.zero_state(n), circ, len(theta0), terms)
     assert abs(E.item() - e_ref) <= 1e-11
     assert np.max(np.abs(theta.grad.numpy() - 2.0 * g_ref)) <= 1e-10
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-3)])
+@pytest.mark.parametrize("n,batch", [(7, 5), (12, 9)])
+def test_adjoint_batched_sets(qs, dtype, tol, n, batch):
+    # several parameter sets share one buffer (psi and lambda of every set);
+    # an odd batch leaves a short last chunk.  Each set must match both the
+    # oracle and the one-set call, with fixed gates of every kind in between.
+    rng = np.random.Generator(np.random.PCG64(300 + n))
+    circ, pi = [], 0
+    for layer in range(2):
+        for q in range(n):
+            circ.append(W.Gate(["RX", "RY", "RZ"][(q + layer) % 3], (q,), (0.0,), pi))
+            pi += 1
+        circ += [W.Gate("H", (1,)), W.Gate("CNOT", (n - 1, 2)), W.Gate("CP", (0, n - 2), (0.4,)),
+                 W.Gate("SWAP", (1, n - 3)), W.Gate("U3", (3,), (0.3, 1.2, -0.5)), W.Gate("CZ", (2, n - 1))]
+    thetas = rng.uniform(-math.pi, math.pi, (batch, pi))
+    terms = W.tfim(n) + W.random_paulis(n, 6, 301 + n)
+    c = qs.Circuit(circ)
+    e, g = qs.adjoint_grad(qs.State(n, dtype), c, thetas, terms)
+    assert e.shape == (batch,) and g.shape == (batch, pi)
+    for b in (0, batch // 2, batch - 1):
+        cb = W.with_params(circ, thetas[b])
+        e_ref, g_ref = oracle.adjoint_grad(oracle.zero_state(n), cb, pi, terms)
+        assert abs(e[b] - e_ref) <= (1e-10 if dtype == "c128" else 1e-4) * max(1.0, abs(e_ref))
+        assert rel(g[b], g_ref) <= tol
+        e1, g1 = qs.adjoint_grad(qs.State(n, dtype), c, thetas[b:b + 1], terms)
+        assert abs(e1[0] - e[b]) <= (1e-12 if dtype == "c128" else 1e-5) * max(1.0, abs(e_ref))
+        assert rel(g1[0], g[b]) <= (1e-10 if dtype == "c128" else 1e-4)
