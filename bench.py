@@ -344,9 +344,10 @@ def batch_workload(qs, torch, device, count=512, layers=8, seed=9):
             "speedup_vs_one_by_one": t_single / t_batch}
 
 
-def adjoint_workload(qs, torch, device, n=20, layers=10, batch=16):
+def adjoint_workload(qs, torch, device, n=20, layers=10, batch=64):
     """Adjoint gradients: 20-qubit hardware-efficient ansatz, 10 layers of RY
-    and RZ (400 parameters), CZ ladder, transverse-field Ising observable."""
+    and RZ (400 parameters), CZ ladder, transverse-field Ising observable,
+    64 parameter sets in one call."""
     circ, _ = W.hea(n, layers, 11)
     thetas = np.stack([W.hea(n, layers, 11 + b)[1] for b in range(batch)])
     terms = W.tfim(n)
@@ -354,7 +355,7 @@ def adjoint_workload(qs, torch, device, n=20, layers=10, batch=16):
     out = {"n": n, "params": thetas.shape[1], "batch": batch}
     for dt in ("c128", "c64"):
         s = qs.State(n, dt, device=device)
-        qs.adjoint_grad(s, c, thetas[:1], terms)
+        qs.adjoint_grad(s, c, thetas[:4], terms)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e, g = qs.adjoint_grad(s, c, thetas, terms)

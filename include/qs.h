@@ -88,7 +88,10 @@ qs_status qs_free(qs_state* st);
 qs_status qs_set_stream(qs_state* st, void* stream);
 
 /* Wait for all work enqueued on the state's stream; reports any pending
- * asynchronous device error as QS_ECUDA. */
+ * asynchronous device error as QS_ECUDA, and QS_ETIMEOUT if a tensor-core
+ * block kernel (dense k = 4, 5 blocks on complex64) gave up waiting for its
+ * matrix unit since the last qs_sync (bounded wait of about 1 s; the state's
+ * contents are then invalid). */
 qs_status qs_sync(qs_state* st);
 
 /* Device pointer and size of the amplitude array. */

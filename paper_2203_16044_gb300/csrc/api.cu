@@ -160,7 +160,8 @@ qs_status qs_set_stream(qs_state* s, void* stream) {
 qs_status qs_sync(qs_state* s) {
   CHECK_STATE(s);
   cudaError_t e = cudaStreamSynchronize(s->stream);
-  return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_sync");
+  if (e != cudaSuccess) return cuda_fail(e, "qs_sync");
+  return fused_tc_status();
 }
 
 qs_status qs_data(qs_state* s, void** dev_ptr, size_t* bytes) {

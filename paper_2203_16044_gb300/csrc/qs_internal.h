@@ -56,6 +56,7 @@ qs_status run_diag(qs_state* s, const int* qubits, int k, const double* d);
 qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M, int unitary = -1);
 // complex64 dense block, 4 <= k <= 6, on the tensor cores (fused_tc.cu)
 qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, int unitary);
+qs_status fused_tc_status();  // QS_ETIMEOUT if a tensor-core wait gave up since the last call
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
 qs_status run_set_basis(qs_state* s, u64 x);
