@@ -3,9 +3,10 @@
 Default workload (the precision + fusion configuration): the 30-qubit brick
 random circuit of depth 40 (U3 on every qubit, then CNOT(i, i+1) on
 alternating pairs; the QSB structure of §IV-F), seed 6, complex64 state
-(8 GiB) in the tiled (multi-gate-per-HBM-pass) plan.  The same circuit in
-complex128 (16 GiB) runs beside it and both are reported, with their
-infidelity measured on the GPU.
+(8 GiB) fused into dense 5-qubit blocks on the tensor cores (tcgen05,
+3xTF32).  The same circuit in complex128 (16 GiB, tiled plan) runs beside
+it and both are reported, with their infidelity measured on the GPU; the
+complex64 tiled and 4-qubit-block plans are timed as extras.
 
 Metric (§IV-F, Eq. 5 traffic model): effective HBM bandwidth
     2 * 2^n * bytes_per_amplitude * #gates / time
@@ -15,7 +16,7 @@ headline dtype (summed over ranks; one independent replica per GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload brick30|brick28|brick26|qft28] [--dtype c64|c128]
-                  [--mode tiled|unfused]
+                  [--mode auto|fused|tiled|unfused] [--fuse-qubits K]
 
 `--impl reference` times the FP64 CPU oracle (a deliberately plain program)
 on the host cores, on a bounded sample of the same workload.
@@ -45,12 +46,17 @@ WORKLOADS = {
     "brick20": dict(n=20, make=lambda: W.brick(20, 40, 6), desc="20-qubit brick random circuit, depth 40, seed 6"),
 }
 
-# DRAM bytes (read + write) per launch of the complex64 tile kernel, from one
-# ncu capture on the 26-qubit workload (profiles/tile_c64_brick26.md); per
-# launch traffic grows with the state, so n qubits scale it by 2^(n - 26).
-# Set to None whenever the tile kernel changes until it is re-captured.
-TILE_C64_TRAFFIC_26Q = 537.064704e6 + 475.623168e6
+# DRAM bytes (read + write) per launch from one ncu capture on the 26-qubit
+# workload (profiles/); per launch traffic grows with the state, so n qubits
+# scale it by 2^(n - 26).  Set to None whenever the kernel changes until it
+# is re-captured.
+TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
+BLOCK_C64_TRAFFIC_26Q = {5: 537.114112e6 + 475.895552e6}  # k_fused_umma<5>, profiles/fused_umma_k5_brick26.md
 S_BYTES = {"c64": 8, "c128": 16}
+
+
+def metric_name(wl):
+    return "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate) & gates/s, %s" % wl["desc"]
 
 
 def measured_peaks():
@@ -191,7 +197,7 @@ def run_reference(args):
     T = sum(per_step)
     gbs = 2.0 * (1 << n) * S * gates / T / 1e9
     line = {
-        "impl": "reference", "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate)",
+        "impl": "reference", "metric": metric_name(wl),
         "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * T / len(per_step), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -377,14 +383,14 @@ def run_ours(args):
     wl = WORKLOADS[args.workload]
     n = wl["n"]
     circ = wl["make"]()
-    mode = qs.PLAN_TILED if args.mode == "tiled" else qs.PLAN_UNFUSED
     peak, peak_kind = measured_peaks()
     results = {}
     dtypes = [args.dtype] + ([d for d in ("c64", "c128") if d != args.dtype] if args.both else [])
     circuit = qs.Circuit(circ)
     states = {}
     for dt in dtypes:
-        plan = qs.Plan(circuit, n, dt, mode=mode)
+        mode_name, mode, fq = plan_mode(qs, args, dt)
+        plan = qs.Plan(circuit, n, dt, mode=mode, fuse_qubits=fq)
         st = plan.stats()
         state = qs.State(n, dt, device=device)
         with ClockSampler(local) as clk:
@@ -406,13 +412,24 @@ def run_ours(args):
             elif TILE_C64_TRAFFIC_26Q is not None:
                 roof["traffic"] = TILE_C64_TRAFFIC_26Q * 2.0 ** (n - 26)
                 roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 26 qubits, scaled by 2^(n-26)"
+        elif roof and roof["kernel"] == "block" and dt == "c64":
+            roof["tensor"] = "tcgen05.mma kind::tf32, 3 MMAs (3xTF32) per K step, TMEM accumulator"
+            if fq in BLOCK_C64_TRAFFIC_26Q:
+                roof["traffic"] = BLOCK_C64_TRAFFIC_26Q[fq] * 2.0 ** (n - 26)
+                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fused_umma<%d> "
+                                          "at 26 qubits, scaled by 2^(n-26)" % fq)
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
+        # launches per step: one per plan step, k_set_one, and for complex64
+        # tensor-core blocks the final renormalisation (3); complex128 plans
+        # without blocks switch storage layout (2)
+        extra = 1 + (3 if (dt == "c64" and mode_name == "fused") else 0) + (2 if dt == "c128" and mode_name != "fused" else 0)
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
+                       "plan": mode_name + (f" k={fq}" if mode_name == "fused" else ""),
                        "passes": st["passes"], "gates": st["gates"], "hbm_bytes_per_step": st["hbm_bytes"],
                        "hbm_GBps": st["hbm_bytes"] / (ms / 1e3) / 1e9, "roofline": roof, "kernels": per_kind,
                        "clocks": clk.summary(), "bytes_per_amp": S,
-                       "gpu_launches": (st["passes"] + 1) * args.steps}
+                       "gpu_launches": (st["passes"] + extra) * args.steps}
         states[dt] = state
         del plan
     # precision: infidelity of the headline run against complex128 on the GPU
@@ -425,21 +442,23 @@ def run_ours(args):
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(qs, torch, args, n, circ, mode, device, world)
+        _, mode, fq = plan_mode(qs, args, args.dtype)
+        e2e = run_e2e(qs, torch, args, n, circ, mode, fq, device, world)
     extras = {}
     if not args.no_extras:
+        extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
         extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
         extras["batch_512_hea"] = batch_workload(qs, torch, device)
         extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
     head = results[args.dtype]
     line = {
-        "metric": "effective HBM GB/s (2*2^n*bytes_per_amp per logical gate) & gates/s, 30-qubit brick circuit",
+        "metric": metric_name(wl),
         "value": head["effective_GBps"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": wl["desc"], "n": n, "gates": head["gates"], "dtype": args.dtype,
-                   "plan": args.mode, "passes": head["passes"], "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (state %.0f GiB)" % (2.0 ** n * S_BYTES[args.dtype] / 2 ** 30)},
+                   "plan": head["plan"], "passes": head["passes"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (state %.0f MiB, L2 126 MiB)" % (2.0 ** n * S_BYTES[args.dtype] / 2 ** 20)},
         "gates_per_s": head["gates_per_s"],
         "hbm_GBps_algorithmic": head["hbm_GBps"],
         "roofline": dict(head["roofline"], peak_source=peak_kind) if head["roofline"] else None,
@@ -464,7 +483,49 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(qs, torch, args, n, circ, mode, device, world):
+def plan_mode(qs, args, dt):
+    """(name, plan mode, fuse_qubits) for a dtype: `auto` picks the fastest
+    measured plan, dense tensor-core blocks for complex64 and tiles for
+    complex128 (its blocks would run on the FP64 pipe)."""
+    name = args.mode
+    if name == "auto":
+        name = "fused" if dt == "c64" else "tiled"
+    mode = {"fused": qs.PLAN_FUSED, "tiled": qs.PLAN_TILED, "unfused": qs.PLAN_UNFUSED}[name]
+    return name, mode, (args.fuse_qubits if name == "fused" else 0)
+
+
+def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
+    """The complex64 circuit under each plan: tiles (SIMT, many gates per
+    pass) and dense 4- and 5-qubit blocks (tensor cores), with the
+    infidelity of each against the complex128 result when it is at hand."""
+    out = {}
+    s = qs.State(n, "c64", device=device)
+    for name, mode, fq in (("tiled", qs.PLAN_TILED, 0), ("fused_k4", qs.PLAN_FUSED, 4), ("fused_k5", qs.PLAN_FUSED, 5)):
+        p = qs.Plan(circuit, n, "c64", mode=mode, fuse_qubits=fq)
+        s.set_basis(0)
+        s.run(p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            s.set_basis(0)
+            e0.record()
+            s.run(p)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = p.stats()
+        r = {"ms": min(ms), "passes": st["passes"], "effective_GBps": st["metric_bytes"] / (min(ms) / 1e3) / 1e9}
+        if ref128 is not None:
+            ov = torch.vdot(s.tensor.to(torch.complex128), ref128.tensor).item()
+            r["infidelity_vs_c128"] = 1.0 - abs(ov) ** 2
+        out[name] = r
+        del p
+    del s
+    return out
+
+
+def run_e2e(qs, torch, args, n, circ, mode, fq, device, world):
     """Per step: host state -> device (pinned), compile the circuit, run it,
     device -> host (pinned); timed on the host around the whole call chain."""
     dt = args.dtype
@@ -481,7 +542,7 @@ def run_e2e(qs, torch, args, n, circ, mode, device, world):
         barrier(world)
         t0 = time.perf_counter()
         c = qs.Circuit(circ)
-        p = qs.Plan(c, n, dt, mode=mode)
+        p = qs.Plan(c, n, dt, mode=mode, fuse_qubits=fq)
         qs.lib().qs_set_stream(state.handle, qs._stream_ptr())
         assert qs.lib().qs_copy_from_host(state.handle, ctypes_ptr(host)) == 0
         state.run(p)
@@ -511,7 +572,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="brick30", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--mode", default="tiled", choices=["tiled", "unfused"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "fused", "tiled", "unfused"])
+    ap.add_argument("--fuse-qubits", type=int, default=5, help="block width of the fused plan (4..6)")
     ap.add_argument("--both", type=int, default=1, help="also run the other dtype")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
