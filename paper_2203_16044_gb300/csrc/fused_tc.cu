@@ -215,6 +215,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* o) {
   for (int j = 0; j < 16; ++j) o[j] = __uint_as_float(r[j]);
 }
 // mbarrier phase wait with a limit of about 2^31 SM cycles; false on timeout.
+// The "memory" clobber keeps the compiler from sinking earlier loads (the
+// next tiles' prefetch) below the wait.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   const long long t0 = clock64();
   for (;;) {
@@ -222,7 +224,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(mbar), "r"(phase));
+        : "r"(mbar), "r"(phase)
+        : "memory");
     if (done) return true;
     if (clock64() - t0 > (1ll << 31)) return false;
   }
@@ -233,11 +236,11 @@ struct UmmaShape {
   static constexpr int D = 1 << K, KR = 2 * D;
   static constexpr uint32_t A_BYTES = kUT * KR * 4, B_BYTES = KR * KR * 4;
   static constexpr uint32_t LBO_A = (kUT / 8) * 128, LBO_B = (KR / 8) * 128, SBO = 128;
-  static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16;
+  static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16 + 2 * 2 * kUT * sizeof(float);
 };
 
-// A group's 2^k amplitudes to / from registers, as D / 2 16-byte words w[j]
-// = amplitudes (2j, 2j + 1) of the group once taken.  The block's qubits are
+// A thread's share of a group's 2^k amplitudes to / from registers, as CH
+// 16-byte words w[j] = amplitudes (2 (j0 + j), 2 (j0 + j) + 1) once taken.  The block's qubits are
 // sorted ascending (the host permutes M to match), so when qubit 0 is in the
 // block it is block bit 0.
 //   lmode 0: 8-byte accesses.
@@ -248,23 +251,25 @@ struct UmmaShape {
 //            lane both groups' amplitude 2j + 1, and group_take exchanges the
 //            halves.  The loads have no dependent instruction until the
 //            tile is consumed, so a prefetch stays in flight.
-template <int D>
+template <int D, int CH>
 __device__ __forceinline__ void group_load(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
-                                           int lmode, float4 (&w)[D / 2]) {
+                                           int lmode, int j0, float4 (&w)[CH]) {
   if (lmode == 1) {
 #pragma unroll
-    for (int j = 0; j < D / 2; ++j)
-      w[j] = valid ? *reinterpret_cast<const float4*>(a + (base | spread[2 * j])) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < CH; ++j)
+      w[j] = valid ? *reinterpret_cast<const float4*>(a + (base | spread[2 * (j0 + j)]))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
   } else if (lmode == 2) {
     const bool odd = threadIdx.x & 1;
     const u64 pb = base & ~u64(1);
 #pragma unroll
-    for (int j = 0; j < D / 2; ++j) w[j] = *reinterpret_cast<const float4*>(a + (pb | spread[2 * j + (odd ? 1 : 0)]));
+    for (int j = 0; j < CH; ++j)
+      w[j] = *reinterpret_cast<const float4*>(a + (pb | spread[2 * (j0 + j) + (odd ? 1 : 0)]));
   } else {
 #pragma unroll
-    for (int j = 0; j < D / 2; ++j) {
-      const float2 x = valid ? a[base | spread[2 * j]] : make_float2(0.f, 0.f);
-      const float2 y = valid ? a[base | spread[2 * j + 1]] : make_float2(0.f, 0.f);
+    for (int j = 0; j < CH; ++j) {
+      const float2 x = valid ? a[base | spread[2 * (j0 + j)]] : make_float2(0.f, 0.f);
+      const float2 y = valid ? a[base | spread[2 * (j0 + j) + 1]] : make_float2(0.f, 0.f);
       w[j] = make_float4(x.x, x.y, y.x, y.y);
     }
   }
@@ -278,38 +283,46 @@ __device__ __forceinline__ float4 group_take(float4 x, int lmode) {
   const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
   return odd ? make_float4(rx, ry, x.z, x.w) : make_float4(x.x, x.y, rx, ry);
 }
-template <int D>
+// o[4j .. 4j + 3] = amplitudes 2 (j0 + j), 2 (j0 + j) + 1 of this thread's group
+template <int D, int CH>
 __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bool valid, const u64* spread, int lmode,
-                                            const float* o, float f) {
+                                            int j0, const float* o, float f) {
   if (lmode == 1) {
     if (!valid) return;
 #pragma unroll
-    for (int j = 0; j < D / 2; ++j)
-      *reinterpret_cast<float4*>(a + (base | spread[2 * j])) =
+    for (int j = 0; j < CH; ++j)
+      *reinterpret_cast<float4*>(a + (base | spread[2 * (j0 + j)])) =
           make_float4(o[4 * j] * f, o[4 * j + 1] * f, o[4 * j + 2] * f, o[4 * j + 3] * f);
   } else if (lmode == 2) {
     const bool odd = threadIdx.x & 1;
     const u64 pb = base & ~u64(1);
 #pragma unroll
-    for (int j = 0; j < D / 2; ++j) {
+    for (int j = 0; j < CH; ++j) {
       // even lane stores (own 2j, partner 2j); odd lane (partner 2j + 1, own 2j + 1)
       const float m0x = o[4 * j] * f, m0y = o[4 * j + 1] * f, m1x = o[4 * j + 2] * f, m1y = o[4 * j + 3] * f;
       const float sx = odd ? m0x : m1x, sy = odd ? m0y : m1y;
       const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
-      *reinterpret_cast<float4*>(a + (pb | spread[2 * j + (odd ? 1 : 0)])) =
+      *reinterpret_cast<float4*>(a + (pb | spread[2 * (j0 + j) + (odd ? 1 : 0)])) =
           odd ? make_float4(rx, ry, m1x, m1y) : make_float4(m0x, m0y, rx, ry);
     }
   } else if (valid) {
 #pragma unroll
-    for (int r = 0; r < D; ++r) a[base | spread[r]] = make_float2(o[2 * r] * f, o[2 * r + 1] * f);
+    for (int j = 0; j < CH; ++j) {
+      a[base | spread[2 * (j0 + j)]] = make_float2(o[4 * j] * f, o[4 * j + 1] * f);
+      a[base | spread[2 * (j0 + j) + 1]] = make_float2(o[4 * j + 2] * f, o[4 * j + 3] * f);
+    }
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
-                                                    const __grid_constant__ FusedArgs args, int renorm, int lmode) {
+// H threads per group row (H = 1 or 2): thread t owns row t % 128 and the
+// half h = t / 128 of its amplitudes (H = 2), so a CTA has 4 H warps.
+template <int K, int H>
+__global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
+    k_fused_umma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
+                 const __grid_constant__ FusedArgs args, int renorm, int lmode) {
   typedef UmmaShape<K> S;
-  constexpr int D = S::D, KR = S::KR;
+  constexpr int D = S::D, KR = S::KR, NT = kUT * H;
+  constexpr int CH = D / 2 / H;  // 16-byte words (amplitude pairs) per thread
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* Ahi = sm;
   unsigned char* Alo = sm + S::A_BYTES;
@@ -317,14 +330,17 @@ __global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 
   unsigned char* Blo = Bhi + S::B_BYTES;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* nin_s = reinterpret_cast<float*>(mbar + 2);  // [H][kUT] partial input norms
+  float* nout_s = nin_s + 2 * kUT;                     // [H][kUT] partial output norms
   const int t = threadIdx.x, warp = t >> 5;
+  const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
   // B operand (N x K, K-major): element (n, k) = B[k][n], split hi + lo
-  for (int i = t; i < KR * KR; i += kUT) {
+  for (int i = t; i < KR * KR; i += NT) {
     const int k = i / KR, n = i % KR;
-    unsigned h, l;
-    split_tf32(Bg[i], h, l);
+    unsigned hh, l;
+    split_tf32(Bg[i], hh, l);
     const uint32_t off = ((k >> 2) * (KR / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (k & 3) * 4;
-    *reinterpret_cast<unsigned*>(Bhi + off) = h;
+    *reinterpret_cast<unsigned*>(Bhi + off) = hh;
     *reinterpret_cast<unsigned*>(Blo + off) = l;
   }
   const uint32_t mb = smem_u32(mbar);
@@ -341,9 +357,10 @@ __global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 TMEM lanes
+  // a warp reads TMEM lanes 32 (warp % 4) .. + 31 = its rows; columns of its half
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * (KR / H));
   const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-  const uint32_t row_off = (uint32_t)(t >> 3) * 128 + (uint32_t)(t & 7) * 16;
+  const uint32_t row_off = (uint32_t)(row >> 3) * 128 + (uint32_t)(row & 7) * 16;
   constexpr uint32_t idesc = umma_idesc(kUT, KR);
   uint32_t phase = 0;
   // Software pipeline, two tiles deep: register buffers wA and wB hold the
@@ -352,31 +369,33 @@ __global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 
   // flight during this tile's MMAs and epilogue and the next tile's step.
   const u64 gstep = (u64)gridDim.x * kUT;
   u64 gA = (u64)blockIdx.x * kUT, gB = gA + gstep;
-  bool vA = gA + t < ngroups, vB = gB + t < ngroups;
-  u64 bA = expand(vA ? gA + t : 0, args.ins), bB = expand(vB ? gB + t : 0, args.ins);
-  float4 wA[D / 2], wB[D / 2];
-  if (gA < ngroups) group_load<D>(a, bA, vA, args.spread, lmode, wA);
-  if (gB < ngroups) group_load<D>(a, bB, vB, args.spread, lmode, wB);
-  auto step = [&](u64& g, bool& valid, u64& base, float4 (&w)[D / 2]) -> bool {
+  bool vA = gA + row < ngroups, vB = gB + row < ngroups;
+  u64 bA = expand(vA ? gA + row : 0, args.ins), bB = expand(vB ? gB + row : 0, args.ins);
+  float4 wA[CH], wB[CH];
+  if (gA < ngroups) group_load<D, CH>(a, bA, vA, args.spread, lmode, j0, wA);
+  if (gB < ngroups) group_load<D, CH>(a, bB, vB, args.spread, lmode, j0, wB);
+  auto step = [&](u64& g, bool& valid, u64& base, float4 (&w)[CH]) -> bool {
     if (g >= ngroups) return false;
     float nin = 0.f;
 #pragma unroll
-    for (int c = 0; c < D / 2; ++c) {  // 16-byte chunk c = reals 4c .. 4c + 3 = amplitudes 2c, 2c + 1
-      const float4 wc = group_take(w[c], lmode);
+    for (int j = 0; j < CH; ++j) {  // 16-byte chunk c = j0 + j = reals 4c .. 4c + 3 = amplitudes 2c, 2c + 1
+      const float4 wc = group_take(w[j], lmode);
       const float x[4] = {wc.x, wc.y, wc.z, wc.w};
-      unsigned h[4], l[4];
+      unsigned hh[4], l[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        nin = fmaf(x[j], x[j], nin);
-        split_tf32(x[j], h[j], l[j]);
+      for (int i = 0; i < 4; ++i) {
+        nin = fmaf(x[i], x[i], nin);
+        split_tf32(x[i], hh[i], l[i]);
       }
-      *reinterpret_cast<uint4*>(Ahi + c * S::LBO_A + row_off) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(Alo + c * S::LBO_A + row_off) = make_uint4(l[0], l[1], l[2], l[3]);
+      *reinterpret_cast<uint4*>(Ahi + (j0 + j) * S::LBO_A + row_off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+      *reinterpret_cast<uint4*>(Alo + (j0 + j) * S::LBO_A + row_off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
+    if (H > 1) nin_s[h * kUT + row] = nin;
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    if (H > 1) nin += nin_s[(h ^ 1) * kUT + row];
     if (t == 0) {
 #pragma unroll
       for (int ks = 0; ks < KR / 8; ++ks) {
@@ -391,27 +410,32 @@ __global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 
     }
     // refill this buffer with the tile two steps ahead
     const u64 gn = g + 2 * gstep;
-    const bool vn = gn + t < ngroups;
-    const u64 bn = expand(vn ? gn + t : 0, args.ins);
-    if (gn < ngroups) group_load<D>(a, bn, vn, args.spread, lmode, w);
+    const bool vn = gn + row < ngroups;
+    const u64 bn = expand(vn ? gn + row : 0, args.ins);
+    if (gn < ngroups) group_load<D, CH>(a, bn, vn, args.spread, lmode, j0, w);
     if (!__syncthreads_and(mbar_wait(mb, phase) ? 1 : 0)) {
       if (t == 0) atomicExch(&g_umma_timeout, 1);
       return false;
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    float o[KR];
+    float o[KR / H];
 #pragma unroll
-    for (int c0 = 0; c0 < KR; c0 += 16) tmem_ld16(trow + (uint32_t)c0, o + c0);
+    for (int c0 = 0; c0 < KR / H; c0 += 16) tmem_ld16(trow + (uint32_t)c0, o + c0);
     asm volatile("tcgen05.wait::ld.sync.aligned;");
     float f = 1.f;
     if (renorm) {
       float nout = 0.f;
 #pragma unroll
-      for (int j = 0; j < KR; ++j) nout = fmaf(o[j], o[j], nout);
+      for (int j = 0; j < KR / H; ++j) nout = fmaf(o[j], o[j], nout);
+      if (H > 1) {
+        nout_s[h * kUT + row] = nout;
+        __syncthreads();
+        nout += nout_s[(h ^ 1) * kUT + row];
+      }
       f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
     }
-    group_store<D>(a, base, valid, args.spread, lmode, o, f);
+    group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, f);
     asm volatile("tcgen05.fence::before_thread_sync;");
     g = gn;
     valid = vn;
@@ -425,10 +449,10 @@ __global__ void __launch_bounds__(kUT) k_fused_umma(float2* __restrict__ a, u64 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(KR));
 }
 
-template <int K>
+template <int K, int H>
 qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renorm, const int* qubits) {
   const size_t smem = UmmaShape<K>::SMEM;
-  auto kern = k_fused_umma<K>;
+  auto kern = k_fused_umma<K, H>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: smem attribute");
@@ -442,14 +466,14 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: occupancy attributes");
   int per_sm = smem_sm / (int)(smem + smem_rsv);
   const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 255;
-  per_sm = std::min(per_sm, 65536 / (regs * kUT));
+  per_sm = std::min(per_sm, 65536 / (regs * kUT * H));
   per_sm = std::min(per_sm, 512 / UmmaShape<K>::KR);
   if (per_sm < 1) per_sm = 1;
   const u64 ngroups = u64(1) << (s->n - K);
   const unsigned grid = grid_for(ngroups, kUT, per_sm);
   // qubits ascending (see run_dense_tc)
   const int lmode = qubits[0] == 0 ? 1 : (ngroups >= (u64)kUT ? 2 : 0);
-  kern<<<grid, kUT, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
+  kern<<<grid, kUT * H, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
   return launch_ok("k_fused_umma");
 }
 
@@ -529,8 +553,8 @@ qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, i
   if (e != cudaSuccess) return cuda_fail(e, "fused_tc: matrix upload");
   const float* Bd = static_cast<const float*>(s->scratch);
   switch (k) {
-    case 4: return launch_umma<4>(s, A, Bd, unitary, q);
-    case 5: return launch_umma<5>(s, A, Bd, unitary, q);
+    case 4: return launch_umma<4, 1>(s, A, Bd, unitary, q);
+    case 5: return launch_umma<5, 2>(s, A, Bd, unitary, q);
     case 6: return launch<6>(s, A, Bd, unitary);
   }
   return fail(QS_EINVAL, "fused_tc: k=%d outside [4, 6]", k);

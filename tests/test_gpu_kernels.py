@@ -226,3 +226,30 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     with pytest.raises(qs.QSError):
         s.permute_qubits([0, 0, 1, 2, 3])
     assert np.array_equal(s.to_numpy(), psi)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n,qubits", [
+    (9, None),            # fewer than 128 groups: 8-byte accesses
+    (14, "with0"),        # qubit 0 in the block: 16-byte amplitude pairs
+    (14, "without0"),     # qubit 0 outside: lane pairs exchange halves
+    (16, "high"),         # the block on the highest qubits
+])
+def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
+    # complex64 k = 4, 5 blocks run on tcgen05; each way a group's amplitudes
+    # are gathered and scattered, against the oracle
+    if qubits is None:
+        qsel = [1, 3, 4, 6, 8][:k]
+    elif qubits == "with0":
+        qsel = [7, 0, 3, 11, 5][:k]
+    elif qubits == "without0":
+        qsel = [2, 9, 5, 12, 1][:k]
+    else:
+        qsel = list(range(n - 1, n - 1 - k, -1))
+    psi = W.random_state(n, 7500 + n + k)
+    M = W.random_unitary(1 << k, 7600 + k)
+    s = gpu_state(qs, psi, "c64")
+    s.apply_fused(qsel, M)
+    want = start(psi, "c64")
+    oracle.apply_dense(want, qsel, M)
+    check(s.to_numpy(), want, "c64")
