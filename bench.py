@@ -447,6 +447,9 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
+        base = c128_unfused(qs, torch, device, n, circuit)
+        base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
+        extras["c128_unfused_%dq" % n] = base
         extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
         extras["batch_512_hea"] = batch_workload(qs, torch, device)
         extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
@@ -522,6 +525,28 @@ def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
         out[name] = r
         del p
     del s
+    return out
+
+
+def c128_unfused(qs, torch, device, n, circuit):
+    """The plain per-gate complex128 path (one kernel per gate, FP64 layout in
+    HBM) on the same circuit: the baseline the fused complex64 path is
+    compared with.  One warm-up run, one timed run (CUDA events)."""
+    s = qs.State(n, "c128", device=device)
+    p = qs.Plan(circuit, n, "c128", mode=qs.PLAN_UNFUSED)
+    s.run(p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.set_basis(0)
+    e0.record()
+    s.run(p)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = p.stats()
+    out = {"ms": ms, "passes": st["passes"], "effective_GBps": st["metric_bytes"] / (ms / 1e3) / 1e9,
+           "hbm_GBps_algorithmic": st["hbm_bytes"] / (ms / 1e3) / 1e9}
+    del s, p
     return out
 
 

@@ -145,11 +145,14 @@ qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
 
 // ---------------------------------------------------------------------------
 // QS_PLAN_FUSED: gates multiplied into dense blocks of at most k qubits.
-// Greedy over the circuit in order: a gate joins the current block when no
-// earlier gate left out of the block touches its qubits and the block's
-// qubit set, with the gate's, stays within k; otherwise its qubits are
-// blocked for the rest of the scan.  The block matrix is built by applying
-// each gate's 2x2 / 4x4 matrix to the rows of the running product.
+// Each block is a qubit set S and the gates that can move to the front of
+// the remaining circuit inside S: scanning in order, a gate joins when its
+// qubits are in S and no earlier gate left out of the block touches them;
+// a gate left out blocks its qubits for the rest of the scan.  S is chosen
+// among the front-greedy set (gates in order join while the set stays within
+// k) and every window of k consecutive qubits, as the one that absorbs most
+// gates.  The block matrix is built by applying each gate's 2x2 / 4x4 matrix
+// to the rows of the running product.
 // ---------------------------------------------------------------------------
 namespace {
 typedef std::complex<double> cd;
@@ -193,6 +196,60 @@ void left_apply(std::vector<cd>& M, int k, const qs_gate_rec& g, const std::vect
 }
 }  // namespace
 
+// Gates of `remaining` (in order) that a block on the qubit set inS can take
+// to the front of the circuit: a gate joins when all its qubits are in the
+// set and none is blocked; any other gate blocks its qubits.  The scan stops
+// once every qubit of the set is blocked.  Returns the number taken.
+int absorb_into(const std::vector<const qs_gate_rec*>& remaining, const std::vector<char>& inS, int nS,
+                std::vector<const qs_gate_rec*>* absorbed, std::vector<const qs_gate_rec*>* rest) {
+  std::vector<char> blocked(inS.size(), 0);
+  int taken = 0, open = nS;
+  size_t i = 0;
+  for (; i < remaining.size() && open > 0; ++i) {
+    const qs_gate_rec* g = remaining[i];
+    const int ng = gate_arity(g->kind);
+    bool ok = true;
+    for (int j = 0; j < ng; ++j) ok &= inS[g->q[j]] && !blocked[g->q[j]];
+    if (ok) {
+      ++taken;
+      if (absorbed) absorbed->push_back(g);
+      continue;
+    }
+    for (int j = 0; j < ng; ++j)
+      if (!blocked[g->q[j]]) {
+        blocked[g->q[j]] = 1;
+        if (inS[g->q[j]]) --open;
+      }
+    if (rest) rest->push_back(g);
+  }
+  if (rest) rest->insert(rest->end(), remaining.begin() + i, remaining.end());
+  return taken;
+}
+
+// Qubit set of the front-greedy block: gates in order join while the set
+// stays within kmax qubits and none of their qubits is blocked.
+std::vector<char> greedy_set(const std::vector<const qs_gate_rec*>& remaining, int n, int kmax, int* nS) {
+  std::vector<char> inB(n, 0), blocked(n, 0);
+  int nb = 0;
+  for (const qs_gate_rec* g : remaining) {
+    const int ng = gate_arity(g->kind);
+    bool blk = false;
+    int add = 0;
+    for (int i = 0; i < ng; ++i) {
+      blk |= blocked[g->q[i]] != 0;
+      add += inB[g->q[i]] ? 0 : 1;
+    }
+    if (!blk && nb + add <= kmax) {
+      for (int i = 0; i < ng; ++i)
+        if (!inB[g->q[i]]) { inB[g->q[i]] = 1; ++nb; }
+      continue;
+    }
+    for (int i = 0; i < ng; ++i) blocked[g->q[i]] = 1;
+  }
+  *nS = nb;
+  return inB;
+}
+
 qs_status plan_fused(qs_plan* p) {
   const int n = p->n;
   int kmax = p->opts.fuse_qubits > 0 ? p->opts.fuse_qubits : 5;
@@ -201,30 +258,30 @@ qs_status plan_fused(qs_plan* p) {
   std::vector<const qs_gate_rec*> remaining;
   for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
   while (!remaining.empty()) {
-    std::vector<char> inB(n, 0), blocked(n, 0);
-    std::vector<int> bq;
-    std::vector<const qs_gate_rec*> absorbed, rest;
-    for (const qs_gate_rec* g : remaining) {
-      int gq[2];
-      gq[0] = g->q[0];
-      const int ng = gate_arity(g->kind);
-      if (ng == 2) gq[1] = g->q[1];
-      bool blk = false;
-      int add = 0;
-      for (int i = 0; i < ng; ++i) {
-        blk |= blocked[gq[i]] != 0;
-        add += inB[gq[i]] ? 0 : 1;
+    // candidate qubit sets: the front-greedy set and every window of kmax
+    // consecutive qubits; the block takes the one that absorbs most gates
+    int nS = 0;
+    std::vector<char> best = greedy_set(remaining, n, kmax, &nS);
+    int best_n = nS, best_taken = absorb_into(remaining, best, nS, nullptr, nullptr);
+    for (int w = 0; w + kmax <= n; ++w) {
+      std::vector<char> inS(n, 0);
+      for (int q = w; q < w + kmax; ++q) inS[q] = 1;
+      const int taken = absorb_into(remaining, inS, kmax, nullptr, nullptr);
+      if (taken > best_taken) {
+        best_taken = taken;
+        best = inS;
+        best_n = kmax;
       }
-      if (!blk && (int)bq.size() + add <= kmax) {
-        for (int i = 0; i < ng; ++i)
-          if (!inB[gq[i]]) { inB[gq[i]] = 1; bq.push_back(gq[i]); }
-        absorbed.push_back(g);
-        continue;
-      }
-      for (int i = 0; i < ng; ++i) blocked[gq[i]] = 1;
-      rest.push_back(g);
     }
-    std::sort(bq.begin(), bq.end());
+    std::vector<const qs_gate_rec*> absorbed, rest;
+    absorb_into(remaining, best, best_n, &absorbed, &rest);
+    // the block's qubits: those its gates touch
+    std::vector<char> used(n, 0);
+    for (const qs_gate_rec* g : absorbed)
+      for (int j = 0; j < gate_arity(g->kind); ++j) used[g->q[j]] = 1;
+    std::vector<int> bq;
+    for (int q = 0; q < n; ++q)
+      if (used[q]) bq.push_back(q);
     qs_block b;
     b.k = (int)bq.size();
     for (int i = 0; i < b.k; ++i) b.q[i] = bq[i];
