@@ -3,10 +3,10 @@
 Default workload (the precision + fusion configuration): the 30-qubit brick
 random circuit of depth 40 (U3 on every qubit, then CNOT(i, i+1) on
 alternating pairs; the QSB structure of §IV-F), seed 6, complex64 state
-(8 GiB) fused into dense 5-qubit blocks on the tensor cores (tcgen05,
+(8 GiB) fused into dense 6-qubit blocks on the tensor cores (tcgen05,
 3xTF32).  The same circuit in complex128 (16 GiB, tiled plan) runs beside
 it and both are reported, with their infidelity measured on the GPU; the
-complex64 tiled and 4-qubit-block plans are timed as extras.
+complex64 tiled and 4-, 5-qubit-block plans are timed as extras.
 
 Metric (§IV-F, Eq. 5 traffic model): effective HBM bandwidth
     2 * 2^n * bytes_per_amplitude * #gates / time
@@ -51,7 +51,7 @@ WORKLOADS = {
 # scale it by 2^(n - 26).  Set to None whenever the kernel changes until it
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
-BLOCK_C64_TRAFFIC_26Q = {5: 537.114112e6 + 475.895552e6}  # k_fused_umma<5>, profiles/fused_umma_k5_brick26.md
+BLOCK_C64_TRAFFIC_26Q = {}  # {k: bytes} of k_fused_umma<k>, profiles/fused_umma_k*_brick26.md
 S_BYTES = {"c64": 8, "c128": 16}
 
 
@@ -420,10 +420,9 @@ def run_ours(args):
                                           "at 26 qubits, scaled by 2^(n-26)" % fq)
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
-        # launches per step: one per plan step, k_set_one, and for complex64
-        # tensor-core blocks the final renormalisation (3); complex128 plans
-        # without blocks switch storage layout (2)
-        extra = 1 + (3 if (dt == "c64" and mode_name == "fused") else 0) + (2 if dt == "c128" and mode_name != "fused" else 0)
+        # launches per step: one per plan step, k_set_one, and for complex128
+        # plans without blocks the two storage-layout switches
+        extra = 1 + (2 if dt == "c128" and mode_name != "fused" else 0)
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
                        "plan": mode_name + (f" k={fq}" if mode_name == "fused" else ""),
                        "passes": st["passes"], "gates": st["gates"], "hbm_bytes_per_step": st["hbm_bytes"],
@@ -499,11 +498,12 @@ def plan_mode(qs, args, dt):
 
 def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
     """The complex64 circuit under each plan: tiles (SIMT, many gates per
-    pass) and dense 4- and 5-qubit blocks (tensor cores), with the
+    pass) and dense 4-, 5- and 6-qubit blocks (tensor cores), with the
     infidelity of each against the complex128 result when it is at hand."""
     out = {}
     s = qs.State(n, "c64", device=device)
-    for name, mode, fq in (("tiled", qs.PLAN_TILED, 0), ("fused_k4", qs.PLAN_FUSED, 4), ("fused_k5", qs.PLAN_FUSED, 5)):
+    for name, mode, fq in (("tiled", qs.PLAN_TILED, 0), ("fused_k4", qs.PLAN_FUSED, 4), ("fused_k5", qs.PLAN_FUSED, 5),
+                           ("fused_k6", qs.PLAN_FUSED, 6)):
         p = qs.Plan(circuit, n, "c64", mode=mode, fuse_qubits=fq)
         s.set_basis(0)
         s.run(p)
@@ -598,7 +598,7 @@ def main():
     ap.add_argument("--workload", default="brick30", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--mode", default="auto", choices=["auto", "fused", "tiled", "unfused"])
-    ap.add_argument("--fuse-qubits", type=int, default=5, help="block width of the fused plan (4..6)")
+    ap.add_argument("--fuse-qubits", type=int, default=6, help="block width of the fused plan (4..6)")
     ap.add_argument("--both", type=int, default=1, help="also run the other dtype")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

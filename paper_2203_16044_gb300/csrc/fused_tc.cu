@@ -8,12 +8,12 @@
 //   B[2c][2r] = Re M[r][c], B[2c+1][2r] = -Im M[r][c],
 //   B[2c][2r+1] = Im M[r][c], B[2c+1][2r+1] = Re M[r][c].
 // Its arithmetic intensity, 2D flops per byte moved at complex64, passes the
-// GB300 FP32-SIMT ridge for k >= 4, so it runs on the tensor cores:
-// mma.sync m16n8k8 with TF32 inputs and FP32 accumulation, each FP32 operand
-// split as x ~ hi + lo (hi = x rounded to TF32, lo = x - hi rounded to
-// TF32) and the product formed from three MMAs, hi*hi + lo*hi + hi*lo
-// ("3xTF32"): about 22 significant bits per product with unbiased rounding,
-// FP32-level for the complex64 path.
+// GB300 FP32-SIMT ridge for k >= 4, so it runs on the 5th-generation tensor
+// cores (tcgen05.mma, kind::tf32, FP32 accumulation in tensor memory).  Each
+// FP32 operand is split as x ~ hi + lo (hi = x rounded to TF32, lo = x - hi
+// rounded to TF32) and a product is formed from three MMAs, lo*hi + hi*lo +
+// hi*hi ("3xTF32"): about 22 significant bits per product with unbiased
+// rounding, FP32-level for the complex64 path.
 //
 // Tensor-core FP32 accumulation truncates its internal sums (rounds toward
 // zero), which shrinks every output by about an ulp per block -- a bias, not
@@ -21,14 +21,8 @@
 // plan builds from circuit gates; qs_apply_fused checks on the host) each
 // group's norm is exactly preserved by the true result, so the kernel
 // rescales every output group to its input group's norm (both summed in
-// FP32 from the MMA fragments, reduced across each quad in a fixed order).
-//
-// A CTA (4 warps) takes chunks of 64 groups: gathers them from HBM into
-// shared memory (row stride 2D + 4 floats: conflict-free MMA fragment
-// loads; each thread owns one group slot, its addresses in registers), each
-// warp multiplies 16 groups by all of B (pre-split into TF32 hi/lo fragment
-// records in shared memory, one 16-byte load per three MMAs), stages the
-// results in shared memory and scatters them back.
+// FP32, reduced across the row's threads in a fixed order; the correction is
+// applied without bias, see norm_correction).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -37,9 +31,6 @@
 
 namespace qs {
 namespace {
-
-constexpr int kFT = 128;  // threads per CTA (4 warps)
-constexpr int kTG = 64;   // groups per chunk (16 per warp)
 
 // x ~ hi + lo with hi, lo TF32 values (10 explicit significand bits), each
 // rounded to nearest (ties away from zero) by adding half a TF32 ulp to the
@@ -55,131 +46,15 @@ __device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) 
   lo = round_tf32(x - __uint_as_float(h));
 }
 
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 struct FusedArgs {
   Ins ins;         // zero insertion at the k qubits (amplitude index space)
   u64 spread[64];  // spread[r]: OR of 2^qubits[i] over the set bits i of r
 };
 
-template <int K>
-__global__ void __launch_bounds__(kFT) k_fused_tc(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
-                                                  const __grid_constant__ FusedArgs args, int renorm) {
-  constexpr int D = 1 << K, KR = 2 * D, NT = KR / 8, KS = KR / 8;
-  constexpr int BQS = KS * 4 + 4;  // uint4 row stride of Bq: = 4 (mod 8), conflict-free LDS.128
-  constexpr int PAD = KR + 4;      // float row stride of As: conflict-free fragment loads
-  constexpr int RPT = D / 2;       // amplitudes per thread per chunk (kTG * D / kFT)
-  extern __shared__ __align__(16) uint4 smq[];
-  uint4* Bq = smq;                                     // [n][ks * 4 + tq] = (hi b0, hi b1, lo b0, lo b1)
-  float* As = reinterpret_cast<float*>(smq + KR * BQS);  // [kTG][PAD]
-  for (int i = threadIdx.x; i < KR * KS * 4; i += kFT) {
-    const int n = i / (KS * 4), rem = i % (KS * 4), ks = rem >> 2, tq = rem & 3;
-    unsigned h0, l0, h1, l1;
-    split_tf32(Bg[(8 * ks + tq) * KR + n], h0, l0);
-    split_tf32(Bg[(8 * ks + tq + 4) * KR + n], h1, l1);
-    Bq[n * BQS + ks * 4 + tq] = make_uint4(h0, h1, l0, l1);
-  }
-  // this thread's group slot within a chunk, and its amplitudes r = rb + 2 j
-  const int bslot = threadIdx.x & (kTG - 1), rb = threadIdx.x >> 6;
-  u64 spr[RPT];
-#pragma unroll
-  for (int j = 0; j < RPT; ++j) spr[j] = args.spread[rb + 2 * j];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int row0 = warp * 16;
-  for (u64 g0 = (u64)blockIdx.x * kTG; g0 < ngroups; g0 += (u64)gridDim.x * kTG) {
-    const u64 g = g0 + bslot;
-    const bool valid = g < ngroups;
-    const u64 base = expand(valid ? g : 0, args.ins);
-    __syncthreads();  // previous chunk's scatter (and the set-up) complete
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-      const float2 v = valid ? a[base | spr[j]] : make_float2(0.f, 0.f);
-      *reinterpret_cast<float2*>(As + bslot * PAD + 2 * (rb + 2 * j)) = v;
-    }
-    __syncthreads();
-    float acc[NT][4];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    float n0 = 0.f, n1 = 0.f;  // input sums of squares, rows gq and gq + 8 (this lane's columns)
-#pragma unroll 2
-    for (int ks = 0; ks < KS; ++ks) {
-      const int kk = 8 * ks;
-      const float x0 = As[(row0 + gq) * PAD + kk + tq], x1 = As[(row0 + gq + 8) * PAD + kk + tq];
-      const float x2 = As[(row0 + gq) * PAD + kk + tq + 4], x3 = As[(row0 + gq + 8) * PAD + kk + tq + 4];
-      n0 = fmaf(x0, x0, fmaf(x2, x2, n0));
-      n1 = fmaf(x1, x1, fmaf(x3, x3, n1));
-      unsigned ah[4], al[4];
-      split_tf32(x0, ah[0], al[0]);
-      split_tf32(x1, ah[1], al[1]);
-      split_tf32(x2, ah[2], al[2]);
-      split_tf32(x3, ah[3], al[3]);
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const uint4 bq = Bq[(nt * 8 + gq) * BQS + ks * 4 + tq];
-        mma_tf32(acc[nt], al, bq.x, bq.y);
-        mma_tf32(acc[nt], ah, bq.z, bq.w);
-        mma_tf32(acc[nt], ah, bq.x, bq.y);
-      }
-    }
-    float f0 = 1.f, f1 = 1.f;
-    if (renorm) {
-      float m0 = 0.f, m1 = 0.f;
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        m0 = fmaf(acc[nt][0], acc[nt][0], fmaf(acc[nt][1], acc[nt][1], m0));
-        m1 = fmaf(acc[nt][2], acc[nt][2], fmaf(acc[nt][3], acc[nt][3], m1));
-      }
-      // the four lanes of a quad hold a row's columns between them
-#pragma unroll
-      for (int o = 1; o <= 2; o <<= 1) {
-        n0 += __shfl_xor_sync(0xffffffffu, n0, o);
-        n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-        m0 += __shfl_xor_sync(0xffffffffu, m0, o);
-        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-      }
-      f0 = m0 > 0.f ? sqrtf(n0 / m0) : 1.f;
-      f1 = m1 > 0.f ? sqrtf(n1 / m1) : 1.f;
-    }
-    __syncthreads();  // every warp is done reading As
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      *reinterpret_cast<float2*>(As + (row0 + gq) * PAD + nt * 8 + 2 * tq) = make_float2(acc[nt][0] * f0, acc[nt][1] * f0);
-      *reinterpret_cast<float2*>(As + (row0 + gq + 8) * PAD + nt * 8 + 2 * tq) = make_float2(acc[nt][2] * f1, acc[nt][3] * f1);
-    }
-    __syncthreads();
-    if (valid) {
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) a[base | spr[j]] = *reinterpret_cast<const float2*>(As + bslot * PAD + 2 * (rb + 2 * j));
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// tcgen05 path (k = 4, 5): the same GEMM with the 5th-generation tensor-core
-// instructions.  One CTA of 128 threads per tile of 128 groups = the MMA's M;
-// thread t owns group (row) t from gather to scatter:
-//   1. gathers its 2^k amplitudes from HBM (constant-bank spread offsets),
-//      sums their squares, splits each real into TF32 hi + lo (rounded) and
-//      writes both rows to shared memory in the tensor core's K-major
-//      "core matrix" layout (8 rows x 16 bytes per 128-byte core matrix);
-//   2. thread 0 issues 3 x (2D / 8) tcgen05.mma (M = 128, N = 2D, K = 8;
-//      lo*hi, hi*lo, hi*hi per K step) into a TMEM accumulator of 2D FP32
-//      columns and commits them to an mbarrier;
-//   3. every thread waits on the mbarrier (bounded), reads its row of the
-//      accumulator with tcgen05.ld (TMEM lane t = row t), restores the
-//      group norm and scatters the result to the same addresses.
-// B (hi and lo) is staged once per CTA.  Each CTA keeps the next two tiles'
-// loads in flight in registers while a tile's MMAs and epilogue run, and
-// several CTAs share an SM (shared memory 40 KB at k = 4, 96 KB at k = 5).  A wait that gives up (about 1 s) sets g_umma_timeout,
-// reported by qs_sync; the CTA then stops, frees its TMEM and returns.
+// tcgen05 helpers
 // ---------------------------------------------------------------------------
-constexpr int kUT = 128;  // threads per CTA = groups per tile = MMA M
+constexpr int kUT = 128;  // groups per tile = MMA M = TMEM lanes
 
 __device__ int g_umma_timeout;
 
@@ -197,12 +72,6 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 // B TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at 24.
 __host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void umma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* o) {
   uint32_t r[16];
@@ -231,18 +100,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   }
 }
 
-template <int K>
-struct UmmaShape {
-  static constexpr int D = 1 << K, KR = 2 * D;
-  static constexpr uint32_t A_BYTES = kUT * KR * 4, B_BYTES = KR * KR * 4;
-  static constexpr uint32_t LBO_A = (kUT / 8) * 128, LBO_B = (KR / 8) * 128, SBO = 128;
-  static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 16 + 2 * 2 * kUT * sizeof(float);
-};
+// Norm restore for a group whose input norm^2 is nin and output norm^2 nout:
+// the output is scaled by sqrt(nin / nout) = 1 + g.  g is formed as a small
+// number, g = d / (1 + sqrt(1 + d)) with d = (nin - nout) / nout, and applied
+// as o + o g: a scale factor rounded to FP32 next to 1.0 would be biased
+// (the FP32 grid is twice as fine just below 1 as just above, so small
+// upward corrections round away while downward ones survive), which shrank
+// every block's output norm by about one unit roundoff.
+__device__ __forceinline__ float norm_correction(float nin, float nout) {
+  if (!(nout > 0.f)) return 0.f;
+  const float d = (nin - nout) / nout;
+  return d / (1.f + sqrtf(1.f + d));
+}
 
 // A thread's share of a group's 2^k amplitudes to / from registers, as CH
-// 16-byte words w[j] = amplitudes (2 (j0 + j), 2 (j0 + j) + 1) once taken.  The block's qubits are
-// sorted ascending (the host permutes M to match), so when qubit 0 is in the
-// block it is block bit 0.
+// 16-byte words w[j] = amplitudes (2 (j0 + j), 2 (j0 + j) + 1) once taken.
+// The block's qubits are sorted ascending (the host permutes M to match), so
+// when qubit 0 is in the block it is block bit 0.
 //   lmode 0: 8-byte accesses.
 //   lmode 1 (qubit 0 in the block): amplitudes 2j and 2j + 1 are adjacent,
 //            one 16-byte access.
@@ -283,23 +157,25 @@ __device__ __forceinline__ float4 group_take(float4 x, int lmode) {
   const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
   return odd ? make_float4(rx, ry, x.z, x.w) : make_float4(x.x, x.y, rx, ry);
 }
-// o[4j .. 4j + 3] = amplitudes 2 (j0 + j), 2 (j0 + j) + 1 of this thread's group
+// o[4j .. 4j + 3] = amplitudes 2 (j0 + j), 2 (j0 + j) + 1 of this thread's
+// group; each value is stored as o (1 + g), one rounding (FMA).
 template <int D, int CH>
 __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bool valid, const u64* spread, int lmode,
-                                            int j0, const float* o, float f) {
+                                            int j0, const float* o, float g) {
+  auto sc = [g](float v) { return fmaf(v, g, v); };
   if (lmode == 1) {
     if (!valid) return;
 #pragma unroll
     for (int j = 0; j < CH; ++j)
       *reinterpret_cast<float4*>(a + (base | spread[2 * (j0 + j)])) =
-          make_float4(o[4 * j] * f, o[4 * j + 1] * f, o[4 * j + 2] * f, o[4 * j + 3] * f);
+          make_float4(sc(o[4 * j]), sc(o[4 * j + 1]), sc(o[4 * j + 2]), sc(o[4 * j + 3]));
   } else if (lmode == 2) {
     const bool odd = threadIdx.x & 1;
     const u64 pb = base & ~u64(1);
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
       // even lane stores (own 2j, partner 2j); odd lane (partner 2j + 1, own 2j + 1)
-      const float m0x = o[4 * j] * f, m0y = o[4 * j + 1] * f, m1x = o[4 * j + 2] * f, m1y = o[4 * j + 3] * f;
+      const float m0x = sc(o[4 * j]), m0y = sc(o[4 * j + 1]), m1x = sc(o[4 * j + 2]), m1y = sc(o[4 * j + 3]);
       const float sx = odd ? m0x : m1x, sy = odd ? m0y : m1y;
       const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
       *reinterpret_cast<float4*>(a + (pb | spread[2 * (j0 + j) + (odd ? 1 : 0)])) =
@@ -308,33 +184,69 @@ __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bo
   } else if (valid) {
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
-      a[base | spread[2 * (j0 + j)]] = make_float2(o[4 * j] * f, o[4 * j + 1] * f);
-      a[base | spread[2 * (j0 + j) + 1]] = make_float2(o[4 * j + 2] * f, o[4 * j + 3] * f);
+      a[base | spread[2 * (j0 + j)]] = make_float2(sc(o[4 * j]), sc(o[4 * j + 1]));
+      a[base | spread[2 * (j0 + j) + 1]] = make_float2(sc(o[4 * j + 2]), sc(o[4 * j + 3]));
     }
   }
 }
 
-// H threads per group row (H = 1 or 2): thread t owns row t % 128 and the
-// half h = t / 128 of its amplitudes (H = 2), so a CTA has 4 H warps.
-template <int K, int H>
-__global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
+// ---------------------------------------------------------------------------
+// The block kernel (k = 4, 5, 6).  The MMA's A operand may
+// live in tensor memory (lane = row, one 32-bit column per K element), so the
+// tile never passes through shared memory: each thread writes its share of
+// its row, split into TF32 hi and lo, straight into its own TMEM lane with
+// tcgen05.st.  Shared memory holds only B (hi and lo: 8 KB at k = 4, 32 KB at
+// k = 5, 128 KB at k = 6), which is what lets k = 6 fit.  TMEM columns: A hi
+// [0, 2D), A lo [2D, 4D), accumulator [4D, 6D) (128, 256 or all 512 columns,
+// so 4, 2 or 1 CTAs share an SM).  H = 2^(k+1) / 32 threads per row, each
+// owning 32 reals (16 amplitudes) of it: 128, 256 or 512 threads.  Per
+// tile: take + split + tcgen05.st, one CTA barrier, 3 (2D / 8)
+// MMAs issued by one thread, the next tiles' loads issued, the bounded
+// mbarrier wait, tcgen05.ld of the thread's 32 accumulator columns, the group
+// norm restored across the row's H threads (shared memory), and the scatter.
+// Two register buffers keep the next two tiles' loads in flight meanwhile.
+// A wait that gives up (about 1 s) sets g_umma_timeout, reported by qs_sync;
+// the CTA then stops, frees its TMEM and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const unsigned* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
+}
+__device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
+                                             uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+template <int K>
+struct TaShape {
+  static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NT = kUT * H;
+  static constexpr uint32_t B_BYTES = KR * KR * 4, LBO_B = (KR / 8) * 128, SBO = 128;
+  static constexpr uint32_t TCOLS = 3 * KR <= 128 ? 128 : (3 * KR <= 256 ? 256 : 512);  // power of two >= 3 KR
+  static constexpr size_t SMEM = 2 * (size_t)B_BYTES + 16 + 2 * H * kUT * sizeof(float);
+};
+
+template <int K>
+__global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
     k_fused_umma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
-                 const __grid_constant__ FusedArgs args, int renorm, int lmode) {
-  typedef UmmaShape<K> S;
-  constexpr int D = S::D, KR = S::KR, NT = kUT * H;
-  constexpr int CH = D / 2 / H;  // 16-byte words (amplitude pairs) per thread
+                    const __grid_constant__ FusedArgs args, int renorm, int lmode) {
+  typedef TaShape<K> S;
+  constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT;
+  constexpr int CH = 8;  // 16-byte words (amplitude pairs) per thread: 32 reals
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = sm + S::A_BYTES;
-  unsigned char* Bhi = sm + 2 * S::A_BYTES;
-  unsigned char* Blo = Bhi + S::B_BYTES;
+  unsigned char* Bhi = sm;
+  unsigned char* Blo = sm + S::B_BYTES;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   float* nin_s = reinterpret_cast<float*>(mbar + 2);  // [H][kUT] partial input norms
-  float* nout_s = nin_s + 2 * kUT;                     // [H][kUT] partial output norms
+  float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
   const int t = threadIdx.x, warp = t >> 5;
   const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
-  // B operand (N x K, K-major): element (n, k) = B[k][n], split hi + lo
   for (int i = t; i < KR * KR; i += NT) {
     const int k = i / KR, n = i % KR;
     unsigned hh, l;
@@ -349,7 +261,8 @@ __global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(KR));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(S::TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;");
@@ -357,16 +270,11 @@ __global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  // a warp reads TMEM lanes 32 (warp % 4) .. + 31 = its rows; columns of its half
-  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * (KR / H));
-  const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-  const uint32_t row_off = (uint32_t)(row >> 3) * 128 + (uint32_t)(row & 7) * 16;
+  // this warp's 32 lanes (= its rows), and this thread's 32 columns in each region
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 32);
+  const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
   constexpr uint32_t idesc = umma_idesc(kUT, KR);
   uint32_t phase = 0;
-  // Software pipeline, two tiles deep: register buffers wA and wB hold the
-  // next two tiles' amplitudes; a buffer is refilled with the tile two steps
-  // ahead as soon as its contents are in shared memory, so its loads stay in
-  // flight during this tile's MMAs and epilogue and the next tile's step.
   const u64 gstep = (u64)gridDim.x * kUT;
   u64 gA = (u64)blockIdx.x * kUT, gB = gA + gstep;
   bool vA = gA + row < ngroups, vB = gB + row < ngroups;
@@ -378,37 +286,41 @@ __global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
     if (g >= ngroups) return false;
     float nin = 0.f;
 #pragma unroll
-    for (int j = 0; j < CH; ++j) {  // 16-byte chunk c = j0 + j = reals 4c .. 4c + 3 = amplitudes 2c, 2c + 1
-      const float4 wc = group_take(w[j], lmode);
-      const float x[4] = {wc.x, wc.y, wc.z, wc.w};
-      unsigned hh[4], l[4];
+    for (int half = 0; half < 2; ++half) {  // 16 columns (4 words) at a time
+      unsigned hv[16], lv[16];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        nin = fmaf(x[i], x[i], nin);
-        split_tf32(x[i], hh[i], l[i]);
+      for (int j = 0; j < 4; ++j) {
+        const float4 wc = group_take(w[4 * half + j], lmode);
+        const float x[4] = {wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          nin = fmaf(x[i], x[i], nin);
+          split_tf32(x[i], hv[4 * j + i], lv[4 * j + i]);
+        }
       }
-      *reinterpret_cast<uint4*>(Ahi + (j0 + j) * S::LBO_A + row_off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
-      *reinterpret_cast<uint4*>(Alo + (j0 + j) * S::LBO_A + row_off) = make_uint4(l[0], l[1], l[2], l[3]);
+      tmem_st16(tl + (uint32_t)(16 * half), hv);
+      tmem_st16(tl + (uint32_t)(KR + 16 * half), lv);
     }
-    if (H > 1) nin_s[h * kUT + row] = nin;
-    asm volatile("fence.proxy.async.shared::cta;");
+    nin_s[h * kUT + row] = nin;
+    asm volatile("tcgen05.wait::st.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (H > 1) nin += nin_s[(h ^ 1) * kUT + row];
+    nin = 0.f;
+#pragma unroll
+    for (int i = 0; i < H; ++i) nin += nin_s[i * kUT + row];
     if (t == 0) {
 #pragma unroll
       for (int ks = 0; ks < KR / 8; ++ks) {
-        const uint32_t ao = ks * 2 * S::LBO_A, bo = ks * 2 * S::LBO_B;
-        const uint64_t dah = umma_desc(ahi + ao, S::LBO_A, S::SBO), dal = umma_desc(alo + ao, S::LBO_A, S::SBO);
+        const uint32_t bo = ks * 2 * S::LBO_B;
         const uint64_t dbh = umma_desc(bhi + bo, S::LBO_B, S::SBO), dbl = umma_desc(blo + bo, S::LBO_B, S::SBO);
-        umma_tf32(tmem, dal, dbh, idesc, ks > 0 ? 1u : 0u);
-        umma_tf32(tmem, dah, dbl, idesc, 1u);
-        umma_tf32(tmem, dah, dbh, idesc, 1u);
+        const uint32_t ahi_t = tmem + (uint32_t)(ks * 8), alo_t = tmem + (uint32_t)(KR + ks * 8);
+        umma_tf32_ta(tmem + 2 * KR, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
+        umma_tf32_ta(tmem + 2 * KR, ahi_t, dbl, idesc, 1u);
+        umma_tf32_ta(tmem + 2 * KR, ahi_t, dbh, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
     }
-    // refill this buffer with the tile two steps ahead
     const u64 gn = g + 2 * gstep;
     const bool vn = gn + row < ngroups;
     const u64 bn = expand(vn ? gn + row : 0, args.ins);
@@ -419,23 +331,23 @@ __global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    float o[KR / H];
-#pragma unroll
-    for (int c0 = 0; c0 < KR / H; c0 += 16) tmem_ld16(trow + (uint32_t)c0, o + c0);
+    float o[32];
+    tmem_ld16(tl + (uint32_t)(2 * KR), o);
+    tmem_ld16(tl + (uint32_t)(2 * KR + 16), o + 16);
     asm volatile("tcgen05.wait::ld.sync.aligned;");
-    float f = 1.f;
+    float gsc = 0.f;  // output = o (1 + gsc)
     if (renorm) {
       float nout = 0.f;
 #pragma unroll
-      for (int j = 0; j < KR / H; ++j) nout = fmaf(o[j], o[j], nout);
-      if (H > 1) {
-        nout_s[h * kUT + row] = nout;
-        __syncthreads();
-        nout += nout_s[(h ^ 1) * kUT + row];
-      }
-      f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+      for (int j = 0; j < 32; ++j) nout = fmaf(o[j], o[j], nout);
+      nout_s[h * kUT + row] = nout;
+      __syncthreads();
+      nout = 0.f;
+#pragma unroll
+      for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
+      gsc = norm_correction(nin, nout);
     }
-    group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, f);
+    group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, gsc);
     asm volatile("tcgen05.fence::before_thread_sync;");
     g = gn;
     valid = vn;
@@ -446,17 +358,16 @@ __global__ void __launch_bounds__(kUT * H, H == 2 ? 2 : 1)
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(KR));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
-template <int K, int H>
+template <int K>
 qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renorm, const int* qubits) {
-  const size_t smem = UmmaShape<K>::SMEM;
-  auto kern = k_fused_umma<K, H>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  typedef TaShape<K> S;
+  auto kern = k_fused_umma<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: smem attribute");
-  // CTAs per SM from registers, shared memory and TMEM columns (512 per SM)
   int dev = 0, smem_sm = 0, smem_rsv = 0;
   cudaFuncAttributes fa{};
   e = cudaGetDevice(&dev);
@@ -464,33 +375,16 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: occupancy attributes");
-  int per_sm = smem_sm / (int)(smem + smem_rsv);
+  int per_sm = smem_sm / (int)(S::SMEM + smem_rsv);
   const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 255;
-  per_sm = std::min(per_sm, 65536 / (regs * kUT * H));
-  per_sm = std::min(per_sm, 512 / UmmaShape<K>::KR);
+  per_sm = std::min(per_sm, 65536 / (regs * S::NT));
+  per_sm = std::min(per_sm, 512 / (int)S::TCOLS);
   if (per_sm < 1) per_sm = 1;
   const u64 ngroups = u64(1) << (s->n - K);
   const unsigned grid = grid_for(ngroups, kUT, per_sm);
-  // qubits ascending (see run_dense_tc)
   const int lmode = qubits[0] == 0 ? 1 : (ngroups >= (u64)kUT ? 2 : 0);
-  kern<<<grid, kUT * H, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
+  kern<<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
   return launch_ok("k_fused_umma");
-}
-
-template <int K>
-qs_status launch(qs_state* s, const FusedArgs& A, const float* B, int renorm) {
-  constexpr int D = 1 << K, KR = 2 * D, KS = KR / 8, BQS = KS * 4 + 4, PAD = KR + 4;
-  const size_t smem = sizeof(uint4) * (size_t)KR * BQS + sizeof(float) * (size_t)kTG * PAD;
-  auto kern = k_fused_tc<K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "fused_tc: smem attribute");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFT, smem);
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  const u64 ngroups = u64(1) << (s->n - K);
-  const unsigned grid = grid_for(ngroups, kTG, per_sm);
-  kern<<<grid, kFT, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm);
-  return launch_ok("k_fused_tc");
 }
 
 }  // namespace
@@ -553,9 +447,9 @@ qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, i
   if (e != cudaSuccess) return cuda_fail(e, "fused_tc: matrix upload");
   const float* Bd = static_cast<const float*>(s->scratch);
   switch (k) {
-    case 4: return launch_umma<4, 1>(s, A, Bd, unitary, q);
-    case 5: return launch_umma<5, 2>(s, A, Bd, unitary, q);
-    case 6: return launch<6>(s, A, Bd, unitary);
+    case 4: return launch_umma<4>(s, A, Bd, unitary, q);
+    case 5: return launch_umma<5>(s, A, Bd, unitary, q);
+    case 6: return launch_umma<6>(s, A, Bd, unitary, q);
   }
   return fail(QS_EINVAL, "fused_tc: k=%d outside [4, 6]", k);
 }

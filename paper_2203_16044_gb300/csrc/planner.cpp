@@ -132,14 +132,6 @@ qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
     const qs_status r2 = run_layout_dfl(s, false);
     if (r == QS_OK) r = r2;
   }
-  // complex64 tensor-core blocks: their FP32 accumulation truncates (rounds
-  // toward zero), a small systematic norm loss per block; the exact circuit
-  // is unitary, so the state is rescaled to its input norm (unit) at the end
-  if (r == QS_OK && s->dtype == QS_C64) {
-    bool tc = false;
-    for (const qs_block& b : p->blocks) tc |= b.k >= 4;
-    if (tc) r = run_normalize(s);
-  }
   return r;
 }
 
@@ -279,6 +271,13 @@ qs_status plan_fused(qs_plan* p) {
     std::vector<char> used(n, 0);
     for (const qs_gate_rec* g : absorbed)
       for (int j = 0; j < gate_arity(g->kind); ++j) used[g->q[j]] = 1;
+    // complex64 blocks of 4 or more qubits run on the tensor cores at HBM
+    // speed; a smaller block is widened with idle qubits (identity on them)
+    // rather than run on the SIMT dense kernel
+    int nused = 0;
+    for (int q = 0; q < n; ++q) nused += used[q];
+    for (int q = 0; q < n && p->dtype == QS_C64 && kmax >= 4 && nused < 4; ++q)
+      if (!used[q]) { used[q] = 1; ++nused; }
     std::vector<int> bq;
     for (int q = 0; q < n; ++q)
       if (used[q]) bq.push_back(q);

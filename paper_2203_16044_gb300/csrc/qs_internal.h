@@ -67,7 +67,6 @@ qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d);
 
 // ---- reductions (reduce.cu) ------------------------------------------------
 qs_status run_norm2(qs_state* s, double* out);
-qs_status run_normalize(qs_state* s);
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask,
                      const double* coeff, double* out);

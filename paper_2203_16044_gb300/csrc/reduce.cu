@@ -141,21 +141,6 @@ __global__ void __launch_bounds__(kThreads) k_pauli(const R* __restrict__ a, int
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
 }
 
-// a <- a / sqrt(norm2), norm2 = res->x read on the device (no host round trip)
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_scale_inv_sqrt(R* __restrict__ a, u64 npk, const double2* res) {
-  constexpr int V = PK<R>::V;
-  const double nrm = res->x;
-  const R f = nrm > 0.0 ? (R)(1.0 / sqrt(nrm)) : (R)1;
-  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
-    R v[V];
-    ld16(a + p * V, v);
-#pragma unroll
-    for (int c = 0; c < V; ++c) v[c] *= f;
-    st16(a + p * V, v);
-  }
-}
-
 qs_status read_result(qs_state* s, const double2* dev, double2* host) {
   cudaError_t e = cudaMemcpyAsync(s->pinned, dev, sizeof(double2), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reduction readback");
@@ -185,26 +170,6 @@ qs_status run_norm2(qs_state* s, double* out) {
   if ((st = read_result(s, res, &h)) != QS_OK) return st;
   *out = h.x;
   return QS_OK;
-}
-
-// Rescale the state to unit norm (FP64-accumulated norm), asynchronously.
-qs_status run_normalize(qs_state* s) {
-  const int LA = s->dtype == QS_C64 ? 1 : 0;
-  const u64 npk = u64(1) << (s->n - LA);
-  const unsigned g = red_grid(npk);
-  qs_status st = ensure_scratch(s, sizeof(double2) * (g + 1));
-  if (st != QS_OK) return st;
-  double2* part = static_cast<double2*>(s->scratch);
-  double2* res = part + g;
-  if (s->dtype == QS_C64) k_norm2<float><<<g, kThreads, 0, s->stream>>>(static_cast<const float*>(s->amp), npk, part);
-  else k_norm2<double><<<g, kThreads, 0, s->stream>>>(static_cast<const double*>(s->amp), npk, part);
-  if ((st = launch_ok("k_norm2")) != QS_OK) return st;
-  k_final<<<1, kThreads, 0, s->stream>>>(part, g, res, 0);
-  if ((st = launch_ok("k_final")) != QS_OK) return st;
-  const unsigned gs = grid_for(npk, kThreads, 8);
-  if (s->dtype == QS_C64) k_scale_inv_sqrt<float><<<gs, kThreads, 0, s->stream>>>(static_cast<float*>(s->amp), npk, res);
-  else k_scale_inv_sqrt<double><<<gs, kThreads, 0, s->stream>>>(static_cast<double*>(s->amp), npk, res);
-  return launch_ok("k_scale_inv_sqrt");
 }
 
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
