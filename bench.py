@@ -51,7 +51,7 @@ WORKLOADS = {
 # scale it by 2^(n - 26).  Set to None whenever the kernel changes until it
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
-BLOCK_C64_TRAFFIC_26Q = {}  # {k: bytes} of k_fused_umma<k>, profiles/fused_umma_k*_brick26.md
+BLOCK_C64_TRAFFIC_26Q = {6: 537.053696e6 + 476.197120e6}  # k_fused_umma<6>, profiles/fused_umma_k6_brick26.md
 S_BYTES = {"c64": 8, "c128": 16}
 
 
