@@ -44,6 +44,7 @@ WORKLOADS = {
     "qft28": dict(n=28, make=lambda: W.qft(28), desc="28-qubit QFT"),
     "brick26": dict(n=26, make=lambda: W.brick(26, 40, 6), desc="26-qubit brick random circuit, depth 40, seed 6"),
     "brick20": dict(n=20, make=lambda: W.brick(20, 40, 6), desc="20-qubit brick random circuit, depth 40, seed 6"),
+    "brick33": dict(n=33, make=lambda: W.brick(33, 20, 7), desc="33-qubit brick random circuit, depth 20, seed 7"),
 }
 
 # DRAM bytes (read + write) per launch from one ncu capture on the 26-qubit
@@ -446,6 +447,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
+        extras["c64_brick33_d20"] = c64_33q(qs, torch, device, args.fuse_qubits)
         base = c128_unfused(qs, torch, device, n, circuit)
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
         extras["c128_unfused_%dq" % n] = base
@@ -525,6 +527,27 @@ def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
         out[name] = r
         del p
     del s
+    return out
+
+
+def c64_33q(qs, torch, device, fq):
+    """The 33-qubit complex64 brick circuit of depth 20 (64 GiB state) under
+    the fused plan: one warm-up run, one timed run (CUDA events)."""
+    wl = WORKLOADS["brick33"]
+    n, circ = wl["n"], wl["make"]()
+    s = qs.State(n, "c64", device=device)
+    p = qs.Plan(qs.Circuit(circ), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=fq)
+    s.run(p)
+    torch.cuda.synchronize()
+    s.set_basis(0)
+    ms = s.run_profiled(p)
+    st = p.stats()
+    t = float(ms.sum())
+    out = {"workload": wl["desc"], "plan": "fused k=%d" % fq, "ms": t, "passes": st["passes"],
+           "effective_GBps": st["metric_bytes"] / (t / 1e3) / 1e9, "gates_per_s": st["gates"] / (t / 1e3),
+           "hbm_GBps_algorithmic": st["hbm_bytes"] / (t / 1e3) / 1e9,
+           "norm2": s.norm2()}
+    del s, p
     return out
 
 

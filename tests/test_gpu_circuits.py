@@ -124,3 +124,20 @@ def test_tile_variants_match_oracle(qs, dtype, slots, gpt, dense, tile, low):
         assert np.max(np.abs(got - want)) <= C128_TOL
     else:
         assert infidelity(got, want) <= C64_INFIDELITY
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_c64_tensor_core_blocks_vs_oracle_22q(qs, k):
+    # complex64 dense blocks on the tensor cores over a depth-40 circuit on a
+    # state larger than one tile row set (2^22 amplitudes): infidelity
+    # against the FP64 oracle and the norm, which the unbiased per-group
+    # restore keeps at 1 without any end-of-plan renormalisation
+    n = 22
+    circ = W.brick(n, 40, 12)
+    want = oracle_state(n, circ)
+    s = qs.State(n, "c64")
+    p = qs.Plan(qs.Circuit(circ), n, "c64", mode=2, fuse_qubits=k)
+    s.run(p)
+    got = s.to_numpy()
+    assert infidelity(got, want) <= C64_INFIDELITY
+    assert abs(np.vdot(got.astype(np.complex128), got).real - 1) <= 1e-6
