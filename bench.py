@@ -447,6 +447,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
+        extras["reductions_%dq" % n] = reductions(qs, torch, states, n)
         extras["c64_brick33_d20"] = c64_33q(qs, torch, device, args.fuse_qubits)
         base = c128_unfused(qs, torch, device, n, circuit)
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
@@ -527,6 +528,36 @@ def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
         out[name] = r
         del p
     del s
+    return out
+
+
+def reductions(qs, torch, states, n, reps=5):
+    """FP64-accumulated reductions on the headline states (a7): norm, inner
+    product with itself, and the TFIM expectation (one pass per X/Y-mask
+    group: the ZZ terms together, each X_i alone).  Each call returns its
+    value to the host, so the host clock around the calls includes the
+    device-to-host read; GB/s counts the state bytes each call reads."""
+    out = {}
+    terms = W.tfim(n)
+    groups = len({t.xmask for t in terms})
+    for dt, s in states.items():
+        S = S_BYTES[dt]
+        N = float(1 << n)
+        r = {}
+        # the inner product of the state with itself reads each byte from
+        # DRAM once (the second operand's loads hit L1): counted once
+        for name, fn, nbytes in (("norm2", lambda: s.norm2(), N * S),
+                                 ("inner_self", lambda: s.inner(s), N * S),
+                                 ("expect_tfim", lambda: s.expect_pauli(terms), groups * N * S)):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                v = fn()
+            t = (time.perf_counter() - t0) / reps
+            r[name] = {"ms": 1e3 * t, "GBps": nbytes / t / 1e9, "value": v.real if isinstance(v, complex) else v}
+        r["tfim_groups"] = groups
+        out[dt] = r
     return out
 
 

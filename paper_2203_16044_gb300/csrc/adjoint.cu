@@ -58,23 +58,6 @@ __device__ __forceinline__ double a_block_sum(double a) {
   return a;
 }
 
-// acc += v in double-float (low part left unnormalised; it only gathers the
-// rounding errors of the high part)
-__device__ __forceinline__ void df_acc(dfl& acc, dfl v) {
-  float e;
-  acc.h = two_sum(acc.h, v.h, e);
-  acc.l = __fadd_rn(acc.l, __fadd_rn(e, v.l));
-}
-
-// a + b in double-float, normalised
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  float e;
-  const float s = two_sum(a.h, b.h, e);
-  dfl r;
-  r.h = fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)), r.l);
-  return r;
-}
-
 // Amplitude storage of the sweep: complex64 as float2 (re, im); complex128
 // in double-float storage as float4 (re_h, re_l, im_h, im_l).
 template <typename R> struct Amp;

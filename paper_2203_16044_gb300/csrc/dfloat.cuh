@@ -91,6 +91,34 @@ __device__ __forceinline__ double df2d(dfl v) {
   return __longlong_as_double((long long)D);
 }
 
+// acc += v in double-float, low part left unnormalised: it gathers the
+// exact rounding errors of the high part (TwoSum) and v's low part.
+__device__ __forceinline__ void df_acc(dfl& acc, dfl v) {
+  float e;
+  acc.h = two_sum(acc.h, v.h, e);
+  acc.l = __fadd_rn(acc.l, __fadd_rn(e, v.l));
+}
+
+// a + b in double-float, normalised
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float e;
+  const float s = two_sum(a.h, b.h, e);
+  dfl r;
+  r.h = fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)), r.l);
+  return r;
+}
+
+// a b in double-float (the l*l term, ~2^-48 relative, dropped), unnormalised:
+// h = a.h b.h rounded, l = its exact error plus the cross terms
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  dfl r;
+  r.h = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -r.h);
+  e = __fmaf_rn(a.h, b.l, e);
+  r.l = __fmaf_rn(a.l, b.h, e);
+  return r;
+}
+
 // sum_{k<4} x_k y_k for double-float x_k, y_k; h + l normalised.
 __device__ __forceinline__ dfl dot4(float xh0, float xl0, float yh0, float yl0, float xh1, float xl1, float yh1,
                                     float yl1, float xh2, float xl2, float yh2, float yl2, float xh3, float xl3,

@@ -6,9 +6,12 @@
 //   f(y) = sum_t c_t i^{nY_t} (-1)^{popcount(y & z_t)}.
 #pragma once
 
+#include <algorithm>
 #include <map>
+#include <tuple>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 
 namespace qs {
@@ -19,18 +22,32 @@ struct PauliGroup {
   int h;           // highest bit of m (-1 if m == 0)
   int nt;          // terms in this launch
   u64 z[kMaxGroupTerms];
-  double wr[kMaxGroupTerms], wi[kMaxGroupTerms];  // c_t * i^{nY_t}
+  // w_t = c_t * i^{nY_t} in double-float: real (h, l) and imaginary (h, l)
+  float wrh[kMaxGroupTerms], wrl[kMaxGroupTerms], wih[kMaxGroupTerms], wil[kMaxGroupTerms];
 };
 
-__device__ __forceinline__ void fval(const PauliGroup& g, u64 x, double& fr, double& fi) {
-  fr = 0.0; fi = 0.0;
+// f(x) in double-float.  The host sorts a group's terms by weight, so equal
+// weights form runs: a run of len terms with weight w contributes
+// w (len - 2 odd), odd = the number of its terms with popcount(x & z_t) odd,
+// counted with integer operations; one double-float product per run.
+__device__ __forceinline__ void fval_df(const PauliGroup& g, u64 x, dfl& fr, dfl& fi) {
+  fr = dfl{0.f, 0.f};
+  fi = dfl{0.f, 0.f};
+  int len = 0, odd = 0;
   for (int t = 0; t < g.nt; ++t) {
-    const double sgn = (__popcll(x & g.z[t]) & 1) ? -1.0 : 1.0;
-    fr += sgn * g.wr[t];
-    fi += sgn * g.wi[t];
+    odd += __popcll(x & g.z[t]) & 1;
+    ++len;
+    const bool last = t + 1 == g.nt || g.wrh[t + 1] != g.wrh[t] || g.wrl[t + 1] != g.wrl[t] ||
+                      g.wih[t + 1] != g.wih[t] || g.wil[t + 1] != g.wil[t];
+    if (last) {
+      const dfl k{(float)(len - 2 * odd), 0.f};  // exact: |k| <= 64
+      df_acc(fr, df_mul(dfl{g.wrh[t], g.wrl[t]}, k));
+      df_acc(fi, df_mul(dfl{g.wih[t], g.wil[t]}, k));
+      len = 0;
+      odd = 0;
+    }
   }
 }
-
 
 // Group terms by X/Y mask in order of first appearance (deterministic), at
 // most kMaxGroupTerms per group.
@@ -56,10 +73,29 @@ inline std::vector<PauliGroup> build_pauli_groups(int nterms, const u64* xmask, 
     PauliGroup& g = groups[gi];
     const int ny = __builtin_popcountll(m & z) & 3;  // i^{nY}
     const double pr[4] = {1, 0, -1, 0}, pim[4] = {0, 1, 0, -1};
+    const double wr = coeff[t] * pr[ny], wi = coeff[t] * pim[ny];
     g.z[g.nt] = z;
-    g.wr[g.nt] = coeff[t] * pr[ny];
-    g.wi[g.nt] = coeff[t] * pim[ny];
+    g.wrh[g.nt] = (float)wr;
+    g.wrl[g.nt] = (float)(wr - (double)g.wrh[g.nt]);
+    g.wih[g.nt] = (float)wi;
+    g.wil[g.nt] = (float)(wi - (double)g.wih[g.nt]);
     ++g.nt;
+  }
+  // terms of equal weight next to each other (fval_df counts them as a run)
+  for (PauliGroup& g : groups) {
+    std::vector<int> ord(g.nt);
+    for (int i = 0; i < g.nt; ++i) ord[i] = i;
+    auto key = [&](int i) { return std::make_tuple(g.wrh[i], g.wrl[i], g.wih[i], g.wil[i]); };
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return key(a) < key(b); });
+    PauliGroup s = g;
+    for (int i = 0; i < g.nt; ++i) {
+      s.z[i] = g.z[ord[i]];
+      s.wrh[i] = g.wrh[ord[i]];
+      s.wrl[i] = g.wrl[ord[i]];
+      s.wih[i] = g.wih[ord[i]];
+      s.wil[i] = g.wil[ord[i]];
+    }
+    g = s;
   }
   return groups;
 }

@@ -1,7 +1,7 @@
 // Reductions over the state vector: norm, inner product, Pauli expectation.
 //
-// Each thread accumulates in FP64 over a grid-stride range of 16-byte
-// packets; warps combine with shuffles, CTAs through shared memory, and the
+// Each thread accumulates over a grid-stride range of elements in
+// double-float, flushed into FP64 (see kU); warps combine in FP64 with shuffles, CTAs through shared memory, and the
 // per-CTA partials are summed by one CTA in index order.  The grid size
 // depends only on the problem size, so results are bitwise reproducible.
 //
@@ -14,6 +14,7 @@
 // h = highest set bit of m), each amplitude read once.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 #include "pauli.cuh"
 
@@ -53,36 +54,101 @@ unsigned red_grid(u64 npk) {
   return (unsigned)(g ? g : 1);
 }
 
+// Per-element arithmetic stays off the FP64 pipe (about 1/64 of FP32 on
+// GB300): values enter as double-float (complex64: (x, 0); complex128: its
+// (hi, lo) split, integer operations only), products are formed with their
+// exact rounding errors (df_mul), and each thread sums them in double-float,
+// flushing into its FP64 accumulator every kU elements.  Within a flush
+// interval the high part's rounding errors are captured exactly (TwoSum) and
+// only the low part rounds (~2^-24 of a few error terms): FP64-level
+// accuracy, with 2 FP64 additions per kU elements.  Loads are unrolled kU
+// deep so that each thread keeps kU independent 16-byte loads in flight.
+constexpr int kU = 4;
+
+__device__ __forceinline__ dfl to_df(float x) { return dfl{x, 0.f}; }
+__device__ __forceinline__ dfl to_df(double x) { return d2df(x); }
+
+__device__ __forceinline__ void df_flush(double& acc, dfl& v) {
+  acc += (double)v.h;
+  acc += (double)v.l;
+  v = dfl{0.f, 0.f};
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_norm2(const R* __restrict__ a, u64 npk, double2* part) {
   constexpr int V = PK<R>::V;
+  const u64 stride = (u64)gridDim.x * kThreads;
   double s = 0.0, dummy = 0.0;
-  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
+  dfl acc{0.f, 0.f};
+  u64 p = (u64)blockIdx.x * kThreads + threadIdx.x;
+  for (; p + (kU - 1) * stride < npk; p += kU * stride) {
+    R v[kU][V];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) ld16(a + (p + u * stride) * V, v[u]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        const dfl x = to_df(v[u][c]);
+        df_acc(acc, df_mul(x, x));
+      }
+    df_flush(s, acc);
+  }
+  for (; p < npk; p += stride) {
     R v[V];
     ld16(a + p * V, v);
 #pragma unroll
-    for (int c = 0; c < V; ++c) s += (double)v[c] * (double)v[c];
+    for (int c = 0; c < V; ++c) {
+      const dfl x = to_df(v[c]);
+      df_acc(acc, df_mul(x, x));
+    }
   }
+  df_flush(s, acc);
   block_sum2(s, dummy);
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(s, 0.0);
+}
+
+// conj(a) b = (ar br + ai bi) + i (ar bi - ai br), reals c, c + 1 of a packet
+template <typename R>
+__device__ __forceinline__ void inner_acc(const R* va, const R* vb, int c, dfl& re, dfl& im) {
+  const dfl ar = to_df(va[c]), ai = to_df(va[c + 1]), br = to_df(vb[c]), bi = to_df(vb[c + 1]);
+  df_acc(re, df_mul(ar, br));
+  df_acc(re, df_mul(ai, bi));
+  df_acc(im, df_mul(ar, bi));
+  df_acc(im, df_mul(dfl{-ai.h, -ai.l}, br));
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_inner(const R* __restrict__ a, const R* __restrict__ b, u64 npk,
                                                     double2* part) {
   constexpr int V = PK<R>::V;
+  const u64 stride = (u64)gridDim.x * kThreads;
   double sr = 0.0, si = 0.0;
-  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
+  dfl re{0.f, 0.f}, im{0.f, 0.f};
+  u64 p = (u64)blockIdx.x * kThreads + threadIdx.x;
+  for (; p + (kU - 1) * stride < npk; p += kU * stride) {
+    R va[kU][V], vb[kU][V];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      ld16(a + (p + u * stride) * V, va[u]);
+      ld16(b + (p + u * stride) * V, vb[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int c = 0; c < V; c += 2) inner_acc(va[u], vb[u], c, re, im);
+    df_flush(sr, re);
+    df_flush(si, im);
+  }
+  for (; p < npk; p += stride) {
     R va[V], vb[V];
     ld16(a + p * V, va);
     ld16(b + p * V, vb);
 #pragma unroll
-    for (int c = 0; c < V; c += 2) {
-      const double ar = va[c], ai = va[c + 1], br = vb[c], bi = vb[c + 1];
-      sr += ar * br + ai * bi;   // conj(a) b
-      si += ar * bi - ai * br;
-    }
+    for (int c = 0; c < V; c += 2) inner_acc(va, vb, c, re, im);
   }
+  df_flush(sr, re);
+  df_flush(si, im);
   block_sum2(sr, si);
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
 }
@@ -102,41 +168,117 @@ __global__ void __launch_bounds__(kThreads) k_final(const double2* part, int n, 
   }
 }
 
+// acc += w f, w and f complex double-float
+__device__ __forceinline__ void cacc(dfl& sr, dfl& si, dfl wr, dfl wi, dfl fr, dfl fi) {
+  df_acc(sr, df_mul(wr, fr));
+  df_acc(sr, df_mul(dfl{-wi.h, -wi.l}, fi));
+  df_acc(si, df_mul(wr, fi));
+  df_acc(si, df_mul(wi, fr));
+}
+
+template <typename R> struct AmpV;
+template <> struct AmpV<float> { typedef float2 T; };
+template <> struct AmpV<double> { typedef double2 T; };
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_pauli(const R* __restrict__ a, int n, const __grid_constant__ PauliGroup g,
                                                     double2* part) {
+  typedef typename AmpV<R>::T A;
+  const A* av = reinterpret_cast<const A*>(a);
   double sr = 0.0, si = 0.0;
+  dfl ar{0.f, 0.f}, ai{0.f, 0.f};
   const u64 N = u64(1) << n;
+  const u64 stride = (u64)gridDim.x * kThreads;
+  u64 i = (u64)blockIdx.x * kThreads + threadIdx.x;
   if (g.m == 0) {
-    for (u64 x = (u64)blockIdx.x * kThreads + threadIdx.x; x < N; x += (u64)gridDim.x * kThreads) {
-      const double ar = a[2 * x], ai = a[2 * x + 1];
-      double fr, fi;
-      fval(g, x, fr, fi);
-      const double p = ar * ar + ai * ai;
-      sr += p * fr;
-      si += p * fi;
+    // sum_x |a_x|^2 f(x); kU elements per iteration, loads first
+    auto term = [&](u64 x, A v) {
+      const dfl xr = to_df(v.x), xi = to_df(v.y);
+      dfl fr, fi;
+      fval_df(g, x, fr, fi);
+      dfl w = df_mul(xr, xr);
+      df_acc(w, df_mul(xi, xi));
+      df_acc(ar, df_mul(w, fr));
+      df_acc(ai, df_mul(w, fi));
+    };
+    for (; i + (kU - 1) * stride < N; i += kU * stride) {
+      A v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) v[u] = av[i + u * stride];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) term(i + u * stride, v[u]);
+      df_flush(sr, ar);
+      df_flush(si, ai);
     }
+    for (; i < N; i += stride) term(i, av[i]);
   } else {
+    // pairs {x, y = x ^ m}, x with bit h clear:
+    //   conj(a_y) a_x f(x) + conj(a_x) a_y f(y)
     const u64 half = N >> 1;
     const u64 lo_mask = (u64(1) << g.h) - 1;
-    for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < half; i += (u64)gridDim.x * kThreads) {
-      const u64 x = ((i & ~lo_mask) << 1) | (i & lo_mask);  // bit h clear
-      const u64 y = x ^ g.m;
-      const double xr = a[2 * x], xi = a[2 * x + 1], yr = a[2 * y], yi = a[2 * y + 1];
-      double fr, fi;
-      // term x: conj(a_y) a_x f(x)
-      fval(g, x, fr, fi);
-      double pr = yr * xr + yi * xi, pi = yr * xi - yi * xr;
-      sr += pr * fr - pi * fi;
-      si += pr * fi + pi * fr;
-      // term y: conj(a_x) a_y f(y)
-      fval(g, y, fr, fi);
-      pr = xr * yr + xi * yi;
-      pi = xr * yi - xi * yr;
-      sr += pr * fr - pi * fi;
-      si += pr * fi + pi * fr;
+    auto xof = [&](u64 k) { return ((k & ~lo_mask) << 1) | (k & lo_mask); };
+    auto term = [&](u64 x, A vx, A vy) {
+      const dfl xr = to_df(vx.x), xi = to_df(vx.y), yr = to_df(vy.x), yi = to_df(vy.y);
+      // conj(a_y) a_x = (yr xr + yi xi) + i (yr xi - yi xr); conj(a_x) a_y is its conjugate
+      dfl pr = df_mul(yr, xr), pi = df_mul(yr, xi);
+      df_acc(pr, df_mul(yi, xi));
+      df_acc(pi, df_mul(dfl{-yi.h, -yi.l}, xr));
+      dfl fr, fi;
+      fval_df(g, x, fr, fi);
+      cacc(ar, ai, pr, pi, fr, fi);
+      fval_df(g, x ^ g.m, fr, fi);
+      cacc(ar, ai, pr, dfl{-pi.h, -pi.l}, fr, fi);
+    };
+    // one term: f(y) = s_m f(x), s_m = (-1)^popcount(m & z), so the pair gives
+    // w s(x) (p + s_m conj(p)) = 2 w s(x) Re p (s_m = 1) or 2 i w s(x) Im p
+    const bool one = g.nt == 1;
+    const bool sm_odd = one && (__popcll(g.m & g.z[0]) & 1);
+    const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
+    auto term1 = [&](u64 x, A vx, A vy) {
+      const dfl xr = to_df(vx.x), xi = to_df(vx.y), yr = to_df(vy.x), yi = to_df(vy.y);
+      dfl c;
+      if (!sm_odd) {  // Re p = yr xr + yi xi
+        c = df_mul(yr, xr);
+        df_acc(c, df_mul(yi, xi));
+      } else {        // Im p = yr xi - yi xr
+        c = df_mul(yr, xi);
+        df_acc(c, df_mul(dfl{-yi.h, -yi.l}, xr));
+      }
+      if (__popcll(x & g.z[0]) & 1) c = dfl{-c.h, -c.l};
+      if (!sm_odd) {  // (w_r + i w_i) c
+        df_acc(ar, df_mul(w_r, c));
+        df_acc(ai, df_mul(w_i, c));
+      } else {        // (w_r + i w_i) i c
+        df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
+        df_acc(ai, df_mul(w_r, c));
+      }
+    };
+    for (; i + (kU - 1) * stride < half; i += kU * stride) {
+      A vx[kU], vy[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const u64 x = xof(i + u * stride);
+        vx[u] = av[x];
+        vy[u] = av[x ^ g.m];
+      }
+      if (one) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) term1(xof(i + u * stride), vx[u], vy[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) term(xof(i + u * stride), vx[u], vy[u]);
+      }
+      df_flush(sr, ar);
+      df_flush(si, ai);
+    }
+    for (; i < half; i += stride) {
+      const u64 x = xof(i);
+      if (one) term1(x, av[x], av[x ^ g.m]);
+      else term(x, av[x], av[x ^ g.m]);
     }
   }
+  df_flush(sr, ar);
+  df_flush(si, ai);
   block_sum2(sr, si);
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
 }
