@@ -11,22 +11,33 @@
 // (dE/dt = 2 Re <lambda_l| (-i P/2) |psi_l> = Im <lambda_l|P|psi_l> with
 // psi_l, lambda_l the states right after gate l.)
 //
+// The reverse sweep runs in steps (build_sweep):
+//  * a run of consecutive diagonal gates in one pass (k_adj_diag): their
+//    trainable RZ gradients all come from the state at the run's end, since
+//    the run's diagonal gates commute with each Z_q;
+//  * a layer of one-qubit gates on distinct qubits in one pass (k_adj_layer):
+//    each generator commutes with the layer's other gates, so all gradient
+//    terms come from the group's values before any of the layer is undone;
+//  * any other trainable gate (k_adj_1q), any other fixed gate (per-gate
+//    kernels).
+//
 // Parameter sets are processed Bc at a time.  psi and lambda of the chunk live
 // in one buffer [psi_0 .. psi_{Bc-1}, lambda_0 .. lambda_{Bc-1}], which is
 // itself a state of n + log2(Bc) + 1 qubits: a fixed gate on qubits < n is
-// un-applied to all 2 Bc vectors by one launch of the per-gate kernel, and a
-// trainable gate by one launch of k_adj_1q over (pairs, set).  Bc is the
-// largest power of two <= batch whose 2 Bc vectors fit a budget (adj_chunk).
-// With Bc = 1 psi is the caller's state and lambda a second vector.
+// un-applied to all 2 Bc vectors by one launch of the per-gate kernel, and the
+// sweep kernels run over (elements, set).  Bc is the largest power of two
+// <= batch whose 2 Bc vectors fit a budget (adj_chunk).  With Bc = 1 psi is
+// the caller's state and lambda a second vector.
 //
 // Arithmetic: complex64 in FP32; complex128 in double-float, with psi and
 // lambda held in double-float storage for the whole reverse sweep (each FP64
 // value as its (hi, lo) float pair in the same 8 bytes, so an amplitude is one
-// float4 and no kernel converts).  Per-pair gradient products are FP32
+// float4 and no kernel converts).  Per-element gradient products are FP32
 // (complex64) or double-float (complex128), summed per thread in
 // double-float; CTA partials are summed in FP64 in a fixed order.
-#include <cmath>
+#include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <map>
 #include <vector>
 
@@ -121,6 +132,220 @@ __global__ void __launch_bounds__(kAT) k_adj_1q(V* __restrict__ psi, V* __restri
   if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = g;
 }
 
+// A run of consecutive diagonal gates (Z, S, T, P, RZ, CZ, CP) of the reverse
+// sweep in one pass.  Every trainable RZ_q in the run has the gradient
+// Im <lambda|Z_q|psi> on the state at the run's end: the run's other gates
+// are diagonal, commute with Z_q and cancel in <lambda|D Z_q D^dagger|psi>.  So
+// the pass takes all of them from one product conj(lambda_x) psi_x, then
+// multiplies psi_x and lambda_x by the run's U^dagger diagonal, a product of
+// one factor per gate (its entry for the gate's bits of x).
+constexpr int kRunF = 64;  // factors per run
+constexpr int kRunG = 24;  // trainable gates per run
+struct DRun {
+  int nf, ng;
+  int nlo;                   // factors [0, nlo) act on qubits below the launch's stride bits only
+  int q0[kRunF], q1[kRunF];  // q1 < 0: one-qubit factor
+  int sign[kRunF];           // 1: -1 when all its bits are set (CZ, Z), else 1 (no table entry used)
+  int gq[kRunG];             // qubit of each trainable RZ, in slot order
+};
+// one factor's U^dagger diagonal entries d[r] (r = bit q0 | bit q1 << 1), double-float
+struct DFac {
+  float rh[4], rl[4], ih[4], il[4];
+};
+
+__device__ __forceinline__ dfl im_conj_mul(float2 l, float2 p) {  // Im(conj(l) p)
+  return dfl{__fmaf_rn(l.x, p.y, -l.y * p.x), 0.0f};
+}
+__device__ __forceinline__ dfl im_conj_mul(float4 l, float4 p) {
+  return dot2(l.x, l.y, p.z, p.w, -l.z, -l.w, p.x, p.y);
+}
+__device__ __forceinline__ void vneg(float2& v) { v = make_float2(-v.x, -v.y); }
+__device__ __forceinline__ void vneg(float4& v) { v = make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ void fac_mul(const DFac& F, int r, float2& v) {
+  const float zr = F.rh[r], zi = F.ih[r];
+  v = make_float2(__fmaf_rn(zr, v.x, -zi * v.y), __fmaf_rn(zr, v.y, zi * v.x));
+}
+__device__ __forceinline__ void fac_mul(const DFac& F, int r, float4& v) {
+  const float zh[2] = {F.rh[r], F.ih[r]}, zl[2] = {F.rl[r], F.il[r]};
+  cdf a{v.x, v.y, v.z, v.w};
+  cmul_df(zh, zl, a);
+  v = make_float4(a.rh, a.rl, a.ih, a.il);
+}
+
+// complex scalar in double-float (complex64 uses the high parts only)
+struct CZf {
+  float rh, rl, ih, il;
+};
+__device__ __forceinline__ void cz_mul(CZf& z, const DFac& F, int r, float2*) {  // z *= d[r], FP32
+  const float fr = F.rh[r], fi = F.ih[r];
+  const float zr = __fmaf_rn(z.rh, fr, -z.ih * fi);
+  z.ih = __fmaf_rn(z.rh, fi, z.ih * fr);
+  z.rh = zr;
+}
+__device__ __forceinline__ void cz_mul(CZf& z, const DFac& F, int r, float4*) {  // double-float
+  const float zh[2] = {F.rh[r], F.ih[r]}, zl[2] = {F.rl[r], F.il[r]};
+  cdf a{z.rh, z.rl, z.ih, z.il};
+  cmul_df(zh, zl, a);
+  z = CZf{a.rh, a.rl, a.ih, a.il};
+}
+__device__ __forceinline__ void cz_apply(const CZf& z, float2& v) {
+  v = make_float2(__fmaf_rn(z.rh, v.x, -z.ih * v.y), __fmaf_rn(z.rh, v.y, z.ih * v.x));
+}
+__device__ __forceinline__ void cz_apply(const CZf& z, float4& v) {
+  const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
+  cdf a{v.x, v.y, v.z, v.w};
+  cmul_df(zh, zl, a);
+  v = make_float4(a.rh, a.rl, a.ih, a.il);
+}
+
+// The grid's stride is 2^lgs (a power of two), so the bits of x below lgs
+// are this thread's constants: the factors on those bits (the first nlo)
+// are multiplied once into a per-thread scalar, and a gradient whose qubit is
+// below lgs is +-(the thread's plain sum).  Only factors and gradients on
+// higher qubits are evaluated per element.
+template <typename V>
+__global__ void __launch_bounds__(kAT) k_adj_diag(V* __restrict__ psi, V* __restrict__ lam, u64 N,
+                                                  const __grid_constant__ DRun R, const DFac* __restrict__ tab,
+                                                  double* __restrict__ part, int Bc, int lgs) {
+  const int b = blockIdx.y;
+  V* ps = psi + N * b;
+  V* lm = lam + N * b;
+  const DFac* T = tab + (size_t)b * R.nf;
+  const u64 x0 = (u64)blockIdx.x * kAT + threadIdx.x;
+  const u64 stride = (u64)gridDim.x * kAT;
+  // per-thread constant part of the phase
+  CZf zc{1.0f, 0.0f, 0.0f, 0.0f};
+  bool neg0 = false, zc_one = true;
+  for (int f = 0; f < R.nlo; ++f) {
+    const int r = (int)((x0 >> R.q0[f]) & 1) | (R.q1[f] >= 0 ? (int)((x0 >> R.q1[f]) & 1) << 1 : 0);
+    if (R.sign[f]) {
+      neg0 ^= r == (R.q1[f] >= 0 ? 3 : 1);
+    } else {
+      cz_mul(zc, T[f], r, (V*)nullptr);
+      zc_one = false;
+    }
+  }
+  dfl tot{0.0f, 0.0f};
+  dfl acc[kRunG];
+#pragma unroll
+  for (int s = 0; s < kRunG; ++s) acc[s] = dfl{0.0f, 0.0f};
+  for (u64 x = x0; x < N; x += stride) {
+    V p = ps[x], l = lm[x];
+    const dfl c = im_conj_mul(l, p);
+    df_acc(tot, c);
+#pragma unroll
+    for (int s = 0; s < kRunG; ++s)
+      if (s < R.ng && R.gq[s] >= lgs) df_acc(acc[s], ((x >> R.gq[s]) & 1) ? dfl{-c.h, -c.l} : c);
+    bool neg = neg0;
+    if (!zc_one) {
+      cz_apply(zc, p);
+      cz_apply(zc, l);
+    }
+    for (int f = R.nlo; f < R.nf; ++f) {
+      const int r = (int)((x >> R.q0[f]) & 1) | (R.q1[f] >= 0 ? (int)((x >> R.q1[f]) & 1) << 1 : 0);
+      if (R.sign[f]) {
+        neg ^= r == (R.q1[f] >= 0 ? 3 : 1);
+      } else {
+        fac_mul(T[f], r, p);
+        fac_mul(T[f], r, l);
+      }
+    }
+    if (neg) {
+      vneg(p);
+      vneg(l);
+    }
+    ps[x] = p;
+    lm[x] = l;
+  }
+#pragma unroll
+  for (int s = 0; s < kRunG; ++s) {
+    if (s < R.ng) {  // uniform: every thread takes part in each block sum
+      dfl v = acc[s];
+      if (R.gq[s] < lgs) v = ((x0 >> R.gq[s]) & 1) ? dfl{-tot.h, -tot.l} : tot;
+      const double g = a_block_sum((double)v.h + (double)v.l);
+      if (threadIdx.x == 0) part[((size_t)s * Bc + b) * gridDim.x + blockIdx.x] = g;
+    }
+  }
+}
+
+// A layer of one-qubit gates on M distinct qubits (trainable RX/RY or fixed
+// non-diagonal gates) in one pass.  Gates on distinct qubits commute, and a
+// gate's generator commutes with the layer's other gates, so every gradient
+// term is taken from the group's values before any of the layer is
+// un-applied; then each U^dagger is applied along its bit of the group.
+// A thread holds the 2^M amplitudes of psi and lambda over the layer's
+// qubits (x with those bits clear, plus every combination).
+constexpr int kLayerMax = 4;
+template <typename Mat>
+struct LayerArgs {
+  Ins ins;               // zero insertion at the layer's qubits (sorted)
+  int q[kLayerMax];      // qubit of gate j
+  int gen[kLayerMax];    // 0: fixed (matrix in fixed[j]); 1, 2, 3: trainable X, Y, Z generator
+  int slot[kLayerMax];   // gradient slot (trainable)
+  Mat fixed[kLayerMax];  // U^dagger of fixed gates
+};
+
+template <typename V, typename Mat, int M>
+__global__ void __launch_bounds__(kAT) k_adj_layer(V* __restrict__ psi, V* __restrict__ lam, u64 N,
+                                                   const __grid_constant__ LayerArgs<Mat> A,
+                                                   const Mat* __restrict__ mats, double* __restrict__ part, int Bc) {
+  constexpr int NR = 1 << M;
+  const int b = blockIdx.y;
+  V* ps = psi + N * b;
+  V* lm = lam + N * b;
+  Mat U[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) U[j] = A.gen[j] ? mats[(size_t)A.slot[j] * Bc + b] : A.fixed[j];
+  dfl acc[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) acc[j] = dfl{0.0f, 0.0f};
+  u64 off[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    u64 o = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) o |= (u64)((r >> j) & 1) << A.q[j];
+    off[r] = o;
+  }
+  const u64 ngroups = N >> M;
+  for (u64 gi = (u64)blockIdx.x * kAT + threadIdx.x; gi < ngroups; gi += (u64)gridDim.x * kAT) {
+    const u64 base = expand(gi, A.ins);
+    V p[NR], l[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      p[r] = ps[base | off[r]];
+      l[r] = lm[base | off[r]];
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (!A.gen[j]) continue;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (!((r >> j) & 1)) df_acc(acc[j], grad_term(A.gen[j], l[r], l[r | (1 << j)], p[r], p[r | (1 << j)]));
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (!((r >> j) & 1)) {
+          upd(U[j], p[r], p[r | (1 << j)]);
+          upd(U[j], l[r], l[r | (1 << j)]);
+        }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      ps[base | off[r]] = p[r];
+      lm[base | off[r]] = l[r];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    if (A.gen[j]) {  // uniform
+      const double g = a_block_sum((double)acc[j].h + (double)acc[j].l);
+      if (threadIdx.x == 0) part[((size_t)A.slot[j] * Bc + b) * gridDim.x + blockIdx.x] = g;
+    }
+  }
+}
+
 // H = sum_t c_t P_t with Pauli strings grouped by their X/Y mask m:
 // P|x> = i^{nY} (-1)^{popcount(x & z)} |x ^ m>, so
 //   (H psi)_x = sum_groups f_g(x ^ m_g) psi_{x ^ m_g},
@@ -199,12 +424,19 @@ __global__ void __launch_bounds__(kAT) k_slot_sums(const double* part, int G, do
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-unsigned adj_grid(u64 work) {
+// CTAs per parameter set for every kernel of the sweep (one partial-sum
+// layout): enough for the work, about the resident CTAs over the chunk's
+// sets (few CTAs, each looping, keep the per-CTA set-up and reduction tail
+// small), and a power of two so a thread's low index bits stay fixed.
+unsigned adj_grid(u64 work, int Bc) {
   const u64 per = (u64)kAT * 4;
   u64 g = (work + per - 1) / per;
-  const u64 cap = (u64)sm_count() * 8;
+  u64 cap = (u64)sm_count() * 4 / (u64)Bc;
+  if (cap < 1) cap = 1;
   if (g > cap) g = cap;
-  return (unsigned)(g ? g : 1);
+  unsigned p = 1;
+  while ((u64)p * 2 <= g) p *= 2;
+  return p;
 }
 
 // conjugate transpose of a 2x2 matrix
@@ -266,7 +498,156 @@ qs_status unapply_fixed(qs_state* v, const qs_gate_rec& g, bool dfl_layout) {
   return dfl_layout ? run_diag_dfl(v, g.q, 2, d) : run_diag(v, g.q, 2, d);
 }
 
+bool is_diag_kind(int k) {
+  return k == QS_GATE_Z || k == QS_GATE_S || k == QS_GATE_T || k == QS_GATE_RZ || k == QS_GATE_P ||
+         k == QS_GATE_CZ || k == QS_GATE_CP;
+}
+
+// The reverse sweep as steps: a trainable RX/RY (k_adj_1q), a fixed
+// non-diagonal gate (per-gate kernels), or a run of diagonal gates
+// (k_adj_diag).  Trainable gates get gradient slots in reverse order.
+struct RunInfo {
+  DRun R;
+  std::vector<int> gates;  // circuit indices, in reverse order (factor order)
+  size_t tab_off;          // first DFac of this run in the chunk's table (x Bc sets)
+  int slot_base;
+};
+struct LayerInfo {
+  int M;
+  int gi[kLayerMax], slot[kLayerMax];
+};
+struct SweepStep {
+  int kind;  // 0 trainable one-qubit, 1 fixed, 2 diagonal run, 3 layer of one-qubit gates
+  int gi, slot, run;
+};
+
+bool layer_kind(const qs_gate_rec& g) { return gate_arity(g.kind) == 1 && !is_diag_kind(g.kind); }
+
+void build_sweep(const qs_circuit* c, int Bc, int max_layer, int lgs, std::vector<SweepStep>& steps,
+                 std::vector<RunInfo>& runs, std::vector<LayerInfo>& layers, size_t& nfac) {
+  int slot = 0;
+  nfac = 0;
+  for (int gi = (int)c->gates.size() - 1; gi >= 0;) {
+    const qs_gate_rec& g = c->gates[gi];
+    if (layer_kind(g) && max_layer >= 2) {
+      // consecutive one-qubit non-diagonal gates on distinct qubits
+      LayerInfo li{};
+      unsigned long long used = 0;
+      int j = gi;
+      while (j >= 0 && li.M < max_layer && layer_kind(c->gates[j]) && !((used >> c->gates[j].q[0]) & 1)) {
+        used |= 1ull << c->gates[j].q[0];
+        li.gi[li.M++] = j;
+        --j;
+      }
+      if (li.M >= 2) {
+        for (int k = 0; k < li.M; ++k) li.slot[k] = c->gates[li.gi[k]].param_index >= 0 ? slot++ : -1;
+        steps.push_back(SweepStep{3, -1, -1, (int)layers.size()});
+        layers.push_back(li);
+        gi = j;
+        continue;
+      }
+    }
+    if (is_diag_kind(g.kind)) {
+      RunInfo ri{};
+      ri.slot_base = slot;
+      ri.tab_off = nfac;
+      while (gi >= 0 && is_diag_kind(c->gates[gi].kind) && ri.R.nf < kRunF) {
+        const qs_gate_rec& d = c->gates[gi];
+        if (d.param_index >= 0 && ri.R.ng == kRunG) break;
+        const int f = ri.R.nf++;
+        ri.R.q0[f] = d.q[0];
+        ri.R.q1[f] = gate_arity(d.kind) == 2 ? d.q[1] : -1;
+        ri.R.sign[f] = (d.kind == QS_GATE_CZ || d.kind == QS_GATE_Z) ? 1 : 0;
+        if (d.param_index >= 0) ri.R.gq[ri.R.ng++] = d.q[0];
+        ri.gates.push_back(gi);
+        --gi;
+      }
+      // factors on qubits below the stride bits first (they commute)
+      {
+        std::vector<int> order(ri.R.nf);
+        for (int f = 0; f < ri.R.nf; ++f) order[f] = f;
+        auto low = [&](int f) { return ri.R.q0[f] < lgs && ri.R.q1[f] < lgs; };
+        std::stable_partition(order.begin(), order.end(), low);
+        DRun R2 = ri.R;
+        std::vector<int> g2(ri.R.nf);
+        for (int f = 0; f < ri.R.nf; ++f) {
+          R2.q0[f] = ri.R.q0[order[f]];
+          R2.q1[f] = ri.R.q1[order[f]];
+          R2.sign[f] = ri.R.sign[order[f]];
+          g2[f] = ri.gates[order[f]];
+        }
+        R2.nlo = 0;
+        while (R2.nlo < R2.nf && low(order[R2.nlo])) ++R2.nlo;
+        ri.R = R2;
+        ri.gates = g2;
+      }
+      slot += ri.R.ng;
+      nfac += (size_t)ri.R.nf * Bc;
+      steps.push_back(SweepStep{2, -1, ri.slot_base, (int)runs.size()});
+      runs.push_back(std::move(ri));
+      continue;
+    }
+    if (g.param_index >= 0) steps.push_back(SweepStep{0, gi, slot++, -1});
+    else steps.push_back(SweepStep{1, gi, -1, -1});
+    --gi;
+  }
+}
+
+// U^dagger diagonal of a diagonal gate with angle p (p[0] replaced for a
+// trainable gate), as a double-float factor
+DFac diag_factor(const qs_gate_rec& g, const double* p) {
+  double m[32];
+  const int nq = gate_matrix(g.kind, p, m);
+  const int D = 1 << nq;
+  DFac F{};
+  for (int r = 0; r < 4; ++r) {
+    const int rr = r < D ? r : 0;
+    const double re = m[2 * (rr * D + rr)], im = -m[2 * (rr * D + rr) + 1];  // conjugate
+    F.rh[r] = (float)re;
+    F.rl[r] = (float)(re - (double)F.rh[r]);
+    F.ih[r] = (float)im;
+    F.il[r] = (float)(im - (double)F.ih[r]);
+  }
+  return F;
+}
+
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <typename V, typename Mat>
+qs_status launch_layer(const LayerInfo& li, const qs_circuit* c, V* psi, V* lam, u64 N, unsigned G, int cnt,
+                       const Mat* mats, double* part, int Bc, cudaStream_t stream) {
+  LayerArgs<Mat> A{};
+  int qs_sorted[kLayerMax];
+  for (int j = 0; j < li.M; ++j) {
+    const qs_gate_rec& g = c->gates[li.gi[j]];
+    A.q[j] = g.q[0];
+    qs_sorted[j] = g.q[0];
+    if (g.param_index >= 0) {
+      A.gen[j] = g.kind == QS_GATE_RX ? 1 : g.kind == QS_GATE_RY ? 2 : 3;
+      A.slot[j] = li.slot[j];
+    } else {
+      double m[32], md[8];
+      gate_matrix(g.kind, g.p, m);
+      dagger2(m, md);
+      A.fixed[j] = to_mat(md, typename std::conditional<sizeof(V) == 8, float, double>::type(0));
+    }
+  }
+  std::sort(qs_sorted, qs_sorted + li.M);
+  A.ins.k = li.M;
+  A.ins.set = 0;
+  for (int j = 0; j < li.M; ++j) A.ins.pos[j] = qs_sorted[j];
+  const dim3 grid(G, cnt);
+  if (li.M == 2) {
+    k_adj_layer<V, Mat, 2><<<grid, kAT, 0, stream>>>(psi, lam, N, A, mats, part, Bc);
+  } else if constexpr (sizeof(V) == 8) {  // complex64 layers of up to 4 (registers)
+    if (li.M == 3) k_adj_layer<V, Mat, 3><<<grid, kAT, 0, stream>>>(psi, lam, N, A, mats, part, Bc);
+    else if (li.M == 4) k_adj_layer<V, Mat, 4><<<grid, kAT, 0, stream>>>(psi, lam, N, A, mats, part, Bc);
+    else return fail(QS_EINVAL, "adjoint layer of %d gates", li.M);
+  } else {
+    return fail(QS_EINVAL, "adjoint layer of %d gates", li.M);
+  }
+  return launch_ok("k_adj_layer");
+}
 
 template <typename R>
 qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, int nparam, int batch, int nterms,
@@ -280,7 +661,7 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
   const int Bc = adj_chunk(batch, sbytes, df);
   int lb = 0;
   while ((1 << lb) < Bc) ++lb;
-  const unsigned G = adj_grid(N >> 1);
+  const unsigned G = adj_grid(N >> 1, Bc);
 
   // trainable gates in reverse order: slot s <-> gate index
   std::vector<int> slot_gate;
@@ -288,6 +669,13 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
     if (c->gates[gi].param_index >= 0) slot_gate.push_back(gi);
   const int nslots = (int)slot_gate.size() + 1;  // trainable gates, then the energy
   const int eslot = nslots - 1;
+  std::vector<SweepStep> steps;
+  std::vector<RunInfo> runs;
+  std::vector<LayerInfo> layers;
+  size_t nfac = 0;
+  int lgs = 0;  // log2 of a sweep kernel's grid stride
+  while ((1ull << lgs) < (u64)G * kAT) ++lgs;
+  build_sweep(c, Bc, df ? 2 : 3, lgs, steps, runs, layers, nfac);  // widths measured best
 
   // Hamiltonian grouped by X/Y mask, in order of first appearance
   std::vector<HGroup> hg;
@@ -323,7 +711,8 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
   const size_t sums_b = up256(sizeof(double) * (size_t)nslots * Bc);
   const size_t mats_b = up256(sizeof(Mat) * (size_t)nslots * Bc);
   const size_t grp_b = up256(sizeof(HGroup) * hg.size()), trm_b = up256(sizeof(HTerm) * ht.size());
-  const size_t bytes = vec_b + part_b + sums_b + mats_b + grp_b + trm_b;
+  const size_t fac_b = up256(sizeof(DFac) * (nfac > 0 ? nfac : 1));
+  const size_t bytes = vec_b + part_b + sums_b + mats_b + grp_b + trm_b + fac_b;
   char* dev = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), bytes, st->stream);
   if (e != cudaSuccess) return fail(QS_ENOMEM, "qs_adjoint_grad: %zu bytes: %s", bytes, cudaGetErrorString(e));
@@ -334,6 +723,8 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
   Mat* mats = reinterpret_cast<Mat*>(dev + vec_b + part_b + sums_b);
   HGroup* dgrp = reinterpret_cast<HGroup*>(dev + vec_b + part_b + sums_b + mats_b);
   HTerm* dtrm = reinterpret_cast<HTerm*>(dev + vec_b + part_b + sums_b + mats_b + grp_b);
+  DFac* dfac = reinterpret_cast<DFac*>(dev + vec_b + part_b + sums_b + mats_b + grp_b + trm_b);
+  std::vector<DFac> hfac(nfac);
   qs_status rc = QS_OK;
   e = cudaMemcpyAsync(dgrp, hg.data(), sizeof(HGroup) * hg.size(), cudaMemcpyHostToDevice, st->stream);
   if (e == cudaSuccess)
@@ -368,16 +759,26 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
       qs_plan_destroy(plan);
       for (size_t s = 0; s < slot_gate.size(); ++s) {  // U^dagger of each trainable gate
         const qs_gate_rec& g = cb.gates[slot_gate[s]];
+        if (is_diag_kind(g.kind)) continue;  // in a diagonal run's table
         double m[32], md[8];
         gate_matrix(g.kind, g.p, m);
         dagger2(m, md);
         hmats[s * Bc + b] = to_mat(md, R(0));
       }
+      for (const RunInfo& ri : runs)  // diagonal-run factors of this set
+        for (int f = 0; f < ri.R.nf; ++f) {
+          const qs_gate_rec& g = cb.gates[ri.gates[f]];
+          hfac[ri.tab_off + (size_t)b * ri.R.nf + f] = diag_factor(g, g.p);
+        }
     }
     if (rc != QS_OK) break;
     if (!slot_gate.empty()) {
       e = cudaMemcpyAsync(mats, hmats.data(), sizeof(Mat) * hmats.size(), cudaMemcpyHostToDevice, st->stream);
       if (e != cudaSuccess) { rc = cuda_fail(e, "qs_adjoint_grad: matrix upload"); break; }
+    }
+    if (nfac > 0) {
+      e = cudaMemcpyAsync(dfac, hfac.data(), sizeof(DFac) * nfac, cudaMemcpyHostToDevice, st->stream);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "qs_adjoint_grad: diagonal factor upload"); break; }
     }
     if (df) {  // psi of the chunk to double-float storage; lambda is written in it
       rc = on_view(st, psi, n + lb, [&](qs_state* v) { return run_layout_dfl(v, true); });
@@ -389,16 +790,28 @@ qs_status adjoint_run(qs_state* st, const qs_circuit* c, const double* theta, in
                                                           part + (size_t)eslot * Bc * G);
     if ((rc = launch_ok("k_hamiltonian")) != QS_OK) break;
     // reverse sweep
-    int slot = 0;
-    for (int gi = (int)c->gates.size() - 1; gi >= 0 && rc == QS_OK; --gi) {
-      const qs_gate_rec& g = c->gates[gi];
-      if (g.param_index >= 0) {
+    for (size_t si = 0; si < steps.size() && rc == QS_OK; ++si) {
+      const SweepStep& sp = steps[si];
+      if (sp.kind == 2) {
+        const RunInfo& ri = runs[sp.run];
+        k_adj_diag<V><<<dim3(G, cnt), kAT, 0, st->stream>>>(reinterpret_cast<V*>(psi), reinterpret_cast<V*>(lam), N,
+                                                           ri.R, dfac + ri.tab_off, part + (size_t)ri.slot_base * Bc * G,
+                                                           Bc, lgs);
+        rc = launch_ok("k_adj_diag");
+        continue;
+      }
+      if (sp.kind == 3) {
+        rc = launch_layer<V, Mat>(layers[sp.run], c, reinterpret_cast<V*>(psi), reinterpret_cast<V*>(lam), N, G, cnt,
+                                  mats, part, Bc, st->stream);
+        continue;
+      }
+      const qs_gate_rec& g = c->gates[sp.gi];
+      if (sp.kind == 0) {
         const int gen = g.kind == QS_GATE_RX ? 1 : g.kind == QS_GATE_RY ? 2 : 3;
         k_adj_1q<V, Mat><<<dim3(G, cnt), kAT, 0, st->stream>>>(reinterpret_cast<V*>(psi), reinterpret_cast<V*>(lam), N,
-                                                               N >> 1, g.q[0], mats + (size_t)slot * Bc, gen,
-                                                               part + (size_t)slot * Bc * G);
+                                                               N >> 1, g.q[0], mats + (size_t)sp.slot * Bc, gen,
+                                                               part + (size_t)sp.slot * Bc * G);
         rc = launch_ok("k_adj_1q");
-        ++slot;
         continue;
       }
       for (size_t t = 0; t < targets.size() && rc == QS_OK; ++t)
