@@ -123,3 +123,30 @@ def test_adjoint_batched_sets(qs, dtype, tol, n, batch):
         e1, g1 = qs.adjoint_grad(qs.State(n, dtype), c, thetas[b:b + 1], terms)
         assert abs(e1[0] - e[b]) <= (1e-12 if dtype == "c128" else 1e-5) * max(1.0, abs(e_ref))
         assert rel(g1[0], g[b]) <= (1e-10 if dtype == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-3)])
+def test_adjoint_hea_tfim_sets_vs_oracle(qs, dtype, tol):
+    # the differentiation workload's shape (RY and RZ layers, CZ ladder,
+    # transverse-field Ising H, several parameter sets in one call) at a size
+    # the oracle runs in seconds; diagonal runs (CZ ladder + RZ layer) and
+    # one-qubit layers (RY) both take the fused sweep steps here
+    n, layers, batch = 16, 4, 6
+    circ, _ = W.hea(n, layers, 51)
+    thetas = np.stack([W.hea(n, layers, 51 + b)[1] for b in range(batch)])
+    terms = W.tfim(n)
+    e, g = qs.adjoint_grad(qs.State(n, dtype), qs.Circuit(circ), thetas, terms)
+    for b in (0, batch - 1):
+        cb = W.with_params(circ, thetas[b])
+        e_ref, g_ref = oracle.adjoint_grad(oracle.zero_state(n), cb, thetas.shape[1], terms)
+        assert abs(e[b] - e_ref) <= (1e-10 if dtype == "c128" else 1e-4) * max(1.0, abs(e_ref))
+        assert rel(g[b], g_ref) <= tol
+    # parameter shift on two parameters of the last set (oracle energies)
+    cb = W.with_params(circ, thetas[-1])
+    for j in (3, thetas.shape[1] - 2):
+        tp, tm = thetas[-1].copy(), thetas[-1].copy()
+        tp[j] += math.pi / 2
+        tm[j] -= math.pi / 2
+        ps = 0.5 * (oracle.expectation_of_circuit(n, W.with_params(circ, tp), terms)
+                    - oracle.expectation_of_circuit(n, W.with_params(circ, tm), terms))
+        assert abs(g[-1, j] - ps) <= (1e-9 if dtype == "c128" else 1e-3 * max(1.0, abs(ps)))
