@@ -202,6 +202,13 @@ qs_status qs_circuit_destroy(qs_circuit* c);
  * qs_adjoint_grad); -1 otherwise. */
 qs_status qs_circuit_add(qs_circuit* c, int kind, const int* qubits, int nq,
                          const double* params, int param_index);
+/* Append `count` gates at once (the same checks as qs_circuit_add, gate by
+ * gate; on an error the gates before the offending one stay appended and
+ * the status names its index).  Per gate i: kinds[i]; qubits[2 i], and
+ * qubits[2 i + 1] for two-qubit kinds; params[3 i .. 3 i + 2], of which the
+ * kind's 0, 1 or 3 angles are read; param_index[i] (NULL: all -1). */
+qs_status qs_circuit_add_many(qs_circuit* c, int count, const int* kinds, const int* qubits, const double* params,
+                              const int* param_index);
 /* Number of gates appended so far. */
 qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
 
@@ -209,7 +216,8 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * (one kernel per gate); QS_PLAN_TILED groups gates into shared-memory tile
  * passes; QS_PLAN_FUSED multiplies gates into dense blocks of at most
  * fuse_qubits qubits, each applied as one pass (complex64 blocks of 4 to 6
- * qubits run on the tensor cores, as qs_apply_fused).  tile_qubits: qubits resident per tile pass (0 = library default
+ * qubits run on the tensor cores, as qs_apply_fused).  tile_qubits: qubits
+ * resident per tile pass (0 = library default
  * for the dtype; at most 14 for QS_C64, 13 for QS_C128); low_qubits: qubits
  * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);
  * slot_qubits: qubits held in registers per stage inside a tile pass, 3 or

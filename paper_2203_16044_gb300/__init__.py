@@ -79,6 +79,7 @@ _SIGS = {
     "qs_circuit_create": ([ctypes.POINTER(_vp)], _int),
     "qs_circuit_destroy": ([_vp], _int),
     "qs_circuit_add": ([_vp, _int, _ip, _int, _dp, _int], _int),
+    "qs_circuit_add_many": ([_vp, _int, _ip, _ip, _dp, _ip], _int),
     "qs_circuit_size": ([_vp, _ip], _int),
     "qs_plan_build": ([_vp, _int, _int, ctypes.POINTER(PlanOpts), ctypes.POINTER(_vp)], _int),
     "qs_plan_stats_get": ([_vp, ctypes.POINTER(PlanStats)], _int),
@@ -292,8 +293,30 @@ class Circuit:
         h = _vp()
         _check(_lib.qs_circuit_create(ctypes.byref(h)), "qs_circuit_create")
         self._h = h
-        for g in gates:
-            self.add(g.name, g.qubits, g.params, getattr(g, "param_index", -1))
+        self.add_many(gates)
+
+    def add_many(self, gates):
+        """Append a sequence of gates (objects with name, qubits, params and
+        optionally param_index) in one call."""
+        gates = list(gates)
+        if not gates:
+            return
+        m = len(gates)
+        kinds = np.empty(m, dtype=np.int32)
+        qubits = np.zeros((m, 2), dtype=np.int32)
+        params = np.zeros((m, 3), dtype=np.float64)
+        pidx = np.full(m, -1, dtype=np.int32)
+        for i, g in enumerate(gates):
+            kinds[i] = GATE_KIND[g.name]
+            q = g.qubits
+            qubits[i, 0] = q[0]
+            if len(q) > 1:
+                qubits[i, 1] = q[1]
+            if len(g.params):
+                params[i, :len(g.params)] = g.params
+            pidx[i] = getattr(g, "param_index", -1)
+        _check(_lib.qs_circuit_add_many(self._h, m, _iptr(kinds), _iptr(qubits), _dptr(params), _iptr(pidx)),
+               "qs_circuit_add_many")
 
     @property
     def handle(self):

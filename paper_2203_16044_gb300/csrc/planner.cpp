@@ -16,6 +16,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "qs_internal.h"
@@ -149,6 +150,12 @@ qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
 namespace {
 typedef std::complex<double> cd;
 
+// complex multiply-add in plain real arithmetic (std::complex's operator*
+// takes the slow Annex G path for infinities and NaNs)
+inline cd cmul(cd a, cd b) {
+  return cd(a.real() * b.real() - a.imag() * b.imag(), a.real() * b.imag() + a.imag() * b.real());
+}
+
 void left_apply(std::vector<cd>& M, int k, const qs_gate_rec& g, const std::vector<int>& bq) {
   const int D = 1 << k;
   auto slot = [&](int q) { return (int)(std::find(bq.begin(), bq.end(), q) - bq.begin()); };
@@ -160,10 +167,12 @@ void left_apply(std::vector<cd>& M, int k, const qs_gate_rec& g, const std::vect
     for (int r0 = 0; r0 < D; ++r0) {
       if ((r0 >> a) & 1) continue;
       const int r1 = r0 | (1 << a);
+      cd* x = &M[(size_t)r0 * D];
+      cd* y = &M[(size_t)r1 * D];
       for (int c = 0; c < D; ++c) {
-        const cd x = M[r0 * D + c], y = M[r1 * D + c];
-        M[r0 * D + c] = u00 * x + u01 * y;
-        M[r1 * D + c] = u10 * x + u11 * y;
+        const cd xv = x[c], yv = y[c];
+        x[c] = cmul(u00, xv) + cmul(u01, yv);
+        y[c] = cmul(u10, xv) + cmul(u11, yv);
       }
     }
   } else {
@@ -171,17 +180,47 @@ void left_apply(std::vector<cd>& M, int k, const qs_gate_rec& g, const std::vect
     cd G[4][4];
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) G[i][j] = cd(m[2 * (i * 4 + j)], m[2 * (i * 4 + j) + 1]);
+    // diagonal (CZ, CP): scale rows; a 0/1 permutation (CNOT, SWAP): move rows
+    bool diag = true, perm = true;
+    int src[4];
+    for (int i = 0; i < 4; ++i) {
+      int ones = 0;
+      for (int j = 0; j < 4; ++j) {
+        if (i != j && G[i][j] != cd(0.0)) diag = false;
+        if (G[i][j] == cd(1.0)) { ++ones; src[i] = j; }
+        else if (G[i][j] != cd(0.0)) perm = false;
+      }
+      if (ones != 1) perm = false;
+    }
+    if (diag || perm) {
+      std::vector<cd> tmp(4 * (size_t)D);
+      for (int base = 0; base < D; ++base) {
+        if (((base >> a) & 1) || ((base >> b) & 1)) continue;
+        const int idx[4] = {base, base | (1 << a), base | (1 << b), base | (1 << a) | (1 << b)};
+        if (diag) {
+          for (int i = 0; i < 4; ++i) {
+            if (G[i][i] == cd(1.0)) continue;
+            cd* row = &M[(size_t)idx[i] * D];
+            for (int c = 0; c < D; ++c) row[c] = cmul(G[i][i], row[c]);
+          }
+        } else {
+          for (int i = 0; i < 4; ++i) std::copy_n(&M[(size_t)idx[i] * D], D, &tmp[(size_t)i * D]);
+          for (int i = 0; i < 4; ++i) std::copy_n(&tmp[(size_t)src[i] * D], D, &M[(size_t)idx[i] * D]);
+        }
+      }
+      return;
+    }
     for (int base = 0; base < D; ++base) {
       if (((base >> a) & 1) || ((base >> b) & 1)) continue;
       const int idx[4] = {base, base | (1 << a), base | (1 << b), base | (1 << a) | (1 << b)};
       for (int c = 0; c < D; ++c) {
-        cd v[4], w[4];
-        for (int j = 0; j < 4; ++j) v[j] = M[idx[j] * D + c];
+        cd v[4];
+        for (int j = 0; j < 4; ++j) v[j] = M[(size_t)idx[j] * D + c];
         for (int i = 0; i < 4; ++i) {
-          w[i] = 0.0;
-          for (int j = 0; j < 4; ++j) w[i] += G[i][j] * v[j];
+          cd w = 0.0;
+          for (int j = 0; j < 4; ++j) w += cmul(G[i][j], v[j]);
+          M[(size_t)idx[i] * D + c] = w;
         }
-        for (int i = 0; i < 4; ++i) M[idx[i] * D + c] = w[i];
       }
     }
   }
@@ -337,6 +376,23 @@ qs_status qs_circuit_add(qs_circuit* c, int kind, const int* qubits, int nq, con
   for (int i = 0; i < np; ++i) g.p[i] = params[i];
   g.param_index = param_index < 0 ? -1 : param_index;
   c->gates.push_back(g);
+  return QS_OK;
+}
+
+qs_status qs_circuit_add_many(qs_circuit* c, int count, const int* kinds, const int* qubits, const double* params,
+                              const int* param_index) {
+  if (!c || count < 0 || (count > 0 && (!kinds || !qubits || !params)))
+    return fail(QS_EINVAL, "qs_circuit_add_many: NULL argument or negative count");
+  c->gates.reserve(c->gates.size() + (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    const int arity = gate_arity(kinds[i]);
+    const qs_status st = qs_circuit_add(c, kinds[i], qubits + 2 * (size_t)i, arity < 0 ? 0 : arity,
+                                        params + 3 * (size_t)i, param_index ? param_index[i] : -1);
+    if (st != QS_OK) {
+      const std::string why = qs_last_error();  // copied: fail() rewrites the same buffer
+      return fail(st, "qs_circuit_add_many: gate %d: %s", i, why.c_str());
+    }
+  }
   return QS_OK;
 }
 
