@@ -389,6 +389,7 @@ def run_ours(args):
     dtypes = [args.dtype] + ([d for d in ("c64", "c128") if d != args.dtype] if args.both else [])
     circuit = qs.Circuit(circ)
     states = {}
+    e2e = None
     for dt in dtypes:
         mode_name, mode, fq = plan_mode(qs, args, dt)
         plan = qs.Plan(circuit, n, dt, mode=mode, fuse_qubits=fq)
@@ -432,6 +433,11 @@ def run_ours(args):
                        "gpu_launches": (st["passes"] + extra) * args.steps}
         states[dt] = state
         del plan
+        if dt == args.dtype and not args.no_e2e:
+            # end to end through the C ABI with host buffers, right after the
+            # headline (before the other dtype's runs)
+            _, mode_e, fq_e = plan_mode(qs, args, dt)
+            e2e = run_e2e(qs, torch, args, n, circ, mode_e, fq_e, device, world)
     # precision: infidelity of the headline run against complex128 on the GPU
     infid = None
     if "c64" in states and "c128" in states:
@@ -439,11 +445,6 @@ def run_ours(args):
         ov = torch.vdot(a64, states["c128"].tensor).item()
         infid = 1.0 - abs(ov) ** 2
         del a64
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        _, mode, fq = plan_mode(qs, args, args.dtype)
-        e2e = run_e2e(qs, torch, args, n, circ, mode, fq, device, world)
     extras = {}
     if not args.no_extras:
         extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
@@ -605,9 +606,9 @@ def c128_unfused(qs, torch, device, n, circuit):
 
 
 def run_e2e(qs, torch, args, n, circ, mode, fq, device, world):
-    """Per step: host state -> device (pinned, asynchronous), build and
-    compile the circuit meanwhile, run it, device -> host (pinned); timed on
-    the host around the whole call chain."""
+    """Per step: host state -> device (pinned), build and compile the
+    circuit, run it, device -> host (pinned); timed on the host around the
+    whole call chain, with the time of each phase reported beside it."""
     dt = args.dtype
     tdt = torch.complex64 if dt == "c64" else torch.complex128
     host = torch.zeros(1 << n, dtype=tdt, pin_memory=True)
@@ -616,29 +617,31 @@ def run_e2e(qs, torch, args, n, circ, mode, fq, device, world):
     S = S_BYTES[dt]
     steps = max(1, min(args.steps, 3))
     gates = len(circ)
-    times = []
+    times, phases = [], []
     for i in range(1 + steps):
         torch.cuda.synchronize()
         barrier(world)
-        t0 = time.perf_counter()
-        # the state's upload is asynchronous: the circuit is built and
-        # compiled on the host while it is in flight
+        t = [time.perf_counter()]
         qs.lib().qs_set_stream(state.handle, qs._stream_ptr())
-        assert qs.lib().qs_copy_from_host(state.handle, ctypes_ptr(host)) == 0
-        c = qs.Circuit(circ)
-        p = qs.Plan(c, n, dt, mode=mode, fuse_qubits=fq)
+        assert qs.lib().qs_copy_from_host(state.handle, ctypes_ptr(host)) == 0  # returns once the data is on the device
+        t.append(time.perf_counter())
+        p = qs.Plan(qs.Circuit(circ), n, dt, mode=mode, fuse_qubits=fq)
+        t.append(time.perf_counter())
         state.run(p)
-        assert qs.lib().qs_copy_to_host(state.handle, ctypes_ptr(host)) == 0
-        t = time.perf_counter() - t0
+        assert qs.lib().qs_copy_to_host(state.handle, ctypes_ptr(host)) == 0  # waits for the run, then copies
+        t.append(time.perf_counter())
         if i > 0:
-            times.append(t)
+            times.append(t[-1] - t[0])
+            phases.append(np.diff(t))
         host.zero_()
         host[0] = 1
     T = allreduce_max(sum(times) / len(times), world, device)
+    ph = np.mean(phases, axis=0) * 1e3
     del state
     return {"value": 2.0 * (1 << n) * S * gates / T / 1e9 * world, "unit": "GB/s",
             "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": (1 << n) * S,
-            "ms_per_step": 1000 * T, "gates_per_s": gates / T * world, "steps": steps}
+            "ms_per_step": 1000 * T, "gates_per_s": gates / T * world, "steps": steps,
+            "phases_ms": {"h2d": float(ph[0]), "circuit_and_plan": float(ph[1]), "run_and_d2h": float(ph[2])}}
 
 
 def ctypes_ptr(t):

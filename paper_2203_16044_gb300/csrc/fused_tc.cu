@@ -389,11 +389,62 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
 
 }  // namespace
 
+// Host-side preparation of a tensor-core block: the qubits in ascending
+// order (q_sorted) and B, the real form of M with its row / column indices
+// reordered to match (bit p of a reordered index is bit ord[p] of the
+// caller's), B[2c + u][2r + w] as in the header comment.
+qs_status tc_prepare(const int* qubits, int k, const double* M, int* q_sorted, std::vector<float>& B) {
+  if (k < 4 || k > 6) return fail(QS_EINVAL, "fused_tc: k=%d outside [4, 6]", k);
+  const int D = 1 << k, KR = 2 * D;
+  int ord[6];
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::sort(ord, ord + k, [&](int x, int y) { return qubits[x] < qubits[y]; });
+  for (int p = 0; p < k; ++p) q_sorted[p] = qubits[ord[p]];
+  int perm[64];
+  for (int rp = 0; rp < D; ++rp) {
+    int r = 0;
+    for (int p = 0; p < k; ++p) r |= ((rp >> p) & 1) << ord[p];
+    perm[rp] = r;
+  }
+  B.assign((size_t)KR * KR, 0.0f);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      const int pr = perm[r], pc = perm[c];
+      const double mr = M[2 * (pr * D + pc)], mi = M[2 * (pr * D + pc) + 1];
+      B[(size_t)(2 * c) * KR + 2 * r] = (float)mr;
+      B[(size_t)(2 * c + 1) * KR + 2 * r] = (float)-mi;
+      B[(size_t)(2 * c) * KR + 2 * r + 1] = (float)mi;
+      B[(size_t)(2 * c + 1) * KR + 2 * r + 1] = (float)mr;
+    }
+  return QS_OK;
+}
+
+// Launch a prepared block; Bdev holds its B on the device.
+qs_status run_dense_tc_prepared(qs_state* s, const int* q_sorted, int k, const float* Bdev, int unitary) {
+  const int D = 1 << k;
+  FusedArgs A{};
+  A.ins.k = k;
+  A.ins.set = 0;
+  for (int i = 0; i < k; ++i) A.ins.pos[i] = q_sorted[i];
+  for (int r = 0; r < D; ++r) {
+    u64 sp = 0;
+    for (int i = 0; i < k; ++i)
+      if ((r >> i) & 1) sp |= u64(1) << q_sorted[i];
+    A.spread[r] = sp;
+  }
+  switch (k) {
+    case 4: return launch_umma<4>(s, A, Bdev, unitary, q_sorted);
+    case 5: return launch_umma<5>(s, A, Bdev, unitary, q_sorted);
+    case 6: return launch_umma<6>(s, A, Bdev, unitary, q_sorted);
+  }
+  return fail(QS_EINVAL, "fused_tc: k=%d outside [4, 6]", k);
+}
+
 // Dense k-qubit block (complex64, 4 <= k <= 6) on the tensor cores.
 // unitary: 1 = M is known unitary (group norms are restored), 0 = not,
 // -1 = check on the host (|M M^dagger - I| <= 1e-9 entrywise).
 qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, int unitary) {
-  const int D = 1 << k, KR = 2 * D;
+  const int D = 1 << k;
   if (unitary < 0) {
     unitary = 1;
     for (int r = 0; r < D && unitary; ++r)
@@ -408,50 +459,15 @@ qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, i
         if (std::fabs(re - (r == c ? 1.0 : 0.0)) > 1e-9 || std::fabs(im) > 1e-9) unitary = 0;
       }
   }
-  // Block qubits in ascending order: bit p of a row / column index r' of the
-  // reordered matrix is bit ord[p] of the caller's index (perm(r')).
-  int ord[6], q[6];
-  for (int i = 0; i < k; ++i) ord[i] = i;
-  std::sort(ord, ord + k, [&](int x, int y) { return qubits[x] < qubits[y]; });
-  for (int p = 0; p < k; ++p) q[p] = qubits[ord[p]];
-  auto perm = [&](int rp) {
-    int r = 0;
-    for (int p = 0; p < k; ++p) r |= ((rp >> p) & 1) << ord[p];
-    return r;
-  };
-  FusedArgs A{};
-  A.ins.k = k;
-  A.ins.set = 0;
-  for (int i = 0; i < k; ++i) A.ins.pos[i] = q[i];
-  for (int r = 0; r < D; ++r) {
-    u64 sp = 0;
-    for (int i = 0; i < k; ++i)
-      if ((r >> i) & 1) sp |= u64(1) << q[i];
-    A.spread[r] = sp;
-  }
-  // real form of the reordered M: B[2c + u][2r + w]
-  std::vector<float> B((size_t)KR * KR);
-  for (int r = 0; r < D; ++r)
-    for (int c = 0; c < D; ++c) {
-      const int pr = perm(r), pc = perm(c);
-      const double mr = M[2 * (pr * D + pc)], mi = M[2 * (pr * D + pc) + 1];
-      B[(size_t)(2 * c) * KR + 2 * r] = (float)mr;
-      B[(size_t)(2 * c + 1) * KR + 2 * r] = (float)-mi;
-      B[(size_t)(2 * c) * KR + 2 * r + 1] = (float)mi;
-      B[(size_t)(2 * c + 1) * KR + 2 * r + 1] = (float)mr;
-    }
-  const size_t bbytes = B.size() * sizeof(float);
-  qs_status st = ensure_scratch(s, bbytes);
+  int q[6];
+  std::vector<float> B;
+  qs_status st = tc_prepare(qubits, k, M, q, B);
   if (st != QS_OK) return st;
+  const size_t bbytes = B.size() * sizeof(float);
+  if ((st = ensure_scratch(s, bbytes)) != QS_OK) return st;
   cudaError_t e = cudaMemcpyAsync(s->scratch, B.data(), bbytes, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "fused_tc: matrix upload");
-  const float* Bd = static_cast<const float*>(s->scratch);
-  switch (k) {
-    case 4: return launch_umma<4>(s, A, Bd, unitary, q);
-    case 5: return launch_umma<5>(s, A, Bd, unitary, q);
-    case 6: return launch_umma<6>(s, A, Bd, unitary, q);
-  }
-  return fail(QS_EINVAL, "fused_tc: k=%d outside [4, 6]", k);
+  return run_dense_tc_prepared(s, q, k, static_cast<const float*>(s->scratch), unitary);
 }
 
 // A tcgen05 wait that gave up since the last call: QS_ETIMEOUT (and clear).

@@ -97,6 +97,8 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::TILE: return run_tile(s, p, st.tile_index, false);
     case qs_step::BLOCK: {
       const qs_block& b = p->blocks[st.tile_index];
+      if (b.tc)  // B uploaded with the plan's other blocks at the start of the run
+        return run_dense_tc_prepared(s, b.q_sorted, b.k, static_cast<const float*>(s->scratch) + b.b_off, 1);
       return run_dense(s, b.q, b.k, b.M.data(), 1);  // a product of unitary gates
     }
   }
@@ -124,6 +126,16 @@ qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
   // blocks (those run on the FP64 layout)
   const bool dfl = s->dtype == QS_C128 && p->blocks.empty();
   qs_status r = dfl ? run_layout_dfl(s, true) : QS_OK;
+  if (r == QS_OK && !p->tc_B.empty()) {
+    // every tensor-core block's B in one upload (one synchronisation with
+    // earlier work on the stream, not one per block)
+    const size_t bytes = p->tc_B.size() * sizeof(float);
+    r = ensure_scratch(s, bytes);
+    if (r == QS_OK) {
+      cudaError_t e = cudaMemcpyAsync(s->scratch, p->tc_B.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+      if (e != cudaSuccess) r = cuda_fail(e, "plan: block matrix upload");
+    }
+  }
   if (ev) cudaEventRecord(ev[0], s->stream);
   for (size_t i = 0; i < p->steps.size() && r == QS_OK; ++i) {
     r = dfl ? run_step_dfl(s, p, p->steps[i]) : run_step(s, p, p->steps[i]);
@@ -331,6 +343,14 @@ qs_status plan_fused(qs_plan* p) {
     for (size_t i = 0; i < M.size(); ++i) {
       b.M[2 * i] = M[i].real();
       b.M[2 * i + 1] = M[i].imag();
+    }
+    if (p->dtype == QS_C64 && b.k >= 4) {  // tensor-core launch data, once
+      std::vector<float> B;
+      qs_status r = tc_prepare(b.q, b.k, b.M.data(), b.q_sorted, B);
+      if (r != QS_OK) return r;
+      b.tc = true;
+      b.b_off = p->tc_B.size();
+      p->tc_B.insert(p->tc_B.end(), B.begin(), B.end());
     }
     p->blocks.push_back(std::move(b));
     qs_step st{};

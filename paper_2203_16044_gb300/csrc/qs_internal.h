@@ -56,6 +56,8 @@ qs_status run_diag(qs_state* s, const int* qubits, int k, const double* d);
 qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M, int unitary = -1);
 // complex64 dense block, 4 <= k <= 6, on the tensor cores (fused_tc.cu)
 qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, int unitary);
+qs_status tc_prepare(const int* qubits, int k, const double* M, int* q_sorted, std::vector<float>& B);
+qs_status run_dense_tc_prepared(qs_state* s, const int* q_sorted, int k, const float* Bdev, int unitary);
 qs_status fused_tc_status();  // QS_ETIMEOUT if a tensor-core wait gave up since the last call
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
@@ -99,6 +101,11 @@ struct qs_block {
   int k;
   int q[6];
   std::vector<double> M;  // row-major (re, im)
+  // complex64 tensor-core blocks (k >= 4): qubits ascending and the offset of
+  // the block's B in the plan's tc_B (prepared once, uploaded once per run)
+  bool tc = false;
+  int q_sorted[6];
+  size_t b_off = 0;
 };
 
 struct qs_tile_pass;    // defined in tile.cu
@@ -113,6 +120,7 @@ struct qs_plan {
   // tile passes (host description; owned by the plan, freed by tile_free)
   std::vector<qs_tile_pass*> tiles;
   std::vector<qs_block> blocks;
+  std::vector<float> tc_B;  // all tensor-core blocks' B, concatenated
 };
 
 namespace qs {
