@@ -5,7 +5,10 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
+
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h")]
@@ -79,3 +82,26 @@ def test_circuit_and_plan_host_logic(qs):
         c.add("CNOT", [3, 3])
     with pytest.raises(qs.QSError):
         c.add("U3", [1], [0.1, 0.2, 0.3], param_index=0)  # only RX/RY/RZ trainable
+
+
+def test_circuit_add_many_matches_single_adds(qs):
+    # host-only: the bulk call and the per-gate call build the same circuit,
+    # and a bad gate is rejected with its index, the gates before it kept
+    import ctypes
+    L = qs.lib()
+    gates = W.brick(6, 3, 2) + W.qft(6)
+    a, b = qs.Circuit(), qs.Circuit()
+    for g in gates:
+        a.add(g.name, g.qubits, g.params)
+    b.add_many(gates)
+    assert len(a) == len(b) == len(gates)
+    kinds = np.array([qs.GATE_KIND["H"], qs.GATE_KIND["CNOT"], qs.GATE_KIND["RX"]], dtype=np.int32)
+    qubits = np.array([[0, 0], [1, 1], [2, 0]], dtype=np.int32)  # the CNOT's qubits coincide
+    params = np.zeros((3, 3))
+    c = qs.Circuit()
+    st = L.qs_circuit_add_many(c.handle, 3, kinds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               qubits.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None)
+    assert st == qs.QS_EINVAL
+    assert b"gate 1" in L.qs_last_error()
+    assert len(c) == 1
