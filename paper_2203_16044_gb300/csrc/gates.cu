@@ -29,7 +29,8 @@ namespace qs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 2;
+constexpr int kUnroll = 2;  // pair kernels: 2 x kUnroll 16-byte loads in flight per thread
+constexpr int kU1 = 4;      // one-vector kernels (diagonals, phases): kU1 loads in flight
 constexpr int kWaves = 8;
 
 // ---------------------------------------------------------------------------
@@ -132,16 +133,16 @@ __global__ void __launch_bounds__(kThreads) k_diag(R* __restrict__ a, u64 npk, c
   const int D = 1 << T.k;
   for (int i = threadIdx.x; i < D; i += kThreads) sd[i] = T.d[i];
   __syncthreads();
-  const u64 step = (u64)gridDim.x * kThreads * kUnroll;
-  for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < npk; base += step) {
-    R v[kUnroll][V];
+  const u64 step = (u64)gridDim.x * kThreads * kU1;
+  for (u64 base = (u64)blockIdx.x * kThreads * kU1 + threadIdx.x; base < npk; base += step) {
+    R v[kU1][V];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kU1; ++u) {
       const u64 p = base + (u64)u * kThreads;
       if (p < npk) ld16(a + p * V, v[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kU1; ++u) {
       const u64 p = base + (u64)u * kThreads;
 #pragma unroll
       for (int j = 0; j < A; ++j) {
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(R* __restrict__ a, u64 npk, c
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kU1; ++u) {
       const u64 p = base + (u64)u * kThreads;
       if (p < npk) st16(a + p * V, v[u]);
     }
@@ -167,24 +168,24 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_phase(R* __restrict__ a, u64 nwork, Ins ins, int jmask,
                                                     typename Ar<R>::Z z) {
   constexpr int V = PK<R>::V, A = PK<R>::A;
-  const u64 step = (u64)gridDim.x * kThreads * kUnroll;
-  for (u64 base = (u64)blockIdx.x * kThreads * kUnroll + threadIdx.x; base < nwork; base += step) {
-    R v[kUnroll][V];
-    u64 p[kUnroll];
+  const u64 step = (u64)gridDim.x * kThreads * kU1;
+  for (u64 base = (u64)blockIdx.x * kThreads * kU1 + threadIdx.x; base < nwork; base += step) {
+    R v[kU1][V];
+    u64 p[kU1];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kU1; ++u) {
       const u64 i = base + (u64)u * kThreads;
       p[u] = expand(i < nwork ? i : 0, ins);
       ld16(a + p[u] * V, v[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kU1; ++u) {
 #pragma unroll
       for (int j = 0; j < A; ++j)
         if ((jmask >> j) & 1) scal_apply(z, v[u][2 * j], v[u][2 * j + 1]);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int u = 0; u < kU1; ++u)
       if (base + (u64)u * kThreads < nwork) st16(a + p[u] * V, v[u]);
   }
 }
@@ -378,12 +379,25 @@ __global__ void __launch_bounds__(kThreads) k_pairs_dfl(float4* __restrict__ a, 
 
 __global__ void __launch_bounds__(kThreads) k_phase_dfl(float4* __restrict__ a, u64 nwork, Ins ins, Zdf z) {
   const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
-  for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < nwork; i += (u64)gridDim.x * kThreads) {
-    const u64 p = expand(i, ins);
-    const float4 v = a[p];
-    cdf x{v.x, v.y, v.z, v.w};
-    cmul_df(zh, zl, x);
-    a[p] = make_float4(x.rh, x.rl, x.ih, x.il);
+  const u64 step = (u64)gridDim.x * kThreads * kU1;
+  for (u64 base = (u64)blockIdx.x * kThreads * kU1 + threadIdx.x; base < nwork; base += step) {
+    float4 v[kU1];
+    u64 p[kU1];
+#pragma unroll
+    for (int u = 0; u < kU1; ++u) {
+      const u64 i = base + (u64)u * kThreads;
+      p[u] = expand(i < nwork ? i : 0, ins);
+      v[u] = a[p[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < kU1; ++u) {
+      cdf x{v[u].x, v[u].y, v[u].z, v[u].w};
+      cmul_df(zh, zl, x);
+      v[u] = make_float4(x.rh, x.rl, x.ih, x.il);
+    }
+#pragma unroll
+    for (int u = 0; u < kU1; ++u)
+      if (base + (u64)u * kThreads < nwork) a[p[u]] = v[u];
   }
 }
 
@@ -393,15 +407,30 @@ __global__ void __launch_bounds__(kThreads) k_diag_dfl(float4* __restrict__ a, u
   const int D = 1 << T.k;
   for (int i = threadIdx.x; i < D; i += kThreads) sd[i] = T.d[i];
   __syncthreads();
-  for (u64 p = (u64)blockIdx.x * kThreads + threadIdx.x; p < npk; p += (u64)gridDim.x * kThreads) {
-    int r = 0;
-    for (int i = 0; i < T.k; ++i) r |= (int)((p >> T.q[i]) & 1u) << i;
-    const float4 v = a[p];
-    cdf x{v.x, v.y, v.z, v.w};
-    const Zdf z = sd[r];
-    const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
-    cmul_df(zh, zl, x);
-    a[p] = make_float4(x.rh, x.rl, x.ih, x.il);
+  const u64 step = (u64)gridDim.x * kThreads * kU1;
+  for (u64 base = (u64)blockIdx.x * kThreads * kU1 + threadIdx.x; base < npk; base += step) {
+    float4 v[kU1];
+#pragma unroll
+    for (int u = 0; u < kU1; ++u) {
+      const u64 p = base + (u64)u * kThreads;
+      if (p < npk) v[u] = a[p];
+    }
+#pragma unroll
+    for (int u = 0; u < kU1; ++u) {
+      const u64 p = base + (u64)u * kThreads;
+      int r = 0;
+      for (int i = 0; i < T.k; ++i) r |= (int)((p >> T.q[i]) & 1u) << i;
+      cdf x{v[u].x, v[u].y, v[u].z, v[u].w};
+      const Zdf z = sd[r];
+      const float zh[2] = {z.rh, z.ih}, zl[2] = {z.rl, z.il};
+      cmul_df(zh, zl, x);
+      v[u] = make_float4(x.rh, x.rl, x.ih, x.il);
+    }
+#pragma unroll
+    for (int u = 0; u < kU1; ++u) {
+      const u64 p = base + (u64)u * kThreads;
+      if (p < npk) a[p] = v[u];
+    }
   }
 }
 
@@ -492,7 +521,7 @@ static qs_status diag_impl(qs_state* s, const int* qubits, int k, const double* 
       else bits.push_back({qubits[i] - LA, 1});
     }
     const u64 nwork = u64(1) << (s->n - LA - (int)bits.size());
-    const unsigned g = grid_for(nwork, (u64)kThreads * kUnroll, kWaves);
+    const unsigned g = grid_for(nwork, (u64)kThreads * kU1, kWaves);
     k_phase<R><<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), jmask, to_z(d[2 * (D - 1)], d[2 * (D - 1) + 1], R(0)));
     return launch_ok("k_phase");
   }
@@ -501,7 +530,7 @@ static qs_status diag_impl(qs_state* s, const int* qubits, int k, const double* 
   for (int i = 0; i < k; ++i) T.q[i] = qubits[i];
   for (int i = 0; i < D; ++i) T.d[i] = to_z(d[2 * i], d[2 * i + 1], R(0));
   const u64 npk = u64(1) << (s->n - LA);
-  const unsigned g = grid_for(npk, (u64)kThreads * kUnroll, kWaves);
+  const unsigned g = grid_for(npk, (u64)kThreads * kU1, kWaves);
   k_diag<R><<<g, kThreads, 0, s->stream>>>(a, npk, T);
   return launch_ok("k_diag");
 }
@@ -641,7 +670,7 @@ qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d) {
     std::vector<std::pair<int, int>> bits;
     for (int i = 0; i < k; ++i) bits.push_back({qubits[i], 1});
     const u64 nwork = u64(1) << (s->n - k);
-    const unsigned g = grid_for(nwork, kThreads, kWaves);
+    const unsigned g = grid_for(nwork, (u64)kThreads * kU1, kWaves);
     k_phase_dfl<<<g, kThreads, 0, s->stream>>>(a, nwork, make_ins(bits), to_z(d[2 * (D - 1)], d[2 * (D - 1) + 1], 0.0));
     return launch_ok("k_phase_dfl");
   }
@@ -650,7 +679,7 @@ qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d) {
   for (int i = 0; i < k; ++i) T.q[i] = qubits[i];
   for (int i = 0; i < D; ++i) T.d[i] = to_z(d[2 * i], d[2 * i + 1], 0.0);
   const u64 npk = u64(1) << s->n;
-  const unsigned g = grid_for(npk, kThreads, kWaves);
+  const unsigned g = grid_for(npk, (u64)kThreads * kU1, kWaves);
   k_diag_dfl<<<g, kThreads, 0, s->stream>>>(a, npk, T);
   return launch_ok("k_diag_dfl");
 }
