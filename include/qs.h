@@ -267,6 +267,13 @@ enum { QS_STEP_1Q = 0, QS_STEP_CTRL = 1, QS_STEP_DIAG = 2, QS_STEP_SWAP = 3, QS_
  * touches) of plan step i, 0 <= i < passes. */
 qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_bytes);
 
+/* The qubits plan step i acts on, in the order its matrix uses them (for a
+ * dense block, qubit j is bit j of the block matrix's row index; for a gate,
+ * controls first, the target last): up to `cap` ints written to `qubits`,
+ * their number to *count.  Tile passes report 0 qubits.  QS_EINVAL if the
+ * step has more than `cap` qubits (nothing written) or i is out of range. */
+qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int* count);
+
 /* As qs_run_plan, and also times every step with CUDA events recorded on the
  * state's stream between launches: step_ms[i] receives the device time of
  * step i (nsteps must equal the plan's pass count).  Synchronises the

@@ -86,6 +86,7 @@ _SIGS = {
     "qs_plan_destroy": ([_vp], _int),
     "qs_run_plan": ([_vp, _vp], _int),
     "qs_plan_step_info": ([_vp, _int, _ip, _dp], _int),
+    "qs_plan_step_qubits": ([_vp, _int, _ip, _int, _ip], _int),
     "qs_run_plan_profiled": ([_vp, _vp, ctypes.POINTER(ctypes.c_float), _int], _int),
     "qs_adjoint_grad": ([_vp, _vp, _dp, _int, _int, _int, _up, _up, _dp, _dp, _dp], _int),
     "qs_batch_create": ([_int, _ip, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(PlanOpts), _vp,
@@ -380,6 +381,14 @@ class Plan:
             _check(_lib.qs_plan_step_info(self._h, i, ctypes.byref(k), ctypes.byref(b)), "qs_plan_step_info")
             out.append((self.STEP_KINDS[k.value], b.value))
         return out
+
+    def step_qubits(self, i: int) -> list:
+        """The qubits of plan step i (block: bit j of its matrix index is
+        qubit j; gate: controls, then target; tile pass: [])."""
+        q = (ctypes.c_int * 8)()
+        cnt = ctypes.c_int()
+        _check(_lib.qs_plan_step_qubits(self._h, int(i), q, 8, ctypes.byref(cnt)), "qs_plan_step_qubits")
+        return list(q[:cnt.value])
 
     def close(self):
         if getattr(self, "_h", None):

@@ -125,6 +125,12 @@ __device__ __forceinline__ float norm_correction(float nin, float nout) {
 //            lane both groups' amplitude 2j + 1, and group_take exchanges the
 //            halves.  The loads have no dependent instruction until the
 //            tile is consumed, so a prefetch stays in flight.
+//   lmode 3 (the block is qubits 0 .. k-1, full tiles): a group is 2^k
+//            contiguous amplitudes, so the rows of a warp are 2^k * 8 bytes
+//            apart and one row per lane would touch 32 cache lines per
+//            instruction; rows_load / rows_store move 4 rows x 128 bytes per
+//            instruction instead, and rows_to_lane / the store path
+//            transpose through a per-warp shared-memory stage.
 template <int D, int CH>
 __device__ __forceinline__ void group_load(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
                                            int lmode, int j0, float4 (&w)[CH]) {
@@ -190,6 +196,52 @@ __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bo
   }
 }
 
+// lmode 3.  Lane i of a warp (rows rb .. rb + 31 of the tile starting at
+// group g, slice words j0 .. j0 + 7) moves word j0 + (i & 7) of row
+// rb + 4 m + (i >> 3) in instruction m.  The stage holds 32 rows of 8 words
+// with a row pitch of 9 words (144 bytes): a row written by 8 consecutive
+// lanes and a column read by 8 consecutive lanes (one row each) both fall on
+// distinct bank quads.
+constexpr int kStgPitch = 9;  // float4 words per staged row
+constexpr int kStgWarp = 32 * kStgPitch;
+template <int K>
+__device__ __forceinline__ void rows_load(const float2* __restrict__ a, u64 g, int j0, float4 (&w)[8]) {
+  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
+    w[m] = *reinterpret_cast<const float4*>(a + (G << K) + 2 * (j0 + (lane & 7)));
+  }
+}
+// words as loaded by rows_load -> w[j] = word j0 + j of this lane's row
+__device__ __forceinline__ void rows_to_lane(float4 (&w)[8], float4* stg) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)] = w[m];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) w[j] = stg[lane * kStgPitch + j];
+  __syncwarp();
+}
+// o[4j .. 4j + 3] (this lane's row, word j0 + j), stored as o (1 + g)
+template <int K>
+__device__ __forceinline__ void rows_store(float2* __restrict__ a, u64 g, int j0, const float* o, float gs,
+                                           float4* stg) {
+  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
+  auto sc = [gs](float v) { return fmaf(v, gs, v); };
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    stg[lane * kStgPitch + j] = make_float4(sc(o[4 * j]), sc(o[4 * j + 1]), sc(o[4 * j + 2]), sc(o[4 * j + 3]));
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
+    *reinterpret_cast<float4*>(a + (G << K) + 2 * (j0 + (lane & 7))) =
+        stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)];
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // The block kernel (k = 4, 5, 6).  The MMA's A operand may
 // live in tensor memory (lane = row, one 32-bit column per K element), so the
@@ -229,6 +281,7 @@ struct TaShape {
   static constexpr uint32_t B_BYTES = KR * KR * 4, LBO_B = (KR / 8) * 128, SBO = 128;
   static constexpr uint32_t TCOLS = 3 * KR <= 128 ? 128 : (3 * KR <= 256 ? 256 : 512);  // power of two >= 3 KR
   static constexpr size_t SMEM = 2 * (size_t)B_BYTES + 16 + 2 * H * kUT * sizeof(float);
+  static constexpr size_t STG = (size_t)(NT / 32) * kStgWarp * sizeof(float4);  // lmode 3 only
 };
 
 template <int K>
@@ -246,6 +299,7 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
   float* nin_s = reinterpret_cast<float*>(mbar + 2);  // [H][kUT] partial input norms
   float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
   const int t = threadIdx.x, warp = t >> 5;
+  float4* stg = reinterpret_cast<float4*>(nout_s + H * kUT) + warp * kStgWarp;  // lmode 3
   const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
   for (int i = t; i < KR * KR; i += NT) {
     const int k = i / KR, n = i % KR;
@@ -280,10 +334,17 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
   bool vA = gA + row < ngroups, vB = gB + row < ngroups;
   u64 bA = expand(vA ? gA + row : 0, args.ins), bB = expand(vB ? gB + row : 0, args.ins);
   float4 wA[CH], wB[CH];
-  if (gA < ngroups) group_load<D, CH>(a, bA, vA, args.spread, lmode, j0, wA);
-  if (gB < ngroups) group_load<D, CH>(a, bB, vB, args.spread, lmode, j0, wB);
+  auto load = [&](u64 g, u64 base, bool valid, float4 (&w)[CH]) {
+    if (lmode == 3)
+      rows_load<K>(a, g, j0, w);
+    else
+      group_load<D, CH>(a, base, valid, args.spread, lmode, j0, w);
+  };
+  if (gA < ngroups) load(gA, bA, vA, wA);
+  if (gB < ngroups) load(gB, bB, vB, wB);
   auto step = [&](u64& g, bool& valid, u64& base, float4 (&w)[CH]) -> bool {
     if (g >= ngroups) return false;
+    if (lmode == 3) rows_to_lane(w, stg);
     float nin = 0.f;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {  // 16 columns (4 words) at a time
@@ -324,7 +385,7 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
     const u64 gn = g + 2 * gstep;
     const bool vn = gn + row < ngroups;
     const u64 bn = expand(vn ? gn + row : 0, args.ins);
-    if (gn < ngroups) group_load<D, CH>(a, bn, vn, args.spread, lmode, j0, w);
+    if (gn < ngroups) load(gn, bn, vn, w);
     if (!__syncthreads_and(mbar_wait(mb, phase) ? 1 : 0)) {
       if (t == 0) atomicExch(&g_umma_timeout, 1);
       return false;
@@ -347,7 +408,10 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
       for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
       gsc = norm_correction(nin, nout);
     }
-    group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, gsc);
+    if (lmode == 3)
+      rows_store<K>(a, g, j0, o, gsc, stg);
+    else
+      group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, gsc);
     asm volatile("tcgen05.fence::before_thread_sync;");
     g = gn;
     valid = vn;
@@ -365,7 +429,13 @@ template <int K>
 qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renorm, const int* qubits) {
   typedef TaShape<K> S;
   auto kern = k_fused_umma<K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+  const u64 ngroups = u64(1) << (s->n - K);
+  // qubits ascending: the block is qubits 0 .. K-1 exactly when the last is K-1
+  const int lmode = ngroups >= (u64)kUT && qubits[K - 1] == K - 1
+                        ? 3
+                        : (qubits[0] == 0 ? 1 : (ngroups >= (u64)kUT ? 2 : 0));
+  const size_t smem = S::SMEM + (lmode == 3 ? S::STG : 0);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(S::SMEM + S::STG));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: smem attribute");
   int dev = 0, smem_sm = 0, smem_rsv = 0;
@@ -375,15 +445,13 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return cuda_fail(e, "fused_umma: occupancy attributes");
-  int per_sm = smem_sm / (int)(S::SMEM + smem_rsv);
+  int per_sm = smem_sm / (int)(smem + smem_rsv);
   const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 255;
   per_sm = std::min(per_sm, 65536 / (regs * S::NT));
   per_sm = std::min(per_sm, 512 / (int)S::TCOLS);
   if (per_sm < 1) per_sm = 1;
-  const u64 ngroups = u64(1) << (s->n - K);
   const unsigned grid = grid_for(ngroups, kUT, per_sm);
-  const int lmode = qubits[0] == 0 ? 1 : (ngroups >= (u64)kUT ? 2 : 0);
-  kern<<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
+  kern<<<grid, S::NT, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
   return launch_ok("k_fused_umma");
 }
 

@@ -505,6 +505,25 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
   return QS_OK;
 }
 
+qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int* count) {
+  if (!p || !count || (cap > 0 && !qubits)) return fail(QS_EINVAL, "qs_plan_step_qubits: NULL argument");
+  if (i < 0 || i >= (int)p->steps.size()) return fail(QS_EINVAL, "qs_plan_step_qubits: step %d out of range", i);
+  const qs_step& st = p->steps[i];
+  const int* q = st.q;
+  int nq = st.nq;
+  if (st.type == qs_step::TILE) {
+    nq = 0;
+  } else if (st.type == qs_step::BLOCK) {
+    const qs_block& b = p->blocks[st.tile_index];
+    q = b.q;
+    nq = b.k;
+  }
+  if (nq > cap) return fail(QS_EINVAL, "qs_plan_step_qubits: step %d has %d qubits, cap %d", i, nq, cap);
+  for (int j = 0; j < nq; ++j) qubits[j] = q[j];
+  *count = nq;
+  return QS_OK;
+}
+
 qs_status qs_run_plan_profiled(qs_state* s, qs_plan* p, float* step_ms, int nsteps) {
   if (!s || !p || !step_ms) return fail(QS_EINVAL, "qs_run_plan_profiled: NULL argument");
   if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan_profiled: plan built for another n/dtype");

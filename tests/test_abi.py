@@ -105,3 +105,26 @@ def test_circuit_add_many_matches_single_adds(qs):
     assert st == qs.QS_EINVAL
     assert b"gate 1" in L.qs_last_error()
     assert len(c) == 1
+
+
+def test_plan_step_qubits(qs):
+    # host-only: an unfused plan's steps are the circuit's gates in order
+    # (controls first); a fused plan's blocks cover at most 6 distinct qubits
+    # in range, and together with its gate steps every qubit the circuit uses
+    gates = W.brick(5, 3, 1) + W.qft(4)
+    p = qs.Plan(qs.Circuit(gates), 5, "c128", mode=qs.PLAN_UNFUSED)
+    assert p.stats()["passes"] == len(gates)
+    for i, g in enumerate(gates):
+        assert p.step_qubits(i) == list(g.qubits)
+    n = 14
+    p = qs.Plan(qs.Circuit(W.brick(n, 12, 3)), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=6)
+    seen = set()
+    for i, (kind, _) in enumerate(p.step_info()):
+        q = p.step_qubits(i)
+        assert len(set(q)) == len(q) and all(0 <= x < n for x in q)
+        if kind == "block":
+            assert 1 <= len(q) <= 6
+        seen.update(q)
+    assert seen == set(range(n))
+    with pytest.raises(qs.QSError):
+        p.step_qubits(p.stats()["passes"])

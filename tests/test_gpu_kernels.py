@@ -228,22 +228,26 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     assert np.array_equal(s.to_numpy(), psi)
 
 
-@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n,qubits", [
     (9, None),            # fewer than 128 groups: 8-byte accesses
     (14, "with0"),        # qubit 0 in the block: 16-byte amplitude pairs
     (14, "without0"),     # qubit 0 outside: lane pairs exchange halves
     (16, "high"),         # the block on the highest qubits
+    (15, "low"),          # the block is qubits 0 .. k-1: staged row transposes
+    (8, "low"),           # ... with fewer than 128 groups (16-byte pairs)
 ])
 def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
-    # complex64 k = 4, 5 blocks run on tcgen05; each way a group's amplitudes
-    # are gathered and scattered, against the oracle
+    # complex64 k = 4, 5, 6 blocks run on tcgen05; each way a group's
+    # amplitudes are gathered and scattered, against the oracle
     if qubits is None:
-        qsel = [1, 3, 4, 6, 8][:k]
+        qsel = [1, 3, 4, 6, 8, 2][:k]
     elif qubits == "with0":
-        qsel = [7, 0, 3, 11, 5][:k]
+        qsel = [7, 0, 3, 11, 5, 9][:k]
     elif qubits == "without0":
-        qsel = [2, 9, 5, 12, 1][:k]
+        qsel = [2, 9, 5, 12, 1, 7][:k]
+    elif qubits == "low":
+        qsel = [q for q in [2, 0, 3, 1, 5, 4] if q < k]
     else:
         qsel = list(range(n - 1, n - 1 - k, -1))
     psi = W.random_state(n, 7500 + n + k)
