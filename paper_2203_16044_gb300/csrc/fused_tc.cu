@@ -125,12 +125,7 @@ __device__ __forceinline__ float norm_correction(float nin, float nout) {
 //            lane both groups' amplitude 2j + 1, and group_take exchanges the
 //            halves.  The loads have no dependent instruction until the
 //            tile is consumed, so a prefetch stays in flight.
-//   lmode 3 (the block is qubits 0 .. k-1, full tiles): a group is 2^k
-//            contiguous amplitudes, so the rows of a warp are 2^k * 8 bytes
-//            apart and one row per lane would touch 32 cache lines per
-//            instruction; rows_load / rows_store move 4 rows x 128 bytes per
-//            instruction instead, and rows_to_lane / the store path
-//            transpose through a per-warp shared-memory stage.
+// (A block on qubits 0 .. k-1 runs in k_fused_umma_rows instead.)
 template <int D, int CH>
 __device__ __forceinline__ void group_load(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
                                            int lmode, int j0, float4 (&w)[CH]) {
@@ -162,6 +157,21 @@ __device__ __forceinline__ float4 group_take(float4 x, int lmode) {
   const float sx = odd ? x.x : x.z, sy = odd ? x.y : x.w;
   const float rx = __shfl_xor_sync(0xffffffffu, sx, 1), ry = __shfl_xor_sync(0xffffffffu, sy, 1);
   return odd ? make_float4(rx, ry, x.z, x.w) : make_float4(x.x, x.y, rx, ry);
+}
+// The addresses group_load would read, fetched into L2 only (no registers
+// held): issued a few tiles ahead, they keep more bytes in flight than the
+// register buffers can, and the later loads hit L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <int D, int CH>
+__device__ __forceinline__ void group_prefetch(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
+                                               int lmode, int j0) {
+  if (!valid) return;
+  if (lmode == 2) base &= ~u64(1);
+  const int odd = lmode == 2 ? (threadIdx.x & 1) : 0;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) prefetch_l2(a + (base | spread[2 * (j0 + j) + odd]));
 }
 // o[4j .. 4j + 3] = amplitudes 2 (j0 + j), 2 (j0 + j) + 1 of this thread's
 // group; each value is stored as o (1 + g), one rounding (FMA).
@@ -196,7 +206,10 @@ __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bo
   }
 }
 
-// lmode 3.  Lane i of a warp (rows rb .. rb + 31 of the tile starting at
+// Blocks on qubits 0 .. k-1 (k_fused_umma_rows): a group is 2^k contiguous
+// amplitudes, so the rows of a warp are 2^k * 8 bytes apart and one row per
+// lane would touch 32 cache lines per instruction.  Lane i of a warp (rows
+// rb .. rb + 31 of the tile starting at
 // group g, slice words j0 .. j0 + 7) moves word j0 + (i & 7) of row
 // rb + 4 m + (i >> 3) in instruction m.  The stage holds 32 rows of 8 words
 // with a row pitch of 9 words (144 bytes): a row written by 8 consecutive
@@ -213,6 +226,24 @@ __device__ __forceinline__ void rows_load(const float2* __restrict__ a, u64 g, i
     w[m] = *reinterpret_cast<const float4*>(a + (G << K) + 2 * (j0 + (lane & 7)));
   }
 }
+// the staged rows (each lane's row written to its stage row) to global
+// memory, 4 rows x 128 bytes per instruction
+template <int K>
+__device__ __forceinline__ void rows_flush(float2* __restrict__ a, u64 g, int j0, float4* stg) {
+  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
+    *reinterpret_cast<float4*>(a + (G << K) + 2 * (j0 + (lane & 7))) =
+        stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)];
+  }
+  __syncwarp();
+}
+// bytes (a multiple of 16) from p (16-byte aligned) into L2, no registers held
+__device__ __forceinline__ void prefetch_bulk_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 // words as loaded by rows_load -> w[j] = word j0 + j of this lane's row
 __device__ __forceinline__ void rows_to_lane(float4 (&w)[8], float4* stg) {
   const int lane = threadIdx.x & 31;
@@ -223,25 +254,6 @@ __device__ __forceinline__ void rows_to_lane(float4 (&w)[8], float4* stg) {
   for (int j = 0; j < 8; ++j) w[j] = stg[lane * kStgPitch + j];
   __syncwarp();
 }
-// o[4j .. 4j + 3] (this lane's row, word j0 + j), stored as o (1 + g)
-template <int K>
-__device__ __forceinline__ void rows_store(float2* __restrict__ a, u64 g, int j0, const float* o, float gs,
-                                           float4* stg) {
-  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
-  auto sc = [gs](float v) { return fmaf(v, gs, v); };
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    stg[lane * kStgPitch + j] = make_float4(sc(o[4 * j]), sc(o[4 * j + 1]), sc(o[4 * j + 2]), sc(o[4 * j + 3]));
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
-    *reinterpret_cast<float4*>(a + (G << K) + 2 * (j0 + (lane & 7))) =
-        stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)];
-  }
-  __syncwarp();
-}
-
 // ---------------------------------------------------------------------------
 // The block kernel (k = 4, 5, 6).  The MMA's A operand may
 // live in tensor memory (lane = row, one 32-bit column per K element), so the
@@ -281,13 +293,12 @@ struct TaShape {
   static constexpr uint32_t B_BYTES = KR * KR * 4, LBO_B = (KR / 8) * 128, SBO = 128;
   static constexpr uint32_t TCOLS = 3 * KR <= 128 ? 128 : (3 * KR <= 256 ? 256 : 512);  // power of two >= 3 KR
   static constexpr size_t SMEM = 2 * (size_t)B_BYTES + 16 + 2 * H * kUT * sizeof(float);
-  static constexpr size_t STG = (size_t)(NT / 32) * kStgWarp * sizeof(float4);  // lmode 3 only
 };
 
 template <int K>
 __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
     k_fused_umma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
-                    const __grid_constant__ FusedArgs args, int renorm, int lmode) {
+                    const __grid_constant__ FusedArgs args, int renorm, int lmode, int pf) {
   typedef TaShape<K> S;
   constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT;
   constexpr int CH = 8;  // 16-byte words (amplitude pairs) per thread: 32 reals
@@ -299,7 +310,6 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
   float* nin_s = reinterpret_cast<float*>(mbar + 2);  // [H][kUT] partial input norms
   float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
   const int t = threadIdx.x, warp = t >> 5;
-  float4* stg = reinterpret_cast<float4*>(nout_s + H * kUT) + warp * kStgWarp;  // lmode 3
   const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
   for (int i = t; i < KR * KR; i += NT) {
     const int k = i / KR, n = i % KR;
@@ -334,17 +344,22 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
   bool vA = gA + row < ngroups, vB = gB + row < ngroups;
   u64 bA = expand(vA ? gA + row : 0, args.ins), bB = expand(vB ? gB + row : 0, args.ins);
   float4 wA[CH], wB[CH];
-  auto load = [&](u64 g, u64 base, bool valid, float4 (&w)[CH]) {
-    if (lmode == 3)
-      rows_load<K>(a, g, j0, w);
-    else
-      group_load<D, CH>(a, base, valid, args.spread, lmode, j0, w);
+  auto load = [&](u64 base, bool valid, float4 (&w)[CH]) {
+    group_load<D, CH>(a, base, valid, args.spread, lmode, j0, w);
   };
-  if (gA < ngroups) load(gA, bA, vA, wA);
-  if (gB < ngroups) load(gB, bB, vB, wB);
+  // L2 prefetch (pf != 0) of the tile two tile-steps ahead of the one
+  // being loaded into registers
+  auto prefetch = [&](u64 g) {
+    if (!pf || g >= ngroups) return;
+    const bool v = g + row < ngroups;
+    group_prefetch<D, CH>(a, expand(v ? g + row : 0, args.ins), v, args.spread, lmode, j0);
+  };
+  if (gA < ngroups) load(bA, vA, wA);
+  if (gB < ngroups) load(bB, vB, wB);
+  prefetch(gA + 2 * gstep);
+  prefetch(gA + 3 * gstep);
   auto step = [&](u64& g, bool& valid, u64& base, float4 (&w)[CH]) -> bool {
     if (g >= ngroups) return false;
-    if (lmode == 3) rows_to_lane(w, stg);
     float nin = 0.f;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {  // 16 columns (4 words) at a time
@@ -385,7 +400,8 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
     const u64 gn = g + 2 * gstep;
     const bool vn = gn + row < ngroups;
     const u64 bn = expand(vn ? gn + row : 0, args.ins);
-    if (gn < ngroups) load(gn, bn, vn, w);
+    if (gn < ngroups) load(bn, vn, w);
+    prefetch(gn + 2 * gstep);
     if (!__syncthreads_and(mbar_wait(mb, phase) ? 1 : 0)) {
       if (t == 0) atomicExch(&g_umma_timeout, 1);
       return false;
@@ -408,10 +424,7 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
       for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
       gsc = norm_correction(nin, nout);
     }
-    if (lmode == 3)
-      rows_store<K>(a, g, j0, o, gsc, stg);
-    else
-      group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, gsc);
+    group_store<D, CH>(a, base, valid, args.spread, lmode, j0, o, gsc);
     asm volatile("tcgen05.fence::before_thread_sync;");
     g = gn;
     valid = vn;
@@ -425,33 +438,277 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
+// ---------------------------------------------------------------------------
+// Blocks on qubits 0 .. k-1 (full tiles): k_fused_umma_rows.  A tile is then
+// 128 x 2^k contiguous amplitudes; the warps move it with rows_load /
+// rows_flush (4 rows x 128 bytes per instruction, transposed through the
+// per-warp stage), and bulk L2 prefetches (16 x 4 KB per tile, no
+// registers held) run two tiles ahead of a one-tile register buffer.  The
+// kernel is warp-specialised: one extra warp issues the MMAs (its first
+// lane), so the 2^(k+1) / 32 * 128 compute threads never wait on the tensor
+// pipe.  Per tile they wait for the previous tile's MMAs (A is then free),
+// split the tile into A, arrive on the "A full" mbarrier, issue the next
+// tile's loads, and run the previous tile's epilogue from the other
+// accumulator while the MMA warp drives the tensor cores on this one.  The
+// compute threads synchronise among themselves with named barriers (1:
+// input norms, 2: output norms, 3: the wait outcome), never with the MMA
+// warp, except at entry and exit.  TMEM columns: A hi [0, 2D), A lo
+// [2D, 4D), accumulators [4D, 6D) and [6D, 8D) for alternate tiles.  (The
+// same structure with gathered groups measured slower than k_fused_umma:
+// there the memory instruction issue, not the tensor pipe, limits a tile.)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// AND of v over the n threads of named barrier id (all of them must call it)
+__device__ __forceinline__ bool named_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
 template <int K>
-qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renorm, const int* qubits) {
-  typedef TaShape<K> S;
-  auto kern = k_fused_umma<K>;
-  const u64 ngroups = u64(1) << (s->n - K);
-  // qubits ascending: the block is qubits 0 .. K-1 exactly when the last is K-1
-  const int lmode = ngroups >= (u64)kUT && qubits[K - 1] == K - 1
-                        ? 3
-                        : (qubits[0] == 0 ? 1 : (ngroups >= (u64)kUT ? 2 : 0));
-  const size_t smem = S::SMEM + (lmode == 3 ? S::STG : 0);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(S::SMEM + S::STG));
+struct RowsShape {
+  static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NC = kUT * H, NTT = NC + 32;
+  static constexpr uint32_t B_BYTES = KR * KR * 4, LBO_B = (KR / 8) * 128, SBO = 128;
+  static constexpr uint32_t TCOLS = 4 * KR;  // A hi, A lo, two accumulators: 128, 256 or 512
+  static constexpr size_t SMEM = 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float) +
+                                 (size_t)(NC / 32) * kStgWarp * sizeof(float4);  // + the per-warp stages
+  static constexpr int MINB = K == 6 ? 1 : (K == 5 ? 2 : 3);
+};
+
+template <int K>
+__global__ void __launch_bounds__(RowsShape<K>::NTT, RowsShape<K>::MINB)
+    k_fused_umma_rows(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg, int renorm) {
+  typedef RowsShape<K> S;
+  constexpr int KR = S::KR, H = S::H, NC = S::NC;
+  constexpr int CH = 8;  // 16-byte words (amplitude pairs) per compute thread: 32 reals
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* Bhi = sm;
+  unsigned char* Blo = sm + S::B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] A full, [1] MMAs done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  float* nin_s = reinterpret_cast<float*>(mbar + 4);  // [H][kUT] partial input norms
+  float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int i = t; i < KR * KR; i += S::NTT) {
+    const int k = i / KR, n = i % KR;
+    unsigned hh, l;
+    split_tf32(Bg[i], hh, l);
+    const uint32_t off = ((k >> 2) * (KR / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (k & 3) * 4;
+    *reinterpret_cast<unsigned*>(Bhi + off) = hh;
+    *reinterpret_cast<unsigned*>(Blo + off) = l;
+  }
+  const uint32_t mb_full = smem_u32(mbar), mb_done = smem_u32(mbar + 1);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full), "r"(NC));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(S::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const u64 gstep = (u64)gridDim.x * kUT;
+  if (warp == NC / 32) {
+    if ((t & 31) == 0) {
+      const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+      constexpr uint32_t idesc = umma_idesc(kUT, KR);
+      uint32_t ph = 0, d = 0;
+      for (u64 g = (u64)blockIdx.x * kUT; g < ngroups; g += gstep) {
+        if (!mbar_wait(mb_full, ph)) {
+          atomicExch(&g_umma_timeout, 1);
+          break;
+        }
+        ph ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dt = tmem + 2 * KR + d * KR;
+#pragma unroll
+        for (int ks = 0; ks < KR / 8; ++ks) {
+          const uint32_t bo = ks * 2 * S::LBO_B;
+          const uint64_t dbh = umma_desc(bhi + bo, S::LBO_B, S::SBO), dbl = umma_desc(blo + bo, S::LBO_B, S::SBO);
+          const uint32_t ahi_t = tmem + (uint32_t)(ks * 8), alo_t = tmem + (uint32_t)(KR + ks * 8);
+          umma_tf32_ta(dt, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
+          umma_tf32_ta(dt, ahi_t, dbl, idesc, 1u);
+          umma_tf32_ta(dt, ahi_t, dbh, idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_done));
+        d ^= 1u;
+      }
+    }
+    __syncwarp();
+  } else {
+    const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
+    float4* stg = reinterpret_cast<float4*>(nout_s + H * kUT) + warp * kStgWarp;
+    // this warp's 32 lanes (= its rows), and this thread's 32 columns in each region
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 32);
+    float4 w[CH];  // the next tile's words, loaded one tile ahead
+    auto load = [&](u64 g) {
+      if (g < ngroups) rows_load<K>(a, g, j0, w);
+    };
+    // the tile (128 groups x 2^K amplitudes, contiguous) into L2 as 16 runs
+    // of 8 groups
+    auto prefetch = [&](u64 g) {
+      if (g < ngroups && t < 16) prefetch_bulk_l2(a + ((g + 8 * (u64)t) << K), 8u << (K + 3));
+    };
+    u64 g = (u64)blockIdx.x * kUT;
+    load(g);
+    prefetch(g + gstep);
+    // the tile whose MMAs were issued last and whose epilogue is still to run
+    bool pend = false, ok = true;
+    u64 pg = 0;
+    float pnin = 0.f;
+    uint32_t pd = 0, ph = 0, dsel = 0;
+    auto mma_done = [&]() -> bool {
+      if (!named_and(3, NC, mbar_wait(mb_done, ph))) {
+        if (t == 0) atomicExch(&g_umma_timeout, 1);
+        return false;
+      }
+      ph ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      return true;
+    };
+    // the pending tile's epilogue, 16 columns at a time: the output norm
+    // (one TMEM read), then the scaled scatter (a second read)
+    auto epilogue = [&]() {
+      float gsc = 0.f;  // output = o (1 + gsc)
+      if (renorm) {
+        float nout = 0.f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float o[16];
+          tmem_ld16(tl + pd + 16 * half, o);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) nout = fmaf(o[j], o[j], nout);
+        }
+        nout_s[h * kUT + row] = nout;
+        named_sync(2, NC);
+        nout = 0.f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
+        gsc = norm_correction(pnin, nout);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float o[16];
+        tmem_ld16(tl + pd + 16 * half, o);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          stg[(t & 31) * kStgPitch + 4 * half + j] =
+              make_float4(fmaf(o[4 * j], gsc, o[4 * j]), fmaf(o[4 * j + 1], gsc, o[4 * j + 1]),
+                          fmaf(o[4 * j + 2], gsc, o[4 * j + 2]), fmaf(o[4 * j + 3], gsc, o[4 * j + 3]));
+      }
+      rows_flush<K>(a, pg, j0, stg);
+      asm volatile("tcgen05.fence::before_thread_sync;");
+    };
+    while (g < ngroups) {
+      if (pend && !mma_done()) {
+        ok = false;
+        break;
+      }
+      rows_to_lane(w, stg);
+      float nin = 0.f;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {  // 16 columns (4 words) at a time
+        unsigned hv[16], lv[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float x[4] = {w[4 * half + j].x, w[4 * half + j].y, w[4 * half + j].z, w[4 * half + j].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            nin = fmaf(x[i], x[i], nin);
+            split_tf32(x[i], hv[4 * j + i], lv[4 * j + i]);
+          }
+        }
+        tmem_st16(tl + (uint32_t)(16 * half), hv);
+        tmem_st16(tl + (uint32_t)(KR + 16 * half), lv);
+      }
+      nin_s[h * kUT + row] = nin;
+      asm volatile("tcgen05.wait::st.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(mb_full);
+      load(g + gstep);
+      prefetch(g + 2 * gstep);
+      named_sync(1, NC);
+      nin = 0.f;
+#pragma unroll
+      for (int i = 0; i < H; ++i) nin += nin_s[i * kUT + row];
+      if (pend) epilogue();
+      pend = true;
+      pg = g;
+      pnin = nin;
+      pd = 2 * KR + dsel * KR;
+      dsel ^= 1u;
+      g += gstep;
+    }
+    if (ok && pend && mma_done()) epilogue();
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
+}
+
+// Grid for a block kernel: CTAs per SM from shared memory, registers and TMEM
+// columns (the occupancy query does not know about TMEM), times the SMs.
+template <int K, typename Kern>
+qs_status block_grid(qs_state* s, Kern kern, int nthreads, size_t smem, int tcols, unsigned& grid) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return cuda_fail(e, "fused_umma: smem attribute");
+  if (e != cudaSuccess) return cuda_fail(e, "fused_tc: smem attribute");
   int dev = 0, smem_sm = 0, smem_rsv = 0;
   cudaFuncAttributes fa{};
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) return cuda_fail(e, "fused_umma: occupancy attributes");
+  if (e != cudaSuccess) return cuda_fail(e, "fused_tc: occupancy attributes");
   int per_sm = smem_sm / (int)(smem + smem_rsv);
   const int regs = fa.numRegs > 0 ? ((fa.numRegs + 7) & ~7) : 255;
-  per_sm = std::min(per_sm, 65536 / (regs * S::NT));
-  per_sm = std::min(per_sm, 512 / (int)S::TCOLS);
+  per_sm = std::min(per_sm, 65536 / (regs * nthreads));
+  per_sm = std::min(per_sm, 512 / tcols);
   if (per_sm < 1) per_sm = 1;
-  const unsigned grid = grid_for(ngroups, kUT, per_sm);
-  kern<<<grid, S::NT, smem, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode);
+  grid = grid_for(u64(1) << (s->n - K), kUT, per_sm);
+  return QS_OK;
+}
+
+template <int K>
+qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renorm, const int* qubits) {
+  const u64 ngroups = u64(1) << (s->n - K);
+  const bool full = ngroups >= (u64)kUT;
+  unsigned grid = 0;
+  // qubits ascending: the block is qubits 0 .. K-1 exactly when the last is K-1
+  if (full && qubits[K - 1] == K - 1) {
+    typedef RowsShape<K> S;
+    qs_status st = block_grid<K>(s, k_fused_umma_rows<K>, S::NTT, S::SMEM, S::TCOLS, grid);
+    if (st != QS_OK) return st;
+    k_fused_umma_rows<K><<<grid, S::NTT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, renorm);
+    return launch_ok("k_fused_umma_rows");
+  }
+  typedef TaShape<K> S;
+  // access mode (see group_load); 8-byte accesses measured faster than the
+  // lane-pair exchange at k = 6 once a warp's 32 groups are contiguous
+  // (lowest block qubit >= 5); L2 prefetch helped k = 4, 5 and slowed k = 6
+  const int lmode = qubits[0] == 0 ? 1 : (full && !(K == 6 && qubits[0] >= 5) ? 2 : 0);
+  const int pf = K < 6 && full;
+  qs_status st = block_grid<K>(s, k_fused_umma<K>, S::NT, S::SMEM, S::TCOLS, grid);
+  if (st != QS_OK) return st;
+  k_fused_umma<K><<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, renorm, lmode, pf);
   return launch_ok("k_fused_umma");
 }
 
