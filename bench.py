@@ -52,7 +52,10 @@ WORKLOADS = {
 # scale it by 2^(n - 26).  Set to None whenever the kernel changes until it
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
-BLOCK_C64_TRAFFIC_26Q = {6: 537.053696e6 + 476.197120e6}  # k_fused_umma<6>, profiles/fused_umma_k6_brick26.md
+BLOCK_C64_TRAFFIC_26Q = {  # profiles/fused_umma_k6_brick26.md
+    "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
+    "k_fused_umma_rows<6>": 537.331968e6 + 476.636160e6,
+}
 S_BYTES = {"c64": 8, "c128": 16}
 
 
@@ -263,10 +266,25 @@ def circuit_flops(circ, n):
     return f
 
 
+def step_kernel(plan, i, kind):
+    """The kernel a plan step launches: block steps are told apart by their
+    qubits (complex64 blocks on qubits 0..k-1 with at least 128 groups run
+    k_fused_umma_rows<k>, other complex64 blocks k_fused_umma<k>, complex128
+    blocks the SIMT k_dense); other steps keep their kind."""
+    if kind != "block":
+        return kind
+    q = sorted(plan.step_qubits(i))
+    k = len(q)
+    if plan.dtype == "c64" and k >= 4:
+        rows = q == list(range(k)) and plan.n - k >= 7
+        return ("k_fused_umma_rows<%d>" if rows else "k_fused_umma<%d>") % k
+    return "k_dense<%d>" % k
+
+
 def kernel_roofline(plan, step_ms, peak):
-    """Per step kind: algorithmic bytes and device time summed over the timed
-    steps; the dominant kind (largest time) gives the roofline object."""
-    info = plan.step_info()
+    """Per kernel: algorithmic bytes and device time summed over the timed
+    steps; the dominant kernel (largest time) gives the roofline object."""
+    info = [(step_kernel(plan, i, kind), b) for i, (kind, b) in enumerate(plan.step_info())]
     tot_t, tot_b, cnt = {}, {}, {}
     for ms in step_ms:
         for (kind, b), t in zip(info, ms):
@@ -414,12 +432,12 @@ def run_ours(args):
             elif TILE_C64_TRAFFIC_26Q is not None:
                 roof["traffic"] = TILE_C64_TRAFFIC_26Q * 2.0 ** (n - 26)
                 roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 26 qubits, scaled by 2^(n-26)"
-        elif roof and roof["kernel"] == "block" and dt == "c64":
+        elif roof and roof["kernel"].startswith("k_fused_umma") and dt == "c64":
             roof["tensor"] = "tcgen05.mma kind::tf32, 3 MMAs (3xTF32) per K step, TMEM accumulator"
-            if fq in BLOCK_C64_TRAFFIC_26Q:
-                roof["traffic"] = BLOCK_C64_TRAFFIC_26Q[fq] * 2.0 ** (n - 26)
-                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_fused_umma<%d> "
-                                          "at 26 qubits, scaled by 2^(n-26)" % fq)
+            if roof["kernel"] in BLOCK_C64_TRAFFIC_26Q:
+                roof["traffic"] = BLOCK_C64_TRAFFIC_26Q[roof["kernel"]] * 2.0 ** (n - 26)
+                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s "
+                                          "at 26 qubits, scaled by 2^(n-26)" % roof["kernel"])
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
         # launches per step: one per plan step, k_set_one, and for complex128

@@ -1,0 +1,32 @@
+"""Host-side pieces of bench.py (no GPU): which kernel each plan step is
+attributed to in the roofline."""
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2203_16044_gb300 as qs
+    return qs
+
+
+def test_step_kernel_labels(qs):
+    import bench
+    n = 14
+    p = qs.Plan(qs.Circuit(W.brick(n, 12, 3)), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=6)
+    seen = set()
+    for i, (kind, _) in enumerate(p.step_info()):
+        lab = bench.step_kernel(p, i, kind)
+        if kind != "block":
+            assert lab == kind
+            continue
+        q = sorted(p.step_qubits(i))
+        want = "k_fused_umma_rows" if q == list(range(len(q))) else "k_fused_umma"
+        assert lab == "%s<%d>" % (want, len(q))
+        seen.add(want)
+    # a brick plan has both: a block on the lowest qubits and others
+    assert seen == {"k_fused_umma_rows", "k_fused_umma"}
+    p128 = qs.Plan(qs.Circuit(W.brick(8, 4, 3)), 8, "c128", mode=qs.PLAN_FUSED, fuse_qubits=4)
+    labs = {bench.step_kernel(p128, i, k) for i, (k, _) in enumerate(p128.step_info())}
+    assert all(lab.startswith("k_dense<") for lab in labs if lab.startswith("k_"))
