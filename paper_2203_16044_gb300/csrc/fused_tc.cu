@@ -9,11 +9,19 @@
 //   B[2c][2r+1] = Im M[r][c], B[2c+1][2r+1] = Re M[r][c].
 // Its arithmetic intensity, 2D flops per byte moved at complex64, passes the
 // GB300 FP32-SIMT ridge for k >= 4, so it runs on the 5th-generation tensor
-// cores (tcgen05.mma, kind::tf32, FP32 accumulation in tensor memory).  Each
-// FP32 operand is split as x ~ hi + lo (hi = x rounded to TF32, lo = x - hi
-// rounded to TF32) and a product is formed from three MMAs, lo*hi + hi*lo +
-// hi*hi ("3xTF32"): about 22 significant bits per product with unbiased
-// rounding, FP32-level for the complex64 path.
+// cores (tcgen05.mma, FP32 accumulation in tensor memory).  Each FP32 operand
+// is split as x ~ hi + lo and a product is formed from three MMAs, lo*hi +
+// hi*lo + hi*hi: with TF32 parts (kind::tf32, "3xTF32") or with FP16 parts
+// under exact power-of-two scaling (kind::f16, twice the rate); either way
+// about 22 significant bits per product with unbiased rounding, FP32-level
+// for the complex64 path.
+//
+// Three kernels, by the block's qubits (sorted ascending):
+//   k_fused_umma_tma   a window s .. s+k-1 with s >= 5: each tile is one TMA
+//                      box; FP16 parts.
+//   k_fused_umma_rows  qubits 0 .. k-1: contiguous rows through shared-memory
+//                      transposes, warp-specialised; TF32 parts.
+//   k_fused_umma       any other set: per-thread gathers; TF32 parts.
 //
 // Tensor-core FP32 accumulation truncates its internal sums (rounds toward
 // zero), which shrinks every output by about an ulp per block -- a bias, not
@@ -26,6 +34,10 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include "kcommon.cuh"
 
@@ -439,6 +451,264 @@ __global__ void __launch_bounds__(TaShape<K>::NT, 512 / TaShape<K>::TCOLS)
 }
 
 // ---------------------------------------------------------------------------
+// FP16 split for the TMA-fed kernel below (kind::f16, twice the TF32 rate).
+// Each operand is split x ~ hi + lo with hi = fp16(x), lo = fp16(x - hi),
+// both round-to-nearest: 11 significant bits each, the same 22-bit products
+// as 3xTF32 from the same three MMAs per K step.  FP16's narrow exponent
+// range is handled with exact powers of two: the block matrix is scaled by
+// 2^f so that max |b| < 2^14, and each group (row) by 2^e so that its norm,
+// hence every |x|, is below 2^14 (e from the row's sum of squares, which the
+// norm restore needs anyway); the accumulator is scaled back by 2^-(e + f)
+// before the epilogue.  Values far below their row's or the matrix's maximum
+// keep an absolute error of about 2^-24 of that maximum.  TMEM: A hi
+// [0, D), A lo [D, 2D) (two FP16 values per 32-bit column, even K index in
+// the low half), accumulator [2D, 4D).  (With the tile gathered by
+// per-thread loads, as in k_fused_umma, this halved the MMA time without
+// making the kernel faster: the load issue then took its place.)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // -126 <= e <= 127
+// E with v in [2^E, 2^(E+1)) for a positive normal float (-127 for subnormals)
+__device__ __forceinline__ int fexp(float v) { return ((__float_as_int(v) >> 23) & 255) - 127; }
+// scale exponent of a value set whose maximum magnitude is below 2^(E+1):
+// the scaled maximum stays below 2^14, and e + f stays within [-126, 126]
+__device__ __forceinline__ int scale_exp(int E, int lo, int hi) { return max(lo, min(hi, 13 - E)); }
+__device__ __forceinline__ uint32_t h2bits(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+// (a, b) -> FP16 pairs hi = (fp16(a), fp16(b)), lo = residuals, a in the low half
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  hi = h2bits(h);
+  lo = h2bits(__floats2half2_rn(a - hf.x, b - hf.y));
+}
+__device__ __forceinline__ void umma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc));
+}
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at 24.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// Blocks on a window of consecutive qubits s .. s+k-1 with s >= 5 (full
+// tiles): k_fused_umma_tma.  An amplitude index is then hi 2^(s+k) + e 2^s
+// + lo (e the block index, lo < 2^s), so a tile of 128 consecutive groups is
+// one box of the 3-D tensor (lo, e, hi): a single TMA copy
+// (cp.async.bulk.tensor, completion counted on an mbarrier) moves it into
+// shared memory, with no per-thread load instructions and no registers
+// held.  In the stage, element e of tile row r sits at
+// ((r >> sp) D + e) 2^sp + (r mod 2^sp), sp = min(s, 7): a warp's 32 rows are
+// 32 consecutive 8-byte words for every e (s >= 5), conflict-free.  The
+// stage is refilled with the next tile as soon as every thread has split
+// the current one into TMEM, so the copy runs under the MMAs and the
+// epilogue.  Arithmetic as k_fused_umma_h (FP16 split, kind::f16); the
+// scatter uses 8-byte stores.  Shared memory: stage 64 KB + B 64 KB at k = 6.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+template <int K>
+struct TShape {
+  static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NT = kUT * H;
+  static constexpr uint32_t STAGE = kUT * D * 8;  // one tile: 128 groups x 2^K amplitudes
+  static constexpr uint32_t B_BYTES = KR * KR * 2, LBO_B = (KR / 8) * 128, SBO = 128;
+  static constexpr uint32_t TCOLS = 2 * KR;  // A hi, A lo (KR / 2 each), accumulator
+  static constexpr size_t SMEM = STAGE + 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float);
+  static constexpr int MINB = K == 6 ? 1 : (K == 5 ? 2 : 4);  // register-limited
+};
+
+template <int K>
+__global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
+    k_fused_umma_tma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
+                     const __grid_constant__ FusedArgs args, const __grid_constant__ CUtensorMap tmap, int renorm,
+                     int s_lo) {
+  typedef TShape<K> S;
+  constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT;
+  constexpr int CH = 8;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const float2* stage = reinterpret_cast<const float2*>(sm);
+  unsigned char* Bhi = sm + S::STAGE;
+  unsigned char* Blo = Bhi + S::B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] tile loaded, [1] MMAs done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint32_t* bmax_s = tslot + 1;
+  float* nin_s = reinterpret_cast<float*>(mbar + 4);  // [H][kUT] partial input norms
+  float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
+  const int t = threadIdx.x, warp = t >> 5;
+  const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
+  const uint32_t mb_full = smem_u32(mbar), mb_mma = smem_u32(mbar + 1);
+  const u64 gstep = (u64)gridDim.x * kUT;
+  const u64 lmask = (u64(1) << s_lo) - 1;
+  u64 g = (u64)blockIdx.x * kUT;
+  auto tile_load = [&](u64 gt) {  // one thread
+    mbar_expect_tx(mb_full, S::STAGE);
+    tma_load_3d(smem_u32(stage), &tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), mb_full);
+  };
+  if (t == 0) {
+    *bmax_s = 0u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_full));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (g < ngroups) tile_load(g);  // under the B set-up
+  }
+  __syncthreads();
+  {
+    float m = 0.f;
+    for (int i = t; i < KR * KR; i += NT) m = fmaxf(m, fabsf(Bg[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0) atomicMax(bmax_s, __float_as_uint(m));
+  }
+  __syncthreads();
+  const float bmax = __uint_as_float(*bmax_s);
+  const int f = bmax > 0.f ? scale_exp(fexp(bmax), -100, 100) : 0;
+  {
+    const float sb = pow2f(f);
+    for (int i = t; i < KR * KR; i += NT) {
+      const int k = i / KR, n = i % KR;
+      const float b = Bg[i] * sb;
+      const __half hh = __float2half_rn(b);
+      const __half ll = __float2half_rn(b - __half2float(hh));
+      const uint32_t off = ((k >> 3) * (KR / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+      *reinterpret_cast<__half*>(Bhi + off) = hh;
+      *reinterpret_cast<__half*>(Blo + off) = ll;
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(S::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t ta = tmem + lanes + (uint32_t)(h * 16), td = tmem + lanes + (uint32_t)(KR + h * 32);
+  const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+  constexpr uint32_t idesc = umma_idesc_f16(kUT, KR);
+  const int sp = s_lo < 7 ? s_lo : 7;
+  // this row's words in the stage: element e at sbase + (e << sp)
+  const int sbase = (((row >> sp) * D) << sp) + (row & ((1 << sp) - 1));
+  uint32_t ph_full = 0, ph_mma = 0;
+  while (g < ngroups) {
+    const bool loaded = mbar_wait(mb_full, ph_full);
+    ph_full ^= 1u;
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = stage[sbase + ((16 * h + i) << sp)];
+    float nin = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) nin = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, nin));
+    nin_s[h * kUT + row] = nin;
+    if (!__syncthreads_and(loaded ? 1 : 0)) {
+      if (t == 0) atomicExch(&g_umma_timeout, 1);
+      break;
+    }
+    nin = 0.f;
+#pragma unroll
+    for (int i = 0; i < H; ++i) nin += nin_s[i * kUT + row];
+    const int e = (nin > 0.f && nin < INFINITY) ? scale_exp((fexp(nin) + 2) >> 1, -126 - f, 126 - f) : 0;
+    {
+      const float sx = pow2f(e);
+      uint32_t hv[16], lv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) split_f16x2(v[i].x * sx, v[i].y * sx, hv[i], lv[i]);
+      tmem_st16(ta, hv);
+      tmem_st16(ta + (uint32_t)(KR / 2), lv);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // A written, and every thread is done with the stage
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (t == 0) {
+      if (g + gstep < ngroups) tile_load(g + gstep);
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ++ks) {
+        const uint32_t bo = ks * 2 * S::LBO_B;
+        const uint64_t dbh = umma_desc(bhi + bo, S::LBO_B, S::SBO), dbl = umma_desc(blo + bo, S::LBO_B, S::SBO);
+        const uint32_t ahi_t = tmem + (uint32_t)(ks * 8), alo_t = tmem + (uint32_t)(KR / 2 + ks * 8);
+        umma_f16_ta(tmem + KR, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
+        umma_f16_ta(tmem + KR, ahi_t, dbl, idesc, 1u);
+        umma_f16_ta(tmem + KR, ahi_t, dbh, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
+    }
+    const u64 base = expand(g + row, args.ins);
+    if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma) ? 1 : 0)) {
+      if (t == 0) atomicExch(&g_umma_timeout, 1);
+      break;
+    }
+    ph_mma ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float o[32];
+    tmem_ld16(td, o);
+    tmem_ld16(td + 16, o + 16);
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    const float so = pow2f(-(e + f));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) o[j] *= so;
+    float gsc = 0.f;
+    if (renorm) {
+      float nout = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) nout = fmaf(o[j], o[j], nout);
+      nout_s[h * kUT + row] = nout;
+      __syncthreads();
+      nout = 0.f;
+#pragma unroll
+      for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
+      gsc = norm_correction(nin, nout);
+    }
+    group_store<D, CH>(a, base, true, args.spread, 0, j0, o, gsc);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    g += gstep;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
+}
+
+// The 3-D tensor map (lo, e, hi) of a state for a block on qubits
+// s .. s+k-1, box = one tile (128 groups).
+qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled not available");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int sp = s_lo < 7 ? s_lo : 7;
+  const cuuint64_t dims[3] = {cuuint64_t(1) << s_lo, cuuint64_t(1) << k, cuuint64_t(1) << (st->n - s_lo - k)};
+  const cuuint64_t strides[2] = {(cuuint64_t(1) << s_lo) * 8, (cuuint64_t(1) << (s_lo + k)) * 8};
+  const cuuint32_t box[3] = {1u << sp, 1u << k, 1u << (7 - sp)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, st->amp, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Blocks on qubits 0 .. k-1 (full tiles): k_fused_umma_rows.  A tile is then
 // 128 x 2^k contiguous amplitudes; the warps move it with rows_load /
 // rows_flush (4 rows x 128 bytes per instruction, transposed through the
@@ -699,6 +969,18 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
     if (st != QS_OK) return st;
     k_fused_umma_rows<K><<<grid, S::NTT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, renorm);
     return launch_ok("k_fused_umma_rows");
+  }
+  // a window of consecutive qubits from 5 up: one TMA box per tile
+  if (full && qubits[0] >= 5 && qubits[K - 1] == qubits[0] + K - 1) {
+    typedef TShape<K> ST;
+    CUtensorMap map;
+    qs_status st = make_block_tmap(s, K, qubits[0], &map);
+    if (st != QS_OK) return st;
+    st = block_grid<K>(s, k_fused_umma_tma<K>, ST::NT, ST::SMEM, ST::TCOLS, grid);
+    if (st != QS_OK) return st;
+    k_fused_umma_tma<K><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, map,
+                                                                 renorm, qubits[0]);
+    return launch_ok("k_fused_umma_tma");
   }
   typedef TaShape<K> S;
   // access mode (see group_load); 8-byte accesses measured faster than the

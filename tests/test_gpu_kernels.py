@@ -236,6 +236,9 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     (16, "high"),         # the block on the highest qubits
     (15, "low"),          # the block is qubits 0 .. k-1: staged row transposes
     (8, "low"),           # ... with fewer than 128 groups (16-byte pairs)
+    (14, "window5"),      # a window of consecutive qubits from 5 (TMA boxes of 4 x 32 rows)
+    (15, "window6"),      # ... from 6 (2 x 64 rows)
+    (17, "window8"),      # ... from 8 (one run of 128 rows)
 ])
 def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
     # complex64 k = 4, 5, 6 blocks run on tcgen05; each way a group's
@@ -248,6 +251,9 @@ def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
         qsel = [2, 9, 5, 12, 1, 7][:k]
     elif qubits == "low":
         qsel = [q for q in [2, 0, 3, 1, 5, 4] if q < k]
+    elif qubits.startswith("window"):
+        s0 = int(qubits[6:])
+        qsel = [s0 + i for i in [3, 0, 5, 1, 4, 2] if i < k]
     else:
         qsel = list(range(n - 1, n - 1 - k, -1))
     psi = W.random_state(n, 7500 + n + k)
