@@ -269,7 +269,7 @@ def circuit_flops(circ, n):
 def step_kernel(plan, i, kind):
     """The kernel a plan step launches: block steps are told apart by their
     qubits (complex64, at least 128 groups: a window of consecutive qubits
-    from 5 up runs k_fused_umma_tma<k>, qubits 0..k-1 k_fused_umma_rows<k>;
+    from 2 up runs k_fused_umma_tma<k>, qubits 0..k-1 k_fused_umma_rows<k>;
     other complex64 blocks k_fused_umma<k>, complex128 blocks the SIMT
     k_dense); other steps keep their kind."""
     if kind != "block":
@@ -278,7 +278,7 @@ def step_kernel(plan, i, kind):
     k = len(q)
     if plan.dtype == "c64" and k >= 4:
         full = plan.n - k >= 7
-        if full and q[0] >= 5 and q == list(range(q[0], q[0] + k)):
+        if full and q[0] >= 2 and q == list(range(q[0], q[0] + k)):
             return "k_fused_umma_tma<%d>" % k
         if full and q == list(range(k)):
             return "k_fused_umma_rows<%d>" % k

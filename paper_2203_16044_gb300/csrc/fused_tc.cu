@@ -17,7 +17,7 @@
 // for the complex64 path.
 //
 // Three kernels, by the block's qubits (sorted ascending):
-//   k_fused_umma_tma   a window s .. s+k-1 with s >= 5: each tile is one TMA
+//   k_fused_umma_tma   a window s .. s+k-1 with s >= 2: each tile is one TMA
 //                      box; FP16 parts.
 //   k_fused_umma_rows  qubits 0 .. k-1: contiguous rows through shared-memory
 //                      transposes, warp-specialised; TF32 parts.
@@ -494,7 +494,7 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
 }
 
 // ---------------------------------------------------------------------------
-// Blocks on a window of consecutive qubits s .. s+k-1 with s >= 5 (full
+// Blocks on a window of consecutive qubits s .. s+k-1 with s >= 2 (full
 // tiles): k_fused_umma_tma.  An amplitude index is then hi 2^(s+k) + e 2^s
 // + lo (e the block index, lo < 2^s), so a tile of 128 consecutive groups is
 // one box of the 3-D tensor (lo, e, hi): a single TMA copy
@@ -502,7 +502,9 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
 // shared memory, with no per-thread load instructions and no registers
 // held.  In the stage, element e of tile row r sits at
 // ((r >> sp) D + e) 2^sp + (r mod 2^sp), sp = min(s, 7): a warp's 32 rows are
-// 32 consecutive 8-byte words for every e (s >= 5), conflict-free.  The
+// 32 consecutive 8-byte words for every e when s >= 5, 32 / 2^s runs of
+// 2^s words D 2^s words apart otherwise (2-way bank conflicts at s = 3,
+// 4-way at s = 2; measured still faster than the per-thread gather).  The
 // stage is refilled with the next tile as soon as every thread has split
 // the current one into TMEM, so the copy runs under the MMAs and the
 // epilogue.  Arithmetic as k_fused_umma_h (FP16 split, kind::f16); the
@@ -970,8 +972,9 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
     k_fused_umma_rows<K><<<grid, S::NTT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, renorm);
     return launch_ok("k_fused_umma_rows");
   }
-  // a window of consecutive qubits from 5 up: one TMA box per tile
-  if (full && qubits[0] >= 5 && qubits[K - 1] == qubits[0] + K - 1) {
+  // a window of consecutive qubits from 2 up: one TMA box per tile (from
+  // qubit 1 the stage reads conflict 8-way and the gather path is faster)
+  if (full && qubits[0] >= 2 && qubits[K - 1] == qubits[0] + K - 1) {
     typedef TShape<K> ST;
     CUtensorMap map;
     qs_status st = make_block_tmap(s, K, qubits[0], &map);

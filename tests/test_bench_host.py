@@ -22,7 +22,7 @@ def test_step_kernel_labels(qs):
             assert lab == kind
             continue
         q = sorted(p.step_qubits(i))
-        if q[0] >= 5 and q == list(range(q[0], q[0] + len(q))):
+        if q[0] >= 2 and q == list(range(q[0], q[0] + len(q))):
             want = "k_fused_umma_tma"
         elif q == list(range(len(q))):
             want = "k_fused_umma_rows"
@@ -30,7 +30,7 @@ def test_step_kernel_labels(qs):
             want = "k_fused_umma"
         assert lab == "%s<%d>" % (want, len(q))
         seen.add(want)
-    # a brick plan has all three: windows from qubit 5 up, a block on the
+    # a brick plan has all three: windows from qubit 2 up, a block on the
     # lowest qubits, and others
     assert seen == {"k_fused_umma_tma", "k_fused_umma_rows", "k_fused_umma"}
     p128 = qs.Plan(qs.Circuit(W.brick(8, 4, 3)), 8, "c128", mode=qs.PLAN_FUSED, fuse_qubits=4)

@@ -236,7 +236,9 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     (16, "high"),         # the block on the highest qubits
     (15, "low"),          # the block is qubits 0 .. k-1: staged row transposes
     (8, "low"),           # ... with fewer than 128 groups (16-byte pairs)
-    (14, "window5"),      # a window of consecutive qubits from 5 (TMA boxes of 4 x 32 rows)
+    (14, "window2"),      # a window of consecutive qubits from 2 (TMA boxes of 32 x 4 rows)
+    (14, "window3"),      # ... from 3 (16 x 8 rows)
+    (14, "window5"),      # ... from 5 (4 x 32 rows)
     (15, "window6"),      # ... from 6 (2 x 64 rows)
     (17, "window8"),      # ... from 8 (one run of 128 rows)
 ])
