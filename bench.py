@@ -53,6 +53,7 @@ WORKLOADS = {
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
 BLOCK_C64_TRAFFIC_26Q = {  # profiles/fused_umma_k6_brick26.md
+    "k_fused_umma_tma<6>": 536.997888e6 + 475.854080e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
     "k_fused_umma_rows<6>": 537.331968e6 + 476.636160e6,
 }
@@ -438,7 +439,10 @@ def run_ours(args):
                 roof["traffic"] = TILE_C64_TRAFFIC_26Q * 2.0 ** (n - 26)
                 roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at 26 qubits, scaled by 2^(n-26)"
         elif roof and roof["kernel"].startswith("k_fused_umma") and dt == "c64":
-            roof["tensor"] = "tcgen05.mma kind::tf32, 3 MMAs (3xTF32) per K step, TMEM accumulator"
+            roof["tensor"] = ("tcgen05.mma kind::f16, 3 MMAs per K step (FP16 hi/lo split under power-of-two "
+                              "scaling), TMEM accumulator; one TMA box per 128-group tile"
+                              if roof["kernel"].startswith("k_fused_umma_tma") else
+                              "tcgen05.mma kind::tf32, 3 MMAs (3xTF32) per K step, TMEM accumulator")
             if roof["kernel"] in BLOCK_C64_TRAFFIC_26Q:
                 roof["traffic"] = BLOCK_C64_TRAFFIC_26Q[roof["kernel"]] * 2.0 ** (n - 26)
                 roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s "
