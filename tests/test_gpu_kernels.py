@@ -234,9 +234,11 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     (14, "with0"),        # qubit 0 in the block: 16-byte amplitude pairs
     (14, "without0"),     # qubit 0 outside: lane pairs exchange halves
     (16, "high"),         # the block on the highest qubits
+    (13, "high"),         # ... with k = 6 exactly one 128-group tile
     (15, "low"),          # the block is qubits 0 .. k-1: staged row transposes
     (8, "low"),           # ... with fewer than 128 groups (16-byte pairs)
     (14, "window2"),      # a window of consecutive qubits from 2 (TMA boxes of 32 x 4 rows)
+    (13, "window2"),      # ... one tile at k = 6
     (14, "window3"),      # ... from 3 (16 x 8 rows)
     (14, "window5"),      # ... from 5 (4 x 32 rows)
     (15, "window6"),      # ... from 6 (2 x 64 rows)
