@@ -293,6 +293,55 @@ std::vector<char> greedy_set(const std::vector<const qs_gate_rec*>& remaining, i
   return inB;
 }
 
+// The qubits touched by a candidate block's gates.
+std::vector<char> touched(const std::vector<const qs_gate_rec*>& gates, int n) {
+  std::vector<char> used(n, 0);
+  for (const qs_gate_rec* g : gates)
+    for (int j = 0; j < gate_arity(g->kind); ++j) used[g->q[j]] = 1;
+  return used;
+}
+
+// Complex64 tensor-core blocks: the qubits a block runs on, given those its
+// gates touch.  Idle qubits cost nothing there (a block is one HBM pass
+// whatever its width), but the kernel depends on the set's shape: a window
+// of consecutive qubits starting at 2 or above (one TMA box per tile), or at
+// 0 (contiguous rows), moves tiles whole; other sets gather per thread and
+// run at about 0.7 of the speed.  The touched qubits are widened to the
+// narrowest such window that holds them (at least 4 qubits, at most kmax,
+// starting at 2 or above if possible); when none exists, to 4 qubits with
+// the lowest idle ones.  *fast tells which.
+std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax, bool* fast) {
+  int lo = n, hi = -1, nused = 0;
+  for (int q = 0; q < n; ++q)
+    if (used[q]) {
+      lo = std::min(lo, q);
+      hi = std::max(hi, q);
+      ++nused;
+    }
+  std::vector<int> bq;
+  if (hi >= 0) {
+    for (int m = std::max(4, hi - lo + 1); m <= kmax && m <= n; ++m) {
+      int pick = -1;
+      for (int w = std::max(0, hi - m + 1); w <= lo && w + m <= n; ++w) {
+        if (w >= 2) { pick = w; break; }
+        if (w == 0 && pick < 0) pick = 0;
+      }
+      if (pick >= 0) {
+        for (int q = pick; q < pick + m; ++q) bq.push_back(q);
+        *fast = true;
+        return bq;
+      }
+    }
+  }
+  *fast = false;
+  std::vector<char> u = used;
+  for (int q = 0; q < n && nused < 4; ++q)
+    if (!u[q]) { u[q] = 1; ++nused; }
+  for (int q = 0; q < n; ++q)
+    if (u[q]) bq.push_back(q);
+  return bq;
+}
+
 qs_status plan_fused(qs_plan* p) {
   const int n = p->n;
   int kmax = p->opts.fuse_qubits > 0 ? p->opts.fuse_qubits : 5;
@@ -302,36 +351,45 @@ qs_status plan_fused(qs_plan* p) {
   for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
   while (!remaining.empty()) {
     // candidate qubit sets: the front-greedy set and every window of kmax
-    // consecutive qubits; the block takes the one that absorbs most gates
+    // consecutive qubits; the block takes the one that absorbs most gates,
+    // for complex64 tensor-core blocks weighted by the kernel its qubit set
+    // gets (a set that must gather per thread counts 0.7 per gate)
+    const bool tc = p->dtype == QS_C64 && kmax >= 4;
+    auto score = [&](const std::vector<char>& inS, int nS) {
+      std::vector<const qs_gate_rec*> abs;
+      const int taken = absorb_into(remaining, inS, nS, &abs, nullptr);
+      if (!tc) return 10 * taken;
+      bool fast = false;
+      tc_block_qubits(touched(abs, n), n, kmax, &fast);
+      return (fast ? 10 : 7) * taken;
+    };
     int nS = 0;
     std::vector<char> best = greedy_set(remaining, n, kmax, &nS);
-    int best_n = nS, best_taken = absorb_into(remaining, best, nS, nullptr, nullptr);
+    int best_n = nS, best_score = score(best, nS);
     for (int w = 0; w + kmax <= n; ++w) {
       std::vector<char> inS(n, 0);
       for (int q = w; q < w + kmax; ++q) inS[q] = 1;
-      const int taken = absorb_into(remaining, inS, kmax, nullptr, nullptr);
-      if (taken > best_taken) {
-        best_taken = taken;
+      const int sc = score(inS, kmax);
+      if (sc > best_score) {
+        best_score = sc;
         best = inS;
         best_n = kmax;
       }
     }
     std::vector<const qs_gate_rec*> absorbed, rest;
     absorb_into(remaining, best, best_n, &absorbed, &rest);
-    // the block's qubits: those its gates touch
-    std::vector<char> used(n, 0);
-    for (const qs_gate_rec* g : absorbed)
-      for (int j = 0; j < gate_arity(g->kind); ++j) used[g->q[j]] = 1;
-    // complex64 blocks of 4 or more qubits run on the tensor cores at HBM
-    // speed; a smaller block is widened with idle qubits (identity on them)
-    // rather than run on the SIMT dense kernel
-    int nused = 0;
-    for (int q = 0; q < n; ++q) nused += used[q];
-    for (int q = 0; q < n && p->dtype == QS_C64 && kmax >= 4 && nused < 4; ++q)
-      if (!used[q]) { used[q] = 1; ++nused; }
+    // the block's qubits: those its gates touch, for complex64 tensor-core
+    // blocks widened with idle qubits (identity on them) to a shape that runs
+    // at HBM speed, and at least 4 qubits rather than the SIMT dense kernel
+    const std::vector<char> used = touched(absorbed, n);
     std::vector<int> bq;
-    for (int q = 0; q < n; ++q)
-      if (used[q]) bq.push_back(q);
+    if (tc) {
+      bool fast = false;
+      bq = tc_block_qubits(used, n, kmax, &fast);
+    } else {
+      for (int q = 0; q < n; ++q)
+        if (used[q]) bq.push_back(q);
+    }
     qs_block b;
     b.k = (int)bq.size();
     for (int i = 0; i < b.k; ++i) b.q[i] = bq[i];
