@@ -53,9 +53,8 @@ WORKLOADS = {
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
 BLOCK_C64_TRAFFIC_26Q = {  # profiles/fused_umma_k6_brick26.md
-    "k_fused_umma_tma<6>": 536.997888e6 + 475.854080e6,
+    "k_fused_umma_tma<6,window>": 536.997888e6 + 475.854080e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
-    "k_fused_umma_rows<6>": 537.331968e6 + 476.636160e6,
 }
 S_BYTES = {"c64": 8, "c128": 16}
 
@@ -270,9 +269,9 @@ def circuit_flops(circ, n):
 def step_kernel(plan, i, kind):
     """The kernel a plan step launches: block steps are told apart by their
     qubits (complex64, at least 128 groups: a window of consecutive qubits
-    from 2 up runs k_fused_umma_tma<k>, qubits 0..k-1 k_fused_umma_rows<k>;
-    other complex64 blocks k_fused_umma<k>, complex128 blocks the SIMT
-    k_dense); other steps keep their kind."""
+    from 2 up runs k_fused_umma_tma<k,window>, qubits 0..k-1
+    k_fused_umma_tma<k,rows>; other complex64 blocks k_fused_umma<k>,
+    complex128 blocks the SIMT k_dense); other steps keep their kind."""
     if kind != "block":
         return kind
     q = sorted(plan.step_qubits(i))
@@ -280,9 +279,9 @@ def step_kernel(plan, i, kind):
     if plan.dtype == "c64" and k >= 4:
         full = plan.n - k >= 7
         if full and q[0] >= 2 and q == list(range(q[0], q[0] + k)):
-            return "k_fused_umma_tma<%d>" % k
+            return "k_fused_umma_tma<%d,window>" % k
         if full and q == list(range(k)):
-            return "k_fused_umma_rows<%d>" % k
+            return "k_fused_umma_tma<%d,rows>" % k
         return "k_fused_umma<%d>" % k
     return "k_dense<%d>" % k
 

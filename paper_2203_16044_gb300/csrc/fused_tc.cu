@@ -16,11 +16,10 @@
 // about 22 significant bits per product with unbiased rounding, FP32-level
 // for the complex64 path.
 //
-// Three kernels, by the block's qubits (sorted ascending):
-//   k_fused_umma_tma   a window s .. s+k-1 with s >= 2: each tile is one TMA
-//                      box; FP16 parts.
-//   k_fused_umma_rows  qubits 0 .. k-1: contiguous rows through shared-memory
-//                      transposes, warp-specialised; TF32 parts.
+// Two kernels, by the block's qubits (sorted ascending):
+//   k_fused_umma_tma   a window s .. s+k-1 with s >= 2, or qubits 0 .. k-1:
+//                      each tile moves by TMA (one 3-D box, or 2^k / 16
+//                      swizzled 2-D boxes in and out); FP16 parts.
 //   k_fused_umma       any other set: per-thread gathers; TF32 parts.
 //
 // Tensor-core FP32 accumulation truncates its internal sums (rounds toward
@@ -137,7 +136,8 @@ __device__ __forceinline__ float norm_correction(float nin, float nout) {
 //            lane both groups' amplitude 2j + 1, and group_take exchanges the
 //            halves.  The loads have no dependent instruction until the
 //            tile is consumed, so a prefetch stays in flight.
-// (A block on qubits 0 .. k-1 runs in k_fused_umma_rows instead.)
+// (Blocks on a window of qubits from 2 up, or on qubits 0 .. k-1, run in
+// k_fused_umma_tma instead.)
 template <int D, int CH>
 __device__ __forceinline__ void group_load(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
                                            int lmode, int j0, float4 (&w)[CH]) {
@@ -218,54 +218,6 @@ __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bo
   }
 }
 
-// Blocks on qubits 0 .. k-1 (k_fused_umma_rows): a group is 2^k contiguous
-// amplitudes, so the rows of a warp are 2^k * 8 bytes apart and one row per
-// lane would touch 32 cache lines per instruction.  Lane i of a warp (rows
-// rb .. rb + 31 of the tile starting at
-// group g, slice words j0 .. j0 + 7) moves word j0 + (i & 7) of row
-// rb + 4 m + (i >> 3) in instruction m.  The stage holds 32 rows of 8 words
-// with a row pitch of 9 words (144 bytes): a row written by 8 consecutive
-// lanes and a column read by 8 consecutive lanes (one row each) both fall on
-// distinct bank quads.
-constexpr int kStgPitch = 9;  // float4 words per staged row
-constexpr int kStgWarp = 32 * kStgPitch;
-template <int K>
-__device__ __forceinline__ void rows_load(const float2* __restrict__ a, u64 g, int j0, float4 (&w)[8]) {
-  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
-    w[m] = *reinterpret_cast<const float4*>(a + (G << K) + 2 * (j0 + (lane & 7)));
-  }
-}
-// the staged rows (each lane's row written to its stage row) to global
-// memory, 4 rows x 128 bytes per instruction
-template <int K>
-__device__ __forceinline__ void rows_flush(float2* __restrict__ a, u64 g, int j0, float4* stg) {
-  const int lane = threadIdx.x & 31, rb = ((threadIdx.x >> 5) & 3) * 32;
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const u64 G = g + (u64)(rb + 4 * m + (lane >> 3));
-    *reinterpret_cast<float4*>(a + (G << K) + 2 * (j0 + (lane & 7))) =
-        stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)];
-  }
-  __syncwarp();
-}
-// bytes (a multiple of 16) from p (16-byte aligned) into L2, no registers held
-__device__ __forceinline__ void prefetch_bulk_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-// words as loaded by rows_load -> w[j] = word j0 + j of this lane's row
-__device__ __forceinline__ void rows_to_lane(float4 (&w)[8], float4* stg) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int m = 0; m < 8; ++m) stg[(4 * m + (lane >> 3)) * kStgPitch + (lane & 7)] = w[m];
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < 8; ++j) w[j] = stg[lane * kStgPitch + j];
-  __syncwarp();
-}
 // ---------------------------------------------------------------------------
 // The block kernel (k = 4, 5, 6).  The MMA's A operand may
 // live in tensor memory (lane = row, one 32-bit column per K element), so the
@@ -507,8 +459,9 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
 // 4-way at s = 2; measured still faster than the per-thread gather).  The
 // stage is refilled with the next tile as soon as every thread has split
 // the current one into TMEM, so the copy runs under the MMAs and the
-// epilogue.  Arithmetic as k_fused_umma_h (FP16 split, kind::f16); the
-// scatter uses 8-byte stores.  Shared memory: stage 64 KB + B 64 KB at k = 6.
+// epilogue.  Arithmetic: the FP16 split above (kind::f16); the scatter uses
+// 8-byte stores.  Shared memory: stage 64 KB + B 64 KB at k = 6.  Blocks on
+// qubits 0 .. k-1 take the same kernel with ROWS set (below).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
@@ -523,27 +476,52 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-template <int K>
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(src)
+               : "memory");
+}
+
+// ROWS = false: a window s .. s+k-1 (s >= 2), one 3-D box per tile, 8-byte
+// stores.  ROWS = true: the block is qubits 0 .. k-1, so a tile is 128
+// contiguous rows of 2^k amplitudes: 2^k / 16 boxes of 16 amplitudes x 128
+// rows each, in 128-byte-swizzled layout (16-byte unit c of row r stored at
+// unit c ^ (r mod 8)), one per 16-amplitude slice, which is exactly one
+// thread's share of a row: the row reads and the output writes are then
+// conflict-free 16-byte accesses, and the outputs leave through a second
+// stage with TMA stores (a row per lane would touch 32 cache lines per
+// warp store).
+template <int K, bool ROWS>
 struct TShape {
   static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NT = kUT * H;
   static constexpr uint32_t STAGE = kUT * D * 8;  // one tile: 128 groups x 2^K amplitudes
+  static constexpr uint32_t OUT = ROWS ? STAGE : 0;
+  static constexpr uint32_t BOX = kUT * 16 * 8;  // ROWS: one 16-amplitude slice of the tile
   static constexpr uint32_t B_BYTES = KR * KR * 2, LBO_B = (KR / 8) * 128, SBO = 128;
   static constexpr uint32_t TCOLS = 2 * KR;  // A hi, A lo (KR / 2 each), accumulator
-  static constexpr size_t SMEM = STAGE + 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float);
+  static constexpr size_t SMEM = STAGE + OUT + 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float);
   static constexpr int MINB = K == 6 ? 1 : (K == 5 ? 2 : 4);  // register-limited
 };
 
-template <int K>
-__global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
+template <int K, bool ROWS>
+__global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
     k_fused_umma_tma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
                      const __grid_constant__ FusedArgs args, const __grid_constant__ CUtensorMap tmap, int renorm,
                      int s_lo) {
-  typedef TShape<K> S;
+  typedef TShape<K, ROWS> S;
   constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT;
   constexpr int CH = 8;
   extern __shared__ __align__(1024) unsigned char sm[];
   const float2* stage = reinterpret_cast<const float2*>(sm);
-  unsigned char* Bhi = sm + S::STAGE;
+  unsigned char* outst = sm + S::STAGE;  // ROWS: the output stage
+  unsigned char* Bhi = sm + S::STAGE + S::OUT;
   unsigned char* Blo = Bhi + S::B_BYTES;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] tile loaded, [1] MMAs done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -558,7 +536,12 @@ __global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
   u64 g = (u64)blockIdx.x * kUT;
   auto tile_load = [&](u64 gt) {  // one thread
     mbar_expect_tx(mb_full, S::STAGE);
-    tma_load_3d(smem_u32(stage), &tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), mb_full);
+    if (ROWS) {
+#pragma unroll
+      for (int b = 0; b < D / 16; ++b) tma_load_2d(smem_u32(stage) + b * S::BOX, &tmap, 16 * b, (int)gt, mb_full);
+    } else {
+      tma_load_3d(smem_u32(stage), &tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), mb_full);
+    }
   };
   if (t == 0) {
     *bmax_s = 0u;
@@ -612,8 +595,19 @@ __global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
     const bool loaded = mbar_wait(mb_full, ph_full);
     ph_full ^= 1u;
     float2 v[16];
+    if (ROWS) {
+      // this thread's slice is box h; its row's 16-byte unit c sits at c ^ (row mod 8)
+      const float4* rowp = reinterpret_cast<const float4*>(sm + h * S::BOX + row * 128);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = stage[sbase + ((16 * h + i) << sp)];
+      for (int c = 0; c < 8; ++c) {
+        const float4 q = rowp[c ^ (row & 7)];
+        v[2 * c] = make_float2(q.x, q.y);
+        v[2 * c + 1] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = stage[sbase + ((16 * h + i) << sp)];
+    }
     float nin = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) nin = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, nin));
@@ -650,8 +644,10 @@ __global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
         umma_f16_ta(tmem + KR, ahi_t, dbh, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
+      // ROWS: the previous tile's TMA stores must have read the output stage
+      if (ROWS) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
-    const u64 base = expand(g + row, args.ins);
+    const u64 base = ROWS ? 0 : expand(g + row, args.ins);
     if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma) ? 1 : 0)) {
       if (t == 0) atomicExch(&g_umma_timeout, 1);
       break;
@@ -677,18 +673,32 @@ __global__ void __launch_bounds__(TShape<K>::NT, TShape<K>::MINB)
       for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
       gsc = norm_correction(nin, nout);
     }
-    group_store<D, CH>(a, base, true, args.spread, 0, j0, o, gsc);
+    if (ROWS) {
+      float4* rowo = reinterpret_cast<float4*>(outst + h * S::BOX + row * 128);
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        rowo[c ^ (row & 7)] = make_float4(fmaf(o[4 * c], gsc, o[4 * c]), fmaf(o[4 * c + 1], gsc, o[4 * c + 1]),
+                                          fmaf(o[4 * c + 2], gsc, o[4 * c + 2]), fmaf(o[4 * c + 3], gsc, o[4 * c + 3]));
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (t == 0) {
+#pragma unroll
+        for (int b = 0; b < D / 16; ++b) tma_store_2d(&tmap, 16 * b, (int)g, smem_u32(outst) + b * S::BOX);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    } else {
+      group_store<D, CH>(a, base, true, args.spread, 0, j0, o, gsc);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     g += gstep;
   }
+  if (ROWS && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
-// The 3-D tensor map (lo, e, hi) of a state for a block on qubits
-// s .. s+k-1, box = one tile (128 groups).
-qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
+qs_status tmap_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -698,6 +708,33 @@ qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
       return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled not available");
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
+  *out = encode;
+  return QS_OK;
+}
+
+// The 2-D tensor map (e, group) of a state for a block on qubits 0 .. k-1:
+// box = 16 amplitudes x 128 groups, 128-byte swizzle.
+qs_status make_rows_tmap(qs_state* st, int k, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  qs_status s0 = tmap_encoder(&encode);
+  if (s0 != QS_OK) return s0;
+  const cuuint64_t dims[2] = {cuuint64_t(1) << k, cuuint64_t(1) << (st->n - k)};
+  const cuuint64_t strides[1] = {(cuuint64_t(1) << k) * 8};
+  const cuuint32_t box[2] = {16, (cuuint32_t)kUT};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, st->amp, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return QS_OK;
+}
+
+// The 3-D tensor map (lo, e, hi) of a state for a block on qubits
+// s .. s+k-1, box = one tile (128 groups).
+qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  qs_status s0 = tmap_encoder(&encode);
+  if (s0 != QS_OK) return s0;
   const int sp = s_lo < 7 ? s_lo : 7;
   const cuuint64_t dims[3] = {cuuint64_t(1) << s_lo, cuuint64_t(1) << k, cuuint64_t(1) << (st->n - s_lo - k)};
   const cuuint64_t strides[2] = {(cuuint64_t(1) << s_lo) * 8, (cuuint64_t(1) << (s_lo + k)) * 8};
@@ -708,232 +745,6 @@ qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
   return QS_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Blocks on qubits 0 .. k-1 (full tiles): k_fused_umma_rows.  A tile is then
-// 128 x 2^k contiguous amplitudes; the warps move it with rows_load /
-// rows_flush (4 rows x 128 bytes per instruction, transposed through the
-// per-warp stage), and bulk L2 prefetches (16 x 4 KB per tile, no
-// registers held) run two tiles ahead of a one-tile register buffer.  The
-// kernel is warp-specialised: one extra warp issues the MMAs (its first
-// lane), so the 2^(k+1) / 32 * 128 compute threads never wait on the tensor
-// pipe.  Per tile they wait for the previous tile's MMAs (A is then free),
-// split the tile into A, arrive on the "A full" mbarrier, issue the next
-// tile's loads, and run the previous tile's epilogue from the other
-// accumulator while the MMA warp drives the tensor cores on this one.  The
-// compute threads synchronise among themselves with named barriers (1:
-// input norms, 2: output norms, 3: the wait outcome), never with the MMA
-// warp, except at entry and exit.  TMEM columns: A hi [0, 2D), A lo
-// [2D, 4D), accumulators [4D, 6D) and [6D, 8D) for alternate tiles.  (The
-// same structure with gathered groups measured slower than k_fused_umma:
-// there the memory instruction issue, not the tensor pipe, limits a tile.)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar) : "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-// AND of v over the n threads of named barrier id (all of them must call it)
-__device__ __forceinline__ bool named_and(int id, int n, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(id), "r"(n)
-      : "memory");
-  return r != 0;
-}
-
-template <int K>
-struct RowsShape {
-  static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NC = kUT * H, NTT = NC + 32;
-  static constexpr uint32_t B_BYTES = KR * KR * 4, LBO_B = (KR / 8) * 128, SBO = 128;
-  static constexpr uint32_t TCOLS = 4 * KR;  // A hi, A lo, two accumulators: 128, 256 or 512
-  static constexpr size_t SMEM = 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float) +
-                                 (size_t)(NC / 32) * kStgWarp * sizeof(float4);  // + the per-warp stages
-  static constexpr int MINB = K == 6 ? 1 : (K == 5 ? 2 : 3);
-};
-
-template <int K>
-__global__ void __launch_bounds__(RowsShape<K>::NTT, RowsShape<K>::MINB)
-    k_fused_umma_rows(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg, int renorm) {
-  typedef RowsShape<K> S;
-  constexpr int KR = S::KR, H = S::H, NC = S::NC;
-  constexpr int CH = 8;  // 16-byte words (amplitude pairs) per compute thread: 32 reals
-  extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* Bhi = sm;
-  unsigned char* Blo = sm + S::B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] A full, [1] MMAs done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-  float* nin_s = reinterpret_cast<float*>(mbar + 4);  // [H][kUT] partial input norms
-  float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
-  const int t = threadIdx.x, warp = t >> 5;
-  for (int i = t; i < KR * KR; i += S::NTT) {
-    const int k = i / KR, n = i % KR;
-    unsigned hh, l;
-    split_tf32(Bg[i], hh, l);
-    const uint32_t off = ((k >> 2) * (KR / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (k & 3) * 4;
-    *reinterpret_cast<unsigned*>(Bhi + off) = hh;
-    *reinterpret_cast<unsigned*>(Blo + off) = l;
-  }
-  const uint32_t mb_full = smem_u32(mbar), mb_done = smem_u32(mbar + 1);
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full), "r"(NC));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(S::TCOLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = *tslot;
-  const u64 gstep = (u64)gridDim.x * kUT;
-  if (warp == NC / 32) {
-    if ((t & 31) == 0) {
-      const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-      constexpr uint32_t idesc = umma_idesc(kUT, KR);
-      uint32_t ph = 0, d = 0;
-      for (u64 g = (u64)blockIdx.x * kUT; g < ngroups; g += gstep) {
-        if (!mbar_wait(mb_full, ph)) {
-          atomicExch(&g_umma_timeout, 1);
-          break;
-        }
-        ph ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t dt = tmem + 2 * KR + d * KR;
-#pragma unroll
-        for (int ks = 0; ks < KR / 8; ++ks) {
-          const uint32_t bo = ks * 2 * S::LBO_B;
-          const uint64_t dbh = umma_desc(bhi + bo, S::LBO_B, S::SBO), dbl = umma_desc(blo + bo, S::LBO_B, S::SBO);
-          const uint32_t ahi_t = tmem + (uint32_t)(ks * 8), alo_t = tmem + (uint32_t)(KR + ks * 8);
-          umma_tf32_ta(dt, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
-          umma_tf32_ta(dt, ahi_t, dbl, idesc, 1u);
-          umma_tf32_ta(dt, ahi_t, dbh, idesc, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_done));
-        d ^= 1u;
-      }
-    }
-    __syncwarp();
-  } else {
-    const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
-    float4* stg = reinterpret_cast<float4*>(nout_s + H * kUT) + warp * kStgWarp;
-    // this warp's 32 lanes (= its rows), and this thread's 32 columns in each region
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 32);
-    float4 w[CH];  // the next tile's words, loaded one tile ahead
-    auto load = [&](u64 g) {
-      if (g < ngroups) rows_load<K>(a, g, j0, w);
-    };
-    // the tile (128 groups x 2^K amplitudes, contiguous) into L2 as 16 runs
-    // of 8 groups
-    auto prefetch = [&](u64 g) {
-      if (g < ngroups && t < 16) prefetch_bulk_l2(a + ((g + 8 * (u64)t) << K), 8u << (K + 3));
-    };
-    u64 g = (u64)blockIdx.x * kUT;
-    load(g);
-    prefetch(g + gstep);
-    // the tile whose MMAs were issued last and whose epilogue is still to run
-    bool pend = false, ok = true;
-    u64 pg = 0;
-    float pnin = 0.f;
-    uint32_t pd = 0, ph = 0, dsel = 0;
-    auto mma_done = [&]() -> bool {
-      if (!named_and(3, NC, mbar_wait(mb_done, ph))) {
-        if (t == 0) atomicExch(&g_umma_timeout, 1);
-        return false;
-      }
-      ph ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      return true;
-    };
-    // the pending tile's epilogue, 16 columns at a time: the output norm
-    // (one TMEM read), then the scaled scatter (a second read)
-    auto epilogue = [&]() {
-      float gsc = 0.f;  // output = o (1 + gsc)
-      if (renorm) {
-        float nout = 0.f;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float o[16];
-          tmem_ld16(tl + pd + 16 * half, o);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-          for (int j = 0; j < 16; ++j) nout = fmaf(o[j], o[j], nout);
-        }
-        nout_s[h * kUT + row] = nout;
-        named_sync(2, NC);
-        nout = 0.f;
-#pragma unroll
-        for (int i = 0; i < H; ++i) nout += nout_s[i * kUT + row];
-        gsc = norm_correction(pnin, nout);
-      }
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float o[16];
-        tmem_ld16(tl + pd + 16 * half, o);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          stg[(t & 31) * kStgPitch + 4 * half + j] =
-              make_float4(fmaf(o[4 * j], gsc, o[4 * j]), fmaf(o[4 * j + 1], gsc, o[4 * j + 1]),
-                          fmaf(o[4 * j + 2], gsc, o[4 * j + 2]), fmaf(o[4 * j + 3], gsc, o[4 * j + 3]));
-      }
-      rows_flush<K>(a, pg, j0, stg);
-      asm volatile("tcgen05.fence::before_thread_sync;");
-    };
-    while (g < ngroups) {
-      if (pend && !mma_done()) {
-        ok = false;
-        break;
-      }
-      rows_to_lane(w, stg);
-      float nin = 0.f;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {  // 16 columns (4 words) at a time
-        unsigned hv[16], lv[16];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float x[4] = {w[4 * half + j].x, w[4 * half + j].y, w[4 * half + j].z, w[4 * half + j].w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            nin = fmaf(x[i], x[i], nin);
-            split_tf32(x[i], hv[4 * j + i], lv[4 * j + i]);
-          }
-        }
-        tmem_st16(tl + (uint32_t)(16 * half), hv);
-        tmem_st16(tl + (uint32_t)(KR + 16 * half), lv);
-      }
-      nin_s[h * kUT + row] = nin;
-      asm volatile("tcgen05.wait::st.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mbar_arrive(mb_full);
-      load(g + gstep);
-      prefetch(g + 2 * gstep);
-      named_sync(1, NC);
-      nin = 0.f;
-#pragma unroll
-      for (int i = 0; i < H; ++i) nin += nin_s[i * kUT + row];
-      if (pend) epilogue();
-      pend = true;
-      pg = g;
-      pnin = nin;
-      pd = 2 * KR + dsel * KR;
-      dsel ^= 1u;
-      g += gstep;
-    }
-    if (ok && pend && mma_done()) epilogue();
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
 // Grid for a block kernel: CTAs per SM from shared memory, registers and TMEM
@@ -966,23 +777,27 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
   unsigned grid = 0;
   // qubits ascending: the block is qubits 0 .. K-1 exactly when the last is K-1
   if (full && qubits[K - 1] == K - 1) {
-    typedef RowsShape<K> S;
-    qs_status st = block_grid<K>(s, k_fused_umma_rows<K>, S::NTT, S::SMEM, S::TCOLS, grid);
+    typedef TShape<K, true> ST;
+    CUtensorMap map;
+    qs_status st = make_rows_tmap(s, K, &map);
     if (st != QS_OK) return st;
-    k_fused_umma_rows<K><<<grid, S::NTT, S::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, renorm);
-    return launch_ok("k_fused_umma_rows");
+    st = block_grid<K>(s, k_fused_umma_tma<K, true>, ST::NT, ST::SMEM, ST::TCOLS, grid);
+    if (st != QS_OK) return st;
+    k_fused_umma_tma<K, true><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A,
+                                                                       map, renorm, 0);
+    return launch_ok("k_fused_umma_tma");
   }
   // a window of consecutive qubits from 2 up: one TMA box per tile (from
   // qubit 1 the stage reads conflict 8-way and the gather path is faster)
   if (full && qubits[0] >= 2 && qubits[K - 1] == qubits[0] + K - 1) {
-    typedef TShape<K> ST;
+    typedef TShape<K, false> ST;
     CUtensorMap map;
     qs_status st = make_block_tmap(s, K, qubits[0], &map);
     if (st != QS_OK) return st;
-    st = block_grid<K>(s, k_fused_umma_tma<K>, ST::NT, ST::SMEM, ST::TCOLS, grid);
+    st = block_grid<K>(s, k_fused_umma_tma<K, false>, ST::NT, ST::SMEM, ST::TCOLS, grid);
     if (st != QS_OK) return st;
-    k_fused_umma_tma<K><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A, map,
-                                                                 renorm, qubits[0]);
+    k_fused_umma_tma<K, false><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A,
+                                                                        map, renorm, qubits[0]);
     return launch_ok("k_fused_umma_tma");
   }
   typedef TaShape<K> S;
