@@ -58,7 +58,7 @@ def infidelity_gpu(s64, s128):
 
 def test_c128_brick_and_qft_28q_vs_oracle_in_full(qs):
     n = 28
-    for circ, x0 in ((W.brick(n, 40, 6), 0), (W.qft(n), W.basis_index(n, 3))):
+    for circ, x0 in ((W.brick(n, 40, 3), 0), (W.qft(n), W.basis_index(n, 4))):
         want = oracle.zero_state(n, x0)
         oracle.run_circuit(want, circ)
         s = gpu_run(qs, n, circ, "c128", qs.PLAN_UNFUSED, x0=x0)
@@ -71,7 +71,7 @@ def test_c128_brick_and_qft_28q_vs_oracle_in_full(qs):
 @pytest.mark.parametrize("k", [4, 5, 6])
 def test_c64_fused_26q_vs_oracle(qs, k):
     n = 26
-    circ = W.brick(n, 40, 6)
+    circ = W.brick(n, 40, 8)
     if not hasattr(test_c64_fused_26q_vs_oracle, "want"):
         want = oracle.zero_state(n)
         oracle.run_circuit(want, circ)
