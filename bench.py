@@ -481,6 +481,7 @@ def run_ours(args):
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
         extras["c128_unfused_%dq" % n] = base
         extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
+        extras["planner_policies_30q"] = planner_policies(qs, torch, device, 30)
         extras["batch_512_hea"] = batch_workload(qs, torch, device)
         extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
     head = results[args.dtype]
@@ -555,6 +556,41 @@ def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
             r["infidelity_vs_c128"] = 1.0 - abs(ov) ** 2
         out[name] = r
         del p
+    del s
+    return out
+
+
+def planner_policies(qs, torch, device, n):
+    """The paper's own workloads at n qubits, complex64, under each plan
+    policy: per-gate passes, tile passes (low qubits plus gathered high
+    ones, many gates per pass), dense 6-qubit tensor-core blocks.  Reports
+    HBM passes per logical gate and the time of one run (after one warm-up)."""
+    wls = {"qsb_sets10": W.qsb(n, 22, sets=10), "hadamard_x11": W.hadamard_bench(n),
+           "qv_like_d10": W.qv_like(n, 10, 13)}
+    out = {}
+    s = qs.State(n, "c64", device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for wname, circ in wls.items():
+        c = qs.Circuit(circ)
+        row = {"gates": len(circ)}
+        for pname, mode, fq in (("unfused", qs.PLAN_UNFUSED, 0), ("tiled", qs.PLAN_TILED, 0),
+                                ("fused_k6", qs.PLAN_FUSED, 6)):
+            p = qs.Plan(c, n, "c64", mode=mode, fuse_qubits=fq)
+            st = p.stats()
+            s.set_basis(0)
+            s.run(p)
+            s.set_basis(0)
+            torch.cuda.synchronize()
+            e0.record()
+            s.run(p)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[pname] = {"passes": st["passes"], "passes_per_gate": st["passes"] / len(circ), "ms": ms,
+                          "effective_GBps": st["metric_bytes"] / (ms / 1e3) / 1e9,
+                          "hbm_GBps_algorithmic": st["hbm_bytes"] / (ms / 1e3) / 1e9}
+            del p
+        out[wname] = row
     del s
     return out
 

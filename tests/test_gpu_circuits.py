@@ -5,7 +5,8 @@
    basis state: complex128 element-wise max error <= 1e-12; complex64
    infidelity 1 - |<psi64|psi128>|^2 <= 1e-5 against the oracle's state.
  * The paper's own synthetic circuits (QSB structure §IV-F, Hadamard
-   benchmark §IV-D) at small n.
+   benchmark §IV-D, the QV-shaped random two-qubit blocks of §IV-E) at
+   small n.
  * Every plan mode gives the same state.
 """
 import math
@@ -55,6 +56,8 @@ CASES = [
     ("brick9_d40", 9, lambda: W.brick(9, 40, 21), 0),
     ("qsb10", 10, lambda: W.qsb(10, 22), 0),
     ("hadamard11x7", 7, lambda: W.hadamard_bench(7), 5),
+    ("qv13_d10", 13, lambda: W.qv_like(13, 10, 13), 0),
+    ("qv14_d10", 14, lambda: W.qv_like(14, 10, 17), 0),
     ("ghz16", 16, lambda: W.ghz(16), 0),
     ("brick3", 3, lambda: W.brick(3, 10, 23), 0),
     ("brick1", 1, lambda: W.brick(1, 5, 24), 0),

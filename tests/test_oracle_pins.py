@@ -335,6 +335,49 @@ def test_qsb_inverse():
     assert np.max(np.abs(got - psi)) < 1e-13
 
 
+@pytest.mark.parametrize("n", [5, 8])
+def test_qv_like_structure_and_inverse(n):
+    # the QV-shaped workload (§IV-E): per layer a permutation pairs the
+    # qubits, every pair gets 10 named gates, each qubit in at most one pair;
+    # the pairings change between layers; the circuit is unitary (norm and
+    # round trip through its inverse)
+    depth = 6
+    circ = W.qv_like(n, depth, 13)
+    W.validate(circ, n)
+    per_layer = 10 * (n // 2)
+    assert len(circ) == depth * per_layer
+    pairings = []
+    for layer in range(depth):
+        gates = circ[layer * per_layer:(layer + 1) * per_layer]
+        pairs = [tuple(gates[i + 2].qubits) for i in range(0, per_layer, 10)]  # the first CNOT (a, b)
+        used = [q for pr in pairs for q in pr]
+        assert len(set(used)) == len(used) == 2 * (n // 2)
+        for i in range(0, per_layer, 10):
+            a, b = gates[i + 2].qubits
+            assert [g.name for g in gates[i:i + 10]] == ["U3", "U3", "CNOT", "RZ", "RY", "CNOT", "RY", "CNOT", "U3", "U3"]
+            assert [g.qubits for g in gates[i:i + 10]] == [(a,), (b,), (a, b), (a,), (b,), (b, a), (b,), (a, b), (a,), (b,)]
+        pairings.append(frozenset(frozenset(pr) for pr in pairs))
+    assert len(set(pairings)) > 1
+    psi = W.random_state(n, 14)
+    got = psi.copy()
+    oracle.run_circuit(got, circ)
+    assert abs(np.vdot(got, got).real - 1.0) < 1e-13
+    oracle.run_circuit(got, W.inverse(circ))
+    assert np.max(np.abs(got - psi)) < 1e-13
+
+
+def test_qv_like_matches_kron_product():
+    n = 4
+    circ = W.qv_like(n, 3, 15)
+    op = np.eye(1 << n, dtype=complex)
+    for g in circ:
+        op = dense_full(n, list(g.qubits), oracle.gate_matrix(g.name, g.params)) @ op
+    psi = W.random_state(n, 16)
+    got = psi.copy()
+    oracle.run_circuit(got, circ)
+    assert np.max(np.abs(got - op @ psi)) < 1e-13
+
+
 # ---------------------------------------------------------------------------
 # Reductions
 # ---------------------------------------------------------------------------

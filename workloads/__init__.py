@@ -145,6 +145,42 @@ def qsb(n: int, seed: int, sets: int = 10) -> List[Gate]:
     return out
 
 
+def qv_like(n: int, depth: int, seed: int) -> List[Gate]:
+    """Random two-qubit blocks on random pairs, shaped like the Quantum Volume
+    model circuit of §IV-E: per layer a seeded random permutation p of the
+    qubit labels (Fisher-Yates, j drawn as next_u64 mod (i + 1) for i from
+    n - 1 down to 1) pairs them as (p[0], p[1]), (p[2], p[3]), ...; every
+    pair (a, b) gets a generic two-qubit block written with named gates:
+    U3 on a, U3 on b, CNOT(a, b), RZ on a, RY on b, CNOT(b, a), RY on b,
+    CNOT(a, b), U3 on a, U3 on b (17 angles uniform in [0, 2*pi), in that
+    gate order).  With odd n the last qubit of p idles."""
+    rng = SplitMix64(seed)
+    two_pi = 2.0 * math.pi
+    out: List[Gate] = []
+
+    def u3(q):
+        out.append(Gate("U3", (q,), (two_pi * rng.uniform(), two_pi * rng.uniform(), two_pi * rng.uniform())))
+
+    for _ in range(depth):
+        p = list(range(n))
+        for i in range(n - 1, 0, -1):
+            j = rng.next_u64() % (i + 1)
+            p[i], p[j] = p[j], p[i]
+        for i in range(0, n - 1, 2):
+            a, b = p[i], p[i + 1]
+            u3(a)
+            u3(b)
+            out.append(Gate("CNOT", (a, b)))
+            out.append(Gate("RZ", (a,), (two_pi * rng.uniform(),)))
+            out.append(Gate("RY", (b,), (two_pi * rng.uniform(),)))
+            out.append(Gate("CNOT", (b, a)))
+            out.append(Gate("RY", (b,), (two_pi * rng.uniform(),)))
+            out.append(Gate("CNOT", (a, b)))
+            u3(a)
+            u3(b)
+    return out
+
+
 def hadamard_bench(n: int, reps: int = 11) -> List[Gate]:
     """Hadamard benchmark of §IV-D: ``reps`` H gates on every qubit."""
     return [Gate("H", (q,)) for _ in range(reps) for q in range(n)]
