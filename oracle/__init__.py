@@ -52,6 +52,10 @@ def lib():
         L.or_apply_pauli_sum.argtypes = [dp, dp, c_int, c_int, up, up, dp]
         L.or_adjoint_grad.argtypes = [dp, c_int, c_int, ip, ip, dp, ip, c_int, c_int, up, up, dp, dp]
         L.or_adjoint_grad.restype = c_d
+        L.or_probabilities.argtypes = [dp, c_int, ip, c_int, dp]
+        L.or_collapse.argtypes = [dp, c_int, c_int, c_int, c_d]
+        L.or_sample.argtypes = [dp, c_int, c_int, dp, up]
+        L.or_sample.restype = c_int
         _lib = L
     return _lib
 
@@ -218,3 +222,33 @@ def expectation_of_circuit(n: int, circuit, terms, x0: int = 0) -> float:
     psi = zero_state(n, x0)
     run_circuit(psi, circuit)
     return expect_pauli(psi, terms)
+
+
+def probabilities(psi, qubits) -> np.ndarray:
+    """Marginal Born-rule probabilities of the given qubits (bit i of the
+    outcome index = qubits[i]), FP64 summed in index order."""
+    psi = _state(psi)
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    out = np.zeros(1 << len(q), dtype=np.float64)
+    lib().or_probabilities(_dp(psi), _nq(psi), _ip(q), len(q), _dp(out))
+    return out
+
+
+def collapse(psi, q: int, outcome: int, p: float) -> None:
+    """In place: the state after measuring qubit q with this outcome of
+    probability p (other branch zeroed, kept one scaled by 1/sqrt(p))."""
+    psi = _state(psi)
+    lib().or_collapse(_dp(psi), _nq(psi), int(q), int(outcome), float(p))
+
+
+def sample(psi, u) -> np.ndarray:
+    """Basis-state samples for the uniforms u (the chunked inverse-CDF
+    definition in oracle.cpp)."""
+    import ctypes
+    psi = _state(psi)
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(uu.size, dtype=np.uint64)
+    r = lib().or_sample(_dp(psi), _nq(psi), uu.size, _dp(uu), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if r != 0:
+        raise ValueError("sampling a state of zero norm")
+    return out

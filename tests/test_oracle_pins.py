@@ -486,3 +486,96 @@ def test_state_memory_accounting():
         assert np.dtype(np.complex128).itemsize * (1 << n) == ex["state_bytes"]
         if "gate_traffic_bytes" in ex:
             assert 2 * ex["state_bytes"] == ex["gate_traffic_bytes"]
+
+
+# ---------------------------------------------------------------------------
+# Measurement, sampling, collapse (§II-A: circuits include measurements)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("qubits", [[0], [3], [6, 1], [2, 5, 0], [0, 1, 2, 3, 4, 5, 6]])
+def test_probabilities_brute_force(qubits):
+    # numpy: |psi|^2 reshaped by bits, summed over the other axes
+    n = 7
+    psi = W.random_state(n, 40)
+    p = (np.abs(psi) ** 2).reshape([2] * n)  # axis j = bit n - 1 - j
+    keep = [n - 1 - q for q in qubits]
+    other = tuple(ax for ax in range(n) if ax not in keep)
+    marg = p.sum(axis=other)
+    # marg axes follow `keep` in increasing axis order; reorder to qubits[0] as bit 0
+    order = sorted(keep)
+    want = np.zeros(1 << len(qubits))
+    for r in range(1 << len(qubits)):
+        idx = [0] * len(order)
+        for i, q in enumerate(qubits):
+            idx[order.index(n - 1 - q)] = (r >> i) & 1
+        want[r] = marg[tuple(idx)]
+    got = oracle.probabilities(psi, qubits)
+    assert np.max(np.abs(got - want)) < 1e-14
+    assert abs(got.sum() - 1.0) < 1e-13
+
+
+def test_probabilities_and_collapse_closed_forms():
+    n = 5
+    ghz = oracle.zero_state(n)
+    oracle.run_circuit(ghz, W.ghz(n))
+    assert np.allclose(oracle.probabilities(ghz, [0]), [0.5, 0.5], atol=1e-15)
+    assert np.allclose(oracle.probabilities(ghz, [0, 4]), [0.5, 0, 0, 0.5], atol=1e-15)
+    x0 = 0b10110
+    basis = oracle.zero_state(n, x0)
+    assert np.array_equal(oracle.probabilities(basis, [1, 2, 4]), [0, 0, 0, 0, 0, 0, 0, 1.0])
+    # measuring a GHZ qubit leaves the matching basis state
+    for outcome in (0, 1):
+        s = ghz.copy()
+        oracle.collapse(s, 2, outcome, 0.5)
+        want = np.zeros(1 << n, complex)
+        want[0 if outcome == 0 else (1 << n) - 1] = 1.0
+        assert np.max(np.abs(s - want)) < 1e-15
+    # collapse of a random state: the kept half renormalised, the other zero
+    psi = W.random_state(6, 41)
+    p1 = oracle.probabilities(psi, [3])[1]
+    s = psi.copy()
+    oracle.collapse(s, 3, 1, p1)
+    idx = np.arange(1 << 6)
+    assert np.all(s[(idx >> 3) & 1 == 0] == 0)
+    assert np.max(np.abs(s[(idx >> 3) & 1 == 1] - psi[(idx >> 3) & 1 == 1] / math.sqrt(p1))) < 1e-15
+    assert abs(np.vdot(s, s).real - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("n", [4, 10, 12])
+def test_sample_uniform_dyadic_is_floor(n):
+    # every p_x = 2^-n exactly (amplitudes 2^(-n/2) set directly), so every
+    # chunk sum, prefix and running sum is exact: sample(u) = floor(u 2^n)
+    psi = np.full(1 << n, 2.0 ** (-n / 2), dtype=complex)
+    u = np.concatenate([[0.0, 0.5, 1 - 2.0 ** -53], np.random.default_rng(42).random(500)])
+    got = oracle.sample(psi, u)
+    assert np.array_equal(got, np.floor(u * (1 << n)).astype(np.uint64))
+
+
+def test_sample_basis_ghz_and_monotone():
+    n = 11
+    x0 = 1234
+    u = np.random.default_rng(43).random(300)
+    assert np.all(oracle.sample(oracle.zero_state(n, x0), u) == x0)
+    ghz = oracle.zero_state(n)
+    oracle.run_circuit(ghz, W.ghz(n))
+    g = oracle.sample(ghz, u)
+    assert np.all(g[u < 0.49] == 0) and np.all(g[u > 0.51] == (1 << n) - 1)
+    # the inverse CDF is monotone in u, and lands only where p_x > 0
+    psi = W.random_state(12, 44)
+    psi[::3] = 0
+    uu = np.sort(np.random.default_rng(45).random(2000))
+    x = oracle.sample(psi, uu)
+    assert np.all(np.diff(x.astype(np.int64)) >= 0)
+    assert np.all(np.abs(psi[x.astype(np.int64)]) > 0)
+
+
+def test_sample_frequencies():
+    # 200k samples of an 8-qubit state: every outcome's frequency within 5
+    # standard deviations of its probability
+    n = 8
+    psi = W.random_state(n, 46)
+    p = np.abs(psi) ** 2
+    u = np.random.default_rng(47).random(200000)
+    counts = np.bincount(oracle.sample(psi, u).astype(np.int64), minlength=1 << n)
+    sd = np.sqrt(p * (1 - p) * u.size)
+    assert np.all(np.abs(counts - p * u.size) <= 5 * sd + 1)
