@@ -476,6 +476,8 @@ def run_ours(args):
     if not args.no_extras:
         extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
         extras["reductions_%dq" % n] = reductions(qs, torch, states, n)
+        if "c64" in states:
+            extras["measure_%dq" % n] = measurement(qs, torch, states["c64"], n)
         extras["c64_brick33_d20"] = c64_33q(qs, torch, device, args.fuse_qubits)
         base = c128_unfused(qs, torch, device, n, circuit)
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
@@ -622,6 +624,39 @@ def reductions(qs, torch, states, n, reps=5):
             r[name] = {"ms": 1e3 * t, "GBps": nbytes / t / 1e9, "value": v.real if isinstance(v, complex) else v}
         r["tfim_groups"] = groups
         out[dt] = r
+    return out
+
+
+def measurement(qs, torch, s, n, reps=3):
+    """Computational-basis measurement on the headline complex64 state after
+    the circuit: marginal probabilities of one and of six qubits (one read
+    pass per 8 outcomes), 2^20 samples (the chunk-sum pass, the host prefix
+    and one scan of up to 1024 amplitudes per sample), and a measurement of
+    one qubit with its collapse (a probability pass plus a read-write
+    pass), last because it changes the state.  Host clock around each call
+    (each returns to the host); GB/s counts the state bytes read and
+    written."""
+    N = float(1 << n)
+    S = 8
+    u = np.random.default_rng(9).random(1 << 20)
+    out = {}
+    for name, fn, nbytes in (("probabilities_1q", lambda: s.probabilities([n - 1]), N * S),
+                             ("probabilities_6q", lambda: s.probabilities([0, 5, 10, 15, 20, 25]), N * S),
+                             ("sample_1M", lambda: s.sample(u), N * S)):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        t = (time.perf_counter() - t0) / reps
+        out[name] = {"ms": 1e3 * t, "GBps": nbytes / t / 1e9}
+    out["sample_1M"]["shots_per_s"] = (1 << 20) / (out["sample_1M"]["ms"] / 1e3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    o, p = s.measure(n // 2, 0.3)
+    t = time.perf_counter() - t0
+    out["measure_collapse"] = {"ms": 1e3 * t, "GBps": 3 * N * S / t / 1e9, "outcome": o, "probability": p,
+                               "norm2_after": s.norm2()}
     return out
 
 

@@ -158,6 +158,45 @@ qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status qs_expect_pauli(qs_state* st, int nterms, const uint64_t* xmask,
                           const uint64_t* zmask, const double* coeff, double* out);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement in the computational basis (§II-A: a circuit is a sequence  */
+/* of gates, measurements and resets).  Probabilities follow the Born rule, */
+/* p_x = |a_x|^2, formed and summed in FP64.                                */
+/* ---------------------------------------------------------------------- */
+
+/* Marginal probabilities of k qubits: out[r] (host, 2^k doubles) = sum of
+ * p_x over x whose bits at qubits[0..k-1] form r (bit i of r = qubits[i]).
+ * 1 <= k <= 6, qubits distinct and < n.  Does not change the state;
+ * synchronises its stream. */
+qs_status qs_probabilities(qs_state* st, const int* qubits, int k, double* out);
+
+/* Measures qubit q with the caller's uniform u in [0, 1): with p0, p1 the
+ * probabilities of 0 and 1 (as qs_probabilities), the outcome is 0 when
+ * u (p0 + p1) < p0, else 1 (the other one if the chosen probability is 0).
+ * The state collapses onto it: amplitudes of the other outcome become 0,
+ * the kept ones are scaled by 1 / sqrt(p_outcome), so the state is
+ * renormalised.  *outcome (host) receives 0 or 1; *prob (host, may be NULL)
+ * the outcome's probability p_outcome / (p0 + p1).  A reset of qubit q is
+ * this followed by an X on q when the outcome is 1.  QS_EINVAL for u outside
+ * [0, 1) or a state of zero norm. */
+qs_status qs_measure(qs_state* st, int q, double u, int* outcome, double* prob);
+
+/* Samples nshots basis states without changing the state: for the caller's
+ * uniforms u[i] in [0, 1) (host), out[i] (host) is the inverse of the
+ * cumulative distribution of p_x in index order at u[i], under this exact
+ * definition (so the result does not depend on the launch shape):
+ *   p_x = re * re + im * im, each product and the sum rounded on its own;
+ *   C = min(2^n, 1024) amplitudes per chunk; the chunk sum S_c combines 32
+ *   lane partials (lane l sums p_{cC + l + 32 i}, i ascending) by
+ *   s_l <- s_l + s_{l xor off} for off = 16, 8, 4, 2, 1;
+ *   P_0 = 0, P_{c+1} = P_c + S_c, T = P_{2^n / C};
+ *   t = u T, c = the largest chunk with P_c <= t; out = the first x >= cC at
+ *   which P_c + p_{cC} + ... + p_x exceeds t, or the largest x with p_x > 0
+ *   if none does.
+ * QS_EINVAL for a uniform outside [0, 1) or a state of zero norm.
+ * Synchronises the state's stream. */
+qs_status qs_sample(qs_state* st, uint64_t nshots, const double* u, uint64_t* out);
+
 /* Allocation-free inner product, for callers that cannot let the library
  * allocate device memory (a framework allocator that owns the GPU's memory,
  * a latency-critical loop where cudaMalloc/cudaFree would synchronise, a

@@ -87,6 +87,9 @@ _SIGS = {
     "qs_run_plan": ([_vp, _vp], _int),
     "qs_plan_step_info": ([_vp, _int, _ip, _dp], _int),
     "qs_plan_step_qubits": ([_vp, _int, _ip, _int, _ip], _int),
+    "qs_probabilities": ([_vp, _ip, _int, _dp], _int),
+    "qs_measure": ([_vp, _int, ctypes.c_double, _ip, _dp], _int),
+    "qs_sample": ([_vp, ctypes.c_uint64, _dp, ctypes.POINTER(ctypes.c_uint64)], _int),
     "qs_run_plan_profiled": ([_vp, _vp, ctypes.POINTER(ctypes.c_float), _int], _int),
     "qs_adjoint_grad": ([_vp, _vp, _dp, _int, _int, _int, _up, _up, _dp, _dp, _dp], _int),
     "qs_batch_create": ([_int, _ip, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(PlanOpts), _vp,
@@ -203,6 +206,31 @@ class State:
     def set_basis(self, x: int) -> "State":
         _check(_lib.qs_set_basis(self._bind(), int(x)), "qs_set_basis")
         return self
+
+    def probabilities(self, qubits: Sequence[int]) -> np.ndarray:
+        """Marginal Born-rule probabilities of the given qubits (qs_probabilities):
+        entry r has bit i = qubits[i]."""
+        q = _iarr(qubits)
+        out = np.zeros(1 << len(q), dtype=np.float64)
+        _check(_lib.qs_probabilities(self._bind(), _iptr(q), len(q), _dptr(out)), "qs_probabilities")
+        return out
+
+    def measure(self, q: int, u: float):
+        """Measure qubit q with the uniform u in [0, 1) (qs_measure); the state
+        collapses.  Returns (outcome, probability of the outcome)."""
+        o = ctypes.c_int()
+        p = ctypes.c_double()
+        _check(_lib.qs_measure(self._bind(), int(q), float(u), ctypes.byref(o), ctypes.byref(p)), "qs_measure")
+        return o.value, p.value
+
+    def sample(self, u) -> np.ndarray:
+        """Basis-state samples for the uniforms u in [0, 1) (qs_sample); the
+        state is unchanged."""
+        uu = np.ascontiguousarray(u, dtype=np.float64).ravel()
+        out = np.zeros(uu.size, dtype=np.uint64)
+        _check(_lib.qs_sample(self._bind(), uu.size, _dptr(uu), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+               "qs_sample")
+        return out
 
     def to_numpy(self) -> np.ndarray:
         out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == "c64" else np.complex128)
