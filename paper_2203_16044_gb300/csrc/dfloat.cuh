@@ -195,4 +195,15 @@ __device__ __forceinline__ void cmul_df(const float* zh, const float* zl, cdf& a
   a.rh = r.h; a.rl = r.l; a.ih = i.h; a.il = i.l;
 }
 
+// A value as double-float: a float exactly, a double by its (h, l) split.
+__device__ __forceinline__ dfl to_df(float x) { return dfl{x, 0.f}; }
+__device__ __forceinline__ dfl to_df(double x) { return d2df(x); }
+// A double-float partial sum into an FP64 accumulator (two FP64 additions),
+// then reset.
+__device__ __forceinline__ void df_flush(double& acc, dfl& v) {
+  acc += (double)v.h;
+  acc += (double)v.l;
+  v = dfl{0.f, 0.f};
+}
+
 }  // namespace qs

@@ -2,11 +2,13 @@
 // measurements and resets): marginal probabilities, the collapse after a
 // single-qubit measurement, and sampling of basis states.
 //
-// Probabilities follow the Born rule, p_x = |a_x|^2, formed and accumulated
-// in FP64 (complex64 amplitudes are widened first, so their squares are
-// exact).  Sampling follows a step-by-step definition whose floating-point
-// operations are taken in a fixed order, so the index it returns for a given
-// uniform does not depend on the launch shape:
+// Probabilities follow the Born rule, p_x = |a_x|^2.  For the marginals the
+// squares are formed exactly in double-float (FP32 pairs with their
+// rounding errors) and summed per thread in double-float with an FP64 flush
+// every few groups: FP64-level accuracy without the FP64 pipe (about 1/64 of
+// the FP32 rate on GB300).  Sampling follows a step-by-step definition whose
+// floating-point operations are taken in a fixed order, so the index it
+// returns for a given uniform does not depend on the launch shape:
 //   p_x = re * re + im * im, each product and the sum rounded on its own;
 //   C = min(N, 1024) amplitudes per chunk; chunk sum S_c = 32 lane partials
 //   (lane l sums p_{cC + l + 32 i}, i ascending) combined by the butterfly
@@ -19,6 +21,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "kcommon.cuh"
 
 namespace qs {
@@ -39,34 +42,50 @@ struct MargArgs {
   u64 spread[64];   // spread[r]: OR of 2^qubits[i] over the set bits i of r
 };
 
-// Outcomes [b0, b0 + nb) (nb <= kBins): each thread sums its groups (the
-// other qubits) in grid-stride order; the CTA reduces every bin into
-// part[blockIdx.x * kBins + j].
-template <typename A>
+// Outcomes [b0, b0 + NB): each thread sums its groups (the other qubits) in
+// grid-stride order, the squares exact in double-float, flushed into FP64
+// every 4 groups; the CTA reduces every bin into part[blockIdx.x * kBins + j].
+template <typename A, int NB>
 __global__ void __launch_bounds__(kMT) k_marginal(const A* __restrict__ a, u64 ngroups,
-                                                  const __grid_constant__ MargArgs args, int b0, int nb,
+                                                  const __grid_constant__ MargArgs args, int b0,
                                                   double* __restrict__ part) {
-  double acc[kBins];
+  double acc[NB];
+  dfl da[NB];
 #pragma unroll
-  for (int j = 0; j < kBins; ++j) acc[j] = 0.0;
+  for (int j = 0; j < NB; ++j) {
+    acc[j] = 0.0;
+    da[j] = dfl{0.f, 0.f};
+  }
   const u64 stride = (u64)gridDim.x * kMT;
+  int since = 0;
   for (u64 g = (u64)blockIdx.x * kMT + threadIdx.x; g < ngroups; g += stride) {
     const u64 base = expand(g, args.ins);
 #pragma unroll
-    for (int j = 0; j < kBins; ++j)
-      if (j < nb) acc[j] += prob(a[base | args.spread[b0 + j]]);
+    for (int j = 0; j < NB; ++j) {
+      const A v = a[base | args.spread[b0 + j]];
+      const dfl x = to_df(v.x), y = to_df(v.y);
+      df_acc(da[j], df_mul(x, x));
+      df_acc(da[j], df_mul(y, y));
+    }
+    if (++since == 4) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) df_flush(acc[j], da[j]);
+      since = 0;
+    }
   }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) df_flush(acc[j], da[j]);
   __shared__ double red[kMT / 32][kBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < kBins; ++j) {
+  for (int j = 0; j < NB; ++j) {
     double v = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp][j] = v;
   }
   __syncthreads();
-  if (threadIdx.x < kBins) {
+  if (threadIdx.x < NB) {
     double s = 0.0;
     for (int w = 0; w < kMT / 32; ++w) s += red[w][threadIdx.x];
     part[(u64)blockIdx.x * kBins + threadIdx.x] = s;
@@ -169,8 +188,11 @@ qs_status marginal(qs_state* s, const int* qubits, int k, double* out) {
   double* part = static_cast<double*>(s->scratch);
   std::vector<double> h((size_t)kBins * g);
   for (int b0 = 0; b0 < (1 << k); b0 += kBins) {
-    const int nb = std::min(kBins, (1 << k) - b0);
-    k_marginal<A><<<g, kMT, 0, s->stream>>>(static_cast<const A*>(s->amp), ngroups, args, b0, nb, part);
+    const int nb = std::min(kBins, (1 << k) - b0);  // 2, 4 or 8
+    const A* amp = static_cast<const A*>(s->amp);
+    if (nb == 2) k_marginal<A, 2><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
+    else if (nb == 4) k_marginal<A, 4><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
+    else k_marginal<A, 8><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
     if ((st = launch_ok("k_marginal")) != QS_OK) return st;
     if ((st = sync_copy(s, h.data(), part, sizeof(double) * kBins * g, cudaMemcpyDeviceToHost)) != QS_OK) return st;
     for (int j = 0; j < nb; ++j) {

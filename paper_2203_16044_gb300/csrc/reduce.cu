@@ -65,14 +65,6 @@ unsigned red_grid(u64 npk) {
 // deep so that each thread keeps kU independent 16-byte loads in flight.
 constexpr int kU = 4;
 
-__device__ __forceinline__ dfl to_df(float x) { return dfl{x, 0.f}; }
-__device__ __forceinline__ dfl to_df(double x) { return d2df(x); }
-
-__device__ __forceinline__ void df_flush(double& acc, dfl& v) {
-  acc += (double)v.h;
-  acc += (double)v.l;
-  v = dfl{0.f, 0.f};
-}
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_norm2(const R* __restrict__ a, u64 npk, double2* part) {
