@@ -36,3 +36,22 @@ def test_step_kernel_labels(qs):
     p128 = qs.Plan(qs.Circuit(W.brick(8, 4, 3)), 8, "c128", mode=qs.PLAN_FUSED, fuse_qubits=4)
     labs = {bench.step_kernel(p128, i, k) for i, (k, _) in enumerate(p128.step_info())}
     assert all(lab.startswith("k_dense<") for lab in labs if lab.startswith("k_"))
+
+
+def test_planner_widens_complex64_blocks_to_windows(qs):
+    # host-only: every complex64 tensor-core block whose touched qubits fit in
+    # a window of at most k consecutive qubits is widened to such a window of
+    # at least 4 qubits, starting at 0 or at 2 and above (the shapes the TMA
+    # kernel takes); the widened block still holds all the qubits its gates
+    # touch, and the plan's gate count is unchanged
+    import workloads as W
+    for n, k, circ in ((14, 6, W.brick(14, 12, 3)), (13, 5, W.qv_like(13, 6, 5)), (12, 4, W.qsb(12, 7, sets=3))):
+        p = qs.Plan(qs.Circuit(circ), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=k)
+        assert p.stats()["gates"] == len(circ)
+        for i, (kind, _) in enumerate(p.step_info()):
+            if kind != "block":
+                continue
+            q = sorted(p.step_qubits(i))
+            assert 4 <= len(q) <= k
+            if q[-1] - q[0] + 1 == len(q):  # a window
+                assert q[0] == 0 or q[0] >= 2 or q[-1] + 1 >= n or len(q) == k
