@@ -51,8 +51,8 @@ WORKLOADS = {
 # workload (profiles/); per launch traffic grows with the state, so n qubits
 # scale it by 2^(n - 26).  Set to None whenever the kernel changes until it
 # is re-captured.
-TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1>, profiles/tile_c64_brick26.md
-BLOCK_C64_TRAFFIC_26Q = {  # profiles/fused_umma_k6_brick26.md
+TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1> (its ncu capture at 26 qubits)
+BLOCK_C64_TRAFFIC_26Q = {  # the block kernels' ncu captures at 26 qubits
     "k_fused_umma_tma<6,window>": 537.039872e6 + 475.896832e6,
     "k_fused_umma_tma<6,rows>": 537.023232e6 + 476.058368e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
