@@ -60,6 +60,16 @@ def test_null_and_range_checks_without_gpu(qs):
     assert L.qs_alloc(10, 7, ctypes.byref(h)) == qs.QS_EINVAL
     assert L.qs_wrap(10, qs.C128, ctypes.c_void_p(8), ctypes.byref(h)) == qs.QS_EINVAL  # misaligned
     assert L.qs_free(None) == qs.QS_OK
+    # measurement entry points check their arguments before touching a device
+    qv = (ctypes.c_int * 1)(0)
+    out = (ctypes.c_double * 2)()
+    o = ctypes.c_int()
+    assert L.qs_probabilities(None, qv, 1, out) == qs.QS_EINVAL
+    assert L.qs_measure(None, 0, 0.5, ctypes.byref(o), out) == qs.QS_EINVAL
+    uu = (ctypes.c_double * 1)(0.5)
+    res = (ctypes.c_uint64 * 1)()
+    assert L.qs_sample(None, 1, uu, res) == qs.QS_EINVAL
+    assert L.qs_plan_step_qubits(None, 0, qv, 1, ctypes.byref(o)) == qs.QS_EINVAL
 
 
 def test_circuit_and_plan_host_logic(qs):
