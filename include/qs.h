@@ -313,6 +313,14 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
  * step has more than `cap` qubits (nothing written) or i is out of range. */
 qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int* count);
 
+/* The 2^k x 2^k complex matrix (row-major, (re, im) per entry, FP64) of a
+ * dense-block step i (QS_PLAN_FUSED plans), in the qubit order of
+ * qs_plan_step_qubits: bit j of its row and column index is qubit j of
+ * that list.  `cap` is the capacity of M in doubles (2 * 4^k needed); *k
+ * receives the block's qubit count.  QS_EINVAL for another step kind, a
+ * step out of range or too small a buffer. */
+qs_status qs_plan_step_matrix(const qs_plan* p, int i, double* M, size_t cap, int* k);
+
 /* As qs_run_plan, and also times every step with CUDA events recorded on the
  * state's stream between launches: step_ms[i] receives the device time of
  * step i (nsteps must equal the plan's pass count).  Synchronises the

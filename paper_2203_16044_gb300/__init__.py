@@ -87,6 +87,7 @@ _SIGS = {
     "qs_run_plan": ([_vp, _vp], _int),
     "qs_plan_step_info": ([_vp, _int, _ip, _dp], _int),
     "qs_plan_step_qubits": ([_vp, _int, _ip, _int, _ip], _int),
+    "qs_plan_step_matrix": ([_vp, _int, _dp, ctypes.c_size_t, _ip], _int),
     "qs_probabilities": ([_vp, _ip, _int, _dp], _int),
     "qs_measure": ([_vp, _int, ctypes.c_double, _ip, _dp], _int),
     "qs_sample": ([_vp, ctypes.c_uint64, _dp, ctypes.POINTER(ctypes.c_uint64)], _int),
@@ -417,6 +418,15 @@ class Plan:
         cnt = ctypes.c_int()
         _check(_lib.qs_plan_step_qubits(self._h, int(i), q, 8, ctypes.byref(cnt)), "qs_plan_step_qubits")
         return list(q[:cnt.value])
+
+    def step_matrix(self, i: int) -> np.ndarray:
+        """The complex matrix of dense-block step i (bit j of its index is
+        step_qubits(i)[j])."""
+        buf = np.zeros(2 * 4 ** 6, dtype=np.float64)
+        k = ctypes.c_int()
+        _check(_lib.qs_plan_step_matrix(self._h, int(i), _dptr(buf), buf.size, ctypes.byref(k)), "qs_plan_step_matrix")
+        D = 1 << k.value
+        return buf[:2 * D * D].view(np.complex128).reshape(D, D).copy()
 
     def close(self):
         if getattr(self, "_h", None):

@@ -582,6 +582,19 @@ qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int
   return QS_OK;
 }
 
+qs_status qs_plan_step_matrix(const qs_plan* p, int i, double* M, size_t cap, int* k) {
+  if (!p || !k) return fail(QS_EINVAL, "qs_plan_step_matrix: NULL argument");
+  if (i < 0 || i >= (int)p->steps.size()) return fail(QS_EINVAL, "qs_plan_step_matrix: step %d out of range", i);
+  const qs_step& st = p->steps[i];
+  if (st.type != qs_step::BLOCK) return fail(QS_EINVAL, "qs_plan_step_matrix: step %d is not a dense block", i);
+  const qs_block& b = p->blocks[st.tile_index];
+  const size_t need = b.M.size();
+  if (cap < need || !M) return fail(QS_EINVAL, "qs_plan_step_matrix: step %d needs %zu doubles, cap %zu", i, need, cap);
+  for (size_t j = 0; j < need; ++j) M[j] = b.M[j];
+  *k = b.k;
+  return QS_OK;
+}
+
 qs_status qs_run_plan_profiled(qs_state* s, qs_plan* p, float* step_ms, int nsteps) {
   if (!s || !p || !step_ms) return fail(QS_EINVAL, "qs_run_plan_profiled: NULL argument");
   if (s->n != p->n || s->dtype != p->dtype) return fail(QS_EINVAL, "qs_run_plan_profiled: plan built for another n/dtype");
