@@ -34,7 +34,7 @@ from . import apply_1q, gate_matrix, run_circuit
 
 
 class ShardedState:
-    def __init__(self, n: int, x0: int = 0):
+    def __init__(self, n: int, x0: int = 0, chunks: int = 1):
         import torch.distributed as dist
         self.dist = dist
         self.rank = dist.get_rank()
@@ -49,6 +49,7 @@ class ShardedState:
         self.phys = list(range(n))  # phys[logical] = physical position
         self.history = []           # fused swaps done, (glob, loc, s)
         self.sent = 0               # bytes this rank has sent
+        self.chunks = chunks        # > 1: double-buffered fused swaps (§III-E)
 
     # ---- communication ---------------------------------------------------
     def _sendrecv(self, partner: int, send: np.ndarray) -> np.ndarray:
@@ -98,13 +99,16 @@ class ShardedState:
         new = np.empty_like(self.local)
         keep = field == w
         new[keep] = self.local[keep]
-        for d in range(1, 1 << s):
-            v = w ^ d
-            partner = (self.rank & ~(fmask << a)) | (v << a)
-            send = self.local[field == v]                    # these move to the rank with field v
-            recv = self._sendrecv(partner, send)            # the partner's amplitudes whose field is w
-            # on arrival their local field becomes the partner's global field v
-            new[field == v] = recv
+        if self.chunks > 1:
+            self._exchange_double_buffered(new, field, w, a, s)
+        else:
+            for d in range(1, 1 << s):
+                v = w ^ d
+                partner = (self.rank & ~(fmask << a)) | (v << a)
+                send = self.local[field == v]                    # these move to the rank with field v
+                recv = self._sendrecv(partner, send)            # the partner's amplitudes whose field is w
+                # on arrival their local field becomes the partner's global field v
+                new[field == v] = recv
         self.local = new
         for lq, ph in enumerate(self.phys):
             if glob <= ph < glob + s:
@@ -113,6 +117,46 @@ class ShardedState:
                 self.phys[lq] = glob + (ph - loc)
         if record:
             self.history.append((glob, loc, s))
+
+    def _exchange_double_buffered(self, new, field, w, a, s):
+        """The exchanges of a fused swap with double buffering (§III-E): each
+        partner's block goes in `chunks` pieces through two send / receive
+        buffer pairs; the transfer of piece j is in flight while piece j - 1
+        is scattered into place and piece j + 1 is gathered, and the first
+        piece for the next partner is posted before the last scatter of the
+        current one."""
+        import torch
+        fmask = (1 << s) - 1
+        pieces = []  # (partner, send piece, destination index array)
+        for d in range(1, 1 << s):
+            v = w ^ d
+            partner = (self.rank & ~(fmask << a)) | (v << a)
+            idx = np.nonzero(field == v)[0]
+            for part in np.array_split(idx, self.chunks):
+                pieces.append((partner, part))
+        bufs = [None, None]  # (requests, receive buffer, destination indices)
+
+        def post(j):
+            partner, part = pieces[j]
+            src = torch.from_numpy(np.ascontiguousarray(self.local[part]).view(np.float64).copy())  # gather
+            out = torch.empty(part.size * 2, dtype=torch.float64)
+            reqs = [self.dist.isend(src, partner), self.dist.irecv(out, partner)]
+            self.sent += part.size * 16
+            bufs[j % 2] = (reqs, out, part, src)
+
+        def finish(j):
+            reqs, out, part, _ = bufs[j % 2]
+            for r in reqs:
+                r.wait()
+            new[part] = out.numpy().view(np.complex128)  # scatter
+            bufs[j % 2] = None
+
+        if pieces:
+            post(0)
+            for j in range(len(pieces)):
+                if j + 1 < len(pieces):
+                    post(j + 1)
+                finish(j)
 
     def swap_gate(self, glob: int, loc: int):
         """A single swap of a global and a local qubit (a fused swap of one)."""
@@ -186,10 +230,11 @@ class ShardedState:
         return int(t.item())
 
 
-def run_sharded(n: int, circuit: Sequence, policy: str = "fused", restore: bool = False, x0: int = 0):
+def run_sharded(n: int, circuit: Sequence, policy: str = "fused", restore: bool = False, x0: int = 0,
+                chunks: int = 1):
     """Run a circuit on the emulated ranks; returns (state on rank 0 or None,
     total bytes sent over all ranks)."""
-    st = ShardedState(n, x0)
+    st = ShardedState(n, x0, chunks)
     for g in circuit:
         st.apply(g, policy)
     if restore:

@@ -9,6 +9,8 @@ fused swap) emulated on CPU ranks (gloo, 127.0.0.1): oracle/sharded.py.
   the single-process oracle's bit for bit (the ranks run the same per-pair
   arithmetic), and every fused swap of s qubits sends 2^(n+4) (1 - 2^-s)
   bytes over all ranks.
+* Double buffering of the fused-swap exchange (§III-E): the same bytes and
+  the same state.
 """
 import json
 import os
@@ -55,6 +57,14 @@ def _worker(rank, world, port, q, job):
                     st.apply(g, policy)
                 st.restore()
                 res[policy] = (st.total_sent(), st.gather())
+        elif job[0] == "buffered":
+            _, n, circ = job
+            for chunks in (1, 4):
+                st = ShardedState(n, chunks=chunks)
+                for g in circ:
+                    st.apply(g, "fused")
+                st.restore()
+                res[chunks] = (st.total_sent(), st.gather(), len(st.history))
         else:
             n, circ = job
             for policy in ("fused", "swap"):
@@ -112,3 +122,17 @@ def test_sharded_circuits_match_oracle(world, kind):
         assert sent == sum(int(2 ** (n + 4) * (1 - 2.0 ** -s)) for s in swaps)
         if policy == "fused":
             assert swaps and all(s == p for s in swaps)
+
+
+def test_double_buffered_fused_swap():
+    # §III-E: the exchanges in 4 pieces per partner through two buffer
+    # pairs move the same bytes and give the same state as in one piece
+    import oracle
+    import workloads as W
+    n = 10
+    circ = W.brick(n, 6, 92)
+    res = run_ranks(4, ("buffered", n, circ))
+    want = oracle.zero_state(n)
+    oracle.run_circuit(want, circ)
+    assert res[1][0] == res[4][0] > 0
+    assert np.array_equal(res[1][1], want) and np.array_equal(res[4][1], want)
