@@ -138,3 +138,24 @@ def test_plan_step_qubits(qs):
     assert seen == set(range(n))
     with pytest.raises(qs.QSError):
         p.step_qubits(p.stats()["passes"])
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 (no torch or
+    # C++ types) and as C++
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "include/qs.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-c", str(src), "-I", ROOT, "-o",
+                        str(tmp_path / "h.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx:
+        src2 = tmp_path / "h.cpp"
+        src2.write_text('#include "include/qs.h"\nint main() { return 0; }\n')
+        r = subprocess.run([cxx, "-std=c++11", "-Wall", "-Werror", "-c", str(src2), "-I", ROOT, "-o",
+                            str(tmp_path / "h2.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
