@@ -159,3 +159,19 @@ def test_header_is_plain_c(tmp_path):
         r = subprocess.run([cxx, "-std=c++11", "-Wall", "-Werror", "-c", str(src2), "-I", ROOT, "-o",
                             str(tmp_path / "h2.o")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_against_the_library(qs, tmp_path):
+    # a plain C caller (tests/c/abi_example.c) compiles against the header and
+    # links against libqs.so; running it needs a GPU
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(qs.LIB_PATH)
+    exe = tmp_path / "abi_example"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", os.path.join(ROOT, "tests", "c", "abi_example.c"),
+                        "-I", ROOT, "-L", libdir, "-lqs", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert exe.exists()
