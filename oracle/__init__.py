@@ -55,6 +55,7 @@ def lib():
         L.or_probabilities.argtypes = [dp, c_int, ip, c_int, dp]
         L.or_collapse.argtypes = [dp, c_int, c_int, c_int, c_d]
         L.or_sample.argtypes = [dp, c_int, c_int, dp, up]
+        L.or_cdf.argtypes = [dp, c_int, dp]
         L.or_sample.restype = c_int
         _lib = L
     return _lib
@@ -241,14 +242,23 @@ def collapse(psi, q: int, outcome: int, p: float) -> None:
     lib().or_collapse(_dp(psi), _nq(psi), int(q), int(outcome), float(p))
 
 
+def cdf(psi) -> np.ndarray:
+    """Cumulative distribution in index order, F[x] = p_0 + ... + p_x, one
+    running FP64 sum (oracle.cpp or_cdf)."""
+    psi = _state(psi)
+    out = np.empty(psi.size, dtype=np.float64)
+    lib().or_cdf(_dp(psi), _nq(psi), _dp(out))
+    return out
+
+
 def sample(psi, u) -> np.ndarray:
-    """Basis-state samples for the uniforms u (the chunked inverse-CDF
-    definition in oracle.cpp)."""
-    import ctypes
+    """Basis-state samples for the uniforms u: the smallest x with
+    F[x] > u T (F = cdf(psi), T = F[-1]), or the largest x with p_x > 0 when
+    rounding leaves none (oracle.cpp or_sample)."""
     psi = _state(psi)
     uu = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(uu.size, dtype=np.uint64)
-    r = lib().or_sample(_dp(psi), _nq(psi), uu.size, _dp(uu), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    r = lib().or_sample(_dp(psi), _nq(psi), uu.size, _dp(uu), _up(out))
     if r != 0:
         raise ValueError("sampling a state of zero norm")
     return out

@@ -23,6 +23,7 @@
 // function below is pinned by tests that do not reuse it (Kronecker-product
 // brute force, closed forms, identities); none is "parity unpinned".
 
+#include <algorithm>
 #include <complex>
 #include <cstdint>
 #include <cstring>
@@ -458,19 +459,12 @@ double or_adjoint_grad(const double* psi0, int n, int ngates, const int* kinds,
 // ---------------------------------------------------------------------------
 // Measurement in the computational basis (§II-A: a circuit is a sequence of
 // gates, measurements and resets).  Outcome probabilities follow the Born
-// rule, p_x = |a_x|^2.  The paper gives no procedure for them; the steps
-// below are this project's definitions, and the GPU path takes the same
-// steps in the same floating-point order.
+// rule, p_x = |a_x|^2.  The paper gives no procedure for them; the functions
+// below are the plain definitions.
 // ---------------------------------------------------------------------------
 
-// p_x = re * re + im * im with each product and the sum rounded on its own
-// (no fused multiply-add; the volatile temporaries keep the compiler from
-// contracting): the sampling definition below depends on these exact bits.
-static double prob_of(const cplx& a) {
-  volatile double r = a.real() * a.real();
-  volatile double i = a.imag() * a.imag();
-  return r + i;
-}
+// Born-rule probability of one amplitude.
+static double prob_of(const cplx& a) { return a.real() * a.real() + a.imag() * a.imag(); }
 
 // Marginal probabilities of k qubits: out[r] = sum of p_x over x whose bits
 // at qubits[0..k-1] form r (bit i of r = qubits[i]), summed in index order.
@@ -495,57 +489,35 @@ void or_collapse(double* state, int n, int q, int outcome, double p) {
   for (u64 x = 0; x < N; ++x) a[x] = ((int)((x >> q) & 1) == outcome) ? a[x] * s : cplx(0.0, 0.0);
 }
 
-// Sampling: the inverse of the cumulative distribution in index order, taken
-// through chunk sums so that a parallel implementation can follow it
-// exactly.
-//   C = min(N, 1024) amplitudes per chunk, chunk c = [cC, (c + 1) C).
-//   S_c: 32 partials s_l = sum of p_{cC + l + 32 i} over i = 0, 1, ... while
-//        l + 32 i < C (in that order), then for off = 16, 8, 4, 2, 1 every
-//        s_l becomes s_l + s_{l xor off}; S_c = s_0.
-//   P_0 = 0, P_{c+1} = P_c + S_c in order; T = P_{N / C}.
-//   For a uniform u in [0, 1): t = u T; c = the largest chunk with P_c <= t;
-//   r = P_c and, for x = cC, cC + 1, ...: r = r + p_x; the sample is the
-//   first x with r > t.  If none up to N - 1 (rounding), the sample is the
-//   largest x with p_x > 0.
-// Returns -1 for a state of zero norm.
+// Cumulative distribution in index order: F[x] = p_0 + p_1 + ... + p_x,
+// one running FP64 sum.
+void or_cdf(const double* state, int n, double* F) {
+  const u64 N = u64(1) << n;
+  const cplx* a = as_c(state);
+  double r = 0.0;
+  for (u64 x = 0; x < N; ++x) {
+    r += prob_of(a[x]);
+    F[x] = r;
+  }
+}
+
+// Sampling by inversion of the cumulative distribution: with F as in or_cdf
+// and T = F[N - 1], a uniform u in [0, 1) gives t = u T and the sample is the
+// smallest x with F[x] > t.  If rounding leaves no such x, the sample is the
+// largest x with p_x > 0.  Returns -1 for a state of zero norm.
 int or_sample(const double* state, int n, int nshots, const double* u, u64* out) {
   const u64 N = u64(1) << n;
-  const u64 C = N < 1024 ? N : 1024;
-  const u64 nch = N / C;
   const cplx* a = as_c(state);
-  std::vector<double> P(nch + 1, 0.0);
-  for (u64 c = 0; c < nch; ++c) {
-    double sl[32];
-    for (int l = 0; l < 32; ++l) {
-      sl[l] = 0.0;
-      for (u64 j = (u64)l; j < C; j += 32) sl[l] += prob_of(a[c * C + j]);
-    }
-    for (int off = 16; off >= 1; off >>= 1) {
-      double nx[32];
-      for (int l = 0; l < 32; ++l) nx[l] = sl[l] + sl[l ^ off];
-      for (int l = 0; l < 32; ++l) sl[l] = nx[l];
-    }
-    P[c + 1] = P[c] + sl[0];
-  }
-  const double T = P[nch];
+  std::vector<double> F(N);
+  or_cdf(state, n, F.data());
+  const double T = F[N - 1];
   if (!(T > 0.0)) return -1;
   u64 last = N - 1;
   while (last > 0 && !(prob_of(a[last]) > 0.0)) --last;
   for (int s = 0; s < nshots; ++s) {
     const double t = u[s] * T;
-    u64 c = 0;
-    for (u64 d = 1; d < nch; ++d)
-      if (P[d] <= t) c = d;
-    double r = P[c];
-    u64 pick = last;
-    for (u64 x = c * C; x < N; ++x) {
-      r = r + prob_of(a[x]);
-      if (r > t) {
-        pick = x;
-        break;
-      }
-    }
-    out[s] = pick;
+    const u64 x = (u64)(std::upper_bound(F.begin(), F.end(), t) - F.begin());
+    out[s] = x < N ? x : last;
   }
   return 0;
 }

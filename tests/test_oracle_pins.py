@@ -544,7 +544,8 @@ def test_probabilities_and_collapse_closed_forms():
 @pytest.mark.parametrize("n", [4, 10, 12])
 def test_sample_uniform_dyadic_is_floor(n):
     # every p_x = 2^-n exactly (amplitudes 2^(-n/2) set directly), so every
-    # chunk sum, prefix and running sum is exact: sample(u) = floor(u 2^n)
+    # running sum is exact, F[x] = (x + 1) 2^-n: sample(u) = floor(u 2^n)
+    # (a search for F[x] >= t instead of F[x] > t fails at u = 0.5)
     psi = np.full(1 << n, 2.0 ** (-n / 2), dtype=complex)
     u = np.concatenate([[0.0, 0.5, 1 - 2.0 ** -53], np.random.default_rng(42).random(500)])
     got = oracle.sample(psi, u)
@@ -579,3 +580,45 @@ def test_sample_frequencies():
     counts = np.bincount(oracle.sample(psi, u).astype(np.int64), minlength=1 << n)
     sd = np.sqrt(p * (1 - p) * u.size)
     assert np.all(np.abs(counts - p * u.size) <= 5 * sd + 1)
+
+
+@pytest.mark.parametrize("n", [1, 7, 14])
+def test_cdf_against_exactly_rounded_prefix(n):
+    # F[x] against math.fsum (the exactly rounded sum of the same squares):
+    # a sequential FP64 sum of x + 1 nonnegative terms is within
+    # (x + 1) 2^-53 F[x] of it; a dropped or repeated term is not
+    psi = W.random_state(n, 48 + n)
+    psi[1::5] = 0
+    p = psi.real ** 2 + psi.imag ** 2
+    F = oracle.cdf(psi)
+    idx = np.unique(np.concatenate([[0, p.size - 1], np.random.default_rng(n).integers(0, p.size, 50)]))
+    for x in idx:
+        exact = math.fsum(p[: x + 1])
+        assert abs(F[x] - exact) <= (x + 1) * 2.0 ** -53 * exact + 1e-300
+    assert np.all(np.diff(F) >= 0)
+
+
+def test_sample_is_inverse_cdf_by_exact_rationals():
+    # 3 qubits: the probabilities as exact rationals, the CDF summed exactly;
+    # every sample x has Fexact(x - 1) <= u T < Fexact(x) up to the rounding
+    # of 8 terms, and where u T is clear of every boundary it is the only x
+    from fractions import Fraction
+    n = 3
+    psi = W.random_state(n, 49)
+    psi[5] = 0
+    p = [Fraction(float(v.real)) ** 2 + Fraction(float(v.imag)) ** 2 for v in psi]
+    Fx = [sum(p[: x + 1], Fraction(0)) for x in range(8)]
+    T = Fx[-1]
+    u = np.concatenate([[0.0, 1 - 2.0 ** -53], np.random.default_rng(50).random(3000)])
+    got = oracle.sample(psi, u)
+    eps = Fraction(16, 2 ** 53) * T
+    for ui, x in zip(u, got):
+        x = int(x)
+        ut = Fraction(float(ui)) * T
+        lo = Fx[x - 1] if x > 0 else Fraction(0)
+        assert p[x] > 0
+        assert lo - eps <= ut < Fx[x] + eps
+        if lo + eps < ut < Fx[x] - eps:
+            continue
+        # within eps of a boundary: x is one of the two neighbours of it
+        assert any(abs(ut - b) <= eps for b in [Fraction(0)] + Fx)
