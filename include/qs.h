@@ -181,20 +181,17 @@ qs_status qs_probabilities(qs_state* st, const int* qubits, int k, double* out);
  * [0, 1) or a state of zero norm. */
 qs_status qs_measure(qs_state* st, int q, double u, int* outcome, double* prob);
 
-/* Samples nshots basis states without changing the state: for the caller's
- * uniforms u[i] in [0, 1) (host), out[i] (host) is the inverse of the
- * cumulative distribution of p_x in index order at u[i], under this exact
- * definition (so the result does not depend on the launch shape):
- *   p_x = re * re + im * im, each product and the sum rounded on its own;
- *   C = min(2^n, 1024) amplitudes per chunk; the chunk sum S_c combines 32
- *   lane partials (lane l sums p_{cC + l + 32 i}, i ascending) by
- *   s_l <- s_l + s_{l xor off} for off = 16, 8, 4, 2, 1;
- *   P_0 = 0, P_{c+1} = P_c + S_c, T = P_{2^n / C};
- *   t = u T, c = the largest chunk with P_c <= t; out = the first x >= cC at
- *   which P_c + p_{cC} + ... + p_x exceeds t, or the largest x with p_x > 0
- *   if none does.
- * QS_EINVAL for a uniform outside [0, 1) or a state of zero norm.
- * Synchronises the state's stream. */
+/* Samples nshots basis states without changing the state, by inversion of
+ * the cumulative distribution in index order, F(x) = p_0 + ... + p_x: for
+ * the caller's uniforms u[i] in [0, 1) (host), with T = F(2^n - 1) and
+ * t = u[i] T, out[i] (host) is the x with F(x - 1) <= t < F(x); it always has
+ * p_x > 0.  The sums are accurate to FP64 level but not taken in index
+ * order, so where t lies within their rounding (a few 2^-53 T per term) of
+ * a boundary F(x), either neighbour may be returned.  The whole search runs
+ * on the GPU (partial sums of 1024- and 32768-amplitude blocks, one warp per
+ * shot); the state's scratch buffer grows to about 2^n / 1024 doubles plus
+ * 16 bytes per shot (up to 2^20 shots at a time).  QS_EINVAL for a uniform
+ * outside [0, 1) or a state of zero norm.  Synchronises the state's stream. */
 qs_status qs_sample(qs_state* st, uint64_t nshots, const double* u, uint64_t* out);
 
 /* Allocation-free inner product, for callers that cannot let the library
@@ -209,8 +206,8 @@ qs_status qs_sample(qs_state* st, uint64_t nshots, const double* u, uint64_t* ou
  * Synchronises `stream` before returning.  Allocates nothing: its partial
  * sums live in a fixed 16 KiB (1024 x 16-byte partials + result) static
  * device array that every GPU loading the library keeps until exit.  The
- * first call on a device looks that array's address up (make it before any
- * stream capture that should contain the call).  All calls share the array:
+ * first call on a device looks that array's address up (make that first
+ * call before any stream capture begins).  All calls share the array:
  * calls that overlap on the GPU race and must be serialised.  Returns
  * QS_EUNSUPPORTED if the reduction would need more than 1024 partials (a
  * device with more than 256 SMs). */

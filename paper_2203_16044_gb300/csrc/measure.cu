@@ -2,21 +2,20 @@
 // measurements and resets): marginal probabilities, the collapse after a
 // single-qubit measurement, and sampling of basis states.
 //
-// Probabilities follow the Born rule, p_x = |a_x|^2.  For the marginals the
-// squares are formed exactly in double-float (FP32 pairs with their
-// rounding errors) and summed per thread in double-float with an FP64 flush
-// every few groups: FP64-level accuracy without the FP64 pipe (about 1/64 of
-// the FP32 rate on GB300).  Sampling follows a step-by-step definition whose
-// floating-point operations are taken in a fixed order, so the index it
-// returns for a given uniform does not depend on the launch shape:
-//   p_x = re * re + im * im, each product and the sum rounded on its own;
-//   C = min(N, 1024) amplitudes per chunk; chunk sum S_c = 32 lane partials
-//   (lane l sums p_{cC + l + 32 i}, i ascending) combined by the butterfly
-//   s_l <- s_l + s_{l xor off} for off = 16, 8, 4, 2, 1;
-//   P_0 = 0, P_{c+1} = P_c + S_c in order, T = P_{N/C};
-//   a uniform u gives t = u T, c = the largest chunk with P_c <= t, and the
-//   sample is the first x >= cC at which the running sum r = P_c + p_{cC} +
-//   ... + p_x exceeds t (the largest x with p_x > 0 if none does).
+// Probabilities follow the Born rule, p_x = |a_x|^2.  The squares are formed
+// exactly in double-float (FP32 pairs with their rounding errors) and summed
+// in double-float, flushed into FP64 where a sum leaves a thread: FP64-level
+// accuracy without the FP64 pipe (about 1/64 of the FP32 rate on GB300).
+//
+// Sampling inverts the cumulative distribution in index order,
+// F(x) = p_0 + ... + p_x: a uniform u gives t = u T (T = F(2^n - 1)) and the
+// sample is the x with F(x - 1) <= t < F(x).  The search runs on the GPU in
+// three levels of partial sums -- superchunks of 32 chunks, chunks of 32 lane
+// ranges, lane ranges of 32 amplitudes -- one warp per shot, each level a
+// 32-wide ballot over prefix sums.  Its sums are taken in another order than
+// a sequential one, so near a boundary of F (within the rounding of the
+// sums, a few 2^-53 T per term) either neighbour can be returned; elsewhere
+// the result is the exact inverse.  An index with p_x = 0 is never returned.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -28,14 +27,13 @@ namespace qs {
 namespace {
 
 constexpr int kMT = 256;        // threads per CTA
-constexpr u64 kChunk = 1024;    // amplitudes per chunk of the sampling definition
 constexpr int kBins = 8;        // outcomes per marginal pass
+// Sampling levels: a lane range is 32 consecutive amplitudes, a chunk 32 lane
+// ranges (1024 amplitudes), a superchunk 32 chunks.
+constexpr u64 kChunk = 1024;
+constexpr int kSuper = 32;
 constexpr u64 kShotBatch = u64(1) << 20;
-
-__device__ __forceinline__ double prob(float2 v) {
-  return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
-}
-__device__ __forceinline__ double prob(double2 v) { return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)); }
+constexpr int kPrefixThreads = 1024;
 
 struct MargArgs {
   Ins ins;          // zero insertion at the measured qubits
@@ -112,46 +110,198 @@ __global__ void __launch_bounds__(kMT) k_collapse(A* __restrict__ a, u64 npairs,
   }
 }
 
-// Chunk sums of the sampling definition: one warp per chunk of C amplitudes.
+// p_x as a double-float: each square exact (TwoProd), their sum rounded once
+// in double-float.
+__device__ __forceinline__ dfl prob_df(float2 v) {
+  const dfl x = to_df(v.x), y = to_df(v.y);
+  dfl r = df_mul(x, x);
+  df_acc(r, df_mul(y, y));
+  return r;
+}
+__device__ __forceinline__ dfl prob_df(double2 v) {
+  const dfl x = to_df(v.x), y = to_df(v.y);
+  dfl r = df_mul(x, x);
+  df_acc(r, df_mul(y, y));
+  return r;
+}
+__device__ __forceinline__ dfl df_norm(dfl a) {
+  dfl r;
+  r.h = fast_two_sum(a.h, a.l, r.l);
+  return r;
+}
+__device__ __forceinline__ dfl df_shfl_up(dfl v, int d) {
+  return dfl{__shfl_up_sync(0xffffffffu, v.h, d), __shfl_up_sync(0xffffffffu, v.l, d)};
+}
+__device__ __forceinline__ dfl df_shfl(dfl v, int src) {
+  return dfl{__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+// a > b for normalised double-floats
+__device__ __forceinline__ bool df_gt(dfl a, dfl b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+// Inclusive prefix over the warp's lanes, in double-float.
+__device__ __forceinline__ dfl df_warp_incl(dfl v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const dfl o = df_shfl_up(v, d);
+    if (lane >= d) v = df_add(v, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double dbl_warp_incl(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += o;
+  }
+  return v;
+}
+__device__ __forceinline__ dfl to_dfl_of(double x) {
+  dfl r;
+  r.h = (float)x;
+  r.l = (float)(x - (double)r.h);
+  return r;
+}
+
+// Level sums: S1[c] for every chunk (1024 amplitudes) and S2[s] for every
+// superchunk (32 chunks), one warp per superchunk; lanes read the chunk
+// coalesced (amplitude cC + lane + 32 i).
 template <typename A>
-__global__ void __launch_bounds__(kMT) k_chunk_sums(const A* __restrict__ a, u64 C, u64 nch, double* __restrict__ S) {
+__global__ void __launch_bounds__(kMT) k_sample_sums(const A* __restrict__ a, u64 N, u64 nch, u64 nsc,
+                                                     double* __restrict__ S1, double* __restrict__ S2) {
   const int lane = threadIdx.x & 31;
   const u64 wstride = (u64)gridDim.x * (kMT / 32);
-  for (u64 c = (u64)blockIdx.x * (kMT / 32) + (threadIdx.x >> 5); c < nch; c += wstride) {
-    double s = 0.0;
-    for (u64 j = (u64)lane; j < C; j += 32) s = __dadd_rn(s, prob(a[c * C + j]));
+  for (u64 sc = (u64)blockIdx.x * (kMT / 32) + (threadIdx.x >> 5); sc < nsc; sc += wstride) {
+    dfl s2{0.f, 0.f};
+    for (int j = 0; j < kSuper; ++j) {
+      const u64 c = sc * kSuper + j;
+      if (c >= nch) break;
+      const u64 x0 = c * kChunk;
+      dfl acc{0.f, 0.f};
+      if (x0 + kChunk <= N) {
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) {
+          const dfl p = prob_df(a[x0 + lane + 32 * i]);
+          df_acc(acc, p);
+        }
+      } else {
+        for (u64 x = x0 + lane; x < N; x += 32) df_acc(acc, prob_df(a[x]));
+      }
+      acc = df_norm(acc);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
-    if (lane == 0) S[c] = s;
+      for (int o = 16; o > 0; o >>= 1) {
+        const dfl t{__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
+        acc = df_add(acc, t);
+      }
+      if (lane == 0) S1[c] = (double)acc.h + (double)acc.l;
+      s2 = df_add(s2, acc);
+    }
+    if (lane == 0) S2[sc] = (double)s2.h + (double)s2.l;
   }
 }
 
-// One thread per shot: the running sum from chunk c[i] until it exceeds
-// t[i]; ~0 when the end of the state is reached first.
-template <typename A>
-__global__ void __launch_bounds__(kMT) k_sample_scan(const A* __restrict__ a, u64 N, u64 C, u64 nshots,
-                                                     const u64* __restrict__ chunk, const double* __restrict__ p0,
-                                                     const double* __restrict__ tt, u64* __restrict__ out) {
-  const u64 i = (u64)blockIdx.x * kMT + threadIdx.x;
-  if (i >= nshots) return;
-  double r = p0[i];
-  const double t = tt[i];
-  u64 x = chunk[i] * C;
-  for (; x < N; ++x) {
-    r = __dadd_rn(r, prob(a[x]));
-    if (r > t) break;
+// Exclusive prefix of the superchunk sums, P2[s] = S2[0] + ... + S2[s - 1],
+// and P2[nsc] = T: one CTA, each thread a contiguous run summed in order.
+__global__ void __launch_bounds__(kPrefixThreads) k_sample_prefix(const double* __restrict__ S2, u64 nsc,
+                                                                  double* __restrict__ P2) {
+  __shared__ double wsum[kPrefixThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const u64 run = (nsc + kPrefixThreads - 1) / kPrefixThreads;
+  const u64 b = (u64)t * run, e = b + run < nsc ? b + run : nsc;
+  double tot = 0.0;
+  for (u64 i = b; i < e; ++i) tot += S2[i];
+  const double incl = dbl_warp_incl(tot);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const double v = wsum[lane];
+    const double wi = dbl_warp_incl(v);
+    wsum[lane] = wi - v;  // exclusive (rounding only shifts this warp's offset)
+    if (lane == 31) P2[nsc] = wi;
   }
-  out[i] = x < N ? x : ~u64(0);
+  __syncthreads();
+  double r = wsum[w] + (incl - tot);
+  for (u64 i = b; i < e; ++i) {
+    P2[i] = r;
+    r += S2[i];
+  }
 }
 
-// The largest x with p_x > 0 (the sampling fallback); *out must start at 0.
+// One warp per shot: t = u T, then at each level the 32 candidate partial
+// sums are prefixed across the lanes and a ballot picks the first one that
+// passes t and is not zero.  Where t sits at T itself after rounding (or on
+// a rounding difference between two levels' sums) and no candidate passes,
+// the last nonzero candidate is taken, so a returned index always has
+// p_x > 0 (in double-float) whenever T > 0.
 template <typename A>
-__global__ void __launch_bounds__(kMT) k_last_nonzero(const A* __restrict__ a, u64 N, unsigned long long* out) {
-  const u64 stride = (u64)gridDim.x * kMT;
-  unsigned long long best = 0;
-  for (u64 x = (u64)blockIdx.x * kMT + threadIdx.x; x < N; x += stride)
-    if (prob(a[x]) > 0.0) best = x;
-  if (best) atomicMax(out, best);
+__global__ void __launch_bounds__(kMT) k_sample_shots(const A* __restrict__ a, u64 N, u64 nch, u64 nsc,
+                                                      const double* __restrict__ S1, const double* __restrict__ S2,
+                                                      const double* __restrict__ P2, const double* __restrict__ u,
+                                                      u64 nshots, u64* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const double T = P2[nsc];
+  const u64 wstride = (u64)gridDim.x * (kMT / 32);
+  for (u64 i = (u64)blockIdx.x * (kMT / 32) + (threadIdx.x >> 5); i < nshots; i += wstride) {
+    const double t = u[i] * T;
+    // superchunk: the largest s with P2[s] <= t (P2[0] = 0 <= t always),
+    // 32-ary: each round the lanes probe 32 evenly spaced candidates
+    u64 lo = 0, len = nsc;
+    while (len > 1) {
+      const u64 step = (len + 31) / 32, off = (u64)lane * step;
+      const unsigned m = __ballot_sync(0xffffffffu, off < len && P2[lo + off] <= t);
+      const u64 j = (u64)(31 - __clz(m));
+      lo += j * step;
+      len = len - j * step < step ? len - j * step : step;
+    }
+    u64 sc = lo;
+    if (!(S2[sc] > 0.0)) {
+      // the nearest superchunk at or below with a nonzero sum (T > 0: one exists)
+      for (long long s0 = (long long)sc; s0 >= 0; s0 -= 32) {
+        const long long idx = s0 - lane;
+        const unsigned mz = __ballot_sync(0xffffffffu, idx >= 0 && S2[idx] > 0.0);
+        if (mz) {
+          sc = (u64)(s0 - (__ffs(mz) - 1));
+          break;
+        }
+      }
+    }
+    // chunk within the superchunk
+    const double base = P2[sc];
+    const u64 c0 = sc * kSuper;
+    const double v = c0 + lane < nch ? S1[c0 + lane] : 0.0;
+    const double incl = dbl_warp_incl(v);
+    unsigned m = __ballot_sync(0xffffffffu, v > 0.0 && base + incl > t);
+    int j = m ? __ffs(m) - 1 : 31 - __clz(__ballot_sync(0xffffffffu, v > 0.0));
+    j = j < 0 ? 0 : j;  // (S2[sc] > 0, so some v > 0: kept in range regardless)
+    const double ex1 = __shfl_sync(0xffffffffu, incl, j > 0 ? j - 1 : 0);
+    const double base1 = base + (j > 0 ? ex1 : 0.0);
+    const u64 c = c0 + (u64)j;
+    const dfl tq = to_dfl_of(t - base1);
+    // lane range within the chunk: lane l sums amplitudes cC + 32 l .. + 31
+    const u64 xl = c * kChunk + (u64)lane * 32;
+    dfl L{0.f, 0.f};
+    if (xl + 32 <= N) {
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) df_acc(L, prob_df(a[xl + k]));
+    } else {
+      for (u64 x = xl; x < N; ++x) df_acc(L, prob_df(a[x]));
+    }
+    L = df_norm(L);
+    const dfl inclL = df_warp_incl(L);
+    m = __ballot_sync(0xffffffffu, L.h > 0.f && df_gt(inclL, tq));
+    int j0 = m ? __ffs(m) - 1 : 31 - __clz(__ballot_sync(0xffffffffu, L.h > 0.f));
+    j0 = j0 < 0 ? 0 : j0;
+    dfl ex0 = df_shfl(inclL, j0 > 0 ? j0 - 1 : 0);
+    if (j0 == 0) ex0 = dfl{0.f, 0.f};
+    // amplitude within the lane range
+    const u64 x = c * kChunk + (u64)j0 * 32 + lane;
+    const dfl p = x < N ? df_norm(prob_df(a[x])) : dfl{0.f, 0.f};
+    const dfl inclp = df_add(ex0, df_warp_incl(p));
+    m = __ballot_sync(0xffffffffu, p.h > 0.f && df_gt(inclp, tq));
+    int j1 = m ? __ffs(m) - 1 : 31 - __clz(__ballot_sync(0xffffffffu, p.h > 0.f));
+    j1 = j1 < 0 ? 0 : j1;
+    if (lane == 0) out[i] = c * kChunk + (u64)j0 * 32 + (u64)j1;
+  }
 }
 
 Ins ins_for(const int* qubits, int k) {
@@ -215,59 +365,34 @@ qs_status collapse(qs_state* s, int q, int outcome, double p) {
 
 template <typename A>
 qs_status sample(qs_state* s, u64 nshots, const double* u, uint64_t* out) {
-  const u64 N = u64(1) << s->n, C = std::min(N, kChunk), nch = N / C;
+  const u64 N = u64(1) << s->n;
+  const u64 nch = (N + kChunk - 1) / kChunk, nsc = (nch + kSuper - 1) / kSuper;
   const u64 batch = std::min(nshots, kShotBatch);
-  // scratch: chunk sums, then per shot chunk, P_c, t, result
-  const size_t need = sizeof(double) * nch + batch * (2 * sizeof(u64) + 2 * sizeof(double)) + sizeof(u64);
+  // scratch: S1 (nch), S2 (nsc), P2 (nsc + 1), uniforms and results of one
+  // batch of shots
+  const size_t need = sizeof(double) * (nch + 2 * nsc + 1) + batch * (sizeof(double) + sizeof(u64));
   qs_status st = ensure_scratch(s, need);
   if (st != QS_OK) return st;
   const A* a = static_cast<const A*>(s->amp);
-  double* S = static_cast<double*>(s->scratch);
-  u64* d_chunk = reinterpret_cast<u64*>(S + nch);
-  double* d_p0 = reinterpret_cast<double*>(d_chunk + batch);
-  double* d_t = d_p0 + batch;
-  u64* d_out = reinterpret_cast<u64*>(d_t + batch);
-  u64* d_last = d_out + batch;
-  k_chunk_sums<A><<<grid_for(nch, kMT / 32, 8), kMT, 0, s->stream>>>(a, C, nch, S);
-  if ((st = launch_ok("k_chunk_sums")) != QS_OK) return st;
-  std::vector<double> P(nch + 1, 0.0), hS(nch);
-  if ((st = sync_copy(s, hS.data(), S, sizeof(double) * nch, cudaMemcpyDeviceToHost)) != QS_OK) return st;
-  for (u64 c = 0; c < nch; ++c) P[c + 1] = P[c] + hS[c];
-  const double T = P[nch];
+  double* S1 = static_cast<double*>(s->scratch);
+  double* S2 = S1 + nch;
+  double* P2 = S2 + nsc;
+  double* d_u = P2 + nsc + 1;
+  u64* d_out = reinterpret_cast<u64*>(d_u + batch);
+  k_sample_sums<A><<<grid_for(nsc, kMT / 32, 8), kMT, 0, s->stream>>>(a, N, nch, nsc, S1, S2);
+  if ((st = launch_ok("k_sample_sums")) != QS_OK) return st;
+  k_sample_prefix<<<1, kPrefixThreads, 0, s->stream>>>(S2, nsc, P2);
+  if ((st = launch_ok("k_sample_prefix")) != QS_OK) return st;
+  double T = 0.0;
+  if ((st = sync_copy(s, &T, P2 + nsc, sizeof(double), cudaMemcpyDeviceToHost)) != QS_OK) return st;
   if (!(T > 0.0) || !std::isfinite(T)) return fail(QS_EINVAL, "qs_sample: the state has zero norm");
-  u64 last = 0;
-  bool have_last = false;
-  std::vector<u64> hc(batch);
-  std::vector<double> hp(batch), ht(batch);
   for (u64 b = 0; b < nshots; b += batch) {
     const u64 m = std::min(batch, nshots - b);
-    for (u64 i = 0; i < m; ++i) {
-      const double t = u[b + i] * T;
-      const u64 c = (u64)(std::upper_bound(P.begin(), P.begin() + nch, t) - P.begin()) - 1;
-      hc[i] = c;
-      hp[i] = P[c];
-      ht[i] = t;
-    }
-    cudaError_t e = cudaMemcpyAsync(d_chunk, hc.data(), sizeof(u64) * m, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p0, hp.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, ht.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s->stream);
+    cudaError_t e = cudaMemcpyAsync(d_u, u + b, sizeof(double) * m, cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "qs_sample: upload");
-    k_sample_scan<A><<<(unsigned)((m + kMT - 1) / kMT), kMT, 0, s->stream>>>(a, N, C, m, d_chunk, d_p0, d_t, d_out);
-    if ((st = launch_ok("k_sample_scan")) != QS_OK) return st;
+    k_sample_shots<A><<<grid_for(m, kMT / 32, 16), kMT, 0, s->stream>>>(a, N, nch, nsc, S1, S2, P2, d_u, m, d_out);
+    if ((st = launch_ok("k_sample_shots")) != QS_OK) return st;
     if ((st = sync_copy(s, out + b, d_out, sizeof(u64) * m, cudaMemcpyDeviceToHost)) != QS_OK) return st;
-    for (u64 i = 0; i < m; ++i) {
-      if (out[b + i] != ~u64(0)) continue;
-      if (!have_last) {
-        e = cudaMemsetAsync(d_last, 0, sizeof(u64), s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "qs_sample: memset");
-        k_last_nonzero<A><<<grid_for(N, kMT, 4), kMT, 0, s->stream>>>(a, N,
-                                                                        reinterpret_cast<unsigned long long*>(d_last));
-        if ((st = launch_ok("k_last_nonzero")) != QS_OK) return st;
-        if ((st = sync_copy(s, &last, d_last, sizeof(u64), cudaMemcpyDeviceToHost)) != QS_OK) return st;
-        have_last = true;
-      }
-      out[b + i] = last;
-    }
   }
   return QS_OK;
 }
