@@ -15,14 +15,16 @@
 // not pass the array's name to a kernel -- on the host that name is only a
 // stand-in, not a device address -- so the first call on each device looks
 // up the device address with cudaGetSymbolAddress (with that device current)
-// and caches it.  That first call therefore does a little set-up work; make
-// it before any stream capture that should contain the entry point.
+// and caches it once the lookup has succeeded (a failed lookup is retried by
+// the next call).  That first call therefore does a little set-up work; make
+// it before any stream capture begins.
 //
 // Every call shares the one array and the last call's partial sums stay in
 // it.  Nothing has to start at zero: each CTA overwrites its own partial
 // before the final pass reads exactly those partials.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads, on the
 // same device) race on the array: serialise them.
+#include <atomic>
 #include <mutex>
 
 #include "kcommon.cuh"
@@ -90,12 +92,27 @@ __global__ void __launch_bounds__(kNaThreads) k_inner_static_final(const double2
   if (threadIdx.x == 0) *out = make_double2(sr, si);
 }
 
-struct DeviceScratch {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
-  double2* ptr = nullptr;
-};
-DeviceScratch g_scratch[kNaMaxDevices];
+// Device address of g_inner_scratch per device, set once a lookup succeeds.
+std::atomic<double2*> g_scratch_ptr[kNaMaxDevices];
+std::mutex g_scratch_mu;
+
+// The scratch array's device address on `dev` (the current device).
+cudaError_t scratch_address(int dev, double2** out) {
+  double2* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (p) {
+    *out = p;
+    return cudaSuccess;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  p = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+  if (!p) {
+    const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_inner_scratch);
+    if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    g_scratch_ptr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -111,11 +128,9 @@ extern "C" qs_status qs_inner_noalloc(const void* a, const void* b, int n, qs_dt
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "qs_inner_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kNaMaxDevices) return fail(QS_EUNSUPPORTED, "qs_inner_noalloc: device %d >= %d", dev, kNaMaxDevices);
-  DeviceScratch& ds = g_scratch[dev];
-  std::call_once(ds.once, [&ds]() {
-    ds.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&ds.ptr), g_inner_scratch);
-  });
-  if (ds.err != cudaSuccess || !ds.ptr) return cuda_fail(ds.err, "qs_inner_noalloc: cudaGetSymbolAddress");
+  double2* scratch = nullptr;
+  e = scratch_address(dev, &scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "qs_inner_noalloc: cudaGetSymbolAddress");
   const int LA = dtype == QS_C64 ? 1 : 0;
   const u64 npk = u64(1) << (n - LA);
   // Same grid rule as qs_inner: at most 4 CTAs per SM, 2048 packets per CTA.
@@ -128,8 +143,8 @@ extern "C" qs_status qs_inner_noalloc(const void* a, const void* b, int n, qs_dt
     return fail(QS_EUNSUPPORTED, "qs_inner_noalloc: needs %llu partial sums, the static scratch holds %d",
                 (unsigned long long)grid, kNaMaxPartials);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  double2* part = ds.ptr;
-  double2* res = ds.ptr + kNaMaxPartials;
+  double2* part = scratch;
+  double2* res = scratch + kNaMaxPartials;
   if (dtype == QS_C64)
     k_inner_static<float><<<(unsigned)grid, kNaThreads, 0, s>>>(static_cast<const float*>(a), static_cast<const float*>(b), npk, part);
   else
