@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import workloads as W
+from fidelity import check_c64
 
 pytestmark = pytest.mark.gpu
 
@@ -34,12 +35,11 @@ def circuits_for(sizes, seed):
     return out
 
 
-def check(got, want, dtype):
+def check(got, want, dtype, gates=None):
     if dtype == "c128":
         assert np.max(np.abs(got - want)) <= 1e-12
     else:
-        ov = np.vdot(got.astype(np.complex128), want)
-        assert 1 - abs(ov) ** 2 <= 1e-5
+        check_c64(got, want, gates=gates)
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
@@ -52,7 +52,7 @@ def test_batch_matches_oracle(qs, dtype):
     for i, (n, c) in enumerate(zip(sizes, circs)):
         want = oracle.zero_state(n)
         oracle.run_circuit(want, c)
-        check(b.state(i).cpu().numpy(), want, dtype)
+        check(b.state(i).cpu().numpy(), want, dtype, gates=len(c))
     st = b.stats()
     assert st["circuits"] == len(sizes) and st["passes"] >= len(sizes)
     # replay (graph) twice more: same result from |0>
@@ -62,7 +62,7 @@ def test_batch_matches_oracle(qs, dtype):
     for i, (n, c) in enumerate(zip(sizes, circs)):
         want = oracle.zero_state(n)
         oracle.run_circuit(want, c)
-        check(b.state(i).cpu().numpy(), want, dtype)
+        check(b.state(i).cpu().numpy(), want, dtype, gates=len(c))
 
 
 def test_batch_on_current_contents(qs):
@@ -91,14 +91,14 @@ def test_batch_tile_options_and_autotune(qs):
         for i, (n, c) in enumerate(zip(sizes, circs)):
             want = oracle.zero_state(n)
             oracle.run_circuit(want, c)
-            check(b.state(i).cpu().numpy(), want, "c64")
+            check(b.state(i).cpu().numpy(), want, "c64", gates=len(c))
     b = qs.Batch(sizes, circs, dtype="c64", autotune=True)
     assert b.tuned_ms is not None and b.tuned_ms > 0
     b.run(True)
     b.sync()
     want = oracle.zero_state(16)
     oracle.run_circuit(want, circs[3])
-    check(b.state(3).cpu().numpy(), want, "c64")
+    check(b.state(3).cpu().numpy(), want, "c64", gates=len(circs[3]))
 
 
 def test_batch_wait_times_out_cleanly(qs):

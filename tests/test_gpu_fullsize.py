@@ -4,7 +4,8 @@
   configuration): the brick circuit (depth 40) and the QFT of a seeded basis
   state, compared with the FP64 oracle in full, max |error| <= 1e-12.
 * 26 qubits, complex64 fused into 4-, 5- and 6-qubit tensor-core blocks, depth
-  40: infidelity against the FP64 oracle <= 1e-5, norm kept.
+  40: infidelity against the FP64 oracle <= 1e-5 (stated and normalised
+  forms), norm within 1e-6.
 * 30 qubits, the benchmark's own launch configuration (complex64,
   QS_PLAN_FUSED, 6-qubit blocks): infidelity against the complex128 GPU path
   (tiled plan, itself oracle-exact at every size above) <= 1e-5; the circuit
@@ -21,11 +22,11 @@ import pytest
 
 import oracle
 import workloads as W
+from fidelity import check_c64_torch, C64_INFIDELITY, C64_NORM
 
 pytestmark = pytest.mark.gpu
 
 C128_TOL = 1e-12
-C64_INFIDELITY = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -50,12 +51,6 @@ def gpu_run(qs, n, circ, dtype, mode, fuse=0, x0=0):
     return s
 
 
-def infidelity_gpu(s64, s128):
-    import torch
-    ov = torch.vdot(s64.tensor.to(torch.complex128), s128.tensor).item()
-    return 1.0 - abs(ov) ** 2
-
-
 def test_c128_brick_and_qft_28q_vs_oracle_in_full(qs):
     n = 28
     for circ, x0 in ((W.brick(n, 40, 3), 0), (W.qft(n), W.basis_index(n, 4))):
@@ -78,9 +73,11 @@ def test_c64_fused_26q_vs_oracle(qs, k):
         test_c64_fused_26q_vs_oracle.want = want
     want = test_c64_fused_26q_vs_oracle.want
     got = gpu_run(qs, n, circ, "c64", qs.PLAN_FUSED, fuse=k).to_numpy().astype(np.complex128)
-    ov = oracle.inner(got, want)
-    assert 1.0 - abs(ov) ** 2 <= C64_INFIDELITY
-    assert abs(oracle.inner(got, got).real - 1.0) <= 1e-6
+    ov = abs(oracle.inner(got, want)) ** 2
+    na, nb = oracle.inner(got, got).real, oracle.inner(want, want).real
+    assert 1.0 - ov <= C64_INFIDELITY
+    assert 1.0 - ov / (na * nb) <= C64_INFIDELITY
+    assert abs(na - nb) <= C64_NORM
 
 
 def test_c64_fused_30q_vs_c128(qs):
@@ -89,8 +86,8 @@ def test_c64_fused_30q_vs_c128(qs):
     circ = W.brick(n, 40, 6)
     s64 = gpu_run(qs, n, circ, "c64", qs.PLAN_FUSED, fuse=6)
     s128 = gpu_run(qs, n, circ, "c128", qs.PLAN_TILED)
-    assert infidelity_gpu(s64, s128) <= C64_INFIDELITY
-    assert abs(s64.norm2() - 1.0) <= 1e-6
+    check_c64_torch(s64.tensor, s128.tensor)
+    assert abs(s64.norm2() - 1.0) <= C64_NORM
     del s64, s128
     torch.cuda.empty_cache()
 

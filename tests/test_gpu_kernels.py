@@ -267,3 +267,73 @@ def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
     want = start(psi, "c64")
     oracle.apply_dense(want, qsel, M)
     check(s.to_numpy(), want, "c64")
+
+
+def _block_sets(k, mode):
+    # one qubit set per tensor-core access path: a window of consecutive
+    # qubits (TMA boxes), qubits 0..k-1 (TMA rows), a gathered set
+    return {"window": [4 + i for i in [2, 0, 3, 1, 5, 4] if i < k],
+            "rows": [q for q in [2, 0, 3, 1, 5, 4] if q < k],
+            "gathered": [1, 9, 4, 12, 6, 2][:k]}[mode]
+
+
+def _group_norms(psi, qsel):
+    # ||v_g|| of every group (the 2^k amplitudes sharing the bits outside
+    # qsel), broadcast back to the amplitudes
+    mask = 0
+    for q in qsel:
+        mask |= 1 << q
+    gid = np.arange(psi.size, dtype=np.int64) & ~mask
+    sums = np.bincount(gid, weights=np.abs(psi) ** 2, minlength=psi.size)
+    return np.sqrt(sums[gid])
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("mode", ["window", "rows", "gathered"])
+def test_apply_fused_c64_non_unitary(qs, k, mode):
+    # a non-unitary block takes no group-norm restore: every output against
+    # the oracle, relative to its own sum of term magnitudes (|M| |v|)_i,
+    # plus the split's absolute floor of 2^-20 of the group norm times max |M|
+    n = 14
+    qsel = _block_sets(k, mode)
+    psi = W.random_state(n, 7700 + k)
+    M = W.random_matrix(1 << k, 7710 + k) * 1.7  # entries ~ N(0, 1.7^2 / 2^(k+1)) (re, im)
+    s = gpu_state(qs, psi, "c64")
+    s.apply_fused(qsel, M)
+    v = start(psi, "c64")
+    want = v.copy()
+    oracle.apply_dense(want, qsel, M)
+    mag = np.abs(v).astype(np.complex128)
+    oracle.apply_dense(mag, qsel, np.abs(M).astype(np.complex128))
+    bound = 4e-6 * mag.real + 2.0 ** -20 * _group_norms(v, qsel) * np.max(np.abs(M))
+    err = np.abs(s.to_numpy().astype(np.complex128) - want)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # the norm is not restored: it changes as M dictates
+    assert abs(np.vdot(want, want).real - 1.0) > 1e-3
+
+
+@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("mode", ["window", "rows", "gathered"])
+def test_apply_fused_c64_dynamic_range(qs, k, mode):
+    # groups whose amplitudes span 2^-20 of dynamic range (and whose norms
+    # span 2^-30 across the state): the power-of-two row scaling keeps every
+    # output within 2^-20 of its group's norm (unitary M: the group norm is
+    # kept), compared element by element
+    n = 14
+    qsel = _block_sets(k, mode)
+    psi = W.random_state(n, 7800 + k)
+    x = np.arange(psi.size, dtype=np.int64)
+    r = np.zeros(psi.size, dtype=np.int64)
+    for i, q in enumerate(qsel):
+        r |= ((x >> q) & 1) << i
+    grp = x & ~sum(1 << q for q in qsel)
+    psi = psi * 2.0 ** (-20.0 * r / ((1 << k) - 1)) * 2.0 ** (-(grp % 31).astype(np.float64))
+    M = W.random_unitary(1 << k, 7810 + k)
+    s = gpu_state(qs, psi, "c64")
+    s.apply_fused(qsel, M)
+    v = start(psi, "c64")
+    want = v.copy()
+    oracle.apply_dense(want, qsel, M)
+    err = np.abs(s.to_numpy().astype(np.complex128) - want)
+    gn = _group_norms(v, qsel)
+    assert np.all(err <= 2.0 ** -20 * gn), float(np.max(err / gn))
