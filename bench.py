@@ -3,10 +3,12 @@
 Default workload (the precision + fusion configuration): the 30-qubit brick
 random circuit of depth 40 (U3 on every qubit, then CNOT(i, i+1) on
 alternating pairs; the QSB structure of §IV-F), seed 6, complex64 state
-(8 GiB) fused into dense 6-qubit blocks on the tensor cores (tcgen05,
-3xTF32).  The same circuit in complex128 (16 GiB, tiled plan) runs beside
-it and both are reported, with their infidelity measured on the GPU; the
-complex64 tiled and 4-, 5-qubit-block plans are timed as extras.
+(8 GiB) fused into dense 6-qubit blocks on the tensor cores (tcgen05, FP16
+hi/lo split products).  The same circuit in complex128 (16 GiB) runs beside
+it, fused into 5-qubit blocks on the tensor cores (FP64 operands split into
+9-bit integer digits, exact digit products), and both are reported, with
+their infidelity measured on the GPU; the other plans of each dtype (tiles,
+4- and 5-qubit blocks) are timed as extras.
 
 Metric (§IV-F, Eq. 5 traffic model): effective HBM bandwidth
     2 * 2^n * bytes_per_amplitude * #gates / time
@@ -57,7 +59,16 @@ BLOCK_C64_TRAFFIC_26Q = {  # the block kernels' ncu captures at 26 qubits
     "k_fused_umma_tma<6,rows>": 537.023232e6 + 476.058368e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
 }
+BLOCK_C128_TRAFFIC_26Q = {}  # filled from the complex128 block kernels' ncu captures
 S_BYTES = {"c64": 8, "c128": 16}
+# what each dtype's arithmetic is, for the report
+ARITHMETIC = {
+    "c64": "complex64 storage; FP32 arithmetic (tensor-core blocks: FP16 hi/lo split products, ~2^-22 per product)",
+    "c128": ("complex128 storage (FP64); tensor-core blocks: each group's values on a 43-bit fixed-point grid split "
+             "into five 9-bit integer digits, exact FP16 digit products and exact FP32 level sums (error ~2^-44 of "
+             "the group's largest amplitude); tiles and per-gate kernels: double-float pairs (~2^-46, float "
+             "exponent range)"),
+}
 
 
 def metric_name(wl):
@@ -271,12 +282,21 @@ def step_kernel(plan, i, kind):
     """The kernel a plan step launches: block steps are told apart by their
     qubits (complex64, at least 128 groups: a window of consecutive qubits
     from 2 up runs k_fused_umma_tma<k,window>, qubits 0..k-1
-    k_fused_umma_tma<k,rows>; other complex64 blocks k_fused_umma<k>,
-    complex128 blocks the SIMT k_dense); other steps keep their kind."""
+    k_fused_umma_tma<k,rows>; other complex64 blocks k_fused_umma<k>;
+    complex128 k = 4, 5 blocks k_fused_c128<k,rows|window|gather> (a window
+    from qubit 1 up); other blocks the SIMT k_dense); other steps keep their
+    kind."""
     if kind != "block":
         return kind
     q = sorted(plan.step_qubits(i))
     k = len(q)
+    if plan.dtype == "c128" and k in (4, 5):
+        full = plan.n - k >= 7
+        if full and q == list(range(k)):
+            return "k_fused_c128<%d,rows>" % k
+        if full and q[0] >= 1 and q == list(range(q[0], q[0] + k)):
+            return "k_fused_c128<%d,window>" % k
+        return "k_fused_c128<%d,gather>" % k
     if plan.dtype == "c64" and k >= 4:
         full = plan.n - k >= 7
         if full and q[0] >= 2 and q == list(range(q[0], q[0] + k)):
@@ -447,6 +467,13 @@ def run_ours(args):
                 roof["traffic"] = BLOCK_C64_TRAFFIC_26Q[roof["kernel"]] * 2.0 ** (n - 26)
                 roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s "
                                           "at 26 qubits, scaled by 2^(n-26)" % roof["kernel"])
+        elif roof and roof["kernel"].startswith("k_fused_c128"):
+            roof["tensor"] = ("tcgen05.mma kind::f16 on exact 9-bit integer digits of the FP64 operands: 5 digits "
+                              "per value, 15 digit-pair products summed exactly per level in TMEM")
+            if roof["kernel"] in BLOCK_C128_TRAFFIC_26Q:
+                roof["traffic"] = BLOCK_C128_TRAFFIC_26Q[roof["kernel"]] * 2.0 ** (n - 26)
+                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s "
+                                          "at 26 qubits, scaled by 2^(n-26)" % roof["kernel"])
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
         # launches per step: one per plan step, k_set_one, and for complex128
@@ -454,6 +481,7 @@ def run_ours(args):
         extra = 1 + (2 if dt == "c128" and mode_name != "fused" else 0)
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
                        "plan": mode_name + (f" k={fq}" if mode_name == "fused" else ""),
+                       "arithmetic": ARITHMETIC[dt],
                        "passes": st["passes"], "gates": st["gates"], "hbm_bytes_per_step": st["hbm_bytes"],
                        "hbm_GBps": st["hbm_bytes"] / (ms / 1e3) / 1e9, "roofline": roof, "kernels": per_kind,
                        "clocks": clk.summary(), "bytes_per_amp": S,
@@ -471,7 +499,8 @@ def run_ours(args):
         infid = fidelity_vs_c128(torch, states["c64"].tensor, states["c128"].tensor)
     extras = {}
     if not args.no_extras:
-        extras["c64_plans_%dq" % n] = c64_plans(qs, torch, device, n, circuit, states.get("c128"))
+        extras["c64_plans_%dq" % n] = dtype_plans(qs, torch, device, n, circuit, "c64", states.get("c128"))
+        extras["c128_plans_%dq" % n] = dtype_plans(qs, torch, device, n, circuit, "c128", None)
         extras["reductions_%dq" % n] = reductions(qs, torch, states, n)
         if "c64" in states:
             extras["measure_%dq" % n] = measurement(qs, torch, states["c64"], n)
@@ -518,13 +547,14 @@ def run_ours(args):
 
 def plan_mode(qs, args, dt):
     """(name, plan mode, fuse_qubits) for a dtype: `auto` picks the fastest
-    measured plan, dense tensor-core blocks for complex64 and tiles for
-    complex128 (its blocks would run on the FP64 pipe)."""
+    measured plan, dense tensor-core blocks for both dtypes (complex128
+    blocks have at most 5 qubits)."""
     name = args.mode
     if name == "auto":
-        name = "fused" if dt == "c64" else "tiled"
+        name = "fused"
     mode = {"fused": qs.PLAN_FUSED, "tiled": qs.PLAN_TILED, "unfused": qs.PLAN_UNFUSED}[name]
-    return name, mode, (args.fuse_qubits if name == "fused" else 0)
+    fq = args.fuse_qubits if dt == "c64" else min(args.fuse_qubits, 5)
+    return name, mode, (fq if name == "fused" else 0)
 
 
 def fidelity_vs_c128(torch, t64, t128):
@@ -540,15 +570,18 @@ def fidelity_vs_c128(torch, t64, t128):
             "norm2_c64": na, "norm2_c128": nb}
 
 
-def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
-    """The complex64 circuit under each plan: tiles (SIMT, many gates per
-    pass) and dense 4-, 5- and 6-qubit blocks (tensor cores), with the
-    infidelity of each against the complex128 result when it is at hand."""
+def dtype_plans(qs, torch, device, n, circuit, dt, ref128, reps=2):
+    """The circuit in one dtype under each plan: tiles (SIMT, many gates per
+    pass) and dense 4-, 5- (and for complex64 6-) qubit blocks (tensor
+    cores), with the infidelity of each complex64 plan against the complex128
+    result when it is at hand."""
     out = {}
-    s = qs.State(n, "c64", device=device)
-    for name, mode, fq in (("tiled", qs.PLAN_TILED, 0), ("fused_k4", qs.PLAN_FUSED, 4), ("fused_k5", qs.PLAN_FUSED, 5),
-                           ("fused_k6", qs.PLAN_FUSED, 6)):
-        p = qs.Plan(circuit, n, "c64", mode=mode, fuse_qubits=fq)
+    s = qs.State(n, dt, device=device)
+    plans = [("tiled", qs.PLAN_TILED, 0), ("fused_k4", qs.PLAN_FUSED, 4), ("fused_k5", qs.PLAN_FUSED, 5)]
+    if dt == "c64":
+        plans.append(("fused_k6", qs.PLAN_FUSED, 6))
+    for name, mode, fq in plans:
+        p = qs.Plan(circuit, n, dt, mode=mode, fuse_qubits=fq)
         s.set_basis(0)
         s.run(p)
         torch.cuda.synchronize()
@@ -563,7 +596,7 @@ def c64_plans(qs, torch, device, n, circuit, ref128, reps=2):
             ms.append(e0.elapsed_time(e1))
         st = p.stats()
         r = {"ms": min(ms), "passes": st["passes"], "effective_GBps": st["metric_bytes"] / (min(ms) / 1e3) / 1e9}
-        if ref128 is not None:
+        if ref128 is not None and dt == "c64":
             r.update(fidelity_vs_c128(torch, s.tensor, ref128.tensor))
         out[name] = r
         del p

@@ -24,11 +24,14 @@
  *    next call that synchronises (qs_sync, reductions, copies).  The library
  *    never aborts the process.  qs_last_error() returns a thread-local
  *    description of the most recent failure.
- *  Numerics: QS_C64 computes in FP32; QS_C128 computes with at least 48-bit
+ *  Numerics: QS_C64 computes in FP32; QS_C128 computes with at least 47-bit
  *    significands (FP64, or double-float pairs of FP32 values where the FP64
- *    pipe would be the bottleneck).  Reductions (norm, inner product,
- *    expectation values) accumulate in at least FP64-equivalent precision for
- *    both dtypes and are deterministic (fixed reduction order).
+ *    pipe would be the bottleneck), except dense blocks of 4 or 5 qubits,
+ *    which put each group of amplitudes on a fixed-point grid of 43 bits
+ *    below the group's largest one (error about 2^-44 of it per block).
+ *    Reductions (norm, inner product, expectation values) accumulate in at
+ *    least FP64-equivalent precision for both dtypes and are deterministic
+ *    (fixed reduction order).
  */
 #ifndef QS_H
 #define QS_H
@@ -89,9 +92,10 @@ qs_status qs_set_stream(qs_state* st, void* stream);
 
 /* Wait for all work enqueued on the state's stream; reports any pending
  * asynchronous device error as QS_ECUDA, and QS_ETIMEOUT if a tensor-core
- * block kernel (dense k = 4, 5 blocks on complex64) gave up waiting for its
- * matrix unit since the last qs_sync (bounded wait of about 1 s; the state's
- * contents are then invalid). */
+ * block kernel (dense blocks of 4 to 6 qubits on complex64, 4 or 5 on
+ * complex128) gave up waiting for its matrix unit or a tile copy since the
+ * last qs_sync (bounded wait of about 1 s; the state's contents are then
+ * invalid). */
 qs_status qs_sync(qs_state* st);
 
 /* Device pointer and size of the amplitude array. */
@@ -127,7 +131,10 @@ qs_status qs_apply_diag(qs_state* st, const int* qubits, int k, const double* d)
 
 /* Dense k-qubit gate (1 <= k <= 6) on distinct qubits: for every base x with
  * the k bits clear, the 2^k amplitudes a[x | spread(r)] are multiplied by
- * the 2^k x 2^k matrix M (2^(2k+1) doubles, row-major, (re, im)). */
+ * the 2^k x 2^k matrix M (2^(2k+1) doubles, row-major, (re, im)).  On the
+ * tensor cores for k >= 4 (complex64) and k = 4, 5 (complex128: each group
+ * and M on fixed-point grids split into 9-bit integer digits, whose products
+ * the MMAs form exactly); M must have finite entries. */
 qs_status qs_apply_fused(qs_state* st, const int* qubits, int k, const double* M);
 
 /* Qubit permutation: out[pi(x)] = in[x] where pi moves bit j of x to bit
@@ -251,8 +258,11 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
 /* Plan options.  mode: QS_PLAN_UNFUSED applies every gate with its own pass
  * (one kernel per gate); QS_PLAN_TILED groups gates into shared-memory tile
  * passes; QS_PLAN_FUSED multiplies gates into dense blocks of at most
- * fuse_qubits qubits, each applied as one pass (complex64 blocks of 4 to 6
- * qubits run on the tensor cores, as qs_apply_fused).  tile_qubits: qubits
+ * fuse_qubits qubits, each applied as one pass on the tensor cores, as
+ * qs_apply_fused (complex64 blocks of 4 to 6 qubits; complex128 blocks of 4
+ * or 5, a fuse_qubits of 6 is taken as 5 there; blocks whose gates touch
+ * fewer qubits are widened with idle ones to a window of consecutive
+ * qubits where one exists).  tile_qubits: qubits
  * resident per tile pass (0 = library default
  * for the dtype; at most 14 for QS_C64, 13 for QS_C128); low_qubits: qubits
  * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);

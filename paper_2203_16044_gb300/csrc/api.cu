@@ -161,7 +161,9 @@ qs_status qs_sync(qs_state* s) {
   CHECK_STATE(s);
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "qs_sync");
-  return fused_tc_status();
+  const qs_status r64 = fused_tc_status();
+  const qs_status r128 = fused_c128_status();
+  return r64 != QS_OK ? r64 : r128;
 }
 
 qs_status qs_data(qs_state* s, void** dev_ptr, size_t* bytes) {

@@ -39,6 +39,7 @@
 #include <cuda_fp16.h>
 
 #include "kcommon.cuh"
+#include "umma.cuh"
 
 namespace qs {
 namespace {
@@ -65,52 +66,14 @@ struct FusedArgs {
 // ---------------------------------------------------------------------------
 // tcgen05 helpers
 // ---------------------------------------------------------------------------
-constexpr int kUT = 128;  // groups per tile = MMA M = TMEM lanes
 
 __device__ int g_umma_timeout;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor of a K-major operand without swizzle:
-// start address, lbo = byte distance between core matrices adjacent along
-// K, sbo = between core matrices adjacent along M (or N); bits 46-48 hold
-// the fixed value 0b001; base offset 0, swizzle mode 0.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
 // Instruction descriptor, kind::tf32: FP32 accumulator (bits 4-5 = 1), A and
 // B TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at 24.
 __host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* o) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 16; ++j) o[j] = __uint_as_float(r[j]);
-}
-// mbarrier phase wait with a limit of about 2^31 SM cycles; false on timeout.
-// The "memory" clobber keeps the compiler from sinking earlier loads (the
-// next tiles' prefetch) below the wait.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  const long long t0 = clock64();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
-  }
-}
-
 // Norm restore for a group whose input norm^2 is nin and output norm^2 nout:
 // the output is scaled by sqrt(nin / nout) = 1 + g.  g is formed as a small
 // number, g = d / (1 + sqrt(1 + d)) with d = (nin - nout) / nout, and applied
@@ -236,13 +199,6 @@ __device__ __forceinline__ void group_store(float2* __restrict__ a, u64 base, bo
 // A wait that gives up (about 1 s) sets g_umma_timeout, reported by qs_sync;
 // the CTA then stops, frees its TMEM and returns.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const unsigned* r) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
-}
 __device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
                                              uint32_t acc) {
   asm volatile(
@@ -432,19 +388,6 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
   hi = h2bits(h);
   lo = h2bits(__floats2half2_rn(a - hf.x, b - hf.y));
 }
-__device__ __forceinline__ void umma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc,
-                                            uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(bd), "r"(idesc), "r"(acc));
-}
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
-// FP16 (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at 24.
-__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // ---------------------------------------------------------------------------
 // Blocks on a window of consecutive qubits s .. s+k-1 with s >= 2 (full
 // tiles): k_fused_umma_tma.  An amplitude index is then hi 2^(s+k) + e 2^s
@@ -463,32 +406,6 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
 // 8-byte stores.  Shared memory: stage 64 KB + B 64 KB at k = 6.  Blocks on
 // qubits 0 .. k-1 take the same kernel with ROWS set (below).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          dst),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(map), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
-               "r"(y), "r"(src)
-               : "memory");
-}
-
 // ROWS = false: a window s .. s+k-1 (s >= 2), one 3-D box per tile, 8-byte
 // stores.  ROWS = true: the block is qubits 0 .. k-1, so a tile is 128
 // contiguous rows of 2^k amplitudes: 2^k / 16 boxes of 16 amplitudes x 128
@@ -696,20 +613,6 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
-}
-
-qs_status tmap_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled not available");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  *out = encode;
-  return QS_OK;
 }
 
 // The 2-D tensor map (e, group) of a state for a block on qubits 0 .. k-1:

@@ -577,6 +577,7 @@ static qs_status dense_impl(qs_state* s, const int* qubits, int k, const double*
 
 qs_status run_dense(qs_state* s, const int* qubits, int k, const double* M, int unitary) {
   if (s->dtype == QS_C64 && k >= 4) return run_dense_tc(s, qubits, k, M, unitary);
+  if (s->dtype == QS_C128 && (k == 4 || k == 5)) return run_dense_tc128(s, qubits, k, M);
   return s->dtype == QS_C64 ? dense_impl<float>(s, qubits, k, M) : dense_impl<double>(s, qubits, k, M);
 }
 

@@ -97,8 +97,11 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::TILE: return run_tile(s, p, st.tile_index, false);
     case qs_step::BLOCK: {
       const qs_block& b = p->blocks[st.tile_index];
-      if (b.tc)  // B uploaded with the plan's other blocks at the start of the run
-        return run_dense_tc_prepared(s, b.q_sorted, b.k, static_cast<const float*>(s->scratch) + b.b_off, 1);
+      if (b.tc) {  // B uploaded with the plan's other blocks at the start of the run
+        const float* bd = static_cast<const float*>(s->scratch) + b.b_off;
+        if (s->dtype == QS_C128) return run_dense_tc128_prepared(s, b.q_sorted, b.k, bd, b.f128);
+        return run_dense_tc_prepared(s, b.q_sorted, b.k, bd, 1);
+      }
       return run_dense(s, b.q, b.k, b.M.data(), 1);  // a product of unitary gates
     }
   }
@@ -301,7 +304,7 @@ std::vector<char> touched(const std::vector<const qs_gate_rec*>& gates, int n) {
   return used;
 }
 
-// Complex64 tensor-core blocks: the qubits a block runs on, given those its
+// Tensor-core blocks (both dtypes): the qubits a block runs on, given those its
 // gates touch.  Idle qubits cost nothing there (a block is one HBM pass
 // whatever its width), but the kernel depends on the set's shape: a window
 // of consecutive qubits starting at 2 or above (one TMA box per tile), or at
@@ -346,6 +349,9 @@ qs_status plan_fused(qs_plan* p) {
   const int n = p->n;
   int kmax = p->opts.fuse_qubits > 0 ? p->opts.fuse_qubits : 5;
   if (kmax < 2 || kmax > 6) return fail(QS_EINVAL, "qs_plan_build: fuse_qubits=%d outside [2, 6]", kmax);
+  // complex128 tensor-core blocks exist for k = 4, 5 (six would need 960
+  // tensor-memory columns)
+  if (p->dtype == QS_C128 && kmax > 5) kmax = 5;
   if (kmax > n) kmax = n;
   std::vector<const qs_gate_rec*> remaining;
   for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
@@ -354,7 +360,7 @@ qs_status plan_fused(qs_plan* p) {
     // consecutive qubits; the block takes the one that absorbs most gates,
     // for complex64 tensor-core blocks weighted by the kernel its qubit set
     // gets (a set that must gather per thread counts 0.7 per gate)
-    const bool tc = p->dtype == QS_C64 && kmax >= 4;
+    const bool tc = kmax >= 4;
     auto score = [&](const std::vector<char>& inS, int nS) {
       std::vector<const qs_gate_rec*> abs;
       const int taken = absorb_into(remaining, inS, nS, &abs, nullptr);
@@ -409,6 +415,14 @@ qs_status plan_fused(qs_plan* p) {
       b.tc = true;
       b.b_off = p->tc_B.size();
       p->tc_B.insert(p->tc_B.end(), B.begin(), B.end());
+    } else if (p->dtype == QS_C128 && (b.k == 4 || b.k == 5)) {
+      std::vector<uint16_t> dig;
+      qs_status r = tc128_prepare(b.q, b.k, b.M.data(), b.q_sorted, dig, &b.f128);
+      if (r != QS_OK) return r;
+      b.tc = true;
+      b.b_off = p->tc_B.size();  // a multiple of 4 floats: 16-byte aligned
+      p->tc_B.resize(b.b_off + dig.size() / 2);
+      std::memcpy(p->tc_B.data() + b.b_off, dig.data(), dig.size() * sizeof(uint16_t));
     }
     p->blocks.push_back(std::move(b));
     qs_step st{};

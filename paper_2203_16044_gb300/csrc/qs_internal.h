@@ -59,6 +59,13 @@ qs_status run_dense_tc(qs_state* s, const int* qubits, int k, const double* M, i
 qs_status tc_prepare(const int* qubits, int k, const double* M, int* q_sorted, std::vector<float>& B);
 qs_status run_dense_tc_prepared(qs_state* s, const int* q_sorted, int k, const float* Bdev, int unitary);
 qs_status fused_tc_status();  // QS_ETIMEOUT if a tensor-core wait gave up since the last call
+// complex128 dense block, k = 4, 5, on the tensor cores (fused_c128.cu): FP64
+// operands split into five 9-bit integer digits, exact FP16 digit products
+qs_status run_dense_tc128(qs_state* s, const int* qubits, int k, const double* M);
+qs_status tc128_prepare(const int* qubits, int k, const double* M, int* q_sorted, std::vector<uint16_t>& dig,
+                        int* F);
+qs_status run_dense_tc128_prepared(qs_state* s, const int* q_sorted, int k, const void* Bdig, int F);
+qs_status fused_c128_status();
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);
 qs_status run_set_basis(qs_state* s, u64 x);
@@ -101,11 +108,14 @@ struct qs_block {
   int k;
   int q[6];
   std::vector<double> M;  // row-major (re, im)
-  // complex64 tensor-core blocks (k >= 4): qubits ascending and the offset of
-  // the block's B in the plan's tc_B (prepared once, uploaded once per run)
+  // tensor-core blocks (k >= 4): qubits ascending and the offset of the
+  // block's B in the plan's tc_B (prepared once, uploaded once per run):
+  // complex64 FP32 values, complex128 FP16 digit matrices (two per float
+  // slot) on the grid 2^(f128 - 43)
   bool tc = false;
   int q_sorted[6];
   size_t b_off = 0;
+  int f128 = 0;
 };
 
 struct qs_tile_pass;    // defined in tile.cu

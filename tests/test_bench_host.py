@@ -33,9 +33,28 @@ def test_step_kernel_labels(qs):
     # a brick plan has windows from qubit 2 up and a block on the lowest
     # qubits
     assert {"k_fused_umma_tma,window>", "k_fused_umma_tma,rows>"} <= seen
-    p128 = qs.Plan(qs.Circuit(W.brick(8, 4, 3)), 8, "c128", mode=qs.PLAN_FUSED, fuse_qubits=4)
-    labs = {bench.step_kernel(p128, i, k) for i, (k, _) in enumerate(p128.step_info())}
-    assert all(lab.startswith("k_dense<") for lab in labs if lab.startswith("k_"))
+    # complex128: 4- and 5-qubit blocks run on k_fused_c128 (rows, windows
+    # from qubit 1 up, gathered sets; fewer than 128 groups always gather),
+    # 6-qubit requests are narrowed to 5, smaller blocks stay on k_dense
+    for n, fq in ((14, 5), (14, 6), (13, 4), (8, 4)):
+        p128 = qs.Plan(qs.Circuit(W.brick(n, 12, 3)), n, "c128", mode=qs.PLAN_FUSED, fuse_qubits=fq)
+        for i, (kind, _) in enumerate(p128.step_info()):
+            if kind != "block":
+                continue
+            q = sorted(p128.step_qubits(i))
+            k = len(q)
+            assert k <= 5
+            lab = bench.step_kernel(p128, i, kind)
+            if k < 4:
+                assert lab == "k_dense<%d>" % k
+            elif n - k < 7:
+                assert lab == "k_fused_c128<%d,gather>" % k
+            elif q == list(range(k)):
+                assert lab == "k_fused_c128<%d,rows>" % k
+            elif q[0] >= 1 and q == list(range(q[0], q[0] + k)):
+                assert lab == "k_fused_c128<%d,window>" % k
+            else:
+                assert lab == "k_fused_c128<%d,gather>" % k
 
 
 def test_planner_widens_complex64_blocks_to_windows(qs):

@@ -1,8 +1,9 @@
 """GPU parity at the benchmark's full sizes.
 
 * 28 qubits, complex128, plain per-gate kernels (the per-gate-class
-  configuration): the brick circuit (depth 40) and the QFT of a seeded basis
-  state, compared with the FP64 oracle in full, max |error| <= 1e-12.
+  configuration) and tensor-core block plans (k = 5, 4): the brick circuit
+  (depth 40) and the QFT of a seeded basis state, compared with the FP64
+  oracle in full, max |error| <= 1e-12.
 * 26 qubits, complex64 fused into 4-, 5- and 6-qubit tensor-core blocks, depth
   40: infidelity against the FP64 oracle <= 1e-5 (stated and normalised
   forms), norm within 1e-6.
@@ -52,15 +53,20 @@ def gpu_run(qs, n, circ, dtype, mode, fuse=0, x0=0):
 
 
 def test_c128_brick_and_qft_28q_vs_oracle_in_full(qs):
+    # the plain per-gate kernels and the complex128 tensor-core block plans
+    # (5- and 4-qubit blocks, FP64 operands split into integer digits)
     n = 28
     for circ, x0 in ((W.brick(n, 40, 3), 0), (W.qft(n), W.basis_index(n, 4))):
         want = oracle.zero_state(n, x0)
         oracle.run_circuit(want, circ)
-        s = gpu_run(qs, n, circ, "c128", qs.PLAN_UNFUSED, x0=x0)
-        got = s.to_numpy()
-        del s
-        assert max_abs_diff(got, want) <= C128_TOL
-        del got, want
+        for mode, fuse in ((qs.PLAN_UNFUSED, 0), (qs.PLAN_FUSED, 5), (qs.PLAN_FUSED, 4)):
+            s = gpu_run(qs, n, circ, "c128", mode, fuse=fuse, x0=x0)
+            got = s.to_numpy()
+            del s
+            err = max_abs_diff(got, want)
+            assert err <= C128_TOL, (mode, fuse, err)
+            del got
+        del want
 
 
 @pytest.mark.parametrize("k", [4, 5, 6])

@@ -337,3 +337,71 @@ def test_apply_fused_c64_dynamic_range(qs, k, mode):
     err = np.abs(s.to_numpy().astype(np.complex128) - want)
     gn = _group_norms(v, qsel)
     assert np.all(err <= 2.0 ** -20 * gn), float(np.max(err / gn))
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n,qubits", [
+    (9, None),            # fewer than 128 groups: gathered, a partial tile
+    (14, "gathered"),     # a set spanning more than k qubits: per-thread gathers
+    (15, "low"),          # qubits 0 .. k-1: 2-D TMA boxes in, TMA stores out
+    (11, "low"),          # ... exactly one or a few tiles
+    (14, "window1"),      # a window from qubit 1: one 3-D TMA box per tile
+    (14, "window2"),
+    (14, "window3"),
+    (15, "window6"),
+    (17, "window8"),      # ... from 8 (runs of 128 rows)
+    (16, "high"),         # the block on the highest qubits
+])
+def test_apply_fused_c128_tensor_core_access_modes(qs, k, n, qubits):
+    # complex128 k = 4, 5 blocks run on tcgen05 with FP64 operands split into
+    # 9-bit integer digits: every output against the oracle within 1e-12 and
+    # within 2^-36 of its group's norm
+    if qubits is None:
+        qsel = [1, 3, 4, 6, 8][:k]
+    elif qubits == "gathered":
+        qsel = [2, 9, 5, 12, 1][:k]
+    elif qubits == "low":
+        qsel = [q for q in [2, 0, 3, 1, 4] if q < k]
+    elif qubits.startswith("window"):
+        s0 = int(qubits[6:])
+        qsel = [s0 + i for i in [3, 0, 1, 4, 2] if i < k]
+    else:
+        qsel = list(range(n - 1, n - 1 - k, -1))
+    psi = W.random_state(n, 7900 + n + k)
+    M = W.random_unitary(1 << k, 7910 + k)
+    s = gpu_state(qs, psi, "c128")
+    s.apply_fused(qsel, M)
+    want = psi.copy()
+    oracle.apply_dense(want, qsel, M)
+    err = np.abs(s.to_numpy() - want)
+    assert np.max(err) <= C128_TOL, float(np.max(err))
+    gn = _group_norms(psi, qsel)
+    assert np.all(err <= 2.0 ** -36 * gn), float(np.max(err / gn))
+
+
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("mode", ["window", "rows", "gathered"])
+def test_apply_fused_c128_dynamic_range_and_non_unitary(qs, k, mode):
+    # groups spanning 2^-40 inside and 2^-60 across the state, some groups
+    # entirely zero, and a non-unitary matrix with entries up to ~4: the
+    # per-group fixed-point grid keeps every output within 2^-36 of its
+    # group's norm times max |M|
+    n = 14
+    qsel = _block_sets(k, mode)
+    psi = W.random_state(n, 7950 + k)
+    x = np.arange(psi.size, dtype=np.int64)
+    r = np.zeros(psi.size, dtype=np.int64)
+    for i, q in enumerate(qsel):
+        r |= ((x >> q) & 1) << i
+    grp = x & ~sum(1 << q for q in qsel)
+    psi = psi * 2.0 ** (-40.0 * r / ((1 << k) - 1)) * 2.0 ** (-((grp * 7) % 61).astype(np.float64))
+    psi[(grp % 13) == 0] = 0
+    M = W.random_matrix(1 << k, 7960 + k) * 4.0
+    s = gpu_state(qs, psi, "c128")
+    s.apply_fused(qsel, M)
+    want = psi.copy()
+    oracle.apply_dense(want, qsel, M)
+    err = np.abs(s.to_numpy() - want)
+    gn = _group_norms(psi, qsel)
+    assert np.all(err <= 2.0 ** -36 * gn * np.max(np.abs(M))), float(np.max(err / np.maximum(gn, 1e-300)))
+    assert np.all(s.to_numpy()[gn == 0] == 0)
