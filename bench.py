@@ -606,9 +606,13 @@ def dtype_plans(qs, torch, device, n, circuit, dt, ref128, reps=2):
 
 def planner_policies(qs, torch, device, n):
     """The paper's own workloads at n qubits, complex64, under each plan
-    policy: per-gate passes, tile passes (low qubits plus gathered high
-    ones, many gates per pass), dense 6-qubit tensor-core blocks.  Reports
-    HBM passes per logical gate and the time of one run (after one warm-up)."""
+    policy: per-gate passes; tile passes over the lowest qubits with a swap
+    inserted for every remote target (swap insertion, §III-D) or one fused
+    bit-pair exchange per routing point (fused-permutation insertion,
+    §III-D, Listing 1); tile passes that gather their high qubits in place
+    (tile-gather); dense 6-qubit tensor-core blocks.  Reports HBM passes per
+    logical gate (and how many are exchanges, with their bytes) and the time
+    of one run (after one warm-up)."""
     wls = {"qsb_sets10": W.qsb(n, 22, sets=10), "hadamard_x11": W.hadamard_bench(n),
            "qv_like_d10": W.qv_like(n, 10, 13)}
     out = {}
@@ -617,10 +621,12 @@ def planner_policies(qs, torch, device, n):
     for wname, circ in wls.items():
         c = qs.Circuit(circ)
         row = {"gates": len(circ)}
-        for pname, mode, fq in (("unfused", qs.PLAN_UNFUSED, 0), ("tiled", qs.PLAN_TILED, 0),
+        for pname, mode, fq in (("unfused", qs.PLAN_UNFUSED, 0), ("swap_insertion", qs.PLAN_SWAP, 0),
+                                ("fused_permutation", qs.PLAN_PERMUTE, 0), ("tile_gather", qs.PLAN_TILED, 0),
                                 ("fused_k6", qs.PLAN_FUSED, 6)):
             p = qs.Plan(c, n, "c64", mode=mode, fuse_qubits=fq)
             st = p.stats()
+            ex = [b for k, b in p.step_info() if k == "swap"]
             s.set_basis(0)
             s.run(p)
             s.set_basis(0)
@@ -631,6 +637,7 @@ def planner_policies(qs, torch, device, n):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             row[pname] = {"passes": st["passes"], "passes_per_gate": st["passes"] / len(circ), "ms": ms,
+                          "exchange_passes": len(ex), "exchange_bytes": sum(ex),
                           "effective_GBps": st["metric_bytes"] / (ms / 1e3) / 1e9,
                           "hbm_GBps_algorithmic": st["hbm_bytes"] / (ms / 1e3) / 1e9}
             del p

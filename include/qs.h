@@ -262,7 +262,14 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * qs_apply_fused (complex64 blocks of 4 to 6 qubits; complex128 blocks of 4
  * or 5, a fuse_qubits of 6 is taken as 5 there; blocks whose gates touch
  * fewer qubits are widened with idle ones to a window of consecutive
- * qubits where one exists).  tile_qubits: qubits
+ * qubits where one exists).  QS_PLAN_SWAP and QS_PLAN_PERMUTE apply the
+ * gates in tile passes over the tile_qubits lowest physical qubits only and
+ * move every other target there first, by in-place bit-pair exchange
+ * passes (§III-D): QS_PLAN_SWAP inserts one exchange of one pair (a swap)
+ * per target that is not local; QS_PLAN_PERMUTE one exchange of up to
+ * tile_qubits pairs (a fused swap) per routing point, for every target the
+ * coming gates need; SWAP gates of the circuit only relabel qubits; the
+ * state ends in logical order (at most two more exchange passes).  tile_qubits: qubits
  * resident per tile pass (0 = library default
  * for the dtype; at most 14 for QS_C64, 13 for QS_C128); low_qubits: qubits
  * 0..low_qubits-1 kept in every tile for coalesced access (0 = default);
@@ -272,7 +279,7 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * 0 = a stage whose gates all act within its three slot qubits may be fused
  * into one 8x8 matrix when the planner estimates that cheaper (complex64,
  * three slots), -1 = never.  Every field must be zero or valid. */
-enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1, QS_PLAN_FUSED = 2 };
+enum { QS_PLAN_UNFUSED = 0, QS_PLAN_TILED = 1, QS_PLAN_FUSED = 2, QS_PLAN_SWAP = 3, QS_PLAN_PERMUTE = 4 };
 typedef struct {
   int mode;
   int tile_qubits;
@@ -310,13 +317,17 @@ qs_status qs_run_plan(qs_state* st, qs_plan* p);
 enum { QS_STEP_1Q = 0, QS_STEP_CTRL = 1, QS_STEP_DIAG = 2, QS_STEP_SWAP = 3, QS_STEP_TILE = 4, QS_STEP_BLOCK = 5 };
 
 /* Kind and algorithmic HBM bytes (read + write of the amplitudes it
- * touches) of plan step i, 0 <= i < passes. */
+ * touches) of plan step i, 0 <= i < passes.  A swap or bit-pair exchange
+ * pass (QS_STEP_SWAP) of s pairs moves the 2^n (1 - 2^-s) amplitudes whose
+ * index changes. */
 qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_bytes);
 
 /* The qubits plan step i acts on, in the order its matrix uses them (for a
  * dense block, qubit j is bit j of the block matrix's row index; for a gate,
- * controls first, the target last): up to `cap` ints written to `qubits`,
- * their number to *count.  Tile passes report 0 qubits.  QS_EINVAL if the
+ * controls first, the target last; for a bit-pair exchange pass of
+ * QS_PLAN_SWAP / QS_PLAN_PERMUTE, its pairs a0, b0, a1, b1, ... of physical
+ * qubit positions): up to `cap` ints written to `qubits`, their number to
+ * *count.  Tile passes report 0 qubits.  QS_EINVAL if the
  * step has more than `cap` qubits (nothing written) or i is out of range. */
 qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int* count);
 

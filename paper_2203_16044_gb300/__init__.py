@@ -30,7 +30,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 C64, C128 = 0, 1
-PLAN_UNFUSED, PLAN_TILED, PLAN_FUSED = 0, 1, 2
+PLAN_UNFUSED, PLAN_TILED, PLAN_FUSED, PLAN_SWAP, PLAN_PERMUTE = 0, 1, 2, 3, 4
 
 GATE_KIND = {"H": 0, "X": 1, "Y": 2, "Z": 3, "S": 4, "T": 5, "RX": 6, "RY": 7, "RZ": 8, "P": 9,
              "U3": 10, "CNOT": 16, "CZ": 17, "CP": 18, "SWAP": 19}
@@ -413,10 +413,11 @@ class Plan:
 
     def step_qubits(self, i: int) -> list:
         """The qubits of plan step i (block: bit j of its matrix index is
-        qubit j; gate: controls, then target; tile pass: [])."""
-        q = (ctypes.c_int * 8)()
+        qubit j; gate: controls, then target; bit-pair exchange pass: its
+        pairs a0, b0, a1, b1, ...; tile pass: [])."""
+        q = (ctypes.c_int * 34)()
         cnt = ctypes.c_int()
-        _check(_lib.qs_plan_step_qubits(self._h, int(i), q, 8, ctypes.byref(cnt)), "qs_plan_step_qubits")
+        _check(_lib.qs_plan_step_qubits(self._h, int(i), q, 34, ctypes.byref(cnt)), "qs_plan_step_qubits")
         return list(q[:cnt.value])
 
     def step_matrix(self, i: int) -> np.ndarray:

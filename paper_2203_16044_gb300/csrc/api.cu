@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "qs_internal.h"
+#include "planner.h"
 
 namespace qs {
 
@@ -258,34 +259,14 @@ qs_status qs_permute_qubits(qs_state* s, const int* perm) {
       return fail(QS_EINVAL, "qs_permute_qubits: not a permutation of 0..%d", n - 1);
     seen[perm[j]] = 1;
   }
-  // Split every cycle c_0 -> c_1 -> ... -> c_{m-1} (perm[c_i] = c_{i+1}) into
-  // two reflections: r1(i) = -i, r2(i) = 1 - i (mod m), with r2 o r1 = +1.
-  std::vector<int> a1, b1, a2, b2;
-  std::vector<int> done(n, 0);
-  for (int j = 0; j < n; ++j) {
-    if (done[j]) continue;
-    std::vector<int> cyc;
-    for (int c = j; !done[c]; c = perm[c]) {
-      done[c] = 1;
-      cyc.push_back(c);
+  // at most two passes of disjoint bit-pair exchanges (17 pairs per pass)
+  for (const auto& pass : permutation_passes(std::vector<int>(perm, perm + n), 17)) {
+    int a[17], b[17];
+    for (size_t i = 0; i < pass.size(); ++i) {
+      a[i] = pass[i].first;
+      b[i] = pass[i].second;
     }
-    const int m = (int)cyc.size();
-    for (int i = 0; i < m; ++i) {
-      const int i1 = (m - i) % m;            // r1 partner
-      if (i < i1) { a1.push_back(cyc[i]); b1.push_back(cyc[i1]); }
-      const int i2 = ((1 - i) % m + m) % m;  // r2 partner
-      if (i < i2) { a2.push_back(cyc[i]); b2.push_back(cyc[i2]); }
-    }
-  }
-  // the bit-field kernel takes at most 17 pairs per pass
-  for (size_t o = 0; o < a1.size(); o += 17) {
-    const int cnt = (int)std::min<size_t>(17, a1.size() - o);
-    qs_status st = run_bitswap(s, a1.data() + o, b1.data() + o, cnt);
-    if (st != QS_OK) return st;
-  }
-  for (size_t o = 0; o < a2.size(); o += 17) {
-    const int cnt = (int)std::min<size_t>(17, a2.size() - o);
-    qs_status st = run_bitswap(s, a2.data() + o, b2.data() + o, cnt);
+    qs_status st = run_bitswap(s, a, b, (int)pass.size());
     if (st != QS_OK) return st;
   }
   return QS_OK;

@@ -41,6 +41,9 @@ double step_bytes(const qs_step& st, int n, int S) {
     case qs_step::GATE_SWAP: return N * S;  // half the amplitudes move
     case qs_step::TILE: return 2.0 * N * S;
     case qs_step::BLOCK: return 2.0 * N * S;
+    // s disjoint pairs: an amplitude moves unless every pair's two bits
+    // agree, a fraction 1 - 2^-s (the fused-swap traffic of §III-D)
+    case qs_step::EXCHANGE: return 2.0 * N * S * (1.0 - std::ldexp(1.0, -st.nq));
   }
   return 0.0;
 }
@@ -88,6 +91,16 @@ qs_step unfused_step(const qs_gate_rec& g) {
   return st;
 }
 
+qs_status run_exchange(qs_state* s, const std::vector<std::pair<int, int>>& pairs) {
+  int a[17], b[17];
+  const int np = (int)pairs.size();
+  for (int i = 0; i < np; ++i) {
+    a[i] = pairs[i].first;
+    b[i] = pairs[i].second;
+  }
+  return run_bitswap(s, a, b, np);
+}
+
 qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
   switch (st.type) {
     case qs_step::GATE_1Q: return run_1q(s, st.q[0], st.m);
@@ -104,6 +117,7 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
       }
       return run_dense(s, b.q, b.k, b.M.data(), 1);  // a product of unitary gates
     }
+    case qs_step::EXCHANGE: return run_exchange(s, p->exchanges[st.tile_index]);
   }
   return fail(QS_EINVAL, "bad plan step");
 }
@@ -117,6 +131,7 @@ qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
     case qs_step::TILE: return run_tile(s, p, st.tile_index, true);
     case qs_step::BLOCK: return fail(QS_EINVAL, "dense blocks do not run in double-float storage");
+    case qs_step::EXCHANGE: return run_exchange(s, p->exchanges[st.tile_index]);  // moves whole amplitudes
   }
   return fail(QS_EINVAL, "bad plan step");
 }
@@ -522,6 +537,8 @@ qs_status qs_plan_build(const qs_circuit* c, int n, qs_dtype dtype, const qs_pla
     st = plan_tiled(p);
   } else if (p->opts.mode == QS_PLAN_FUSED) {
     st = plan_fused(p);
+  } else if (p->opts.mode == QS_PLAN_SWAP || p->opts.mode == QS_PLAN_PERMUTE) {
+    st = plan_routed(p, p->opts.mode == QS_PLAN_PERMUTE);
   } else {
     st = fail(QS_EINVAL, "qs_plan_build: unknown mode %d", p->opts.mode);
   }
@@ -572,6 +589,7 @@ qs_status qs_plan_step_info(const qs_plan* p, int i, int* kind, double* hbm_byte
     case qs_step::GATE_SWAP: *kind = QS_STEP_SWAP; break;
     case qs_step::TILE: *kind = QS_STEP_TILE; break;
     case qs_step::BLOCK: *kind = QS_STEP_BLOCK; break;
+    case qs_step::EXCHANGE: *kind = QS_STEP_SWAP; break;
   }
   *hbm_bytes = step_bytes(st, p->n, amp_bytes(p->dtype));
   return QS_OK;
@@ -583,8 +601,17 @@ qs_status qs_plan_step_qubits(const qs_plan* p, int i, int* qubits, int cap, int
   const qs_step& st = p->steps[i];
   const int* q = st.q;
   int nq = st.nq;
+  int pq[34];
   if (st.type == qs_step::TILE) {
     nq = 0;
+  } else if (st.type == qs_step::EXCHANGE) {
+    const auto& pr = p->exchanges[st.tile_index];
+    nq = 2 * (int)pr.size();
+    for (size_t j = 0; j < pr.size(); ++j) {
+      pq[2 * j] = pr[j].first;
+      pq[2 * j + 1] = pr[j].second;
+    }
+    q = pq;
   } else if (st.type == qs_step::BLOCK) {
     const qs_block& b = p->blocks[st.tile_index];
     q = b.q;

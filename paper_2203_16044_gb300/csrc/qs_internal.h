@@ -96,11 +96,12 @@ struct qs_circuit {
 
 // One step of a compiled plan.
 struct qs_step {
-  enum Type { GATE_1Q, GATE_CTRL, GATE_DIAG, GATE_SWAP, TILE, BLOCK } type;
+  enum Type { GATE_1Q, GATE_CTRL, GATE_DIAG, GATE_SWAP, TILE, BLOCK, EXCHANGE } type;
   int q[4];
   int nq;
   double m[32];         // matrix / diagonal (FP64)
-  int tile_index;       // TILE: index into plan->tiles; BLOCK: into plan->blocks
+  int tile_index;       // TILE: index into plan->tiles; BLOCK: into plan->blocks;
+                        // EXCHANGE: into plan->exchanges
 };
 
 // A dense block of a QS_PLAN_FUSED plan: 2^k x 2^k complex matrix over qubits.
@@ -131,6 +132,8 @@ struct qs_plan {
   std::vector<qs_tile_pass*> tiles;
   std::vector<qs_block> blocks;
   std::vector<float> tc_B;  // all tensor-core blocks' B, concatenated
+  // EXCHANGE steps: disjoint bit pairs (a_i, b_i) exchanged in one pass
+  std::vector<std::vector<std::pair<int, int>>> exchanges;
 };
 
 namespace qs {

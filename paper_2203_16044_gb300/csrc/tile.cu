@@ -381,6 +381,8 @@ qs_status launch_tile(qs_state* s, const TileArgs& A, size_t smem, unsigned grid
 
 }  // namespace
 
+int tile_targets(const qs_gate_rec& g, int* q) { return tile_needs(g, q); }
+
 int tile_stage_count(const qs_plan* p, int* dense) {
   int n = 0, d = 0;
   for (const qs_tile_pass* t : p->tiles) {
@@ -391,12 +393,9 @@ int tile_stage_count(const qs_plan* p, int* dense) {
   return n;
 }
 
-qs_status plan_tiled(qs_plan* p) {
+// Tile options of a plan (validated; defaults filled in); n >= 4.
+qs_status tile_options(qs_plan* p, int* m_out, int* L_out, int* G_out) {
   const int n = p->n;
-  if (n < 4) {  // a tile needs its slot qubits: per-gate passes instead
-    for (const qs_gate_rec& g : p->gates) p->steps.push_back(unfused_step(g));
-    return QS_OK;
-  }
   const qs_plan_opts& o = p->opts;
   int m = o.tile_qubits > 0 ? o.tile_qubits : default_tile_qubits(p->dtype);
   int L = o.low_qubits > 0 ? o.low_qubits : default_low_qubits(p->dtype);
@@ -410,15 +409,25 @@ qs_status plan_tiled(qs_plan* p) {
   if (o.dense != 0 && o.dense != -1) return fail(QS_EINVAL, "qs_plan_build: dense must be 0 or -1");
   if (m > n) m = n;
   if (L > m) L = m;
-  const int r = m - L;
-  if (r > kMaxR) return fail(QS_EINVAL, "qs_plan_build: at most %d high tile qubits", kMaxR);
+  if (m - L > kMaxR) return fail(QS_EINVAL, "qs_plan_build: at most %d high tile qubits", kMaxR);
   p->opts.slot_qubits = G;
   // complex128 with four slots holds 64 floats per group: one group per
   // thread (two would spill registers)
   p->opts.groups_per_thread = (p->dtype == QS_C128 && G == 4) ? 1 : gpt;
+  *m_out = m;
+  *L_out = L;
+  *G_out = G;
+  return QS_OK;
+}
 
-  std::vector<const qs_gate_rec*> remaining;
-  for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
+// Tile passes for a gate list, appended to p->steps: each pass keeps the L
+// lowest qubits and up to m - L chosen higher ones resident and absorbs, in
+// order, every gate whose targets it holds (a gate left out blocks its
+// qubits for the rest of the scan).
+qs_status tile_gates(qs_plan* p, std::vector<const qs_gate_rec*> remaining, int m, int L, int G) {
+  const int n = p->n;
+  const int r = m - L;
+  const bool dense = p->opts.dense >= 0;
   while (!remaining.empty()) {
     std::vector<char> inT(n, 0), blocked(n, 0);
     for (int q = 0; q < L; ++q) inT[q] = 1;
@@ -456,7 +465,7 @@ qs_status plan_tiled(qs_plan* p) {
     tp->m = m;
     tp->G = G;
     for (int i = 0; i < r; ++i) tp->H[i] = H[i];
-    build_pass_ops(*tp, absorbed, p->dtype, n, o.dense >= 0);
+    build_pass_ops(*tp, absorbed, p->dtype, n, dense);
     if ((int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
       // too many stages for one parameter block: split the pass's gates
       delete tp;
@@ -468,7 +477,7 @@ qs_status plan_tiled(qs_plan* p) {
       tp = new qs_tile_pass();
       tp->L = L; tp->r = r; tp->m = m; tp->G = G;
       for (int i = 0; i < r; ++i) tp->H[i] = H[i];
-      build_pass_ops(*tp, first, p->dtype, n, o.dense >= 0);
+      build_pass_ops(*tp, first, p->dtype, n, dense);
       if (half == 0 || (int)tp->ops.size() > kMaxOps || (int)tp->stages.size() > kMaxStages) {
         delete tp;
         return fail(QS_EUNSUPPORTED, "qs_plan_build: tile pass too large");
@@ -483,6 +492,19 @@ qs_status plan_tiled(qs_plan* p) {
     remaining.swap(rest);
   }
   return QS_OK;
+}
+
+qs_status plan_tiled(qs_plan* p) {
+  if (p->n < 4) {  // a tile needs its slot qubits: per-gate passes instead
+    for (const qs_gate_rec& g : p->gates) p->steps.push_back(unfused_step(g));
+    return QS_OK;
+  }
+  int m = 0, L = 0, G = 0;
+  qs_status st = tile_options(p, &m, &L, &G);
+  if (st != QS_OK) return st;
+  std::vector<const qs_gate_rec*> all;
+  for (const qs_gate_rec& g : p->gates) all.push_back(&g);
+  return tile_gates(p, all, m, L, G);
 }
 
 qs_status run_tile(qs_state* s, qs_plan* p, int tile_index, bool dfl) {

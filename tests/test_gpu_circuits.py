@@ -138,3 +138,35 @@ def test_c64_tensor_core_blocks_vs_oracle_22q(qs, k):
     s.run(p)
     got = s.to_numpy()
     check_c64(got, want)
+
+
+ROUTED = [
+    ("qsb14", 14, lambda: W.qsb(14, 41, sets=2), 0),
+    ("brick15_d12", 15, lambda: W.brick(15, 12, 42), 0),
+    ("qv13_d6", 13, lambda: W.qv_like(13, 6, 43), 0),
+    ("hadamard11x12", 12, lambda: W.hadamard_bench(12), 9),
+    ("qft13", 13, lambda: W.qft(13), W.basis_index(13, 44)),
+    ("ghz16", 16, lambda: W.ghz(16), 0),
+]
+
+
+@pytest.mark.parametrize("name,n,make,x0", ROUTED, ids=[r[0] for r in ROUTED])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("mode", [3, 4], ids=["swap", "permute"])
+@pytest.mark.parametrize("m", [6, 9])
+def test_routed_plans_match_oracle(qs, name, n, make, x0, dtype, mode, m):
+    # swap insertion and fused-permutation insertion (§III-D): tile passes
+    # over the m lowest physical qubits, bit-pair exchange passes bringing
+    # the other targets in, the state back in logical order at the end
+    circ = make()
+    want = oracle_state(n, circ, x0)
+    s = qs.State(n, dtype)
+    s.set_basis(x0)
+    p = qs.Plan(qs.Circuit(circ), n, dtype, mode=mode, tile_qubits=m)
+    s.run(p)
+    got = s.to_numpy()
+    assert any(k == "swap" for k, _ in p.step_info())
+    if dtype == "c128":
+        assert np.max(np.abs(got - want)) <= C128_TOL
+    else:
+        check_c64(got, want, gates=len(circ))

@@ -68,3 +68,73 @@ def test_step_matrix_errors(qs):
     p = qs.Plan(qs.Circuit(W.brick(6, 2, 1)), 6, "c64", mode=qs.PLAN_FUSED, fuse_qubits=4)
     with pytest.raises(qs.QSError):
         p.step_matrix(p.stats()["passes"])
+
+
+ROUTED = [("qsb", 14, lambda: W.qsb(14, 3, sets=2)), ("brick", 15, lambda: W.brick(15, 8, 4)),
+          ("qv", 14, lambda: W.qv_like(14, 4, 5)), ("hadamard", 13, lambda: W.hadamard_bench(13))]
+
+
+def _compose_exchanges(p, n):
+    # where each physical bit position ends up after all exchange passes
+    pos = list(range(n))
+    passes = []
+    for i, (kind, b) in enumerate(p.step_info()):
+        if kind != "swap":
+            continue
+        q = p.step_qubits(i)
+        pairs = list(zip(q[0::2], q[1::2]))
+        flat = [x for pr in pairs for x in pr]
+        assert len(set(flat)) == len(flat), "pairs of one pass must be disjoint"
+        assert all(0 <= x < n for x in flat)
+        s = len(pairs)
+        N = 2.0 ** n
+        assert b == pytest.approx(2 * N * 8 * (1 - 2.0 ** -s))  # complex64 plans here
+        passes.append(pairs)
+        for a_, b_ in pairs:
+            pos[a_], pos[b_] = pos[b_], pos[a_]
+    return pos, passes
+
+
+@pytest.mark.parametrize("name,n,make", ROUTED, ids=[r[0] for r in ROUTED])
+@pytest.mark.parametrize("mode", ["swap", "permute"])
+def test_routed_plans_end_in_logical_order(qs, name, n, make, mode):
+    # the swap-insertion and fused-permutation policies (§III-D): every
+    # exchange pass has disjoint pairs and the fused-swap traffic
+    # 2 N S (1 - 2^-s); without SWAP gates in the circuit the passes compose
+    # to the identity (the state ends in logical order); the tile passes
+    # hold only the tile_qubits lowest qubits
+    circ = make()
+    m = 6
+    md = qs.PLAN_SWAP if mode == "swap" else qs.PLAN_PERMUTE
+    p = qs.Plan(qs.Circuit(circ), n, "c64", mode=md, tile_qubits=m)
+    pos, passes = _compose_exchanges(p, n)
+    assert pos == list(range(n))
+    assert passes, "a circuit on more than the tile's qubits needs exchanges"
+    if mode == "swap":
+        # one pair per pass except the final return to logical order
+        assert sum(len(x) == 1 for x in passes) >= len(passes) - 2
+    assert p.stats()["gates"] == len(circ)
+
+
+def test_fused_permutation_moves_less_than_swaps(qs):
+    # on the QSB circuit the fused swaps need fewer exchange passes and fewer
+    # bytes than one swap per remote target (§III-D)
+    n, m = 16, 8
+    circ = W.qsb(n, 9, sets=3)
+    res = {}
+    for mode, md in (("swap", qs.PLAN_SWAP), ("permute", qs.PLAN_PERMUTE)):
+        p = qs.Plan(qs.Circuit(circ), n, "c64", mode=md, tile_qubits=m)
+        ex = [b for k, b in p.step_info() if k == "swap"]
+        res[mode] = (len(ex), sum(ex), p.stats()["passes"])
+    assert res["permute"][0] < res["swap"][0]
+    assert res["permute"][1] < res["swap"][1]
+    assert res["permute"][2] < res["swap"][2]
+
+
+def test_routed_qft_swaps_are_relabellings(qs):
+    # SWAP gates of the circuit cost no pass: the exchanges compose to the
+    # bit reversal that the QFT's final swaps perform
+    n = 12
+    p = qs.Plan(qs.Circuit(W.qft(n)), n, "c64", mode=qs.PLAN_PERMUTE, tile_qubits=6)
+    pos, _ = _compose_exchanges(p, n)
+    assert pos == [n - 1 - q for q in range(n)]
