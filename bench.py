@@ -330,9 +330,11 @@ def kernel_roofline(plan, step_ms, peak):
 
 def unfused_classes(qs, torch, device, n, reps=10):
     """Per-gate-class unfused passes (the RX-per-qubit sweep of §IV-C widened
-    to four classes): algorithmic HBM GB/s per class and dtype over targets."""
+    to four classes) on every target 0..n-1: algorithmic HBM GB/s per class,
+    dtype and target (10 gates per target, device time of the 10 passes);
+    the fraction of the measured HBM peak is reported beside the median."""
     out = {}
-    targets = sorted({0, 1, 2, 5, n // 2, n - 2, n - 1})
+    targets = list(range(n))
     for dt in ("c64", "c128"):
         s = qs.State(n, dt, device=device)
         # a dense state (a U3 on every qubit): no amplitude is zero, so no
@@ -348,7 +350,8 @@ def unfused_classes(qs, torch, device, n, reps=10):
                 b = sum(x[1] for x in p.step_info())
                 res.append(b / (ms.sum() / 1e3) / 1e9)
             out.setdefault(cls, {})[dt] = {"targets": targets, "GBps": [round(x, 1) for x in res],
-                                           "min": round(min(res), 1), "median": round(float(np.median(res)), 1)}
+                                           "min": round(min(res), 1), "median": round(float(np.median(res)), 1),
+                                           "argmin": targets[int(np.argmin(res))]}
         del s
     return out
 
@@ -509,6 +512,7 @@ def run_ours(args):
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
         extras["c128_unfused_%dq" % n] = base
         extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
+        extras["c128_brick_qft_28q"] = c128_config2(qs, torch, device, 28)
         extras["planner_policies_30q"] = planner_policies(qs, torch, device, 30)
         extras["batch_512_hea"] = batch_workload(qs, torch, device)
         extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
@@ -727,6 +731,36 @@ def c64_33q(qs, torch, device, fq):
            "hbm_GBps_algorithmic": st["hbm_bytes"] / (t / 1e3) / 1e9,
            "norm2": s.norm2()}
     del s, p
+    return out
+
+
+def c128_config2(qs, torch, device, n=28):
+    """The 28-qubit complex128 brick (depth 40, seed 3) and QFT (seeded
+    basis state) under the plain per-gate kernels and the 5-qubit
+    tensor-core block plan: one warm-up run, one timed run each (CUDA
+    events)."""
+    out = {}
+    s = qs.State(n, "c128", device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for wname, circ, x0 in (("brick_d40", W.brick(n, 40, 3), 0), ("qft", W.qft(n), W.basis_index(n, 4))):
+        c = qs.Circuit(circ)
+        for pname, mode, fq in (("unfused", qs.PLAN_UNFUSED, 0), ("fused_k5", qs.PLAN_FUSED, 5)):
+            p = qs.Plan(c, n, "c128", mode=mode, fuse_qubits=fq)
+            s.set_basis(x0)
+            s.run(p)
+            s.set_basis(x0)
+            torch.cuda.synchronize()
+            e0.record()
+            s.run(p)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = p.stats()
+            out.setdefault(wname, {"gates": len(circ)})[pname] = {
+                "ms": ms, "passes": st["passes"], "effective_GBps": st["metric_bytes"] / (ms / 1e3) / 1e9,
+                "gates_per_s": len(circ) / (ms / 1e3), "hbm_GBps_algorithmic": st["hbm_bytes"] / (ms / 1e3) / 1e9}
+            del p
+    del s
     return out
 
 
