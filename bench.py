@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -437,11 +438,27 @@ def run_ours(args):
     circuit = qs.Circuit(circ)
     states = {}
     e2e = None
+    tune_file = os.path.join(tempfile.gettempdir(), "qs_tune_cache_%d.txt" % os.getpid())
+    qs.set_tune_cache(tune_file)
+    tuned = {}
     for dt in dtypes:
-        mode_name, mode, fq = plan_mode(qs, args, dt)
-        plan = qs.Plan(circuit, n, dt, mode=mode, fuse_qubits=fq)
-        st = plan.stats()
         state = qs.State(n, dt, device=device)
+        if args.mode == "auto":
+            # the library's autotuner picks the plan shape (dense-block width
+            # k or tile shape) by timing candidates on this state, before the
+            # timed region
+            t0 = time.perf_counter()
+            opts, tms = qs.autotune(circuit, state)
+            kw = qs.plan_kwargs(opts)
+            plan = qs.Plan(circuit, n, dt, **kw)
+            mode_name = {qs.PLAN_FUSED: "fused", qs.PLAN_TILED: "tiled"}.get(opts.mode, str(opts.mode))
+            fq = opts.fuse_qubits
+            tuned[dt] = {"opts": {k: v for k, v in kw.items() if v}, "tuned_ms": tms,
+                         "tuning_s": time.perf_counter() - t0}
+        else:
+            mode_name, mode, fq = plan_mode(qs, args, dt)
+            plan = qs.Plan(circuit, n, dt, mode=mode, fuse_qubits=fq)
+        st = plan.stats()
         with ClockSampler(local) as clk:
             ms, step_ms = timed_run(qs, torch, state, plan, args.steps, args.warmup, world, device)
         roof, per_kind = kernel_roofline(plan, step_ms, peak)
@@ -472,7 +489,7 @@ def run_ours(args):
                                           "at 26 qubits, scaled by 2^(n-26)" % roof["kernel"])
         elif roof and roof["kernel"].startswith("k_fused_c128"):
             roof["tensor"] = ("tcgen05.mma kind::f16 on exact 9-bit integer digits of the FP64 operands: 5 digits "
-                              "per value, 15 digit-pair products summed exactly per level in TMEM")
+                              "per value, 19 digit-pair products (levels 0-5) summed per level in TMEM")
             if roof["kernel"] in BLOCK_C128_TRAFFIC_26Q:
                 roof["traffic"] = BLOCK_C128_TRAFFIC_26Q[roof["kernel"]] * 2.0 ** (n - 26)
                 roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of %s "
@@ -484,6 +501,7 @@ def run_ours(args):
         extra = 1 + (2 if dt == "c128" and mode_name != "fused" else 0)
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
                        "plan": mode_name + (f" k={fq}" if mode_name == "fused" else ""),
+                       "autotune": tuned.get(dt),
                        "arithmetic": ARITHMETIC[dt],
                        "passes": st["passes"], "gates": st["gates"], "hbm_bytes_per_step": st["hbm_bytes"],
                        "hbm_GBps": st["hbm_bytes"] / (ms / 1e3) / 1e9, "roofline": roof, "kernels": per_kind,
@@ -493,9 +511,9 @@ def run_ours(args):
         del plan
         if dt == args.dtype and not args.no_e2e:
             # end to end through the C ABI with host buffers, right after the
-            # headline (before the other dtype's runs)
-            _, mode_e, fq_e = plan_mode(qs, args, dt)
-            e2e = run_e2e(qs, torch, args, n, circ, mode_e, fq_e, device, world)
+            # headline (before the other dtype's runs), with the same plan
+            # shape (the autotuner's cached answer is looked up again inside)
+            e2e = run_e2e(qs, torch, args, n, circ, dt, device, world)
     # precision: infidelity of the headline run against complex128 on the GPU
     infid = None
     if "c64" in states and "c128" in states:
@@ -526,6 +544,7 @@ def run_ours(args):
                    "plan": head["plan"], "passes": head["passes"], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (state %.0f MiB, L2 126 MiB)" % (2.0 ** n * S_BYTES[args.dtype] / 2 ** 20)},
         "gates_per_s": head["gates_per_s"],
+        "autotune": head["autotune"],
         "hbm_GBps_algorithmic": head["hbm_GBps"],
         "roofline": dict(head["roofline"], peak_source=peak_kind) if head["roofline"] else None,
         "kernels": head["kernels"],
@@ -786,14 +805,14 @@ def c128_unfused(qs, torch, device, n, circuit):
     return out
 
 
-def run_e2e(qs, torch, args, n, circ, mode, fq, device, world):
-    """Per step: host state -> device (pinned), build and compile the
-    circuit, run it, device -> host (pinned); timed on the host around the
-    whole call chain, with the time of each phase reported beside it.  The
+def run_e2e(qs, torch, args, n, circ, dt, device, world):
+    """Per step: host state -> device (pinned), build the circuit, look its
+    plan shape up in the autotuner's cache (or take the --mode given),
+    compile it, run it, device -> host (pinned); timed on the host around
+    the whole call chain, with the time of each phase reported beside it.  The
     value is the median step (the host link is shared with the machine's
     other GPUs, and single steps have measured up to 3x slower transfers);
     every step's time and phases are reported too."""
-    dt = args.dtype
     tdt = torch.complex64 if dt == "c64" else torch.complex128
     host = torch.zeros(1 << n, dtype=tdt, pin_memory=True)
     host[0] = 1
@@ -809,7 +828,13 @@ def run_e2e(qs, torch, args, n, circ, mode, fq, device, world):
         qs.lib().qs_set_stream(state.handle, qs._stream_ptr())
         assert qs.lib().qs_copy_from_host(state.handle, ctypes_ptr(host)) == 0  # returns once the data is on the device
         t.append(time.perf_counter())
-        p = qs.Plan(qs.Circuit(circ), n, dt, mode=mode, fuse_qubits=fq)
+        c = qs.Circuit(circ)
+        if args.mode == "auto":
+            opts, _ = qs.autotune(c, state)  # a cache hit: tuned before the timed steps
+            p = qs.Plan(c, n, dt, **qs.plan_kwargs(opts))
+        else:
+            _, mode, fq = plan_mode(qs, args, dt)
+            p = qs.Plan(c, n, dt, mode=mode, fuse_qubits=fq)
         t.append(time.perf_counter())
         state.run(p)
         assert qs.lib().qs_copy_to_host(state.handle, ctypes_ptr(host)) == 0  # waits for the run, then copies

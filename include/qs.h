@@ -394,11 +394,36 @@ qs_status qs_batch_destroy(qs_batch* b);
 /* Autotuner: builds and times the batch for candidate tile sizes and
  * register slot counts (two runs each, starting from |0...0>, so the states
  * are overwritten) and returns the fastest options in *best (and its time
- * in *best_ms if non-NULL).  Cached per process for the same dtype, count,
- * total qubits and total gates. */
+ * in *best_ms if non-NULL).  Cached under a hash of every circuit, the
+ * qubit counts, the dtype and the GPU, as for qs_plan_autotune. */
 qs_status qs_batch_autotune(int count, const int* n, qs_dtype dtype, void* const* dev_states,
                             const qs_circuit* const* circuits, void* stream, qs_plan_opts* best,
                             double* best_ms);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuning                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Picks the fastest plan shape for circuit c on state st by timing
+ * candidates on st itself (its contents are overwritten): dense blocks of
+ * k = 4, 5, 6 qubits (complex128: 4, 5) and tile passes of 12 to 14 qubits
+ * with 3 or 4 register slots.  *best receives options for qs_plan_build,
+ * *best_ms (may be NULL) the time of one run of that plan.  The result is
+ * cached under a hash of the circuit's gates, n, the dtype and the GPU
+ * (name, SM count, compute capability): later calls with the same circuit
+ * return at once, also in later processes when a cache file is set. */
+qs_status qs_plan_autotune(const qs_circuit* c, qs_state* st, qs_plan_opts* best, double* best_ms);
+
+/* Sets the file that persists autotuning results (one text line per
+ * result, appended as results are found) and loads the results it already
+ * holds, replacing those in memory.  NULL keeps results in memory only (and
+ * clears them).  A file that cannot be written only loses persistence. */
+qs_status qs_tune_cache_file(const char* path);
+
+/* 64-bit FNV-1a hash of a circuit's gates (kind, qubits, angle bits,
+ * parameter index) with n and dtype: the device-independent part of the
+ * autotuner's key. */
+qs_status qs_circuit_hash(const qs_circuit* c, int n, qs_dtype dtype, uint64_t* out);
 
 /* ---------------------------------------------------------------------- */
 /* Differentiation                                                        */

@@ -76,6 +76,9 @@ _SIGS = {
     "qs_inner": ([_vp, _vp, _dp], _int),
     "qs_expect_pauli": ([_vp, _int, _up, _up, _dp, _dp], _int),
     "qs_inner_noalloc": ([_vp, _vp, _int, _int, _vp, _dp], _int),
+    "qs_plan_autotune": ([_vp, _vp, ctypes.POINTER(PlanOpts), _dp], _int),
+    "qs_tune_cache_file": ([ctypes.c_char_p], _int),
+    "qs_circuit_hash": ([_vp, _int, _int, ctypes.POINTER(ctypes.c_uint64)], _int),
     "qs_circuit_create": ([ctypes.POINTER(_vp)], _int),
     "qs_circuit_destroy": ([_vp], _int),
     "qs_circuit_add": ([_vp, _int, _ip, _int, _dp, _int], _int),
@@ -373,6 +376,34 @@ class Circuit:
             self.close()
         except Exception:
             pass
+
+
+def plan_kwargs(opts: PlanOpts) -> dict:
+    """PlanOpts as keyword arguments of Plan."""
+    return {f: getattr(opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"}
+
+
+def autotune(circuit: "Circuit", state: "State"):
+    """qs_plan_autotune: (PlanOpts, ms) of the fastest plan shape for this
+    circuit on this state (whose contents are overwritten); cached."""
+    best = PlanOpts()
+    ms = ctypes.c_double()
+    _check(_lib.qs_plan_autotune(circuit.handle, state._bind(), ctypes.byref(best), ctypes.byref(ms)),
+           "qs_plan_autotune")
+    return best, ms.value
+
+
+def set_tune_cache(path) -> None:
+    """qs_tune_cache_file: persist autotuning results in `path` (None: in
+    memory only) and load those it holds."""
+    _check(_lib.qs_tune_cache_file(None if path is None else os.fsencode(path)), "qs_tune_cache_file")
+
+
+def circuit_hash(circuit: "Circuit", n: int, dtype: str) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib.qs_circuit_hash(circuit.handle, int(n), C64 if dtype == "c64" else C128, ctypes.byref(out)),
+           "qs_circuit_hash")
+    return out.value
 
 
 class Plan:

@@ -452,36 +452,18 @@ qs_status qs_batch_destroy(qs_batch* b) {
 }
 
 // Autotuner: times candidate plan shapes on the batch itself and keeps the
-// fastest.  Results are cached per (dtype, count, total qubits, total gates)
-// for the life of the process.
+// fastest.  Results are cached under a hash of every circuit, the qubit
+// counts, the dtype and the GPU (tune.cpp): in memory for the process and in
+// the cache file when one is set (qs_tune_cache_file).
 qs_status qs_batch_autotune(int count, const int* nq, qs_dtype dtype, void* const* dev_states,
                             const qs_circuit* const* circuits, void* stream, qs_plan_opts* best,
                             double* best_ms) {
   if (!best) return fail(QS_EINVAL, "qs_batch_autotune: best is NULL");
   if (count < 1 || !nq || !circuits) return fail(QS_EINVAL, "qs_batch_autotune: bad arguments");
-  struct Key {
-    int dt, count;
-    long long nsum, gsum;
-    bool operator<(const Key& o) const {
-      return std::tie(dt, count, nsum, gsum) < std::tie(o.dt, o.count, o.nsum, o.gsum);
-    }
-  };
-  static std::mutex mu;
-  static std::map<Key, std::pair<qs_plan_opts, double>> cache;
-  Key key{(int)dtype, count, 0, 0};
-  for (int i = 0; i < count; ++i) {
-    key.nsum += nq[i];
-    key.gsum += circuits[i] ? (long long)circuits[i]->gates.size() : 0;
-  }
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) {
-      *best = it->second.first;
-      if (best_ms) *best_ms = it->second.second;
-      return QS_OK;
-    }
-  }
+  qs_status kst = QS_OK;
+  const unsigned long long key = batch_tune_key(count, nq, dtype, circuits, &kst);
+  if (kst != QS_OK) return kst;
+  if (batch_tune_lookup(key, best, best_ms)) return QS_OK;
   const int mcands[] = {11, 12, 13};
   const int gcands[][2] = {{3, 1}, {3, 2}, {4, 1}};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -526,8 +508,7 @@ qs_status qs_batch_autotune(int count, const int* nq, qs_dtype dtype, void* cons
   if (rc != QS_OK) return rc;
   *best = bo;
   if (best_ms) *best_ms = bestt;
-  std::lock_guard<std::mutex> lk(mu);
-  cache[key] = {bo, bestt};
+  batch_tune_remember(key, bo, bestt);
   return QS_OK;
 }
 

@@ -74,6 +74,12 @@ qs_status run_layout_dfl(qs_state* s, bool to_dfl);
 qs_status run_controlled_dfl(qs_state* s, const int* ctrl, int nc, int t, const double U[8]);
 qs_status run_diag_dfl(qs_state* s, const int* qubits, int k, const double* d);
 
+// ---- autotuning cache (tune.cpp) -------------------------------------------
+unsigned long long batch_tune_key(int count, const int* nq, qs_dtype dtype, const qs_circuit* const* circuits,
+                                  qs_status* st);
+bool batch_tune_lookup(unsigned long long key, qs_plan_opts* best, double* best_ms);
+void batch_tune_remember(unsigned long long key, const qs_plan_opts& o, double ms);
+
 // ---- reductions (reduce.cu) ------------------------------------------------
 qs_status run_norm2(qs_state* s, double* out);
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]);

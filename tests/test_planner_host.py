@@ -138,3 +138,24 @@ def test_routed_qft_swaps_are_relabellings(qs):
     p = qs.Plan(qs.Circuit(W.qft(n)), n, "c64", mode=qs.PLAN_PERMUTE, tile_qubits=6)
     pos, _ = _compose_exchanges(p, n)
     assert pos == [n - 1 - q for q in range(n)]
+
+
+def test_circuit_hash_keys_the_tuner(qs, tmp_path):
+    # the autotuner's circuit key: equal for equal gate lists, different when
+    # any angle bit, qubit, n or dtype differs (no GPU needed)
+    a = W.brick(10, 3, 1)
+    h = qs.circuit_hash(qs.Circuit(a), 10, "c64")
+    assert h == qs.circuit_hash(qs.Circuit(W.brick(10, 3, 1)), 10, "c64")
+    b = list(a)
+    g = b[5]
+    b[5] = W.Gate(g.name, g.qubits, (g.params[0] + 2.0 ** -40,) + tuple(g.params[1:]), g.param_index)
+    assert qs.circuit_hash(qs.Circuit(b), 10, "c64") != h
+    assert qs.circuit_hash(qs.Circuit(a), 11, "c64") != h
+    assert qs.circuit_hash(qs.Circuit(a), 10, "c128") != h
+    assert qs.circuit_hash(qs.Circuit(W.brick(10, 3, 2)), 10, "c64") != h
+    # cache files: absent, well formed, garbage -- all accepted
+    qs.set_tune_cache(str(tmp_path / "none.txt"))
+    f = tmp_path / "c.txt"
+    f.write_text("qs-tune-v1 0123456789abcdef plan 2 0 0 0 0 0 6 1.5\nnot a cache line\n")
+    qs.set_tune_cache(str(f))
+    qs.set_tune_cache(None)
