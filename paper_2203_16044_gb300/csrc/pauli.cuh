@@ -17,6 +17,7 @@
 namespace qs {
 
 constexpr int kMaxGroupTerms = 64;
+constexpr int kMaxClasses = 8;
 struct PauliGroup {
   u64 m;           // X/Y mask shared by the group
   int h;           // highest bit of m (-1 if m == 0)
@@ -24,6 +25,15 @@ struct PauliGroup {
   u64 z[kMaxGroupTerms];
   // w_t = c_t * i^{nY_t} in double-float: real (h, l) and imaginary (h, l)
   float wrh[kMaxGroupTerms], wrl[kMaxGroupTerms], wih[kMaxGroupTerms], wil[kMaxGroupTerms];
+  // Z-only groups whose terms each have two Z bits, i apart from j = i + d:
+  // terms of equal d and weight form a class, and popcount(x & z_t) is odd
+  // exactly when bit i of x ^ (x >> d) is set, so a class of len terms gives
+  // w (len - 2 popcount((x ^ (x >> d)) & mask)), mask = the terms' lower
+  // bits.  ncls = 0: the term list is used.
+  int ncls;
+  int cls_d[kMaxClasses], cls_len[kMaxClasses];
+  u64 cls_mask[kMaxClasses];
+  float cwrh[kMaxClasses], cwrl[kMaxClasses], cwih[kMaxClasses], cwil[kMaxClasses];
 };
 
 // f(x) in double-float.  The host sorts a group's terms by weight, so equal
@@ -33,6 +43,14 @@ struct PauliGroup {
 __device__ __forceinline__ void fval_df(const PauliGroup& g, u64 x, dfl& fr, dfl& fi) {
   fr = dfl{0.f, 0.f};
   fi = dfl{0.f, 0.f};
+  if (g.ncls > 0) {
+    for (int c = 0; c < g.ncls; ++c) {
+      const dfl k{(float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c])), 0.f};
+      df_acc(fr, df_mul(dfl{g.cwrh[c], g.cwrl[c]}, k));
+      df_acc(fi, df_mul(dfl{g.cwih[c], g.cwil[c]}, k));
+    }
+    return;
+  }
   int len = 0, odd = 0;
   for (int t = 0; t < g.nt; ++t) {
     odd += __popcll(x & g.z[t]) & 1;
@@ -96,6 +114,36 @@ inline std::vector<PauliGroup> build_pauli_groups(int nterms, const u64* xmask, 
       s.wil[i] = g.wil[ord[i]];
     }
     g = s;
+  }
+  // Z-only groups of two-bit terms: classes by (bit distance, weight)
+  for (PauliGroup& g : groups) {
+    g.ncls = 0;
+    if (g.m != 0) continue;
+    bool ok = true;
+    for (int t = 0; t < g.nt && ok; ++t) {
+      if (__builtin_popcountll(g.z[t]) != 2) { ok = false; break; }
+      const int i = __builtin_ctzll(g.z[t]), j = 63 - __builtin_clzll(g.z[t]), d = j - i;
+      int c = 0;
+      for (; c < g.ncls; ++c)
+        if (g.cls_d[c] == d && g.cwrh[c] == g.wrh[t] && g.cwrl[c] == g.wrl[t] && g.cwih[c] == g.wih[t] &&
+            g.cwil[c] == g.wil[t])
+          break;
+      if (c == g.ncls) {
+        if (g.ncls == kMaxClasses) { ok = false; break; }
+        g.cls_d[c] = d;
+        g.cls_len[c] = 0;
+        g.cls_mask[c] = 0;
+        g.cwrh[c] = g.wrh[t];
+        g.cwrl[c] = g.wrl[t];
+        g.cwih[c] = g.wih[t];
+        g.cwil[c] = g.wil[t];
+        ++g.ncls;
+      }
+      if ((g.cls_mask[c] >> i) & 1) { ok = false; break; }  // a repeated term: keep the list
+      g.cls_mask[c] |= u64(1) << i;
+      ++g.cls_len[c];
+    }
+    if (!ok) g.ncls = 0;
   }
   return groups;
 }

@@ -12,7 +12,16 @@
 //   f(x) = sum_t c_t i^{nY_t} (-1)^{popcount(x & z_t)}.
 // For m != 0 the pairs {x, x^m} are visited once (x with bit h of m clear,
 // h = highest set bit of m), each amplitude read once.
+//
+// Groups whose X/Y bits all lie in one tile's qubit set -- the kTL lowest
+// qubits and up to kTH chosen higher ones -- share one read of the state: a
+// tile pass loads each tile (one assignment of the other qubits) into
+// shared memory once and evaluates every group of the pass on it, since x
+// and x ^ m then lie in the same tile.  The transverse-field Ising energy at
+// 30 qubits (one Z-only group and 30 single-X groups) takes three such
+// passes instead of 31.  Groups that fit no tile get a pass of their own.
 #include <algorithm>
+#include <vector>
 
 #include "dfloat.cuh"
 #include "kcommon.cuh"
@@ -275,6 +284,218 @@ __global__ void __launch_bounds__(kThreads) k_pauli(const R* __restrict__ a, int
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
 }
 
+// ---- tile passes shared by several groups ----------------------------------
+constexpr int kTL = 4;          // low qubits of every expectation tile (runs of 16 amplitudes)
+constexpr int kTH = 9;          // at most this many chosen higher qubits per tile (8 for complex128)
+constexpr int kPassGroups = 16; // groups per tile pass
+
+struct PTilePass {
+  int L, r;                    // tile = L low qubits + r high qubits H[0..r)
+  int H[kTH];
+  Ins tins;                    // zero insertion at the high qubits (the tile base)
+  int ng;
+  int gi[kPassGroups];         // groups of this pass (indices into the group array)
+  int hloc[kPassGroups];       // highest tile-local bit of the group's mask (-1: diagonal group)
+  unsigned mloc[kPassGroups];  // the group's X/Y mask in tile-local bits
+};
+
+// h + l renormalised (the accumulators' low parts gather unnormalised error terms)
+__device__ __forceinline__ dfl df_norm2(dfl a) {
+  dfl r;
+  r.h = fast_two_sum(a.h, a.l, r.l);
+  return r;
+}
+
+// Tile-local index l (bits [0, L) = qubits [0, L), bit L + j = qubit H[j]) to
+// the global index, given the tile base F.
+__device__ __forceinline__ u64 ptile_global(u64 F, const u64* spreadH, int L, unsigned l) {
+  return F | (u64)(l & ((1u << L) - 1)) | spreadH[l >> L];
+}
+
+// A tile amplitude in shared memory: complex64 as it is, complex128 as its
+// double-float split (converted once per tile, not once per group).
+template <typename R> struct TileAmp;
+template <> struct TileAmp<float> {
+  typedef float2 T;
+  __device__ static T from(float2 v) { return v; }
+  __device__ static void get(const T& v, dfl& re, dfl& im) {
+    re = dfl{v.x, 0.f};
+    im = dfl{v.y, 0.f};
+  }
+};
+template <> struct TileAmp<double> {
+  typedef float4 T;
+  __device__ static T from(double2 v) {
+    const dfl r = d2df(v.x), i = d2df(v.y);
+    return make_float4(r.h, r.l, i.h, i.l);
+  }
+  __device__ static void get(const T& v, dfl& re, dfl& im) {
+    re = dfl{v.x, v.y};
+    im = dfl{v.z, v.w};
+  }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict__ a, int n,
+                                                          const __grid_constant__ PTilePass P,
+                                                          const PauliGroup* __restrict__ groups, double2* part) {
+  typedef typename AmpV<R>::T A;
+  typedef TileAmp<R> TA;
+  typedef typename TA::T E;
+  extern __shared__ __align__(16) unsigned char psm[];
+  u64* spreadH = reinterpret_cast<u64*>(psm);             // [2^r]
+  E* t = reinterpret_cast<E*>(psm + sizeof(u64) * (1u << kTH));  // [2^(L + r)]
+  const A* av = reinterpret_cast<const A*>(a);
+  const int L = P.L, r = P.r, m = L + r;
+  const unsigned tile = 1u << m;
+  for (unsigned i = threadIdx.x; i < (1u << r); i += kThreads) {
+    u64 sp = 0;
+    for (int j = 0; j < r; ++j)
+      if ((i >> j) & 1u) sp |= u64(1) << P.H[j];
+    spreadH[i] = sp;
+  }
+  const u64 ntiles = u64(1) << (n - m);
+  double sr = 0.0, si = 0.0;
+  dfl ar{0.f, 0.f}, ai{0.f, 0.f};
+  __syncthreads();
+  for (u64 ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const u64 F = expand(ti << L, P.tins);
+    // the tile into shared memory, 4 loads in flight per thread
+    for (unsigned e0 = threadIdx.x; e0 < tile; e0 += 4 * kThreads) {
+      A v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned e = e0 + u * kThreads;
+        if (e < tile) v[u] = av[ptile_global(F, spreadH, L, e)];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned e = e0 + u * kThreads;
+        if (e < tile) t[e] = TA::from(v[u]);
+      }
+    }
+    __syncthreads();
+    for (int gg = 0; gg < P.ng; ++gg) {
+      const PauliGroup& g = groups[P.gi[gg]];
+      const int h = P.hloc[gg];
+      if (h < 0 && g.ncls > 0) {
+        // Z-only two-bit terms in classes: f(x) = sum_c w_c k_c(x) with
+        // integer k_c, so sum_x p_x f(x) = sum_c w_c sum_x p_x k_c(x): the
+        // inner sums are formed first, one double-float chain per class
+        const int nc = g.ncls;
+        dfl sc[kMaxClasses];
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) sc[c] = dfl{0.f, 0.f};
+        for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
+          dfl xr, xi;
+          TA::get(t[l], xr, xi);
+          dfl pw = df_mul(xr, xr);
+          df_acc(pw, df_mul(xi, xi));
+          const u64 x = ptile_global(F, spreadH, L, l);
+#pragma unroll
+          for (int c = 0; c < kMaxClasses; ++c) {
+            if (c >= nc) break;
+            const float k = (float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c]));
+            df_acc(sc[c], df_mul(pw, dfl{k, 0.f}));
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxClasses; ++c) {
+          if (c >= nc) break;
+          const dfl v = df_norm2(sc[c]);
+          df_acc(ar, df_mul(dfl{g.cwrh[c], g.cwrl[c]}, v));
+          df_acc(ai, df_mul(dfl{g.cwih[c], g.cwil[c]}, v));
+        }
+      } else if (h < 0) {  // diagonal group: sum_x |a_x|^2 f(x)
+        int since = 0;  // flush the double-float sums into FP64 every kU terms
+        for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
+          dfl xr, xi;
+          TA::get(t[l], xr, xi);
+          dfl fr, fi;
+          fval_df(g, ptile_global(F, spreadH, L, l), fr, fi);
+          dfl w = df_mul(xr, xr);
+          df_acc(w, df_mul(xi, xi));
+          df_acc(ar, df_mul(w, fr));
+          df_acc(ai, df_mul(w, fi));
+          if (++since == kU) {
+            df_flush(sr, ar);
+            df_flush(si, ai);
+            since = 0;
+          }
+        }
+      } else if (g.nt == 1) {
+        // one term: the pair {x, y = x ^ m} gives 2 w s(x) Re p (m and z of
+        // even overlap) or 2 i w s(x) Im p, p = conj(a_y) a_x; the sum of
+        // s(x) Re p (or Im p) over this thread's pairs is formed first, in
+        // four independent double-float chains, and weighted once
+        const unsigned mloc = P.mloc[gg], lo_mask = (1u << h) - 1u;
+        const u64 z0 = g.z[0];
+        const bool sm_odd = __popcll(g.m & z0) & 1;
+        dfl c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const unsigned k = k0 + u * kThreads;
+            if (k >= tile / 2) break;
+            const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
+            dfl xr, xi, yr, yi;
+            TA::get(t[l], xr, xi);
+            TA::get(t[l ^ mloc], yr, yi);
+            dfl c;
+            if (!sm_odd) {
+              c = df_mul(yr, xr);
+              df_acc(c, df_mul(yi, xi));
+            } else {
+              c = df_mul(yr, xi);
+              df_acc(c, df_mul(dfl{-yi.h, -yi.l}, xr));
+            }
+            if (z0 && (__popcll(ptile_global(F, spreadH, L, l) & z0) & 1)) c = dfl{-c.h, -c.l};
+            df_acc(c4[u], c);
+          }
+        }
+        const dfl c = df_add(df_add(df_norm2(c4[0]), df_norm2(c4[1])), df_add(df_norm2(c4[2]), df_norm2(c4[3])));
+        const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
+        if (!sm_odd) {
+          df_acc(ar, df_mul(w_r, c));
+          df_acc(ai, df_mul(w_i, c));
+        } else {
+          df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
+          df_acc(ai, df_mul(w_r, c));
+        }
+      } else {
+        const unsigned mloc = P.mloc[gg], lo_mask = (1u << h) - 1u;
+        int since = 0;
+        for (unsigned k = threadIdx.x; k < tile / 2; k += kThreads) {
+          const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
+          dfl xr, xi, yr, yi;
+          TA::get(t[l], xr, xi);
+          TA::get(t[l ^ mloc], yr, yi);
+          const u64 x = ptile_global(F, spreadH, L, l);
+          dfl pr = df_mul(yr, xr), pi = df_mul(yr, xi);
+          df_acc(pr, df_mul(yi, xi));
+          df_acc(pi, df_mul(dfl{-yi.h, -yi.l}, xr));
+          dfl fr, fi;
+          fval_df(g, x, fr, fi);
+          cacc(ar, ai, pr, pi, fr, fi);
+          fval_df(g, x ^ g.m, fr, fi);
+          cacc(ar, ai, pr, dfl{-pi.h, -pi.l}, fr, fi);
+          if (++since == kU) {
+            df_flush(sr, ar);
+            df_flush(si, ai);
+            since = 0;
+          }
+        }
+      }
+    }
+    // into FP64 once per tile (the FP64 pipe is about 1/64 of FP32 on GB300)
+    df_flush(sr, ar);
+    df_flush(si, ai);
+    __syncthreads();
+  }
+  block_sum2(sr, si);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
+}
+
 qs_status read_result(qs_state* s, const double2* dev, double2* host) {
   cudaError_t e = cudaMemcpyAsync(s->pinned, dev, sizeof(double2), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reduction readback");
@@ -337,20 +558,104 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
                      double* out) {
   const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
   const u64 N = u64(1) << s->n;
-  const unsigned gsz = red_grid(N / 2);
   const size_t ng = groups.size();
-  qs_status st = ensure_scratch(s, sizeof(double2) * (gsz * ng + 1));
+  // tile passes: first fit of every group whose mask bits above the kTL low
+  // qubits number at most kTH; the others (and every group of a state too
+  // small for a tile) get a pass of their own
+  std::vector<PTilePass> tp;
+  std::vector<int> alone;
+  const bool tiles = s->n >= kTL + 1 && ng > 1;
+  const int rmax = s->dtype == QS_C64 ? kTH : kTH - 1;  // tiles of 64 KB
+  for (size_t i = 0; i < ng; ++i) {
+    const u64 hi = groups[i].m >> kTL;
+    if (!tiles || __builtin_popcountll(hi) > rmax) {
+      alone.push_back((int)i);
+      continue;
+    }
+    size_t p = 0;
+    for (; p < tp.size(); ++p) {
+      u64 cur = 0;
+      for (int j = 0; j < tp[p].r; ++j) cur |= u64(1) << tp[p].H[j];
+      const u64 need = (groups[i].m & ~((u64(1) << kTL) - 1)) | cur;
+      if (tp[p].ng < kPassGroups && __builtin_popcountll(need) <= rmax && kTL + __builtin_popcountll(need) <= s->n)
+        break;
+    }
+    if (p == tp.size()) {
+      PTilePass q{};
+      q.L = kTL;
+      tp.push_back(q);
+    }
+    PTilePass& q = tp[p];
+    u64 need = groups[i].m & ~((u64(1) << kTL) - 1);
+    for (int j = 0; j < q.r; ++j) need |= u64(1) << q.H[j];
+    q.r = 0;
+    for (int b = kTL; b < s->n; ++b)
+      if ((need >> b) & 1) q.H[q.r++] = b;
+    q.gi[q.ng++] = (int)i;
+  }
+  // each pass's tile-local masks, and its tiles at least 2^(kTL + 1) amplitudes
+  for (PTilePass& q : tp) {
+    for (int b = kTL; b < s->n && q.r == 0; ++b) q.H[q.r++] = b;
+    q.tins.k = q.r;
+    q.tins.set = 0;
+    for (int j = 0; j < q.r; ++j) q.tins.pos[j] = q.H[j];
+    for (int gg = 0; gg < q.ng; ++gg) {
+      const u64 mg = groups[q.gi[gg]].m;
+      unsigned ml = (unsigned)(mg & ((u64(1) << kTL) - 1));
+      for (int j = 0; j < q.r; ++j)
+        if ((mg >> q.H[j]) & 1) ml |= 1u << (kTL + j);
+      q.mloc[gg] = ml;
+      q.hloc[gg] = ml ? 31 - __builtin_clz(ml) : -1;
+    }
+  }
+  const unsigned gsz = red_grid(N / 2);
+  const size_t npart = gsz * (tp.size() + alone.size());
+  const size_t gbytes = sizeof(PauliGroup) * ng;
+  const size_t goff = ((sizeof(double2) * (npart + 1) + 255) / 256) * 256;
+  qs_status st = ensure_scratch(s, goff + gbytes);
   if (st != QS_OK) return st;
   double2* part = static_cast<double2*>(s->scratch);
-  double2* res = part + gsz * ng;
-  for (size_t i = 0; i < ng; ++i) {
-    if (s->dtype == QS_C64)
-      k_pauli<float><<<gsz, kThreads, 0, s->stream>>>(static_cast<const float*>(s->amp), s->n, groups[i], part + gsz * i);
-    else
-      k_pauli<double><<<gsz, kThreads, 0, s->stream>>>(static_cast<const double*>(s->amp), s->n, groups[i], part + gsz * i);
-    if ((st = launch_ok("k_pauli")) != QS_OK) return st;
+  double2* res = part + npart;
+  PauliGroup* dgroups = reinterpret_cast<PauliGroup*>(static_cast<char*>(s->scratch) + goff);
+  size_t pi = 0;
+  if (!tp.empty()) {
+    cudaError_t e = cudaMemcpyAsync(dgroups, groups.data(), gbytes, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "expectation: group upload");
   }
-  k_final<<<1, kThreads, 0, s->stream>>>(part, (int)(gsz * ng), res, 0);
+  for (const PTilePass& q : tp) {
+    const size_t asz = s->dtype == QS_C64 ? sizeof(float2) : sizeof(double2);
+    const size_t smem = sizeof(u64) * (1u << kTH) + asz * (size_t(1) << (q.L + q.r));
+    const u64 ntiles = u64(1) << (s->n - q.L - q.r);
+    const unsigned g = (unsigned)std::min<u64>(ntiles, (u64)gsz);
+    cudaError_t e;
+    if (s->dtype == QS_C64) {
+      e = cudaFuncSetAttribute(k_pauli_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
+      k_pauli_tiles<float><<<g, kThreads, smem, s->stream>>>(static_cast<const float*>(s->amp), s->n, q, dgroups,
+                                                             part + gsz * pi);
+    } else {
+      e = cudaFuncSetAttribute(k_pauli_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
+      k_pauli_tiles<double><<<g, kThreads, smem, s->stream>>>(static_cast<const double*>(s->amp), s->n, q, dgroups,
+                                                              part + gsz * pi);
+    }
+    if ((st = launch_ok("k_pauli_tiles")) != QS_OK) return st;
+    // CTAs beyond the tiles write no partial: zero their slots
+    if (g < gsz) {
+      e = cudaMemsetAsync(part + gsz * pi + g, 0, sizeof(double2) * (gsz - g), s->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "expectation: memset");
+    }
+    ++pi;
+  }
+  for (int i : alone) {
+    if (s->dtype == QS_C64)
+      k_pauli<float><<<gsz, kThreads, 0, s->stream>>>(static_cast<const float*>(s->amp), s->n, groups[i], part + gsz * pi);
+    else
+      k_pauli<double><<<gsz, kThreads, 0, s->stream>>>(static_cast<const double*>(s->amp), s->n, groups[i], part + gsz * pi);
+    if ((st = launch_ok("k_pauli")) != QS_OK) return st;
+    ++pi;
+  }
+  k_final<<<1, kThreads, 0, s->stream>>>(part, (int)npart, res, 0);
   if ((st = launch_ok("k_final")) != QS_OK) return st;
   double2 h;
   if ((st = read_result(s, res, &h)) != QS_OK) return st;

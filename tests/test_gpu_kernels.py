@@ -405,3 +405,31 @@ def test_apply_fused_c128_dynamic_range_and_non_unitary(qs, k, mode):
     gn = _group_norms(psi, qsel)
     assert np.all(err <= 2.0 ** -36 * gn * np.max(np.abs(M))), float(np.max(err / np.maximum(gn, 1e-300)))
     assert np.all(s.to_numpy()[gn == 0] == 0)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [5, 9, 14, 21])
+def test_expect_pauli_tile_passes(qs, dtype, n):
+    # groups whose X/Y bits fit a tile (the 4 lowest qubits plus up to 9, or
+    # 8 for complex128, higher ones) share tile-resident passes: the
+    # transverse-field Ising chain (one Z-only group, n single-X groups),
+    # strings with X on a low and a high qubit, many Z-only and Y terms in
+    # one group, and strings spanning too many high qubits for any tile
+    psi = W.random_state(n, 11500 + n)
+    terms = list(W.tfim(n))
+    rng = np.random.default_rng(n)
+    for _ in range(12):
+        q = rng.choice(n, size=min(2, n), replace=False)
+        x = int(sum(1 << int(v) for v in q))
+        z = x if rng.random() < 0.5 else int(rng.integers(0, 1 << n))
+        terms.append(W.PauliTerm(float(rng.normal()), x, z))
+    for _ in range(20):  # one big diagonal group
+        terms.append(W.PauliTerm(float(rng.normal()), 0, int(rng.integers(0, 1 << n))))
+    if n >= 15:
+        terms.append(W.PauliTerm(0.7, (1 << n) - 1 - 7, 5))  # X on every high qubit: a pass of its own
+    s = gpu_state(qs, psi, dtype)
+    want = oracle.expect_pauli(start(psi, dtype), terms)
+    got = s.expect_pauli(terms)
+    assert abs(got - want) <= 1e-12 * sum(abs(t.coeff) for t in terms), (got, want)
+    # the state is unchanged
+    assert np.array_equal(s.to_numpy(), psi.astype(s.to_numpy().dtype))
