@@ -419,7 +419,11 @@ template <int K, bool ROWS>
 struct TShape {
   static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NT = kUT * H;
   static constexpr uint32_t STAGE = kUT * D * 8;  // one tile: 128 groups x 2^K amplitudes
-  static constexpr uint32_t OUT = ROWS ? STAGE : 0;
+  // outputs leave through a second stage by TMA stores for qubits 0 .. k-1,
+  // and for windows at k = 6 (one CTA per SM there, where the per-thread
+  // scatter's store issue was the longest phase)
+  static constexpr bool TSTORE = ROWS || K == 6;
+  static constexpr uint32_t OUT = TSTORE ? STAGE : 0;
   static constexpr uint32_t BOX = kUT * 16 * 8;  // ROWS: one 16-amplitude slice of the tile
   static constexpr uint32_t B_BYTES = KR * KR * 2, LBO_B = (KR / 8) * 128, SBO = 128;
   static constexpr uint32_t TCOLS = 2 * KR;  // A hi, A lo (KR / 2 each), accumulator
@@ -561,10 +565,10 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
         umma_f16_ta(tmem + KR, ahi_t, dbh, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
-      // ROWS: the previous tile's TMA stores must have read the output stage
-      if (ROWS) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      // the previous tile's TMA stores must have read the output stage
+      if (S::TSTORE) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
-    const u64 base = ROWS ? 0 : expand(g + row, args.ins);
+    const u64 base = S::TSTORE ? 0 : expand(g + row, args.ins);
     if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma) ? 1 : 0)) {
       if (t == 0) atomicExch(&g_umma_timeout, 1);
       break;
@@ -603,13 +607,27 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
         for (int b = 0; b < D / 16; ++b) tma_store_2d(&tmap, 16 * b, (int)g, smem_u32(outst) + b * S::BOX);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
+    } else if (S::TSTORE) {
+      // the output tile in the input stage's layout, then one 3-D TMA store
+      float2* outw = reinterpret_cast<float2*>(outst);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int j = 2 * i;
+        outw[sbase + ((16 * h + i) << sp)] = make_float2(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]));
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      if (t == 0) {
+        tma_store_3d(&tmap, (int)(g & lmask), 0, (int)(g >> s_lo), smem_u32(outst));
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
     } else {
       group_store<D, CH>(a, base, true, args.spread, 0, j0, o, gsc);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     g += gstep;
   }
-  if (ROWS && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (S::TSTORE && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
