@@ -48,7 +48,8 @@
 //           (8 amplitudes x 128 rows, 128-byte swizzle) in, the same boxes
 //           out by TMA stores from a second stage;
 //   MODE 1: a window s .. s+k-1 with s >= 1: one three-dimensional TMA box
-//           (lo, e, hi) per tile, per-thread 16-byte stores;
+//           (lo, e, hi) per tile in, the same box out by a TMA store from a
+//           second stage;
 //   MODE 0: any other set: per-thread 16-byte gathers and scatters.
 // The next tile's TMA copy is issued as soon as the current one has been
 // split, so it runs under the MMAs and the epilogue.  Where the time goes
@@ -91,7 +92,7 @@ struct CShape {
   static constexpr uint32_t SET = kDig * D + kDig * KR;     // TMEM columns of one tile: digits, levels
   static constexpr uint32_t TCOLS = SET <= 256 ? 256 : 512;
   static constexpr int NSTAGE = MODE ? 1 : 0;               // TMA input stage
-  static constexpr uint32_t OUT = MODE == 2 ? TILE : 0;
+  static constexpr uint32_t OUT = MODE ? TILE : 0;     // output stage (TMA stores)
   static constexpr uint32_t BOX = kUT * 128;                // MODE 2: 8 amplitudes x 128 rows
   static constexpr uint32_t DIG_BYTES = KR * KR * 2;        // one FP16 digit matrix of B
   static constexpr int NBLK = 2 * kDig - 1;                 // e_0 .. e_4, then e_4 .. e_1 scaled by 2^-9
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT, APT = S::APT;
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* stage = sm;                             // MODE 1, 2: the input tile
-  unsigned char* outst = sm + S::NSTAGE * S::TILE;       // MODE 2 output stage
+  unsigned char* outst = sm + S::NSTAGE * S::TILE;       // MODE 1, 2: output stage
   unsigned char* Bs = outst + S::OUT;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + S::NBLK * S::DIG_BYTES);  // [0] stage full, [2] MMAs done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   };
   // Wait for the MMAs of set `buf`, then the outputs of tile gt.
   auto epilogue = [&](u64 gt, int buf, int em, bool valid) -> bool {
-    if (MODE == 2 && t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // out stage free
+    if (MODE && t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // out stage free
     const bool done = mbar_wait(mb0 + 8 * (2 + buf), (ph_mma >> buf) & 1u);
     ph_mma ^= 1u << buf;
     if (!__syncthreads_and(done ? 1 : 0)) return false;
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
     }
     asm volatile("tcgen05.wait::ld.sync.aligned;");
     const int delta = em - 1022 + Fexp - 14;
-    const u64 base = MODE == 2 ? 0 : expand(valid ? gt + row : 0, args.ins);
+    const u64 base = MODE ? 0 : expand(valid ? gt + row : 0, args.ins);
 #pragma unroll
     for (int p = 0; p < APT; ++p) {
       double2 o;
@@ -337,16 +338,22 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
           delta);
       if (MODE == 2) {
         *reinterpret_cast<double2*>(outst + (h / S::BPR) * S::BOX + row * 128 + (((u0 + p) ^ (row & 7)) << 4)) = o;
+      } else if (MODE == 1) {
+        reinterpret_cast<double2*>(outst)[sbase + ((APT * h + p) << sp)] = o;  // the input stage's layout
       } else if (valid) {
         a[base | args.spread[APT * h + p]] = o;
       }
     }
-    if (MODE == 2) {
+    if (MODE) {
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
       if (t == 0) {
+        if (MODE == 2) {
 #pragma unroll
-        for (int b = 0; b < D / 8; ++b) tma_store_2d(&tmap, 16 * b, (int)gt, smem_u32(outst) + b * S::BOX);
+          for (int b = 0; b < D / 8; ++b) tma_store_2d(&tmap, 16 * b, (int)gt, smem_u32(outst) + b * S::BOX);
+        } else {
+          tma_store_3d(&tmap, (int)(2 * (gt & lmask)), 0, (int)(gt >> s_lo), smem_u32(outst));
+        }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
     g += gstep;
   }
   if (!fine && t == 0) atomicExch(&g_c128_timeout, 1);
-  if (MODE == 2 && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (MODE && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
