@@ -109,6 +109,13 @@ qs_status qs_set_basis(qs_state* st, uint64_t x);
  * host memory gives full link bandwidth; pageable memory also works. */
 qs_status qs_copy_to_host(qs_state* st, void* dst);
 qs_status qs_copy_from_host(qs_state* st, const void* src);
+/* As qs_copy_from_host, but returns once the copy is queued on the state's
+ * stream: work queued after it on that stream (a plan run) starts when the
+ * data is on the device, and the host can build circuits and plans
+ * meanwhile.  src must stay valid and unchanged until the stream has passed
+ * the copy (qs_sync, or a later synchronous call on the state); with
+ * pageable memory the call may return only after the copy. */
+qs_status qs_copy_from_host_async(qs_state* st, const void* src);
 
 /* ---------------------------------------------------------------------- */
 /* Gate application (one HBM pass each)                                   */
@@ -262,7 +269,13 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * qs_apply_fused (complex64 blocks of 4 to 6 qubits; complex128 blocks of 4
  * or 5, a fuse_qubits of 6 is taken as 5 there; blocks whose gates touch
  * fewer qubits are widened with idle ones to a window of consecutive
- * qubits where one exists).  QS_PLAN_SWAP and QS_PLAN_PERMUTE apply the
+ * qubits where one exists).  The order of a fused plan's blocks comes from
+ * a search over partial schedules (search: how many are kept at each
+ * block; 1 takes, at every block, the qubit set that absorbs the most
+ * gates): a block's set decides which gates later blocks can take, so the
+ * greedy order is not the fewest passes (a brick circuit of depth 40 on 30
+ * qubits: 67 passes greedy, 64 with the default search).  QS_PLAN_SWAP and
+ * QS_PLAN_PERMUTE apply the
  * gates in tile passes over the tile_qubits lowest physical qubits only and
  * move every other target there first, by in-place bit-pair exchange
  * passes (§III-D): QS_PLAN_SWAP inserts one exchange of one pair (a swap)
@@ -288,6 +301,8 @@ typedef struct {
   int groups_per_thread;
   int dense;
   int fuse_qubits;    /* QS_PLAN_FUSED: qubits per dense block, 2..6 (0 = 5) */
+  int search;         /* QS_PLAN_FUSED: block-order search width, 1..256
+                         (1 = greedy; 0 = 16)                           */
   int reserved[1];
 } qs_plan_opts;
 

@@ -45,7 +45,7 @@ _int = ctypes.c_int
 class PlanOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("low_qubits", ctypes.c_int),
                 ("slot_qubits", ctypes.c_int), ("groups_per_thread", ctypes.c_int), ("dense", ctypes.c_int),
-                ("fuse_qubits", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("fuse_qubits", ctypes.c_int), ("search", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class PlanStats(ctypes.Structure):
@@ -66,6 +66,7 @@ _SIGS = {
     "qs_set_basis": ([_vp, ctypes.c_uint64], _int),
     "qs_copy_to_host": ([_vp, _vp], _int),
     "qs_copy_from_host": ([_vp, _vp], _int),
+    "qs_copy_from_host_async": ([_vp, _vp], _int),
     "qs_apply_1q": ([_vp, _int, _dp], _int),
     "qs_apply_controlled": ([_vp, _ip, _int, _int, _dp], _int),
     "qs_apply_diag": ([_vp, _ip, _int, _dp], _int),
@@ -248,6 +249,13 @@ class State:
         _check(_lib.qs_copy_from_host(self._bind(), a.ctypes.data_as(_vp)), "qs_copy_from_host")
         return self
 
+    def copy_from_host_async(self, ptr: int) -> "State":
+        """Queue the copy of 2^n amplitudes from host address ptr (pinned
+        memory, kept unchanged until the stream passes the copy) on the
+        state's stream and return (qs_copy_from_host_async)."""
+        _check(_lib.qs_copy_from_host_async(self._bind(), _vp(int(ptr))), "qs_copy_from_host_async")
+        return self
+
     def sync(self) -> None:
         _check(_lib.qs_sync(self._bind()), "qs_sync")
 
@@ -411,9 +419,9 @@ class Plan:
 
     def __init__(self, circuit: Circuit, n: int, dtype: str = "c128", mode: int = PLAN_TILED,
                  tile_qubits: int = 0, low_qubits: int = 0, slot_qubits: int = 0, groups_per_thread: int = 0,
-                 dense: int = 0, fuse_qubits: int = 0):
+                 dense: int = 0, fuse_qubits: int = 0, search: int = 0):
         opts = PlanOpts(mode=mode, tile_qubits=tile_qubits, low_qubits=low_qubits, slot_qubits=slot_qubits,
-                        groups_per_thread=groups_per_thread, dense=dense, fuse_qubits=fuse_qubits)
+                        groups_per_thread=groups_per_thread, dense=dense, fuse_qubits=fuse_qubits, search=search)
         h = _vp()
         _check(_lib.qs_plan_build(circuit.handle, int(n), C64 if dtype == "c64" else C128, ctypes.byref(opts),
                                   ctypes.byref(h)), "qs_plan_build")

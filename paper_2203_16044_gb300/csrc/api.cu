@@ -198,6 +198,13 @@ qs_status qs_copy_from_host(qs_state* s, const void* src) {
   return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_copy_from_host: sync");
 }
 
+qs_status qs_copy_from_host_async(qs_state* s, const void* src) {
+  CHECK_STATE(s);
+  if (!src) return fail(QS_EINVAL, "qs_copy_from_host_async: src is NULL");
+  const cudaError_t e = cudaMemcpyAsync(s->amp, src, state_bytes(s), cudaMemcpyHostToDevice, s->stream);
+  return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_copy_from_host_async");
+}
+
 qs_status qs_apply_1q(qs_state* s, int q, const double U[8]) {
   CHECK_STATE(s);
   if (!U) return fail(QS_EINVAL, "qs_apply_1q: U is NULL");

@@ -287,30 +287,6 @@ int absorb_into(const std::vector<const qs_gate_rec*>& remaining, const std::vec
   return taken;
 }
 
-// Qubit set of the front-greedy block: gates in order join while the set
-// stays within kmax qubits and none of their qubits is blocked.
-std::vector<char> greedy_set(const std::vector<const qs_gate_rec*>& remaining, int n, int kmax, int* nS) {
-  std::vector<char> inB(n, 0), blocked(n, 0);
-  int nb = 0;
-  for (const qs_gate_rec* g : remaining) {
-    const int ng = gate_arity(g->kind);
-    bool blk = false;
-    int add = 0;
-    for (int i = 0; i < ng; ++i) {
-      blk |= blocked[g->q[i]] != 0;
-      add += inB[g->q[i]] ? 0 : 1;
-    }
-    if (!blk && nb + add <= kmax) {
-      for (int i = 0; i < ng; ++i)
-        if (!inB[g->q[i]]) { inB[g->q[i]] = 1; ++nb; }
-      continue;
-    }
-    for (int i = 0; i < ng; ++i) blocked[g->q[i]] = 1;
-  }
-  *nS = nb;
-  return inB;
-}
-
 // The qubits touched by a candidate block's gates.
 std::vector<char> touched(const std::vector<const qs_gate_rec*>& gates, int n) {
   std::vector<char> used(n, 0);
@@ -360,43 +336,232 @@ std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax,
   return bq;
 }
 
+// ---------------------------------------------------------------------------
+// The order of the blocks.  A block's set only decides which gates can move
+// to the front now; what the next blocks can take depends on it, so taking
+// the most gates at every step (the greedy rule) is not the fewest passes:
+// on brick circuits a window that advances the qubits' gate frontiers
+// unevenly leaves steps that later windows can climb.  The search keeps the
+// `beam` best partial schedules (fewest gates left, then lowest cost) and
+// extends each by its kBranch best next sets (most gates per unit of cost);
+// a beam of 1 is the greedy rule.  Candidate sets: the front-greedy set and
+// every window of kmax consecutive qubits.  Cost of a block: 1, or 10/7 for
+// a tensor-core block whose qubits must be gathered per thread (the gather
+// kernels run at about 0.7 of the TMA kernels' speed).  Qubit sets are
+// 64-bit masks (n <= 34); a schedule's gate set is identified by the XOR of
+// random 64-bit keys of its gates (SplitMix64 of the gate index), so that
+// two orders reaching the same gates count once.
+// ---------------------------------------------------------------------------
+namespace {
+typedef unsigned long long u64m;
+constexpr int kBranch = 8;
+}  // namespace
+
+constexpr int kDefaultBeam = 16;  // QS_PLAN_FUSED search width when opts.search is 0
+
+namespace {
+
+struct SchedNode {
+  int parent;
+  u64m set;
+  int nS;
+};
+struct SchedState {
+  std::vector<int> rem;  // gate indices still to apply, in circuit order
+  double cost;
+  u64m key;
+  int node;
+};
+
+u64m gate_key(u64m i) {  // SplitMix64 finaliser of the index
+  u64m z = (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Gates of rem a block on S (nS qubits) takes (the rule of absorb_into), and
+// the qubits they touch.
+int take_count(const std::vector<int>& rem, const u64m* gm, u64m S, int nS, u64m* touched_out) {
+  u64m blocked = 0, touched = 0;
+  int taken = 0, open = nS;
+  for (size_t i = 0; i < rem.size() && open > 0; ++i) {
+    const u64m m = gm[rem[i]];
+    if (!(m & ~S) && !(m & blocked)) {
+      ++taken;
+      touched |= m;
+      continue;
+    }
+    open -= __builtin_popcountll(m & ~blocked & S);
+    blocked |= m;
+  }
+  *touched_out = touched;
+  return taken;
+}
+
+// The same scan, splitting rem into the rest (returned) and the key of the
+// gates taken.
+std::vector<int> take_rest(const std::vector<int>& rem, const u64m* gm, u64m S, int nS, u64m* key) {
+  std::vector<int> rest;
+  rest.reserve(rem.size());
+  u64m blocked = 0, k = 0;
+  int open = nS;
+  size_t i = 0;
+  for (; i < rem.size() && open > 0; ++i) {
+    const u64m m = gm[rem[i]];
+    if (!(m & ~S) && !(m & blocked)) {
+      k ^= gate_key((u64m)rem[i]);
+      continue;
+    }
+    open -= __builtin_popcountll(m & ~blocked & S);
+    blocked |= m;
+    rest.push_back(rem[i]);
+  }
+  rest.insert(rest.end(), rem.begin() + i, rem.end());
+  *key = k;
+  return rest;
+}
+
+u64m key_of_taken(const std::vector<int>& rem, const u64m* gm, u64m S, int nS) {
+  u64m blocked = 0, k = 0;
+  int open = nS;
+  for (size_t i = 0; i < rem.size() && open > 0; ++i) {
+    const u64m m = gm[rem[i]];
+    if (!(m & ~S) && !(m & blocked)) {
+      k ^= gate_key((u64m)rem[i]);
+      continue;
+    }
+    open -= __builtin_popcountll(m & ~blocked & S);
+    blocked |= m;
+  }
+  return k;
+}
+}  // namespace
+
+// Whether a tensor-core block whose gates touch `touched` gets a TMA shape
+// (the test of tc_block_qubits, without building the list).
+bool tc_fast_shape(u64m touched, int n, int kmax) {
+  if (!touched) return true;
+  const int lo = __builtin_ctzll(touched), hi = 63 - __builtin_clzll(touched);
+  for (int m = std::max(4, hi - lo + 1); m <= kmax && m <= n; ++m)
+    for (int w = std::max(0, hi - m + 1); w <= lo && w + m <= n; ++w)
+      if (w >= 2 || w == 0) return true;
+  return false;
+}
+
+// The qubit sets of the blocks, in order (masks and sizes), and their cost.
+std::vector<std::pair<u64m, int>> search_blocks(const std::vector<qs_gate_rec>& gates, int n, int kmax, bool tc,
+                                                int beam, double* cost) {
+  const int G = (int)gates.size();
+  std::vector<u64m> gm(G);
+  for (int i = 0; i < G; ++i) {
+    gm[i] = 0;
+    for (int j = 0; j < gate_arity(gates[i].kind); ++j) gm[i] |= 1ull << gates[i].q[j];
+  }
+  std::vector<SchedNode> nodes;
+  std::vector<SchedState> cur(1);
+  cur[0].rem.resize(G);
+  for (int i = 0; i < G; ++i) cur[0].rem[i] = i;
+  cur[0].cost = 0.0;
+  cur[0].key = 0;
+  cur[0].node = -1;
+  struct Child {
+    int st;
+    u64m set;
+    int nS, taken;
+    double cost, score;
+  };
+  const int branch = beam > 1 ? kBranch : 1;
+  for (;;) {
+    int done = -1;
+    for (int s = 0; s < (int)cur.size(); ++s)
+      if (cur[s].rem.empty() && (done < 0 || cur[s].cost < cur[done].cost)) done = s;
+    if (done >= 0) {
+      std::vector<std::pair<u64m, int>> out;
+      for (int v = cur[done].node; v >= 0; v = nodes[v].parent) out.push_back({nodes[v].set, nodes[v].nS});
+      std::reverse(out.begin(), out.end());
+      *cost = cur[done].cost;
+      return out;
+    }
+    std::vector<Child> kids;
+    for (int s = 0; s < (int)cur.size(); ++s) {
+      const SchedState& S0 = cur[s];
+      std::vector<Child> mine;
+      auto consider = [&](u64m set, int nS) {
+        u64m touched = 0;
+        const int taken = take_count(S0.rem, gm.data(), set, nS, &touched);
+        if (taken == 0) return;
+        const double c = tc && !tc_fast_shape(touched, n, kmax) ? 10.0 / 7.0 : 1.0;
+        mine.push_back(Child{s, set, nS, taken, S0.cost + c, taken / c});
+      };
+      {  // the front-greedy set: gates in order join while the set stays within kmax
+        u64m inB = 0, blocked = 0;
+        for (int idx : S0.rem) {
+          const u64m m = gm[idx];
+          if (!(m & blocked) && __builtin_popcountll(inB | m) <= kmax) inB |= m;
+          else blocked |= m;
+        }
+        consider(inB, __builtin_popcountll(inB));
+      }
+      for (int w = 0; w + kmax <= n; ++w) consider(((1ull << kmax) - 1) << w, kmax);
+      // most gates per unit of cost first; ties keep the candidate order
+      std::stable_sort(mine.begin(), mine.end(), [](const Child& a, const Child& b) { return a.score > b.score; });
+      if ((int)mine.size() > branch) mine.resize(branch);
+      kids.insert(kids.end(), mine.begin(), mine.end());
+    }
+    std::stable_sort(kids.begin(), kids.end(), [&](const Child& a, const Child& b) {
+      const size_t ra = cur[a.st].rem.size() - a.taken, rb = cur[b.st].rem.size() - b.taken;
+      return ra != rb ? ra < rb : a.cost < b.cost;
+    });
+    std::vector<SchedState> nxt;
+    std::vector<u64m> seen;
+    for (const Child& c : kids) {
+      if ((int)nxt.size() >= beam) break;
+      const SchedState& S0 = cur[c.st];
+      const u64m k = S0.key ^ key_of_taken(S0.rem, gm.data(), c.set, c.nS);
+      if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
+      seen.push_back(k);
+      SchedState ns;
+      u64m kk = 0;
+      ns.rem = take_rest(S0.rem, gm.data(), c.set, c.nS, &kk);
+      ns.cost = c.cost;
+      ns.key = k;
+      nodes.push_back(SchedNode{S0.node, c.set, c.nS});
+      ns.node = (int)nodes.size() - 1;
+      nxt.push_back(std::move(ns));
+    }
+    cur.swap(nxt);
+  }
+}
+
+// The search's schedule, or the greedy one where that costs less (a beam
+// can drop the greedy path), so a wider search is never worse.
+std::vector<std::pair<u64m, int>> schedule_blocks(const std::vector<qs_gate_rec>& gates, int n, int kmax, bool tc,
+                                                  int beam) {
+  double cg = 0.0, cb = 0.0;
+  std::vector<std::pair<u64m, int>> greedy = search_blocks(gates, n, kmax, tc, 1, &cg);
+  if (beam <= 1) return greedy;
+  std::vector<std::pair<u64m, int>> found = search_blocks(gates, n, kmax, tc, beam, &cb);
+  return cb < cg || (cb == cg && found.size() <= greedy.size()) ? found : greedy;
+}
+
 qs_status plan_fused(qs_plan* p) {
   const int n = p->n;
   int kmax = p->opts.fuse_qubits > 0 ? p->opts.fuse_qubits : 5;
   if (kmax < 2 || kmax > 6) return fail(QS_EINVAL, "qs_plan_build: fuse_qubits=%d outside [2, 6]", kmax);
+  const int beam = p->opts.search > 0 ? p->opts.search : kDefaultBeam;
+  if (beam > 256) return fail(QS_EINVAL, "qs_plan_build: search=%d outside [0, 256]", p->opts.search);
   // complex128 tensor-core blocks exist for k = 4, 5 (six would need 960
   // tensor-memory columns)
   if (p->dtype == QS_C128 && kmax > 5) kmax = 5;
   if (kmax > n) kmax = n;
+  const bool tc = kmax >= 4;
   std::vector<const qs_gate_rec*> remaining;
   for (const qs_gate_rec& g : p->gates) remaining.push_back(&g);
-  while (!remaining.empty()) {
-    // candidate qubit sets: the front-greedy set and every window of kmax
-    // consecutive qubits; the block takes the one that absorbs most gates,
-    // for complex64 tensor-core blocks weighted by the kernel its qubit set
-    // gets (a set that must gather per thread counts 0.7 per gate)
-    const bool tc = kmax >= 4;
-    auto score = [&](const std::vector<char>& inS, int nS) {
-      std::vector<const qs_gate_rec*> abs;
-      const int taken = absorb_into(remaining, inS, nS, &abs, nullptr);
-      if (!tc) return 10 * taken;
-      bool fast = false;
-      tc_block_qubits(touched(abs, n), n, kmax, &fast);
-      return (fast ? 10 : 7) * taken;
-    };
-    int nS = 0;
-    std::vector<char> best = greedy_set(remaining, n, kmax, &nS);
-    int best_n = nS, best_score = score(best, nS);
-    for (int w = 0; w + kmax <= n; ++w) {
-      std::vector<char> inS(n, 0);
-      for (int q = w; q < w + kmax; ++q) inS[q] = 1;
-      const int sc = score(inS, kmax);
-      if (sc > best_score) {
-        best_score = sc;
-        best = inS;
-        best_n = kmax;
-      }
-    }
+  for (const auto& blk : schedule_blocks(p->gates, n, kmax, tc, beam)) {
+    std::vector<char> best(n, 0);
+    for (int q = 0; q < n; ++q) best[q] = (blk.first >> q) & 1;
+    const int best_n = blk.second;
     std::vector<const qs_gate_rec*> absorbed, rest;
     absorb_into(remaining, best, best_n, &absorbed, &rest);
     // the block's qubits: those its gates touch, for complex64 tensor-core

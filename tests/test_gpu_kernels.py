@@ -433,3 +433,21 @@ def test_expect_pauli_tile_passes(qs, dtype, n):
     assert abs(got - want) <= 1e-12 * sum(abs(t.coeff) for t in terms), (got, want)
     # the state is unchanged
     assert np.array_equal(s.to_numpy(), psi.astype(s.to_numpy().dtype))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_copy_from_host_async_then_plan(qs, dtype):
+    # the queued copy lands before work queued behind it on the state's
+    # stream: a plan run right after the call sees the copied state, bit for
+    # bit the same as after the synchronous copy
+    import torch
+    n = 14
+    psi = W.random_state(n, 77).astype(np.complex64 if dtype == "c64" else np.complex128)
+    host = torch.from_numpy(psi.copy()).pin_memory()
+    circ = qs.Circuit(W.brick(n, 6, 2))
+    a = qs.State(n, dtype).copy_from_host_async(host.data_ptr())
+    p = qs.Plan(circ, n, dtype, mode=qs.PLAN_FUSED, fuse_qubits=6 if dtype == "c64" else 5)
+    a.run(p)
+    b = qs.State(n, dtype).from_numpy(psi)
+    b.run(p)
+    assert np.array_equal(a.to_numpy(), b.to_numpy())

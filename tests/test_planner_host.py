@@ -42,12 +42,13 @@ CIRCUITS = [
 ]
 
 
+@pytest.mark.parametrize("search", [1, 0])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("name,n,make", CIRCUITS, ids=[c[0] for c in CIRCUITS])
-def test_fused_plan_replays_circuit(qs, dtype, k, name, n, make):
+def test_fused_plan_replays_circuit(qs, dtype, k, name, n, make, search):
     circ = make()
-    p = qs.Plan(qs.Circuit(circ), n, dtype, mode=qs.PLAN_FUSED, fuse_qubits=k)
+    p = qs.Plan(qs.Circuit(circ), n, dtype, mode=qs.PLAN_FUSED, fuse_qubits=k, search=search)
     psi = W.random_state(n, 100 + n + k)
     got = psi.copy()
     for i, (kind, _) in enumerate(p.step_info()):
@@ -59,6 +60,23 @@ def test_fused_plan_replays_circuit(qs, dtype, k, name, n, make):
     want = psi.copy()
     oracle.run_circuit(want, circ)
     assert np.max(np.abs(got - want)) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_block_order_search(qs, dtype):
+    # a wider search never gives more passes than the greedy order (the
+    # planner keeps the greedy schedule when it is cheaper), and on brick
+    # circuits it gives fewer; every gate is still applied exactly once (the
+    # replay test above checks the products)
+    fewer = 0
+    for n, circ in ((16, W.brick(16, 24, 6)), (14, W.qft(14)), (15, W.qsb(15, 2, sets=4)), (14, W.qv_like(14, 6, 1))):
+        c = qs.Circuit(circ)
+        passes = [qs.Plan(c, n, dtype, mode=qs.PLAN_FUSED, fuse_qubits=6, search=s).stats()["passes"] for s in (1, 4, 16)]
+        assert passes[1] <= passes[0] and passes[2] <= passes[0], passes
+        fewer += passes[2] < passes[0]
+    assert fewer >= 1
+    with pytest.raises(RuntimeError):
+        qs.Plan(qs.Circuit(W.brick(8, 2, 1)), 8, dtype, mode=qs.PLAN_FUSED, fuse_qubits=5, search=257)
 
 
 def test_step_matrix_errors(qs):
@@ -156,6 +174,6 @@ def test_circuit_hash_keys_the_tuner(qs, tmp_path):
     # cache files: absent, well formed, garbage -- all accepted
     qs.set_tune_cache(str(tmp_path / "none.txt"))
     f = tmp_path / "c.txt"
-    f.write_text("qs-tune-v1 0123456789abcdef plan 2 0 0 0 0 0 6 1.5\nnot a cache line\n")
+    f.write_text("qs-tune-v2 0123456789abcdef plan 2 0 0 0 0 0 6 0 1.5\nnot a cache line\n")
     qs.set_tune_cache(str(f))
     qs.set_tune_cache(None)
