@@ -65,10 +65,10 @@ S_BYTES = {"c64": 8, "c128": 16}
 # what each dtype's arithmetic is, for the report
 ARITHMETIC = {
     "c64": "complex64 storage; FP32 arithmetic (tensor-core blocks: FP16 hi/lo split products, ~2^-22 per product)",
-    "c128": ("complex128 storage (FP64); tensor-core blocks: each group's values on a 43-bit fixed-point grid split "
-             "into five 9-bit integer digits, exact FP16 digit products and exact FP32 level sums (error ~2^-44 of "
-             "the group's largest amplitude); tiles and per-gate kernels: double-float pairs (~2^-46, float "
-             "exponent range)"),
+    "c128": ("complex128 in and out (FP64); during a plan, double-float pairs (~2^-46 relative down to 2^-80, "
+             "float precision below, zero below 2^-126); tensor-core blocks: each group's values on a 43-bit "
+             "fixed-point grid split into five 9-bit integer digits, exact FP16 digit products and exact FP32 level "
+             "sums (error ~2^-44 of the group's largest amplitude)"),
 }
 
 
@@ -497,8 +497,8 @@ def run_ours(args):
         S = S_BYTES[dt]
         eff = st["metric_bytes"] / (ms / 1e3) / 1e9
         # launches per step: one per plan step, k_set_one, and for complex128
-        # plans without blocks the two storage-layout switches
-        extra = 1 + (2 if dt == "c128" and mode_name != "fused" else 0)
+        # the two storage-layout switches (FP64 <-> double-float)
+        extra = 1 + (2 if dt == "c128" else 0)
         results[dt] = {"ms_per_step": ms, "effective_GBps": eff * world, "gates_per_s": st["gates"] / (ms / 1e3) * world,
                        "plan": mode_name + (f" k={fq}" if mode_name == "fused" else ""),
                        "autotune": tuned.get(dt),

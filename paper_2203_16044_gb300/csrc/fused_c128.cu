@@ -154,7 +154,47 @@ __device__ __forceinline__ double df2d_scaled(dfl v, int delta) {
   return __longlong_as_double((long long)D);
 }
 
-template <int K, int MODE>
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // -126 <= e <= 127
+// the two floats of a 64-bit word of double-float storage (low half first)
+__device__ __forceinline__ float lo_f(unsigned long long w) { return __uint_as_float((unsigned)w); }
+__device__ __forceinline__ float hi_f(unsigned long long w) { return __uint_as_float((unsigned)(w >> 32)); }
+
+// Digits of X ~ x + y (x, y already on the grid: |x + y| < 2^43, y below
+// half an ulp of x) as FP32 integers: d_0 .. d_2 rounded to nearest
+// multiples of 2^36, 2^27, 2^18 of x (each remainder exact), then y added
+// (rounding below 2^-7) and d_3, d_4 to multiples of 2^9 and 1.  Rounding to
+// an integer: x 2^-s + 1.5 2^23 rounds once in FP32 (the FMA), and
+// subtracting 1.5 2^23 again is exact.  |d_0| <= 128, the others <= 256,
+// sum d_i 2^(36 - 9i) within 0.51 of x + y: the FP64 path's digits, by
+// floating-point operations instead of integer ones.
+__device__ __forceinline__ void digits_df(float x, float y, float (&d)[kDig][4], int i) {
+  constexpr float kR = 0x1.8p23f;
+  d[0][i] = fmaf(x, 0x1p-36f, kR) - kR;
+  x = fmaf(-d[0][i], 0x1p36f, x);
+  d[1][i] = fmaf(x, 0x1p-27f, kR) - kR;
+  x = fmaf(-d[1][i], 0x1p27f, x);
+  d[2][i] = fmaf(x, 0x1p-18f, kR) - kR;
+  x = fmaf(-d[2][i], 0x1p18f, x) + y;
+  d[3][i] = fmaf(x, 0x1p-9f, kR) - kR;
+  x = fmaf(-d[3][i], 0x1p9f, x);
+  d[4][i] = (x + kR) - kR;
+}
+
+// (h + l) 2^delta of the real and imaginary parts as one 16-byte word of
+// double-float storage (re h, re l, im h, im l); delta outside the FP32
+// scale range takes scalbnf (rows far from unit scale).
+__device__ __forceinline__ double2 scaled_pairs(dfl r, dfl i, int delta) {
+  float4 o;
+  if (delta >= -126 && delta <= 127) {
+    const float p = pow2f(delta);
+    o = make_float4(r.h * p, r.l * p, i.h * p, i.l * p);
+  } else {
+    o = make_float4(scalbnf(r.h, delta), scalbnf(r.l, delta), scalbnf(i.h, delta), scalbnf(i.l, delta));
+  }
+  return *reinterpret_cast<const double2*>(&o);
+}
+
+template <int K, int MODE, int IO>
 __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
     k_fused_c128(double2* __restrict__ a, u64 ngroups, const uint4* __restrict__ Bdig, int Fexp,
                  const __grid_constant__ C128Args args, const __grid_constant__ CUtensorMap tmap, int s_lo) {
@@ -246,36 +286,72 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       }
     }
     em = 0;
+    if constexpr (IO == 0) {
 #pragma unroll
-    for (int i = 0; i < APT; ++i) em = max(em, max(fp64_exp(v[i].x), fp64_exp(v[i].y)));
+      for (int i = 0; i < APT; ++i) em = max(em, max(fp64_exp(v[i].x), fp64_exp(v[i].y)));
+    } else {  // the high floats bound the values: em = biased FP32 exponent of the largest
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < APT; ++i) mx = fmaxf(mx, fmaxf(fabsf(lo_f(v[i].x)), fabsf(lo_f(v[i].y))));
+      em = (int)(__float_as_uint(mx) >> 23);
+    }
     emax_s[h * kUT + row] = em;
     if (!__syncthreads_and(ok ? 1 : 0)) return false;
     em = 0;
 #pragma unroll
     for (int j = 0; j < H; ++j) em = max(em, emax_s[j * kUT + row]);
-    unsigned long long xp[2 * APT];
-#pragma unroll
-    for (int i = 0; i < APT; ++i) {
-      xp[2 * i] = fixed_point(v[i].x, em);
-      xp[2 * i + 1] = fixed_point(v[i].y, em);
-    }
-    // digit slice j, column APT h + i: (d_j(re), d_j(im)) of amplitude
-    // APT h + i; FP16 bits 0x6400 | u are the value 1024 + u, so subtracting
-    // 1280 leaves the digit u - 256 exactly
     const uint32_t ta = tmem + lanes + (uint32_t)(buf * S::SET + h * APT);
-#pragma unroll
-    for (int j = 0; j < kDig; ++j) {
-      const int sh = 9 * (4 - j);
-      unsigned w[APT];
+    if constexpr (IO == 0) {
+      unsigned long long xp[2 * APT];
 #pragma unroll
       for (int i = 0; i < APT; ++i) {
-        const unsigned ur = (unsigned)(xp[2 * i] >> sh) & 511u, ui = (unsigned)(xp[2 * i + 1] >> sh) & 511u;
-        const unsigned raw = 0x64006400u | ur | (ui << 16);
-        const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&raw), k1280);
-        w[i] = *reinterpret_cast<const unsigned*>(&d);
+        xp[2 * i] = fixed_point(v[i].x, em);
+        xp[2 * i + 1] = fixed_point(v[i].y, em);
       }
-      if (APT == 8) tmem_st8(ta + (uint32_t)(j * D), w);
-      else tmem_st4(ta + (uint32_t)(j * D), w);
+      // digit slice j, column APT h + i: (d_j(re), d_j(im)) of amplitude
+      // APT h + i; FP16 bits 0x6400 | u are the value 1024 + u, so subtracting
+      // 1280 leaves the digit u - 256 exactly
+#pragma unroll
+      for (int j = 0; j < kDig; ++j) {
+        const int sh = 9 * (4 - j);
+        unsigned w[APT];
+#pragma unroll
+        for (int i = 0; i < APT; ++i) {
+          const unsigned ur = (unsigned)(xp[2 * i] >> sh) & 511u, ui = (unsigned)(xp[2 * i + 1] >> sh) & 511u;
+          const unsigned raw = 0x64006400u | ur | (ui << 16);
+          const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&raw), k1280);
+          w[i] = *reinterpret_cast<const unsigned*>(&d);
+        }
+        tmem_st4(ta + (uint32_t)(j * D), w);
+      }
+    } else {
+      // scale 2^(43 - E), E = em - 126: two factors where it exceeds 2^127
+      // (rows below 2^-85); an all-zero row (em = 0) scales to zero
+      const int sc = 169 - em;
+      const float s1 = em == 0 ? 0.f : pow2f(min(sc, 127)), s2 = pow2f(max(sc - 127, 0));
+      float dr[kDig][APT], di[kDig][APT];
+#pragma unroll
+      for (int i = 0; i < APT; ++i) {
+        float xr = lo_f(v[i].x) * s1, yr = hi_f(v[i].x) * s1, xi = lo_f(v[i].y) * s1, yi = hi_f(v[i].y) * s1;
+        if (sc > 127) {
+          xr *= s2;
+          yr *= s2;
+          xi *= s2;
+          yi *= s2;
+        }
+        digits_df(xr, yr, dr, i);
+        digits_df(xi, yi, di, i);
+      }
+#pragma unroll
+      for (int j = 0; j < kDig; ++j) {
+        unsigned w[APT];
+#pragma unroll
+        for (int i = 0; i < APT; ++i) {
+          const __half2 d = __floats2half2_rn(dr[j][i], di[j][i]);  // exact: integers below 2^9
+          w[i] = *reinterpret_cast<const unsigned*>(&d);
+        }
+        tmem_st4(ta + (uint32_t)(j * D), w);
+      }
     }
     asm volatile("tcgen05.wait::st.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -327,15 +403,20 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       else tmem_ld8(td + (uint32_t)(l * KR), acc[l]);
     }
     asm volatile("tcgen05.wait::ld.sync.aligned;");
-    const int delta = em - 1022 + Fexp - 14;
+    const int delta = (IO == 0 ? em - 1022 : em - 126) + Fexp - 14;
     const u64 base = MODE ? 0 : expand(valid ? gt + row : 0, args.ins);
 #pragma unroll
     for (int p = 0; p < APT; ++p) {
+      const dfl vr = levels_to_df(acc[0][2 * p], acc[1][2 * p], acc[2][2 * p], acc[3][2 * p], acc[4][2 * p]);
+      const dfl vi =
+          levels_to_df(acc[0][2 * p + 1], acc[1][2 * p + 1], acc[2][2 * p + 1], acc[3][2 * p + 1], acc[4][2 * p + 1]);
       double2 o;
-      o.x = df2d_scaled(levels_to_df(acc[0][2 * p], acc[1][2 * p], acc[2][2 * p], acc[3][2 * p], acc[4][2 * p]), delta);
-      o.y = df2d_scaled(
-          levels_to_df(acc[0][2 * p + 1], acc[1][2 * p + 1], acc[2][2 * p + 1], acc[3][2 * p + 1], acc[4][2 * p + 1]),
-          delta);
+      if constexpr (IO == 0) {
+        o.x = df2d_scaled(vr, delta);
+        o.y = df2d_scaled(vi, delta);
+      } else {  // the double-float pairs times 2^delta: (re h, re l, im h, im l)
+        o = scaled_pairs(vr, vi, delta);
+      }
       if (MODE == 2) {
         *reinterpret_cast<double2*>(outst + (h / S::BPR) * S::BOX + row * 128 + (((u0 + p) ^ (row & 7)) << 4)) = o;
       } else if (MODE == 1) {
@@ -440,19 +521,24 @@ qs_status c128_grid(qs_state* s, int K, Kern kern, int nthreads, size_t smem, in
   return QS_OK;
 }
 
-template <int K, int MODE>
-qs_status launch_mode(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, int s_lo) {
+template <int K, int MODE, int IO>
+qs_status launch_io(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, int s_lo) {
   typedef CShape<K, MODE> S;
   unsigned grid = 0;
-  qs_status st = c128_grid(s, K, k_fused_c128<K, MODE>, S::NT, S::SMEM, S::TCOLS, grid);
+  qs_status st = c128_grid(s, K, k_fused_c128<K, MODE, IO>, S::NT, S::SMEM, S::TCOLS, grid);
   if (st != QS_OK) return st;
-  k_fused_c128<K, MODE><<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<double2*>(s->amp), u64(1) << (s->n - K),
-                                                             Bdig, F, A, map, s_lo);
+  k_fused_c128<K, MODE, IO><<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<double2*>(s->amp),
+                                                                 u64(1) << (s->n - K), Bdig, F, A, map, s_lo);
   return launch_ok("k_fused_c128");
+}
+template <int K, int MODE>
+qs_status launch_mode(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, int s_lo,
+                      bool dfl) {
+  return dfl ? launch_io<K, MODE, 1>(s, A, Bdig, F, map, s_lo) : launch_io<K, MODE, 0>(s, A, Bdig, F, map, s_lo);
 }
 
 template <int K>
-qs_status launch_c128(qs_state* s, const int* q, const uint4* Bdig, int F) {
+qs_status launch_c128(qs_state* s, const int* q, const uint4* Bdig, int F, bool dfl) {
   C128Args A{};
   A.ins.k = K;
   A.ins.set = 0;
@@ -469,14 +555,14 @@ qs_status launch_c128(qs_state* s, const int* q, const uint4* Bdig, int F) {
   if (full && q[K - 1] == K - 1) {
     qs_status st = make_rows_tmap128(s, K, &map);
     if (st != QS_OK) return st;
-    return launch_mode<K, 2>(s, A, Bdig, F, map, 0);
+    return launch_mode<K, 2>(s, A, Bdig, F, map, 0, dfl);
   }
   if (full && q[0] >= 1 && q[K - 1] == q[0] + K - 1) {
     qs_status st = make_window_tmap128(s, K, q[0], &map);
     if (st != QS_OK) return st;
-    return launch_mode<K, 1>(s, A, Bdig, F, map, q[0]);
+    return launch_mode<K, 1>(s, A, Bdig, F, map, q[0], dfl);
   }
-  return launch_mode<K, 0>(s, A, Bdig, F, map, 0);
+  return launch_mode<K, 0>(s, A, Bdig, F, map, 0, dfl);
 }
 
 // FP16 bit pattern of d 2^-p for an integer |d| < 2^11 whose value stays in
@@ -551,11 +637,13 @@ qs_status tc128_prepare(const int* qubits, int k, const double* M, int* q_sorted
 }
 
 // Launch a prepared block; Bdig (device, 16-byte aligned) holds its digits.
-qs_status run_dense_tc128_prepared(qs_state* s, const int* q_sorted, int k, const void* Bdig, int F) {
+// dfl: the state is in double-float storage (re h, re l, im h, im l per
+// amplitude, as complex128 plans hold it) rather than FP64.
+qs_status run_dense_tc128_prepared(qs_state* s, const int* q_sorted, int k, const void* Bdig, int F, bool dfl) {
   const uint4* b = static_cast<const uint4*>(Bdig);
   switch (k) {
-    case 4: return launch_c128<4>(s, q_sorted, b, F);
-    case 5: return launch_c128<5>(s, q_sorted, b, F);
+    case 4: return launch_c128<4>(s, q_sorted, b, F, dfl);
+    case 5: return launch_c128<5>(s, q_sorted, b, F, dfl);
   }
   return fail(QS_EINVAL, "fused_c128: k=%d outside [4, 5]", k);
 }
@@ -570,7 +658,7 @@ qs_status run_dense_tc128(qs_state* s, const int* qubits, int k, const double* M
   if ((st = ensure_scratch(s, bytes)) != QS_OK) return st;
   cudaError_t e = cudaMemcpyAsync(s->scratch, dig.data(), bytes, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "fused_c128: digit upload");
-  return run_dense_tc128_prepared(s, q, k, s->scratch, F);
+  return run_dense_tc128_prepared(s, q, k, s->scratch, F, false);
 }
 
 // A complex128 tensor-core wait that gave up since the last call: QS_ETIMEOUT (and clear).

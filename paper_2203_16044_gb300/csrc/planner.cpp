@@ -112,7 +112,7 @@ qs_status run_step(qs_state* s, qs_plan* p, const qs_step& st) {
       const qs_block& b = p->blocks[st.tile_index];
       if (b.tc) {  // B uploaded with the plan's other blocks at the start of the run
         const float* bd = static_cast<const float*>(s->scratch) + b.b_off;
-        if (s->dtype == QS_C128) return run_dense_tc128_prepared(s, b.q_sorted, b.k, bd, b.f128);
+        if (s->dtype == QS_C128) return run_dense_tc128_prepared(s, b.q_sorted, b.k, bd, b.f128, false);
         return run_dense_tc_prepared(s, b.q_sorted, b.k, bd, 1);
       }
       return run_dense(s, b.q, b.k, b.M.data(), 1);  // a product of unitary gates
@@ -130,7 +130,12 @@ qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
     case qs_step::GATE_DIAG: return run_diag_dfl(s, st.q, st.nq, st.m);
     case qs_step::GATE_SWAP: return run_bitswap(s, &st.q[0], &st.q[1], 1);
     case qs_step::TILE: return run_tile(s, p, st.tile_index, true);
-    case qs_step::BLOCK: return fail(QS_EINVAL, "dense blocks do not run in double-float storage");
+    case qs_step::BLOCK: {
+      const qs_block& b = p->blocks[st.tile_index];
+      if (!b.tc) return fail(QS_EINVAL, "SIMT dense blocks do not run in double-float storage");
+      const float* bd = static_cast<const float*>(s->scratch) + b.b_off;
+      return run_dense_tc128_prepared(s, b.q_sorted, b.k, bd, b.f128, true);
+    }
     case qs_step::EXCHANGE: return run_exchange(s, p->exchanges[st.tile_index]);  // moves whole amplitudes
   }
   return fail(QS_EINVAL, "bad plan step");
@@ -140,9 +145,11 @@ qs_status run_step_dfl(qs_state* s, qs_plan* p, const qs_step& st) {
 // after each one).  A complex128 state is switched to double-float storage
 // for the duration of the plan and switched back even if a step fails.
 qs_status run_all_steps(qs_state* s, qs_plan* p, cudaEvent_t* ev) {
-  // complex128 plans switch to double-float storage unless they hold dense
-  // blocks (those run on the FP64 layout)
-  const bool dfl = s->dtype == QS_C128 && p->blocks.empty();
+  // complex128 plans switch to double-float storage unless they hold SIMT
+  // dense blocks (those run on the FP64 layout); the tensor-core blocks take
+  // either
+  bool dfl = s->dtype == QS_C128;
+  for (const qs_block& b : p->blocks) dfl = dfl && b.tc;
   qs_status r = dfl ? run_layout_dfl(s, true) : QS_OK;
   if (r == QS_OK && !p->tc_B.empty()) {
     // every tensor-core block's B in one upload (one synchronisation with

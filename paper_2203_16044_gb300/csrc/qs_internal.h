@@ -64,7 +64,7 @@ qs_status fused_tc_status();  // QS_ETIMEOUT if a tensor-core wait gave up since
 qs_status run_dense_tc128(qs_state* s, const int* qubits, int k, const double* M);
 qs_status tc128_prepare(const int* qubits, int k, const double* M, int* q_sorted, std::vector<uint16_t>& dig,
                         int* F);
-qs_status run_dense_tc128_prepared(qs_state* s, const int* q_sorted, int k, const void* Bdig, int F);
+qs_status run_dense_tc128_prepared(qs_state* s, const int* q_sorted, int k, const void* Bdig, int F, bool dfl);
 qs_status fused_c128_status();
 // In-place exchange of disjoint bit pairs (a[i], b[i]), i < npairs.
 qs_status run_bitswap(qs_state* s, const int* a, const int* b, int npairs);

@@ -407,6 +407,50 @@ def test_apply_fused_c128_dynamic_range_and_non_unitary(qs, k, mode):
     assert np.all(s.to_numpy()[gn == 0] == 0)
 
 
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("mode", ["window", "rows", "gathered"])
+def test_c128_plan_blocks_in_double_float_storage(qs, k, mode):
+    # inside a complex128 plan the tensor-core blocks read and write the
+    # double-float storage the plan switches to (digits formed by FP32
+    # rounding, outputs left as float pairs): one block of gates on the
+    # set, on a state whose groups span 2^-20 inside and down to 2^-89
+    # across (rows below 2^-85 take the two-factor scaling), some groups
+    # zero.  Every output within 2^-36 of its group's norm where the group's
+    # values stay above 2^-80; below that the storage itself holds values to
+    # float precision (the low float's last bit would leave FP32's normal
+    # range), so there within 2^-22; zero groups stay zero
+    n = 14
+    qsel = sorted(_block_sets(k, mode))
+    circ = []
+    for layer in range(3):
+        for q in qsel:
+            circ.append(W.Gate("U3", (q,), tuple(0.3 + 0.7 * i + 0.11 * q + layer for i in range(3))))
+        for a, b in zip(qsel[layer % 2::2], qsel[layer % 2 + 1::2]):
+            circ.append(W.Gate("CNOT", (a, b)))
+    p = qs.Plan(qs.Circuit(circ), n, "c128", mode=qs.PLAN_FUSED, fuse_qubits=k)
+    assert [kind for kind, _ in p.step_info()] == ["block"] and sorted(p.step_qubits(0)) == qsel
+    psi = W.random_state(n, 7970 + k)
+    x = np.arange(psi.size, dtype=np.int64)
+    r = np.zeros(psi.size, dtype=np.int64)
+    for i, q in enumerate(qsel):
+        r |= ((x >> q) & 1) << i
+    grp = x & ~sum(1 << q for q in qsel)
+    psi = psi * 2.0 ** (-20.0 * r / ((1 << k) - 1)) * 2.0 ** (-((grp * 7) % 90).astype(np.float64))
+    psi[(grp % 13) == 0] = 0
+    s = gpu_state(qs, psi, "c128")
+    s.run(p)
+    s.sync()
+    want = psi.copy()
+    oracle.run_circuit(want, circ)
+    got = s.to_numpy()
+    err = np.abs(got - want)
+    gn = _group_norms(psi, qsel)
+    tol = np.where(gn >= 2.0 ** -59, 2.0 ** -36, 2.0 ** -22) * gn
+    assert np.all(err <= tol), float(np.max(err / np.maximum(tol, 1e-300)))
+    assert np.any((gn > 0) & (gn < 2.0 ** -85))  # the two-factor scaling ran
+    assert np.all(got[gn == 0] == 0)
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("n", [5, 9, 14, 21])
 def test_expect_pauli_tile_passes(qs, dtype, n):
