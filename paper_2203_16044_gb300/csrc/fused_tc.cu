@@ -400,14 +400,18 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
 // 32 consecutive 8-byte words for every e when s >= 5, 32 / 2^s runs of
 // 2^s words D 2^s words apart otherwise (2-way bank conflicts at s = 3,
 // 4-way at s = 2; measured still faster than the per-thread gather).  The
-// stage is refilled with the next tile as soon as every thread has split
-// the current one into TMEM, so the copy runs under the MMAs and the
-// epilogue.  Arithmetic: the FP16 split above (kind::f16); the scatter uses
-// 8-byte stores.  Shared memory: stage 64 KB + B 64 KB at k = 6.  Blocks on
-// qubits 0 .. k-1 take the same kernel with ROWS set (below).
+// stage is refilled with the next tile as soon as every thread has read the
+// current one, so the copy runs under the split, the MMAs and the epilogue.
+// Two tiles are in flight on two TMEM sets (A hi, A lo and the accumulator
+// each): tile j is split and its MMAs issued, then tile j-1's epilogue runs
+// while those MMAs do (2 x 256 TMEM columns at k = 6, one CTA per SM).
+// Arithmetic: the FP16 split above (kind::f16).  Shared memory at k = 6:
+// stage 64 KB, output stage 64 KB, B 64 KB.  Blocks on qubits 0 .. k-1 take
+// the same kernel with ROWS set (below).
 // ---------------------------------------------------------------------------
-// ROWS = false: a window s .. s+k-1 (s >= 2), one 3-D box per tile, 8-byte
-// stores.  ROWS = true: the block is qubits 0 .. k-1, so a tile is 128
+// ROWS = false: a window s .. s+k-1 (s >= 2), one 3-D box per tile; the
+// outputs go out by one 3-D TMA store from a second stage at k = 6, by
+// 8-byte stores at k = 4, 5.  ROWS = true: the block is qubits 0 .. k-1, so a tile is 128
 // contiguous rows of 2^k amplitudes: 2^k / 16 boxes of 16 amplitudes x 128
 // rows each, in 128-byte-swizzled layout (16-byte unit c of row r stored at
 // unit c ^ (r mod 8)), one per 16-amplitude slice, which is exactly one
@@ -426,7 +430,8 @@ struct TShape {
   static constexpr uint32_t OUT = TSTORE ? STAGE : 0;
   static constexpr uint32_t BOX = kUT * 16 * 8;  // ROWS: one 16-amplitude slice of the tile
   static constexpr uint32_t B_BYTES = KR * KR * 2, LBO_B = (KR / 8) * 128, SBO = 128;
-  static constexpr uint32_t TCOLS = 2 * KR;  // A hi, A lo (KR / 2 each), accumulator
+  static constexpr uint32_t SETCOLS = 2 * KR;  // one tile's TMEM: A hi, A lo (KR / 2 each), accumulator
+  static constexpr uint32_t TCOLS = 2 * SETCOLS;  // two tiles in flight
   static constexpr size_t SMEM = STAGE + OUT + 2 * (size_t)B_BYTES + 32 + 2 * H * kUT * sizeof(float);
   static constexpr int MINB = K == 6 ? 1 : (K == 5 ? 2 : 4);  // register-limited
 };
@@ -444,14 +449,14 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   unsigned char* outst = sm + S::STAGE;  // ROWS: the output stage
   unsigned char* Bhi = sm + S::STAGE + S::OUT;
   unsigned char* Blo = Bhi + S::B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] tile loaded, [1] MMAs done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + S::B_BYTES);  // [0] tile loaded, [1 + b] MMAs of set b done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
   uint32_t* bmax_s = tslot + 1;
   float* nin_s = reinterpret_cast<float*>(mbar + 4);  // [H][kUT] partial input norms
   float* nout_s = nin_s + H * kUT;                     // [H][kUT] partial output norms
   const int t = threadIdx.x, warp = t >> 5;
   const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
-  const uint32_t mb_full = smem_u32(mbar), mb_mma = smem_u32(mbar + 1);
+  const uint32_t mb_full = smem_u32(mbar), mb_mma0 = smem_u32(mbar + 1);
   const u64 gstep = (u64)gridDim.x * kUT;
   const u64 lmask = (u64(1) << s_lo) - 1;
   u64 g = (u64)blockIdx.x * kUT;
@@ -467,7 +472,8 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   if (t == 0) {
     *bmax_s = 0u;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_full));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma0 + 8));
     asm volatile("fence.mbarrier_init.release.cluster;");
     if (g < ngroups) tile_load(g);  // under the B set-up
   }
@@ -505,14 +511,19 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
   const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t ta = tmem + lanes + (uint32_t)(h * 16), td = tmem + lanes + (uint32_t)(KR + h * 32);
   const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
   constexpr uint32_t idesc = umma_idesc_f16(kUT, KR);
   const int sp = s_lo < 7 ? s_lo : 7;
   // this row's words in the stage: element e at sbase + (e << sp)
   const int sbase = (((row >> sp) * D) << sp) + (row & ((1 << sp) - 1));
-  uint32_t ph_full = 0, ph_mma = 0;
-  while (g < ngroups) {
+  uint32_t ph_full = 0, ph_mma = 0;  // ph_mma bit b: TMEM set b
+  uint32_t outstanding = 0;           // bit b: MMAs of set b issued and not yet waited for
+
+  // Tile gt from the stage into TMEM set b (A hi, A lo), then its MMAs
+  // issued; e (the row scale) and nin (the row's input norm^2) for its
+  // epilogue.  The next tile's copy starts as soon as every thread has read
+  // the stage.  False (in every thread) if a bounded wait gave up.
+  auto split_issue = [&](u64 gt, int b, int& e, float& nin) -> bool {
     const bool loaded = mbar_wait(mb_full, ph_full);
     ph_full ^= 1u;
     float2 v[16];
@@ -529,18 +540,17 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = stage[sbase + ((16 * h + i) << sp)];
     }
-    float nin = 0.f;
+    nin = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) nin = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, nin));
     nin_s[h * kUT + row] = nin;
-    if (!__syncthreads_and(loaded ? 1 : 0)) {
-      if (t == 0) atomicExch(&g_umma_timeout, 1);
-      break;
-    }
+    if (!__syncthreads_and(loaded ? 1 : 0)) return false;
+    if (t == 0 && gt + gstep < ngroups) tile_load(gt + gstep);  // the stage has been read
     nin = 0.f;
 #pragma unroll
     for (int i = 0; i < H; ++i) nin += nin_s[i * kUT + row];
-    const int e = (nin > 0.f && nin < INFINITY) ? scale_exp((fexp(nin) + 2) >> 1, -126 - f, 126 - f) : 0;
+    e = (nin > 0.f && nin < INFINITY) ? scale_exp((fexp(nin) + 2) >> 1, -126 - f, 126 - f) : 0;
+    const uint32_t ta = tmem + lanes + (uint32_t)(b * S::SETCOLS + h * 16);
     {
       const float sx = pow2f(e);
       uint32_t hv[16], lv[16];
@@ -551,34 +561,41 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
     }
     asm volatile("tcgen05.wait::st.sync.aligned;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // A written, and every thread is done with the stage
+    __syncthreads();  // A of set b written by every thread
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (t == 0) {
-      if (g + gstep < ngroups) tile_load(g + gstep);
+      const uint32_t set = tmem + (uint32_t)(b * S::SETCOLS);
 #pragma unroll
       for (int ks = 0; ks < KR / 16; ++ks) {
         const uint32_t bo = ks * 2 * S::LBO_B;
         const uint64_t dbh = umma_desc(bhi + bo, S::LBO_B, S::SBO), dbl = umma_desc(blo + bo, S::LBO_B, S::SBO);
-        const uint32_t ahi_t = tmem + (uint32_t)(ks * 8), alo_t = tmem + (uint32_t)(KR / 2 + ks * 8);
-        umma_f16_ta(tmem + KR, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
-        umma_f16_ta(tmem + KR, ahi_t, dbl, idesc, 1u);
-        umma_f16_ta(tmem + KR, ahi_t, dbh, idesc, 1u);
+        const uint32_t ahi_t = set + (uint32_t)(ks * 8), alo_t = set + (uint32_t)(KR / 2 + ks * 8);
+        umma_f16_ta(set + KR, alo_t, dbh, idesc, ks > 0 ? 1u : 0u);
+        umma_f16_ta(set + KR, ahi_t, dbl, idesc, 1u);
+        umma_f16_ta(set + KR, ahi_t, dbh, idesc, 1u);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma));
-      // the previous tile's TMA stores must have read the output stage
-      if (S::TSTORE) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma0 + 8 * b));
     }
-    const u64 base = S::TSTORE ? 0 : expand(g + row, args.ins);
-    if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma) ? 1 : 0)) {
-      if (t == 0) atomicExch(&g_umma_timeout, 1);
-      break;
-    }
-    ph_mma ^= 1u;
+    outstanding |= 1u << b;
+    return true;
+  };
+  // The outputs of tile gt from TMEM set b: scaled back, the group norm
+  // restored, and stored (through the output stage and a TMA store, or
+  // directly).
+  auto epilogue = [&](u64 gt, int b, int e, float nin) -> bool {
+    // the previous tile's TMA stores must have read the output stage
+    if (S::TSTORE && t == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    const bool done = mbar_wait(mb_mma0 + 8 * b, (ph_mma >> b) & 1u);
+    if (!__syncthreads_and(done ? 1 : 0)) return false;
+    ph_mma ^= 1u << b;
+    outstanding &= ~(1u << b);
     asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t td = tmem + lanes + (uint32_t)(b * S::SETCOLS + KR + h * 32);
     float o[32];
     tmem_ld16(td, o);
     tmem_ld16(td + 16, o + 16);
     asm volatile("tcgen05.wait::ld.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
     const float so = pow2f(-(e + f));
 #pragma unroll
     for (int j = 0; j < 32; ++j) o[j] *= so;
@@ -604,7 +621,7 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
       __syncthreads();
       if (t == 0) {
 #pragma unroll
-        for (int b = 0; b < D / 16; ++b) tma_store_2d(&tmap, 16 * b, (int)g, smem_u32(outst) + b * S::BOX);
+        for (int bx = 0; bx < D / 16; ++bx) tma_store_2d(&tmap, 16 * bx, (int)gt, smem_u32(outst) + bx * S::BOX);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     } else if (S::TSTORE) {
@@ -618,14 +635,39 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
       if (t == 0) {
-        tma_store_3d(&tmap, (int)(g & lmask), 0, (int)(g >> s_lo), smem_u32(outst));
+        tma_store_3d(&tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), smem_u32(outst));
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     } else {
-      group_store<D, CH>(a, base, true, args.spread, 0, j0, o, gsc);
+      group_store<D, CH>(a, expand(gt + row, args.ins), true, args.spread, 0, j0, o, gsc);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
+    return true;
+  };
+
+  // Two tiles in flight on the two TMEM sets: tile g is split and its MMAs
+  // issued, then the previous tile's epilogue runs while those MMAs do.
+  bool fine = true, prev = false;
+  u64 gp = 0;
+  int ep = 0, it = 0;
+  float ninp = 0.f;
+  while (g < ngroups) {
+    int e = 0;
+    float nin = 0.f;
+    if (!(fine = split_issue(g, it & 1, e, nin))) break;
+    if (prev && !(fine = epilogue(gp, (it - 1) & 1, ep, ninp))) break;
+    prev = true;
+    gp = g;
+    ep = e;
+    ninp = nin;
     g += gstep;
+    ++it;
+  }
+  if (fine && prev) fine = epilogue(gp, (it - 1) & 1, ep, ninp);
+  if (!fine) {
+    if (t == 0) atomicExch(&g_umma_timeout, 1);
+    // let MMAs already issued finish before the tensor memory is freed (bounded)
+    for (int b2 = 0; b2 < 2; ++b2)
+      if ((outstanding >> b2) & 1u) mbar_wait(mb_mma0 + 8 * b2, (ph_mma >> b2) & 1u);
   }
   if (S::TSTORE && t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   __syncthreads();
