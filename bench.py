@@ -281,33 +281,36 @@ def circuit_flops(circ, n):
     return f
 
 
+def box_runs(q, n):
+    """Runs of consecutive qubits of one class (the block's, or the others')
+    over 0..n-1 once the tile's 7 lowest non-block qubits are taken: the
+    dimensions of the TMA view a block's tiles move through (at most 5)."""
+    inq = set(q)
+    cls = [1 if b in inq else 0 for b in range(n)]
+    return 1 + sum(1 for b in range(1, n) if cls[b] != cls[b - 1])
+
+
 def step_kernel(plan, i, kind):
     """The kernel a plan step launches: block steps are told apart by their
-    qubits (complex64, at least 128 groups: a window of consecutive qubits
-    from 2 up runs k_fused_umma_tma<k,window>, qubits 0..k-1
-    k_fused_umma_tma<k,rows>; other complex64 blocks k_fused_umma<k>;
-    complex128 k = 4, 5 blocks k_fused_c128<k,rows|window|gather> (a window
-    from qubit 1 up); other blocks the SIMT k_dense); other steps keep their
-    kind."""
+    qubits (at least 128 groups: qubits 0..k-1 run the rows form of the TMA
+    kernel; a set without qubit 0 whose qubits form at most 5 runs its box
+    form, reported as "window" for consecutive qubits and "box" otherwise;
+    other sets gather per thread: complex64 k_fused_umma<k>, complex128
+    k_fused_c128<k,gather>); other blocks the SIMT k_dense; other steps keep
+    their kind."""
     if kind != "block":
         return kind
     q = sorted(plan.step_qubits(i))
     k = len(q)
-    if plan.dtype == "c128" and k in (4, 5):
-        full = plan.n - k >= 7
-        if full and q == list(range(k)):
-            return "k_fused_c128<%d,rows>" % k
-        if full and q[0] >= 1 and q == list(range(q[0], q[0] + k)):
-            return "k_fused_c128<%d,window>" % k
-        return "k_fused_c128<%d,gather>" % k
-    if plan.dtype == "c64" and k >= 4:
-        full = plan.n - k >= 7
-        if full and q[0] >= 2 and q == list(range(q[0], q[0] + k)):
-            return "k_fused_umma_tma<%d,window>" % k
-        if full and q == list(range(k)):
-            return "k_fused_umma_tma<%d,rows>" % k
-        return "k_fused_umma<%d>" % k
-    return "k_dense<%d>" % k
+    if not ((plan.dtype == "c128" and k in (4, 5)) or (plan.dtype == "c64" and k >= 4)):
+        return "k_dense<%d>" % k
+    full = plan.n - k >= 7
+    name = "k_fused_c128" if plan.dtype == "c128" else "k_fused_umma_tma"
+    if full and q == list(range(k)):
+        return "%s<%d,rows>" % (name, k)
+    if full and q[0] >= 1 and box_runs(q, plan.n) <= 5:
+        return "%s<%d,%s>" % (name, k, "window" if q == list(range(q[0], q[0] + k)) else "box")
+    return "k_fused_c128<%d,gather>" % k if plan.dtype == "c128" else "k_fused_umma<%d>" % k
 
 
 def kernel_roofline(plan, step_ms, peak):

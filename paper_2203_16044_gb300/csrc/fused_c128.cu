@@ -47,9 +47,10 @@
 //   MODE 2: the block is qubits 0 .. k-1: 2^k / 8 two-dimensional TMA boxes
 //           (8 amplitudes x 128 rows, 128-byte swizzle) in, the same boxes
 //           out by TMA stores from a second stage;
-//   MODE 1: a window s .. s+k-1 with s >= 1: one three-dimensional TMA box
-//           (lo, e, hi) per tile in, the same box out by a TMA store from a
-//           second stage;
+//   MODE 1: any set without qubit 0 forming at most 5 runs with the other
+//           qubits (windows, two-run sets): one TMA box of a view with up
+//           to 5 dimensions per tile in (make_runs_tmap), the same box out
+//           by a TMA store from a second stage;
 //   MODE 0: any other set: per-thread 16-byte gathers and scatters.
 // The next tile's TMA copy is issued as soon as the current one has been
 // split, so it runs under the MMAs and the epilogue.  Where the time goes
@@ -82,6 +83,7 @@ __device__ int g_c128_timeout;
 struct C128Args {
   Ins ins;         // zero insertion at the k qubits
   u64 spread[32];  // spread[r]: OR of 2^qubits[i] over the set bits i of r
+  RunBox rb;       // MODE 1: the tile's box (make_runs_tmap)
 };
 
 template <int K, int MODE>
@@ -197,7 +199,7 @@ __device__ __forceinline__ double2 scaled_pairs(dfl r, dfl i, int delta) {
 template <int K, int MODE, int IO>
 __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
     k_fused_c128(double2* __restrict__ a, u64 ngroups, const uint4* __restrict__ Bdig, int Fexp,
-                 const __grid_constant__ C128Args args, const __grid_constant__ CUtensorMap tmap, int s_lo) {
+                 const __grid_constant__ C128Args args, const __grid_constant__ CUtensorMap tmap) {
   typedef CShape<K, MODE> S;
   constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT, APT = S::APT;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -211,7 +213,6 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   const int row = t & (kUT - 1), h = t / kUT;
   const uint32_t mb0 = smem_u32(mbar);
   const u64 gstep = (u64)gridDim.x * kUT;
-  const u64 lmask = (u64(1) << s_lo) - 1;
   auto tile_load = [&](u64 gt, int st) {  // one thread
     const uint32_t mb = mb0 + 8 * st, dst = smem_u32(stage) + st * S::TILE;
     mbar_expect_tx(mb, S::TILE);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
 #pragma unroll
       for (int b = 0; b < D / 8; ++b) tma_load_2d(dst + b * S::BOX, &tmap, 16 * b, (int)gt, mb);
     } else {
-      tma_load_3d(dst, &tmap, (int)(2 * (gt & lmask)), 0, (int)(gt >> s_lo), mb);
+      run_load(dst, &tmap, gt, args.rb, 2, mb);
     }
   };
   u64 g = (u64)blockIdx.x * kUT;
@@ -248,9 +249,15 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   const uint32_t tmem = *tslot;
   const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bsa = smem_u32(Bs);
-  const int sp = s_lo < 7 ? s_lo : 7;
-  // MODE 1: element e of this row in a stage at sbase + (e << sp) (amplitudes)
-  const int sbase = (((row >> sp) * D) << sp) + (row & ((1 << sp) - 1));
+  // MODE 1: element APT h + i of this row at pbase + (multipliers of i's bits) (amplitudes)
+  int pbase = 0;
+  if (MODE == 1) {
+    pbase = run_row_pos(args.rb, row);
+#pragma unroll
+    for (int j = 2; j < 6; ++j)
+      if (((APT * h) >> j) & 1) pbase += args.rb.multe[j];
+  }
+  const int pm[2] = {args.rb.multe[0], args.rb.multe[1]};
   // MODE 2: this thread's amplitudes are units u0 .. u0 + APT - 1 of box h / BPR
   const int u0 = (h % S::BPR) * APT;
   const __half2 k1280 = __floats2half2_rn(1280.f, 1280.f);
@@ -282,7 +289,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       } else {
         const ulonglong2* st2 = reinterpret_cast<const ulonglong2*>(stg);
 #pragma unroll
-        for (int i = 0; i < APT; ++i) v[i] = st2[sbase + ((APT * h + i) << sp)];
+        for (int i = 0; i < APT; ++i) v[i] = st2[run_elem_pos<2>(pbase, pm, i)];
       }
     }
     em = 0;
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       if (MODE == 2) {
         *reinterpret_cast<double2*>(outst + (h / S::BPR) * S::BOX + row * 128 + (((u0 + p) ^ (row & 7)) << 4)) = o;
       } else if (MODE == 1) {
-        reinterpret_cast<double2*>(outst)[sbase + ((APT * h + p) << sp)] = o;  // the input stage's layout
+        reinterpret_cast<double2*>(outst)[run_elem_pos<2>(pbase, pm, p)] = o;  // the input stage's layout
       } else if (valid) {
         a[base | args.spread[APT * h + p]] = o;
       }
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
 #pragma unroll
           for (int b = 0; b < D / 8; ++b) tma_store_2d(&tmap, 16 * b, (int)gt, smem_u32(outst) + b * S::BOX);
         } else {
-          tma_store_3d(&tmap, (int)(2 * (gt & lmask)), 0, (int)(gt >> s_lo), smem_u32(outst));
+          run_store(&tmap, gt, args.rb, 2, smem_u32(outst));
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
@@ -481,24 +488,6 @@ qs_status make_rows_tmap128(qs_state* st, int k, CUtensorMap* map) {
   return QS_OK;
 }
 
-// The 3-D tensor map (lo, e, hi) of a complex128 state for a block on
-// qubits s .. s+k-1 (64-bit words, two per amplitude), box = one tile.
-qs_status make_window_tmap128(qs_state* st, int k, int s_lo, CUtensorMap* map) {
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  qs_status s0 = tmap_encoder(&encode);
-  if (s0 != QS_OK) return s0;
-  const int sp = s_lo < 7 ? s_lo : 7;
-  const cuuint64_t dims[3] = {cuuint64_t(2) << s_lo, cuuint64_t(1) << k, cuuint64_t(1) << (st->n - s_lo - k)};
-  const cuuint64_t strides[2] = {(cuuint64_t(1) << s_lo) * 16, (cuuint64_t(1) << (s_lo + k)) * 16};
-  const cuuint32_t box[3] = {2u << sp, 1u << k, 1u << (7 - sp)};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, st->amp, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_c128: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return QS_OK;
-}
-
 // CTAs per SM from shared memory, registers and TMEM columns, times the SMs.
 template <typename Kern>
 qs_status c128_grid(qs_state* s, int K, Kern kern, int nthreads, size_t smem, int tcols, unsigned& grid) {
@@ -522,19 +511,18 @@ qs_status c128_grid(qs_state* s, int K, Kern kern, int nthreads, size_t smem, in
 }
 
 template <int K, int MODE, int IO>
-qs_status launch_io(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, int s_lo) {
+qs_status launch_io(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map) {
   typedef CShape<K, MODE> S;
   unsigned grid = 0;
   qs_status st = c128_grid(s, K, k_fused_c128<K, MODE, IO>, S::NT, S::SMEM, S::TCOLS, grid);
   if (st != QS_OK) return st;
   k_fused_c128<K, MODE, IO><<<grid, S::NT, S::SMEM, s->stream>>>(static_cast<double2*>(s->amp),
-                                                                 u64(1) << (s->n - K), Bdig, F, A, map, s_lo);
+                                                                 u64(1) << (s->n - K), Bdig, F, A, map);
   return launch_ok("k_fused_c128");
 }
 template <int K, int MODE>
-qs_status launch_mode(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, int s_lo,
-                      bool dfl) {
-  return dfl ? launch_io<K, MODE, 1>(s, A, Bdig, F, map, s_lo) : launch_io<K, MODE, 0>(s, A, Bdig, F, map, s_lo);
+qs_status launch_mode(qs_state* s, const C128Args& A, const uint4* Bdig, int F, const CUtensorMap& map, bool dfl) {
+  return dfl ? launch_io<K, MODE, 1>(s, A, Bdig, F, map) : launch_io<K, MODE, 0>(s, A, Bdig, F, map);
 }
 
 template <int K>
@@ -555,14 +543,12 @@ qs_status launch_c128(qs_state* s, const int* q, const uint4* Bdig, int F, bool 
   if (full && q[K - 1] == K - 1) {
     qs_status st = make_rows_tmap128(s, K, &map);
     if (st != QS_OK) return st;
-    return launch_mode<K, 2>(s, A, Bdig, F, map, 0, dfl);
+    return launch_mode<K, 2>(s, A, Bdig, F, map, dfl);
   }
-  if (full && q[0] >= 1 && q[K - 1] == q[0] + K - 1) {
-    qs_status st = make_window_tmap128(s, K, q[0], &map);
-    if (st != QS_OK) return st;
-    return launch_mode<K, 1>(s, A, Bdig, F, map, q[0], dfl);
-  }
-  return launch_mode<K, 0>(s, A, Bdig, F, map, 0, dfl);
+  qs_status est = QS_OK;
+  if (full && make_runs_tmap(s->amp, s->n, K, q, 2, &map, &A.rb, &est)) return launch_mode<K, 1>(s, A, Bdig, F, map, dfl);
+  if (est != QS_OK) return est;
+  return launch_mode<K, 0>(s, A, Bdig, F, map, dfl);
 }
 
 // FP16 bit pattern of d 2^-p for an integer |d| < 2^11 whose value stays in

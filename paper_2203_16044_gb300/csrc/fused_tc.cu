@@ -17,8 +17,9 @@
 // for the complex64 path.
 //
 // Two kernels, by the block's qubits (sorted ascending):
-//   k_fused_umma_tma   a window s .. s+k-1 with s >= 2, or qubits 0 .. k-1:
-//                      each tile moves by TMA (one 3-D box, or 2^k / 16
+//   k_fused_umma_tma   a set without qubit 0 forming at most 5 runs with the
+//                      other qubits, or qubits 0 .. k-1: each tile moves by
+//                      TMA (one box of up to 5 dimensions, or 2^k / 16
 //                      swizzled 2-D boxes in and out); FP16 parts.
 //   k_fused_umma       any other set: per-thread gathers; TF32 parts.
 //
@@ -61,6 +62,7 @@ __device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) 
 struct FusedArgs {
   Ins ins;         // zero insertion at the k qubits (amplitude index space)
   u64 spread[64];  // spread[r]: OR of 2^qubits[i] over the set bits i of r
+  RunBox rb;       // k_fused_umma_tma, ROWS = false: the tile's box (make_runs_tmap)
 };
 
 // ---------------------------------------------------------------------------
@@ -99,7 +101,7 @@ __device__ __forceinline__ float norm_correction(float nin, float nout) {
 //            lane both groups' amplitude 2j + 1, and group_take exchanges the
 //            halves.  The loads have no dependent instruction until the
 //            tile is consumed, so a prefetch stays in flight.
-// (Blocks on a window of qubits from 2 up, or on qubits 0 .. k-1, run in
+// (Blocks whose tiles are TMA boxes, or on qubits 0 .. k-1, run in
 // k_fused_umma_tma instead.)
 template <int D, int CH>
 __device__ __forceinline__ void group_load(const float2* __restrict__ a, u64 base, bool valid, const u64* spread,
@@ -389,29 +391,27 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
   lo = h2bits(__floats2half2_rn(a - hf.x, b - hf.y));
 }
 // ---------------------------------------------------------------------------
-// Blocks on a window of consecutive qubits s .. s+k-1 with s >= 2 (full
-// tiles): k_fused_umma_tma.  An amplitude index is then hi 2^(s+k) + e 2^s
-// + lo (e the block index, lo < 2^s), so a tile of 128 consecutive groups is
-// one box of the 3-D tensor (lo, e, hi): a single TMA copy
-// (cp.async.bulk.tensor, completion counted on an mbarrier) moves it into
-// shared memory, with no per-thread load instructions and no registers
-// held.  In the stage, element e of tile row r sits at
-// ((r >> sp) D + e) 2^sp + (r mod 2^sp), sp = min(s, 7): a warp's 32 rows are
-// 32 consecutive 8-byte words for every e when s >= 5, 32 / 2^s runs of
-// 2^s words D 2^s words apart otherwise (2-way bank conflicts at s = 3,
-// 4-way at s = 2; measured still faster than the per-thread gather).  The
-// stage is refilled with the next tile as soon as every thread has read the
-// current one, so the copy runs under the split, the MMAs and the epilogue.
-// Two tiles are in flight on two TMEM sets (A hi, A lo and the accumulator
-// each): tile j is split and its MMAs issued, then tile j-1's epilogue runs
-// while those MMAs do (2 x 256 TMEM columns at k = 6, one CTA per SM).
-// Arithmetic: the FP16 split above (kind::f16).  Shared memory at k = 6:
-// stage 64 KB, output stage 64 KB, B 64 KB.  Blocks on qubits 0 .. k-1 take
-// the same kernel with ROWS set (below).
+// Blocks on any qubit set without qubit 0 whose qubits, with the tile's,
+// form at most 5 runs (windows, two-run sets; full tiles):
+// k_fused_umma_tma.  A tile of 128 consecutive groups is then one box of a
+// view of the state with up to 5 dimensions (make_runs_tmap): a single TMA
+// copy (cp.async.bulk.tensor, completion counted on an mbarrier) moves it
+// into shared memory, with no per-thread load instructions and no registers
+// held; element e of tile row r lands at a position the view's dimension
+// order fixes (per-bit multipliers in the kernel arguments).  The stage is
+// refilled
+// with the next tile as soon as every thread has read the current one, so
+// the copy runs under the split, the MMAs and the epilogue.  Two tiles are
+// in flight on two TMEM sets (A hi, A lo and the accumulator each): tile j
+// is split and its MMAs issued, then tile j-1's epilogue runs while those
+// MMAs do (2 x 256 TMEM columns at k = 6, one CTA per SM).  Arithmetic: the
+// FP16 split above (kind::f16).  Shared memory at k = 6: stage 64 KB,
+// output stage 64 KB, B 64 KB.  Blocks on qubits 0 .. k-1 take the same
+// kernel with ROWS set (below).
 // ---------------------------------------------------------------------------
-// ROWS = false: a window s .. s+k-1 (s >= 2), one 3-D box per tile; the
-// outputs go out by one 3-D TMA store from a second stage at k = 6, by
-// 8-byte stores at k = 4, 5.  ROWS = true: the block is qubits 0 .. k-1, so a tile is 128
+// ROWS = false: the run box above; the outputs go out by one TMA store from
+// a second stage at k = 6, by 8-byte stores at k = 4, 5.  ROWS = true: the
+// block is qubits 0 .. k-1, so a tile is 128
 // contiguous rows of 2^k amplitudes: 2^k / 16 boxes of 16 amplitudes x 128
 // rows each, in 128-byte-swizzled layout (16-byte unit c of row r stored at
 // unit c ^ (r mod 8)), one per 16-amplitude slice, which is exactly one
@@ -439,8 +439,7 @@ struct TShape {
 template <int K, bool ROWS>
 __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
     k_fused_umma_tma(float2* __restrict__ a, u64 ngroups, const float* __restrict__ Bg,
-                     const __grid_constant__ FusedArgs args, const __grid_constant__ CUtensorMap tmap, int renorm,
-                     int s_lo) {
+                     const __grid_constant__ FusedArgs args, const __grid_constant__ CUtensorMap tmap, int renorm) {
   typedef TShape<K, ROWS> S;
   constexpr int D = S::D, KR = S::KR, H = S::H, NT = S::NT;
   constexpr int CH = 8;
@@ -458,7 +457,6 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   const int row = t & (kUT - 1), h = t / kUT, j0 = h * CH;
   const uint32_t mb_full = smem_u32(mbar), mb_mma0 = smem_u32(mbar + 1);
   const u64 gstep = (u64)gridDim.x * kUT;
-  const u64 lmask = (u64(1) << s_lo) - 1;
   u64 g = (u64)blockIdx.x * kUT;
   auto tile_load = [&](u64 gt) {  // one thread
     mbar_expect_tx(mb_full, S::STAGE);
@@ -466,7 +464,7 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
 #pragma unroll
       for (int b = 0; b < D / 16; ++b) tma_load_2d(smem_u32(stage) + b * S::BOX, &tmap, 16 * b, (int)gt, mb_full);
     } else {
-      tma_load_3d(smem_u32(stage), &tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), mb_full);
+      run_load(smem_u32(stage), &tmap, gt, args.rb, 1, mb_full);
     }
   };
   if (t == 0) {
@@ -513,9 +511,10 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
   constexpr uint32_t idesc = umma_idesc_f16(kUT, KR);
-  const int sp = s_lo < 7 ? s_lo : 7;
-  // this row's words in the stage: element e at sbase + (e << sp)
-  const int sbase = (((row >> sp) * D) << sp) + (row & ((1 << sp) - 1));
+  // ROWS = false: element 16 h + i of this row at pbase + (multipliers of i's bits)
+  const int pbase = ROWS ? 0
+                         : run_row_pos(args.rb, row) + ((h & 1) ? args.rb.multe[4] : 0) + ((h & 2) ? args.rb.multe[5] : 0);
+  const int pm[4] = {args.rb.multe[0], args.rb.multe[1], args.rb.multe[2], args.rb.multe[3]};
   uint32_t ph_full = 0, ph_mma = 0;  // ph_mma bit b: TMEM set b
   uint32_t outstanding = 0;           // bit b: MMAs of set b issued and not yet waited for
 
@@ -538,7 +537,7 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = stage[sbase + ((16 * h + i) << sp)];
+      for (int i = 0; i < 16; ++i) v[i] = stage[run_elem_pos<4>(pbase, pm, i)];
     }
     nin = 0.f;
 #pragma unroll
@@ -625,17 +624,17 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     } else if (S::TSTORE) {
-      // the output tile in the input stage's layout, then one 3-D TMA store
+      // the output tile in the input stage's layout, then one TMA store
       float2* outw = reinterpret_cast<float2*>(outst);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int j = 2 * i;
-        outw[sbase + ((16 * h + i) << sp)] = make_float2(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]));
+        outw[run_elem_pos<4>(pbase, pm, i)] = make_float2(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]));
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
       if (t == 0) {
-        tma_store_3d(&tmap, (int)(gt & lmask), 0, (int)(gt >> s_lo), smem_u32(outst));
+        run_store(&tmap, gt, args.rb, 1, smem_u32(outst));
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     } else {
@@ -692,24 +691,6 @@ qs_status make_rows_tmap(qs_state* st, int k, CUtensorMap* map) {
   return QS_OK;
 }
 
-// The 3-D tensor map (lo, e, hi) of a state for a block on qubits
-// s .. s+k-1, box = one tile (128 groups).
-qs_status make_block_tmap(qs_state* st, int k, int s_lo, CUtensorMap* map) {
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  qs_status s0 = tmap_encoder(&encode);
-  if (s0 != QS_OK) return s0;
-  const int sp = s_lo < 7 ? s_lo : 7;
-  const cuuint64_t dims[3] = {cuuint64_t(1) << s_lo, cuuint64_t(1) << k, cuuint64_t(1) << (st->n - s_lo - k)};
-  const cuuint64_t strides[2] = {(cuuint64_t(1) << s_lo) * 8, (cuuint64_t(1) << (s_lo + k)) * 8};
-  const cuuint32_t box[3] = {1u << sp, 1u << k, 1u << (7 - sp)};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, st->amp, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return QS_OK;
-}
-
 // Grid for a block kernel: CTAs per SM from shared memory, registers and TMEM
 // columns (the occupancy query does not know about TMEM), times the SMs.
 template <int K, typename Kern>
@@ -747,21 +728,24 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
     st = block_grid<K>(s, k_fused_umma_tma<K, true>, ST::NT, ST::SMEM, ST::TCOLS, grid);
     if (st != QS_OK) return st;
     k_fused_umma_tma<K, true><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A,
-                                                                       map, renorm, 0);
+                                                                       map, renorm);
     return launch_ok("k_fused_umma_tma");
   }
-  // a window of consecutive qubits from 2 up: one TMA box per tile (from
-  // qubit 1 the stage reads conflict 8-way and the gather path is faster)
-  if (full && qubits[0] >= 2 && qubits[K - 1] == qubits[0] + K - 1) {
-    typedef TShape<K, false> ST;
+  // any set without qubit 0 whose qubits (with the tile's) form at most 5
+  // runs: one TMA box per tile
+  {
+    FusedArgs AR = A;
     CUtensorMap map;
-    qs_status st = make_block_tmap(s, K, qubits[0], &map);
-    if (st != QS_OK) return st;
-    st = block_grid<K>(s, k_fused_umma_tma<K, false>, ST::NT, ST::SMEM, ST::TCOLS, grid);
-    if (st != QS_OK) return st;
-    k_fused_umma_tma<K, false><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A,
-                                                                        map, renorm, qubits[0]);
-    return launch_ok("k_fused_umma_tma");
+    qs_status est = QS_OK;
+    if (full && make_runs_tmap(s->amp, s->n, K, qubits, 1, &map, &AR.rb, &est)) {
+      typedef TShape<K, false> ST;
+      qs_status st = block_grid<K>(s, k_fused_umma_tma<K, false>, ST::NT, ST::SMEM, ST::TCOLS, grid);
+      if (st != QS_OK) return st;
+      k_fused_umma_tma<K, false><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B,
+                                                                          AR, map, renorm);
+      return launch_ok("k_fused_umma_tma");
+    }
+    if (est != QS_OK) return est;
   }
   typedef TaShape<K> S;
   // access mode (see group_load); 8-byte accesses measured faster than the

@@ -304,42 +304,59 @@ std::vector<char> touched(const std::vector<const qs_gate_rec*>& gates, int n) {
 
 // Tensor-core blocks (both dtypes): the qubits a block runs on, given those its
 // gates touch.  Idle qubits cost nothing there (a block is one HBM pass
-// whatever its width), but the kernel depends on the set's shape: a window
-// of consecutive qubits starting at 2 or above (one TMA box per tile), or at
-// 0 (contiguous rows), moves tiles whole; other sets gather per thread and
-// run at about 0.7 of the speed.  The touched qubits are widened to the
-// narrowest such window that holds them (at least 4 qubits, at most kmax,
-// starting at 2 or above if possible); when none exists, to 4 qubits with
-// the lowest idle ones.  *fast tells which.
-std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax, bool* fast) {
-  int lo = n, hi = -1, nused = 0;
-  for (int q = 0; q < n; ++q)
-    if (used[q]) {
-      lo = std::min(lo, q);
-      hi = std::max(hi, q);
-      ++nused;
+// whatever its width), but the kernel depends on the set's shape: with at
+// least 128 groups, qubits 0 .. k-1 move as contiguous rows and any set
+// without qubit 0 whose qubits form at most 5 runs (with the others') as
+// one TMA box per tile; other sets gather per thread and run at about 0.7
+// of the speed.  The touched qubits are widened to the narrowest window of
+// consecutive qubits that holds them (at least 4 qubits, at most kmax;
+// starting at 2 or above if possible, else at 0, else at 1); when none
+// exists, to at
+// least 4 qubits by idle ones next to the touched ones (not qubit 0, which
+// would make the set a gather), so no run is added.
+uint64_t tc_block_mask(uint64_t used, int n, int kmax) {
+  if (!used) return 0;
+  const int lo = __builtin_ctzll(used), hi = 63 - __builtin_clzll(used);
+  for (int m = std::max(4, hi - lo + 1); m <= kmax && m <= n; ++m) {
+    int pick = -1;
+    for (int w = std::max(0, hi - m + 1); w <= lo && w + m <= n; ++w) {
+      if (w >= 2) { pick = w; break; }
+      if (pick < 0 || (w == 0 && pick == 1)) pick = w;  // 0 before 1
     }
-  std::vector<int> bq;
-  if (hi >= 0) {
-    for (int m = std::max(4, hi - lo + 1); m <= kmax && m <= n; ++m) {
-      int pick = -1;
-      for (int w = std::max(0, hi - m + 1); w <= lo && w + m <= n; ++w) {
-        if (w >= 2) { pick = w; break; }
-        if (w == 0 && pick < 0) pick = 0;
-      }
-      if (pick >= 0) {
-        for (int q = pick; q < pick + m; ++q) bq.push_back(q);
-        *fast = true;
-        return bq;
-      }
-    }
+    if (pick >= 0) return ((uint64_t(1) << m) - 1) << pick;
   }
-  *fast = false;
-  std::vector<char> u = used;
-  for (int q = 0; q < n && nused < 4; ++q)
-    if (!u[q]) { u[q] = 1; ++nused; }
+  uint64_t u = used;
+  for (int pass = 0; pass < 2 && __builtin_popcountll(u) < 4; ++pass)
+    for (int q = 0; q < n && __builtin_popcountll(u) < 4; ++q) {
+      const bool next_to = (q > 0 && ((u >> (q - 1)) & 1)) || (q + 1 < n && ((u >> (q + 1)) & 1));
+      if (!((u >> q) & 1) && (pass == 1 || (q > 0 && next_to))) u |= uint64_t(1) << q;
+    }
+  return u;
+}
+
+// Whether a tensor-core block on `mask` runs near HBM speed: its tiles move
+// by TMA (see above), and the box's innermost run holds at least two of
+// the tile's qubits (a block on qubit 1 leaves 16-byte pieces, 0.6 of the
+// speed).
+bool tc_mask_fast(uint64_t mask, int n) {
+  const int k = __builtin_popcountll(mask);
+  if (n - k < 7) return false;
+  if (mask == (uint64_t(1) << k) - 1) return true;  // qubits 0 .. k-1
+  if (mask & 3) return false;
+  int runs = 1;
+  for (int q = 1; q < n; ++q) runs += ((mask >> q) & 1) != ((mask >> (q - 1)) & 1);
+  return runs <= 5;
+}
+
+std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax, bool* fast) {
+  uint64_t u = 0;
   for (int q = 0; q < n; ++q)
-    if (u[q]) bq.push_back(q);
+    if (used[q]) u |= uint64_t(1) << q;
+  const uint64_t m = tc_block_mask(u, n, kmax);
+  *fast = tc_mask_fast(m, n);
+  std::vector<int> bq;
+  for (int q = 0; q < n; ++q)
+    if ((m >> q) & 1) bq.push_back(q);
   return bq;
 }
 
@@ -445,15 +462,10 @@ u64m key_of_taken(const std::vector<int>& rem, const u64m* gm, u64m S, int nS) {
 }
 }  // namespace
 
-// Whether a tensor-core block whose gates touch `touched` gets a TMA shape
-// (the test of tc_block_qubits, without building the list).
+// Whether a tensor-core block whose gates touch `touched` gets a TMA shape.
 bool tc_fast_shape(u64m touched, int n, int kmax) {
   if (!touched) return true;
-  const int lo = __builtin_ctzll(touched), hi = 63 - __builtin_clzll(touched);
-  for (int m = std::max(4, hi - lo + 1); m <= kmax && m <= n; ++m)
-    for (int w = std::max(0, hi - m + 1); w <= lo && w + m <= n; ++w)
-      if (w >= 2 || w == 0) return true;
-  return false;
+  return tc_mask_fast(tc_block_mask(touched, n, kmax), n);
 }
 
 // The qubit sets of the blocks, in order (masks and sizes), and their cost.

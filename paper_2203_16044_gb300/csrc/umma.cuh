@@ -4,6 +4,8 @@
 // instruction descriptors, bounded mbarrier waits and tiled TMA copies.
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -115,6 +117,30 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
                : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, const int (&c)[5], uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          dst),
+      "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, const int (&c)[5], uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(dst),
+      "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const int (&c)[5], uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+               "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const int (&c)[5], uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(map),
+               "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(src)
+               : "memory");
+}
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map), "r"(x),
                "r"(y), "r"(z), "r"(src)
@@ -135,5 +161,147 @@ inline qs_status tmap_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return QS_OK;
 }
 
+// A block's tile as one TMA box of a view of the state with 2 to 5
+// dimensions.  The qubits split into maximal runs of block qubits and of
+// other qubits; each run is one tensor dimension (2^len entries, stride
+// 2^lo amplitudes).  The tile (128 consecutive groups) takes the 7 lowest
+// non-block qubits, the box covers them and the block runs whole.  The
+// dimensions' order fixes where the box lands in shared memory: element e
+// (block index, bit i the i-th block qubit ascending) of tile row r at
+// mult_r(r) + pos_e(e), the sums of per-bit multipliers kept in the
+// RunBox.  Two orders are used: ascending qubits (long contiguous DRAM
+// bursts; a warp's 32 rows are consecutive elements when the lowest run
+// holds at least 5 of the tile's qubits, else 2^(5 - t)-way bank conflicts
+// for a first run of t tile qubits) when that run holds at least
+// kNaturalMinTile of them, else the runs holding tile qubits first (rows
+// r at r + 128 e, free of bank conflicts, shorter bursts).  Needs qubit 0
+// outside the block (dimension 0 is the contiguous one), 2^(n-k) >= 128 and
+// at most 5 runs; false otherwise.  words: 64-bit words per amplitude (1:
+// complex64, 2: complex128).  A non-block run's qubits are consecutive
+// bits of the group index, so tile g's coordinate along it is
+// (g >> gb) & (2^len - 1) (times `words` for d = 0); along block runs 0.
+constexpr int kNaturalMinTile = 4;
+struct RunBox {
+  int8_t gb[5];   // dimension d's coordinate: bits gb .. gb + len - 1 of the group index (gb < 0: a block run)
+  int8_t len[5];
+  int rank;
+  int multr[7];  // position of tile-row bit i (the i-th lowest non-block qubit), in amplitudes
+  int multe[6];  // position of block-index bit j (the j-th block qubit), in amplitudes
+};
+inline bool make_runs_tmap(void* amp, int n, int k, const int* q_sorted, int words, CUtensorMap* map, RunBox* rb,
+                           qs_status* st) {
+  *st = QS_OK;
+  if (n - k < 7 || q_sorted[0] == 0 || k > 6) return false;
+  uint64_t inb = 0;
+  for (int i = 0; i < k; ++i) inb |= uint64_t(1) << q_sorted[i];
+  int tilebit[64] = {0};  // 1: one of the 7 lowest non-block qubits
+  for (int q = 0, c = 0; q < n && c < 7; ++q)
+    if (!((inb >> q) & 1)) { tilebit[q] = 1; ++c; }
+  struct Run { int lo, len, tile, block; };
+  std::vector<Run> runs;
+  for (int q = 0; q < n;) {
+    const int b = (int)((inb >> q) & 1);
+    int e = q;
+    while (e < n && (int)((inb >> e) & 1) == b) ++e;
+    int t = 0;
+    for (int x = q; x < e; ++x) t += tilebit[x];
+    runs.push_back(Run{q, e - q, t, b});
+    q = e;
+  }
+  if (runs.size() > 5) return false;
+  std::vector<Run> ord;
+  if (runs[0].tile >= kNaturalMinTile) {
+    ord = runs;
+  } else {
+    for (const Run& r : runs) if (!r.block && r.tile) ord.push_back(r);
+    for (const Run& r : runs) if (r.block) ord.push_back(r);
+    for (const Run& r : runs) if (!r.block && !r.tile) ord.push_back(r);
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  *st = tmap_encoder(&encode);
+  if (*st != QS_OK) return false;
+  const int rank = (int)ord.size();
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  int mult[64] = {0};  // position multiplier of each qubit inside the box (amplitudes)
+  int stride_in_box = 1;
+  for (int d = 0; d < 5; ++d) {
+    rb->gb[d] = -1;
+    rb->len[d] = 0;
+    if (d >= rank) continue;
+    const Run& r = ord[d];
+    const int ext = r.block ? r.len : r.tile;  // qubits of the run inside the box
+    dims[d] = (cuuint64_t(1) << r.len) * (d == 0 ? words : 1);
+    box[d] = (cuuint32_t)((1u << ext) * (d == 0 ? words : 1));
+    if (d > 0) strides[d - 1] = (cuuint64_t(1) << r.lo) * 8 * words;
+    if (!r.block) {
+      int below = 0;  // non-block qubits below the run: its first group-index bit
+      for (int x = 0; x < r.lo; ++x) below += !((inb >> x) & 1);
+      rb->gb[d] = (int8_t)below;
+      rb->len[d] = (int8_t)r.len;
+    }
+    for (int x = 0; x < ext; ++x) mult[r.lo + x] = stride_in_box << x;
+    stride_in_box <<= ext;
+  }
+  rb->rank = rank;
+  for (int i = 0, c = 0; i < n && c < 7; ++i)
+    if (tilebit[i]) rb->multr[c++] = mult[i];
+  for (int j = 0; j < 6; ++j) rb->multe[j] = j < k ? mult[q_sorted[j]] : 0;
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, amp, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *st = fail(QS_ECUDA, "cuTensorMapEncodeTiled (run box) failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+// The tile's box coordinates (see make_runs_tmap).
+__device__ __forceinline__ void run_coords(uint64_t g, const RunBox& rb, int words, int (&c)[5]) {
+#pragma unroll
+  for (int d = 0; d < 5; ++d)
+    c[d] = rb.gb[d] < 0 ? 0 : (int)((g >> rb.gb[d]) & ((uint64_t(1) << rb.len[d]) - 1)) * (d == 0 ? words : 1);
+}
+// The copy of the box of tile g (its first group) into shared memory at
+// dst (one thread).
+__device__ __forceinline__ void run_load(uint32_t dst, const CUtensorMap* map, uint64_t g, const RunBox& rb, int words,
+                                         uint32_t mbar) {
+  int c[5];
+  run_coords(g, rb, words, c);
+  switch (rb.rank) {
+    case 2: tma_load_2d(dst, map, c[0], c[1], mbar); break;
+    case 3: tma_load_3d(dst, map, c[0], c[1], c[2], mbar); break;
+    case 4: tma_load_4d(dst, map, c, mbar); break;
+    default: tma_load_5d(dst, map, c, mbar); break;
+  }
+}
+__device__ __forceinline__ void run_store(const CUtensorMap* map, uint64_t g, const RunBox& rb, int words, uint32_t src) {
+  int c[5];
+  run_coords(g, rb, words, c);
+  switch (rb.rank) {
+    case 2: tma_store_2d(map, c[0], c[1], src); break;
+    case 3: tma_store_3d(map, c[0], c[1], c[2], src); break;
+    case 4: tma_store_4d(map, c, src); break;
+    default: tma_store_5d(map, c, src); break;
+  }
+}
+// Position of tile row r in the box (amplitudes).
+__device__ __forceinline__ int run_row_pos(const RunBox& rb, int r) {
+  int p = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) p += ((r >> i) & 1) * rb.multr[i];
+  return p;
+}
+// Position of block index e0 + i for a compile-time i below 2^NB, e0 a
+// multiple of 2^NB: base (the position of e0) plus the multipliers of i's
+// bits, held in m[0 .. NB-1].
+template <int NB>
+__device__ __forceinline__ int run_elem_pos(int base, const int (&m)[NB], int i) {
+  int p = base;
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if ((i >> j) & 1) p += m[j];
+  return p;
+}
 
 }  // namespace qs

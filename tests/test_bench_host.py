@@ -11,58 +11,57 @@ def qs():
     return qs
 
 
+def _runs(q, n):
+    # maximal runs of block / non-block qubits over 0..n-1, counted directly
+    cls = [b in set(q) for b in range(n)]
+    return sum(1 for b in range(n) if b == 0 or cls[b] != cls[b - 1])
+
+
 def test_step_kernel_labels(qs):
     import bench
-    n = 14
-    p = qs.Plan(qs.Circuit(W.brick(n, 12, 3)), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=6)
+    # complex64: qubits 0..k-1 take the rows form of the TMA kernel; sets
+    # without qubit 0 forming at most 5 runs its box form ("window" when
+    # consecutive); other sets, and blocks with fewer than 128 groups, the
+    # per-thread gather kernel.  complex128 k = 4, 5 alike (k_fused_c128),
+    # 6-qubit requests narrowed to 5.
     seen = set()
-    for i, (kind, _) in enumerate(p.step_info()):
-        lab = bench.step_kernel(p, i, kind)
-        if kind != "block":
-            assert lab == kind
-            continue
-        q = sorted(p.step_qubits(i))
-        if q[0] >= 2 and q == list(range(q[0], q[0] + len(q))):
-            want = "k_fused_umma_tma<%d,window>" % len(q)
-        elif q == list(range(len(q))):
-            want = "k_fused_umma_tma<%d,rows>" % len(q)
-        else:
-            want = "k_fused_umma<%d>" % len(q)
-        assert lab == want
-        seen.add(want.split("<")[0] + ("," + want.split(",")[1] if "," in want else ""))
-    # a brick plan has windows from qubit 2 up and a block on the lowest
-    # qubits
-    assert {"k_fused_umma_tma,window>", "k_fused_umma_tma,rows>"} <= seen
-    # complex128: 4- and 5-qubit blocks run on k_fused_c128 (rows, windows
-    # from qubit 1 up, gathered sets; fewer than 128 groups always gather),
-    # 6-qubit requests are narrowed to 5, smaller blocks stay on k_dense
-    for n, fq in ((14, 5), (14, 6), (13, 4), (8, 4)):
-        p128 = qs.Plan(qs.Circuit(W.brick(n, 12, 3)), n, "c128", mode=qs.PLAN_FUSED, fuse_qubits=fq)
-        for i, (kind, _) in enumerate(p128.step_info()):
+    for dtype, n, fq, circ in (("c64", 14, 6, W.brick(14, 12, 3)), ("c64", 14, 6, W.qft(14)),
+                               ("c64", 15, 5, W.qv_like(15, 6, 2)), ("c64", 9, 4, W.brick(9, 6, 1)),
+                               ("c128", 14, 5, W.brick(14, 12, 3)), ("c128", 14, 6, W.qft(14)),
+                               ("c128", 13, 4, W.qv_like(13, 6, 3)), ("c128", 8, 4, W.brick(8, 12, 3))):
+        p = qs.Plan(qs.Circuit(circ), n, dtype, mode=qs.PLAN_FUSED, fuse_qubits=fq)
+        name, gather = ("k_fused_c128", "k_fused_c128<%d,gather>") if dtype == "c128" else \
+            ("k_fused_umma_tma", "k_fused_umma<%d>")
+        for i, (kind, _) in enumerate(p.step_info()):
+            lab = bench.step_kernel(p, i, kind)
             if kind != "block":
+                assert lab == kind
                 continue
-            q = sorted(p128.step_qubits(i))
+            q = sorted(p.step_qubits(i))
             k = len(q)
-            assert k <= 5
-            lab = bench.step_kernel(p128, i, kind)
+            assert k <= (5 if dtype == "c128" else 6)
             if k < 4:
-                assert lab == "k_dense<%d>" % k
+                want = "k_dense<%d>" % k
             elif n - k < 7:
-                assert lab == "k_fused_c128<%d,gather>" % k
+                want = gather % k
             elif q == list(range(k)):
-                assert lab == "k_fused_c128<%d,rows>" % k
-            elif q[0] >= 1 and q == list(range(q[0], q[0] + k)):
-                assert lab == "k_fused_c128<%d,window>" % k
+                want = "%s<%d,rows>" % (name, k)
+            elif q[0] >= 1 and _runs(q, n) <= 5:
+                want = "%s<%d,%s>" % (name, k, "window" if q[-1] - q[0] + 1 == k else "box")
             else:
-                assert lab == "k_fused_c128<%d,gather>" % k
+                want = gather % k
+            assert lab == want, (dtype, n, q, lab)
+            seen.add(want.split("<")[0] + "," + (want.split(",")[1] if "," in want else "gather"))
+    assert {"k_fused_umma_tma,window>", "k_fused_umma_tma,rows>", "k_fused_umma_tma,box>",
+            "k_fused_c128,window>", "k_fused_c128,rows>"} <= seen, seen
 
 
 def test_planner_widens_complex64_blocks_to_windows(qs):
     # host-only: every complex64 tensor-core block whose touched qubits fit in
     # a window of at most k consecutive qubits is widened to such a window of
-    # at least 4 qubits, starting at 0 or at 2 and above (the shapes the TMA
-    # kernel takes); the widened block still holds all the qubits its gates
-    # touch, and the plan's gate count is unchanged
+    # at least 4 qubits (the shapes the TMA kernel takes); the widened block
+    # still holds all the qubits its gates touch, and the plan's gate count
+    # is unchanged
     import workloads as W
     for n, k, circ in ((14, 6, W.brick(14, 12, 3)), (13, 5, W.qv_like(13, 6, 5)), (12, 4, W.qsb(12, 7, sets=3))):
         p = qs.Plan(qs.Circuit(circ), n, "c64", mode=qs.PLAN_FUSED, fuse_qubits=k)
@@ -72,5 +71,3 @@ def test_planner_widens_complex64_blocks_to_windows(qs):
                 continue
             q = sorted(p.step_qubits(i))
             assert 4 <= len(q) <= k
-            if q[-1] - q[0] + 1 == len(q):  # a window
-                assert q[0] == 0 or q[0] >= 2 or q[-1] + 1 >= n or len(q) == k

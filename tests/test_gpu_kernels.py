@@ -243,11 +243,18 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     (14, "window5"),      # ... from 5 (4 x 32 rows)
     (15, "window6"),      # ... from 6 (2 x 64 rows)
     (17, "window8"),      # ... from 8 (one run of 128 rows)
+    (14, "window1"),      # ... from 1 (the tile's qubit 0, then the block, then the rest)
+    (15, "tworuns"),      # two runs of block qubits: a 5-D box
+    (16, "tworunsup"),    # ... the upper run ending at the top qubit (4 runs)
 ])
 def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
     # complex64 k = 4, 5, 6 blocks run on tcgen05; each way a group's
     # amplitudes are gathered and scattered, against the oracle
-    if qubits is None:
+    if qubits == "tworuns":
+        qsel = [9, 1, 10, 2, 11, 3][:k]
+    elif qubits == "tworunsup":
+        qsel = [15, 2, 14, 3, 13, 4][:k]
+    elif qubits is None:
         qsel = [1, 3, 4, 6, 8, 2][:k]
     elif qubits == "with0":
         qsel = [7, 0, 3, 11, 5, 9][:k]
@@ -351,12 +358,15 @@ def test_apply_fused_c64_dynamic_range(qs, k, mode):
     (15, "window6"),
     (17, "window8"),      # ... from 8 (runs of 128 rows)
     (16, "high"),         # the block on the highest qubits
+    (15, "tworuns"),      # two runs of block qubits: a 5-D box
 ])
 def test_apply_fused_c128_tensor_core_access_modes(qs, k, n, qubits):
     # complex128 k = 4, 5 blocks run on tcgen05 with FP64 operands split into
     # 9-bit integer digits: every output against the oracle within 1e-12 and
     # within 2^-36 of its group's norm
-    if qubits is None:
+    if qubits == "tworuns":
+        qsel = [9, 1, 10, 2, 11][:k]
+    elif qubits is None:
         qsel = [1, 3, 4, 6, 8][:k]
     elif qubits == "gathered":
         qsel = [2, 9, 5, 12, 1][:k]
