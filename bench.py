@@ -364,8 +364,10 @@ def unfused_classes(qs, torch, device, n, reps=10):
 
 def batch_workload(qs, torch, device, count=512, layers=8, seed=9):
     """512 hardware-efficient-ansatz circuits, n uniform in [10, 20], complex64:
-    one persistent launch (graph replay, autotuned tiles) vs one plan per
-    circuit launched one after another."""
+    one batch (graph replay; the autotuner picks the tile shape and from how
+    many qubits circuits run as fused tensor-core plans on side streams
+    instead of in the persistent launch) vs one tiled plan per circuit
+    launched one after another."""
     sizes = W.batch_sizes(count, 10, 20, seed)
     circs = [W.hea(n, layers, 10 + i)[0] for i, n in enumerate(sizes)]
     b = qs.Batch(sizes, circs, dtype="c64", autotune=True)
@@ -397,9 +399,11 @@ def batch_workload(qs, torch, device, count=512, layers=8, seed=9):
     return {"circuits": count, "n_range": [10, 20], "gates": gates, "passes": st["passes"], "units": st["units"],
             "grid": st["grid"], "graph": st["graph"], "tuned_opts": {"tile_qubits": b.opts.tile_qubits,
                                                                      "slot_qubits": b.opts.slot_qubits,
-                                                                     "groups_per_thread": b.opts.groups_per_thread},
+                                                                     "groups_per_thread": b.opts.groups_per_thread,
+                                                                     "fuse_min_qubits": b.opts.fuse_min_qubits},
             "batched_ms": 1e3 * t_batch, "circuits_per_s": count / t_batch,
             "hbm_GBps_batched": st["hbm_bytes"] / t_batch / 1e9,
+            "hbm_frac_batched": st["hbm_bytes"] / t_batch / 1e9 / measured_peaks()[0],
             "one_by_one_ms": 1e3 * t_single, "one_by_one_circuits_per_s": count / t_single,
             "speedup_vs_one_by_one": t_single / t_batch}
 

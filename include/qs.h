@@ -303,6 +303,10 @@ typedef struct {
   int fuse_qubits;    /* QS_PLAN_FUSED: qubits per dense block, 2..6 (0 = 5) */
   int search;         /* QS_PLAN_FUSED: block-order search width, 1..256
                          (1 = greedy; 0 = 16)                           */
+  int fuse_min_qubits;/* qs_batch_create: circuits of at least this many
+                         qubits run as QS_PLAN_FUSED plans (fuse_qubits,
+                         0 = 6 for QS_C64, 5 for QS_C128) on parallel
+                         streams; 0 = every circuit as tile passes      */
   int reserved[1];
 } qs_plan_opts;
 
@@ -383,9 +387,14 @@ typedef struct {
  * caller-owned) into one batch run on `stream`.  Every circuit becomes tile
  * passes (opts as for qs_plan_build, mode ignored; NULL = defaults); the
  * batch is a work queue of (circuit, pass, tiles) units executed by one
- * persistent cooperative launch.  The paper runs circuits one at a time; this
- * is the library's own scheduling.  The first qs_batch_run captures the
- * launch in a CUDA graph (unless `stream` is the legacy default stream).
+ * persistent cooperative launch.  With opts->fuse_min_qubits > 0, circuits
+ * of at least that many qubits instead run as QS_PLAN_FUSED plans (dense
+ * blocks of opts->fuse_qubits qubits on the tensor cores, block matrices
+ * uploaded once here), spread over 8 streams forked from `stream` and
+ * joined back, alongside the persistent launch.  The paper runs circuits
+ * one at a time; this is the library's own scheduling.  The first
+ * qs_batch_run captures the launches in a CUDA graph (unless `stream` is
+ * the legacy default stream).
  * opts->reserved[0] is a test hook and must be 0 in normal use: a positive
  * value makes every wait for a previous pass demand that many tiles more
  * than exist, so the bounded wait runs out (QS_ETIMEOUT from
@@ -407,9 +416,11 @@ qs_status qs_batch_stats_get(const qs_batch* b, qs_batch_stats* out);
 qs_status qs_batch_destroy(qs_batch* b);
 
 /* Autotuner: builds and times the batch for candidate tile sizes and
- * register slot counts (two runs each, starting from |0...0>, so the states
- * are overwritten) and returns the fastest options in *best (and its time
- * in *best_ms if non-NULL).  Cached under a hash of every circuit, the
+ * register slot counts, then, with the best of those, for the qubit counts
+ * from which circuits run as fused tensor-core plans (fuse_min_qubits 16,
+ * 18, 20 at the dtype's default block width), two runs each, starting from
+ * |0...0> (the states are overwritten), and returns the fastest options in
+ * *best (and its time in *best_ms if non-NULL).  Cached under a hash of every circuit, the
  * qubit counts, the dtype and the GPU, as for qs_plan_autotune. */
 qs_status qs_batch_autotune(int count, const int* n, qs_dtype dtype, void* const* dev_states,
                             const qs_circuit* const* circuits, void* stream, qs_plan_opts* best,

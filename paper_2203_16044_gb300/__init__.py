@@ -45,7 +45,8 @@ _int = ctypes.c_int
 class PlanOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("low_qubits", ctypes.c_int),
                 ("slot_qubits", ctypes.c_int), ("groups_per_thread", ctypes.c_int), ("dense", ctypes.c_int),
-                ("fuse_qubits", ctypes.c_int), ("search", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("fuse_qubits", ctypes.c_int), ("search", ctypes.c_int), ("fuse_min_qubits", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class PlanStats(ctypes.Structure):

@@ -200,6 +200,15 @@ struct qs_batch {
   cudaGraphExec_t exec = nullptr;
   qs_batch_stats stats{};
   std::vector<qs_plan*> plans;
+  // circuits run as fused tensor-core plans (fuse_min_qubits): their plans,
+  // states (wrapping the caller's vectors) and block matrices on the device
+  int ntiled = 0;                 // circuits in the persistent launch
+  std::vector<qs_plan*> fplans;
+  std::vector<qs_state*> fstates;
+  void* fB = nullptr;             // every fused plan's tc_B, concatenated
+  std::vector<size_t> fB_off;     // per fused plan, in floats
+  cudaStream_t fs[8] = {};        // streams the fused plans spread over
+  cudaEvent_t fork = nullptr, join[8] = {};
 };
 
 namespace qs {
@@ -233,13 +242,47 @@ qs_status enqueue_batch(qs_batch* b) {
   return QS_OK;
 }
 
-qs_status enqueue(qs_batch* b) {
+qs_status enqueue_tiled(qs_batch* b) {
+  if (b->ntiled == 0) return QS_OK;
   if (b->dtype == QS_C64) {
     if (b->G == 4) return b->gpt == 2 ? enqueue_batch<0, 4, 2>(b) : enqueue_batch<0, 4, 1>(b);
     return b->gpt == 2 ? enqueue_batch<0, 3, 2>(b) : enqueue_batch<0, 3, 1>(b);
   }
   if (b->G == 4) return enqueue_batch<1, 4, 1>(b);
   return b->gpt == 2 ? enqueue_batch<1, 3, 2>(b) : enqueue_batch<1, 3, 1>(b);
+}
+
+// The fused circuits: forked from the batch's stream onto the side streams
+// (circuit j on stream j mod 8, largest circuits first), each its blocks in
+// order, joined back; the persistent launch runs on the batch's stream
+// meanwhile.
+qs_status enqueue(qs_batch* b) {
+  const int nf = (int)b->fplans.size();
+  if (nf == 0) return enqueue_tiled(b);
+  const int ns = std::min(nf, 8);
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->fs[i], b->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch: fork");
+  qs_status st = QS_OK;
+  for (int j = 0; j < nf && st == QS_OK; ++j) {
+    qs_state* s = b->fstates[j];
+    s->stream = b->fs[j % ns];
+    if (b->args.init_zero) st = run_set_basis(s, 0);
+    const qs_plan* p = b->fplans[j];
+    const float* B = static_cast<const float*>(b->fB) + b->fB_off[j];
+    for (size_t i = 0; i < p->steps.size() && st == QS_OK; ++i) {
+      const qs_block& blk = p->blocks[p->steps[i].tile_index];
+      st = b->dtype == QS_C64 ? run_dense_tc_prepared(s, blk.q_sorted, blk.k, B + blk.b_off, 1)
+                              : run_dense_tc128_prepared(s, blk.q_sorted, blk.k, B + blk.b_off, blk.f128, false);
+    }
+  }
+  if (st == QS_OK) st = enqueue_tiled(b);
+  for (int i = 0; i < ns; ++i) {
+    e = cudaEventRecord(b->join[i], b->fs[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    if (e != cudaSuccess && st == QS_OK) st = cuda_fail(e, "batch: join");
+  }
+  return st;
 }
 
 }  // namespace
@@ -264,6 +307,86 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
   qs_plan_opts o{};
   if (opts) o = *opts;
   o.mode = QS_PLAN_TILED;
+  if (o.fuse_min_qubits < 0) {
+    qs_batch_destroy(b);
+    return fail(QS_EINVAL, "qs_batch_create: fuse_min_qubits=%d < 0", o.fuse_min_qubits);
+  }
+  // circuits of at least fuse_min_qubits qubits: fused tensor-core plans
+  std::vector<int> tiled;
+  std::vector<int> fused;
+  for (int i = 0; i < count; ++i) (o.fuse_min_qubits > 0 && nq[i] >= o.fuse_min_qubits ? fused : tiled).push_back(i);
+  std::stable_sort(fused.begin(), fused.end(), [&](int x, int y) { return nq[x] > nq[y]; });
+  double fhbm = 0, fmetric = 0;
+  int fpasses = 0;
+  if (!fused.empty()) {
+    qs_plan_opts fo{};
+    fo.mode = QS_PLAN_FUSED;
+    fo.fuse_qubits = o.fuse_qubits > 0 ? o.fuse_qubits : (dtype == QS_C64 ? 6 : 5);
+    fo.search = o.search;
+    std::vector<float> allB;
+    for (int i : fused) {
+      if (!circuits[i] || !dev_states[i] || (reinterpret_cast<uintptr_t>(dev_states[i]) & 15)) {
+        qs_batch_destroy(b);
+        return fail(QS_EINVAL, "qs_batch_create: circuit %d: NULL or misaligned state", i);
+      }
+      qs_plan* p = nullptr;
+      qs_status r = qs_plan_build(circuits[i], nq[i], dtype, &fo, &p);
+      if (r == QS_OK && (p->steps.empty() || p->tc_B.empty())) {
+        qs_plan_destroy(p);
+        r = fail(QS_EINVAL, "qs_batch_create: circuit %d gives no tensor-core blocks", i);
+      }
+      if (r == QS_OK)
+        for (const qs_step& st : p->steps)
+          if (st.type != qs_step::BLOCK || !p->blocks[st.tile_index].tc)
+            r = fail(QS_EINVAL, "qs_batch_create: circuit %d: a fused step is not a tensor-core block", i);
+      qs_state* s = nullptr;
+      if (r == QS_OK) r = qs_wrap(nq[i], dtype, dev_states[i], &s);
+      if (r != QS_OK) {
+        if (p) qs_plan_destroy(p);
+        qs_batch_destroy(b);
+        return r;
+      }
+      b->fplans.push_back(p);
+      b->fstates.push_back(s);
+      b->fB_off.push_back(allB.size());
+      allB.insert(allB.end(), p->tc_B.begin(), p->tc_B.end());
+      fhbm += p->stats.hbm_bytes;
+      fmetric += p->stats.metric_bytes;
+      fpasses += p->stats.passes;
+    }
+    cudaError_t e = cudaMalloc(&b->fB, allB.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(b->fB, allB.data(), allB.size() * sizeof(float), cudaMemcpyHostToDevice);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&b->fs[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      qs_batch_destroy(b);
+      return cuda_fail(e, "qs_batch_create: fused circuits' set-up");
+    }
+  }
+  b->ntiled = (int)tiled.size();
+  if (tiled.empty()) {
+    b->stats.circuits = count;
+    b->stats.passes = fpasses;
+    b->stats.hbm_bytes = fhbm;
+    b->stats.metric_bytes = fmetric;
+    *out = b;
+    return QS_OK;
+  }
+  const int count_all = count;
+  std::vector<int> nq_t;
+  std::vector<void*> ds_t;
+  std::vector<const qs_circuit*> c_t;
+  for (int i : tiled) {
+    nq_t.push_back(nq[i]);
+    ds_t.push_back(dev_states[i]);
+    c_t.push_back(circuits[i]);
+  }
+  count = (int)tiled.size();
+  nq = nq_t.data();
+  dev_states = ds_t.data();
+  circuits = c_t.data();
+  b->count = count;
   std::vector<BCircuit> hc(count);
   std::vector<BPass> hp;
   std::vector<TOp> hops;
@@ -378,11 +501,11 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
   b->args.wait_bias = (unsigned)std::max(0, o.reserved[0]);
   const size_t esize = dtype == QS_C64 ? sizeof(float2) : sizeof(cdf);
   b->smem = 2 * 64 * sizeof(u64) + (size_t(1) << maxm) * esize;
-  b->stats.circuits = count;
+  b->stats.circuits = count_all;
   b->stats.units = (int)hu.size();
-  b->stats.passes = (int)hp.size();
-  b->stats.hbm_bytes = hbm;
-  b->stats.metric_bytes = metric;
+  b->stats.passes = (int)hp.size() + fpasses;
+  b->stats.hbm_bytes = hbm + fhbm;
+  b->stats.metric_bytes = metric + fmetric;
   *out = b;
   return QS_OK;
 }
@@ -422,6 +545,11 @@ qs_status qs_batch_sync(qs_batch* b) {
   if (!b) return fail(QS_EINVAL, "qs_batch_sync: NULL batch");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "qs_batch_sync");
+  if (!b->fplans.empty()) {
+    const qs_status t = b->dtype == QS_C64 ? fused_tc_status() : fused_c128_status();
+    if (t != QS_OK) return t;
+  }
+  if (b->ntiled == 0) return QS_OK;
   int err = 0;
   e = cudaMemcpy(&err, b->args.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "qs_batch_sync: error flag");
@@ -445,8 +573,21 @@ qs_status qs_batch_destroy(qs_batch* b) {
   if (b->stream || b->dev) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (int i = 0; i < 8; ++i)
+    if (b->fs[i]) cudaStreamSynchronize(b->fs[i]);
   if (b->dev) cudaFree(b->dev);
   for (qs_plan* p : b->plans) qs_plan_destroy(p);
+  for (qs_plan* p : b->fplans) qs_plan_destroy(p);
+  for (qs_state* s : b->fstates) {
+    s->stream = nullptr;
+    qs_free(s);
+  }
+  if (b->fB) cudaFree(b->fB);
+  for (int i = 0; i < 8; ++i) {
+    if (b->fs[i]) cudaStreamDestroy(b->fs[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
   return QS_OK;
 }
@@ -502,6 +643,34 @@ qs_status qs_batch_autotune(int count, const int* nq, qs_dtype dtype, void* cons
       }
     }
     if (rc != QS_OK) break;
+  }
+  // then circuits from 16, 18 or 20 qubits up as fused tensor-core plans
+  const int fmins[] = {16, 18, 20};
+  for (int fm : fmins) {
+    if (rc != QS_OK) break;
+    bool any = false;
+    for (int i = 0; i < count; ++i) any |= nq[i] >= fm;
+    if (!any) continue;
+    qs_plan_opts o = bo;
+    o.fuse_min_qubits = fm;
+    qs_batch* b = nullptr;
+    rc = qs_batch_create(count, nq, dtype, dev_states, circuits, &o, stream, &b);
+    if (rc != QS_OK) break;
+    rc = qs_batch_run(b, 1);
+    if (rc == QS_OK) rc = qs_batch_sync(b);
+    float ms = 0.f;
+    if (rc == QS_OK) {
+      cudaEventRecord(e0, s);
+      rc = qs_batch_run(b, 1);
+      cudaEventRecord(e1, s);
+      if (rc == QS_OK) rc = qs_batch_sync(b);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    qs_batch_destroy(b);
+    if (rc == QS_OK && ms < bestt) {
+      bestt = ms;
+      bo = o;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

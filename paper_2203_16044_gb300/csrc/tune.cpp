@@ -11,7 +11,7 @@
 // index), the qubit count(s), the dtype -- and of the GPU (name, SM count,
 // compute capability), kept in memory for the process and, when a cache
 // file is set, appended to it as one text line per result:
-//   qs-tune-v2 <key hex> <what> <mode> <tile> <low> <slots> <gpt> <dense> <fuse> <search> <ms>
+//   qs-tune-v3 <key hex> <what> <mode> <tile> <low> <slots> <gpt> <dense> <fuse> <search> <fuse_min> <ms>
 // where <what> is "plan" or "batch".  A file written on another GPU never
 // matches (the key covers the device).  Timing runs overwrite the state.
 #include <cstdio>
@@ -91,8 +91,8 @@ void remember(unsigned long long key, const char* what, const qs_plan_opts& o, d
   if (g_tune_file.empty()) return;
   FILE* fp = std::fopen(g_tune_file.c_str(), "a");
   if (!fp) return;  // the cache is an optimisation: an unwritable file only loses persistence
-  std::fprintf(fp, "qs-tune-v2 %016llx %s %d %d %d %d %d %d %d %d %.6f\n", key, what, o.mode, o.tile_qubits,
-               o.low_qubits, o.slot_qubits, o.groups_per_thread, o.dense, o.fuse_qubits, o.search, ms);
+  std::fprintf(fp, "qs-tune-v3 %016llx %s %d %d %d %d %d %d %d %d %d %.6f\n", key, what, o.mode, o.tile_qubits,
+               o.low_qubits, o.slot_qubits, o.groups_per_thread, o.dense, o.fuse_qubits, o.search, o.fuse_min_qubits, ms);
   std::fclose(fp);
 }
 
@@ -180,9 +180,9 @@ qs_status qs_tune_cache_file(const char* path) {
     char what[16];
     qs_plan_opts o{};
     double ms = 0.0;
-    if (std::sscanf(line, "qs-tune-v2 %llx %15s %d %d %d %d %d %d %d %d %lf", &key, what, &o.mode, &o.tile_qubits,
+    if (std::sscanf(line, "qs-tune-v3 %llx %15s %d %d %d %d %d %d %d %d %d %lf", &key, what, &o.mode, &o.tile_qubits,
                     &o.low_qubits, &o.slot_qubits, &o.groups_per_thread, &o.dense, &o.fuse_qubits, &o.search,
-                    &ms) == 11)
+                    &o.fuse_min_qubits, &ms) == 12)
       g_tune[key] = TuneRec{o, ms};  // a later line for the same key wins
   }
   std::fclose(fp);

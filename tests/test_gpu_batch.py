@@ -65,6 +65,44 @@ def test_batch_matches_oracle(qs, dtype):
         check(b.state(i).cpu().numpy(), want, dtype, gates=len(c))
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_with_fused_circuits(qs, dtype):
+    # circuits of at least 14 qubits run as fused tensor-core plans on side
+    # streams (more of them than streams), the rest in the persistent
+    # launch; every circuit against the oracle, from |0> and on current
+    # contents, over graph replays
+    sizes = [14, 9, 15, 16, 12, 14, 15, 16, 14, 15, 10, 16]
+    circs = circuits_for(sizes, 300)
+    b = qs.Batch(sizes, circs, dtype=dtype, fuse_min_qubits=14)
+    st = b.stats()
+    assert st["circuits"] == len(sizes)
+    wants = []
+    for n, c in zip(sizes, circs):
+        w = oracle.zero_state(n)
+        oracle.run_circuit(w, c)
+        wants.append(w)
+    for _ in range(2):
+        b.run(init_zero=True)
+        b.sync()
+        for i, c in enumerate(circs):
+            check(b.state(i).cpu().numpy(), wants[i], dtype, gates=len(c))
+    assert b.stats()["graph"] == 1
+    # every circuit fused (no persistent launch at all)
+    big = [i for i, n in enumerate(sizes) if n >= 14]
+    b2 = qs.Batch([sizes[i] for i in big], [circs[i] for i in big], dtype=dtype, fuse_min_qubits=14)
+    b2.run(True)
+    b2.sync()
+    for j, i in enumerate(big):
+        check(b2.state(j).cpu().numpy(), wants[i], dtype, gates=len(circs[i]))
+    # on current contents: the inverse circuits take every state back to |0>
+    inv = qs.Batch(sizes, [W.inverse(c) for c in circs], dtype=dtype, fuse_min_qubits=14)
+    inv.buffer.copy_(b.buffer)
+    inv.run(init_zero=False)
+    inv.sync()
+    for i, n in enumerate(sizes):
+        check(inv.state(i).cpu().numpy(), oracle.zero_state(n), dtype, gates=2 * len(circs[i]))
+
+
 def test_batch_on_current_contents(qs):
     # circuits then their inverses as a second batch acting on the results
     sizes = [6, 11, 15]

@@ -41,7 +41,7 @@ def test_plan_autotune_picks_a_correct_plan_and_caches(qs, dtype, tmp_path):
     if opts.mode == qs.PLAN_FUSED:
         assert 4 <= opts.fuse_qubits <= (6 if dtype == "c64" else 5)
     lines = cache.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("qs-tune-v2 ") and " plan " in lines[0]
+    assert len(lines) == 1 and lines[0].startswith("qs-tune-v3 ") and " plan " in lines[0]
     # the chosen plan is correct
     want = oracle.zero_state(n)
     oracle.run_circuit(want, circ)

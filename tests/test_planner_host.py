@@ -174,6 +174,6 @@ def test_circuit_hash_keys_the_tuner(qs, tmp_path):
     # cache files: absent, well formed, garbage -- all accepted
     qs.set_tune_cache(str(tmp_path / "none.txt"))
     f = tmp_path / "c.txt"
-    f.write_text("qs-tune-v2 0123456789abcdef plan 2 0 0 0 0 0 6 0 1.5\nnot a cache line\n")
+    f.write_text("qs-tune-v3 0123456789abcdef plan 2 0 0 0 0 0 6 0 0 1.5\nnot a cache line\n")
     qs.set_tune_cache(str(f))
     qs.set_tune_cache(None)
