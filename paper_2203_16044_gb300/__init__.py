@@ -389,7 +389,7 @@ class Circuit:
 
 def plan_kwargs(opts: PlanOpts) -> dict:
     """PlanOpts as keyword arguments of Plan."""
-    return {f: getattr(opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"}
+    return {f: getattr(opts, f) for f, _ in PlanOpts._fields_ if f not in ("reserved", "fuse_min_qubits")}
 
 
 def autotune(circuit: "Circuit", state: "State"):

@@ -79,6 +79,17 @@ def test_block_order_search(qs, dtype):
         qs.Plan(qs.Circuit(W.brick(8, 2, 1)), 8, dtype, mode=qs.PLAN_FUSED, fuse_qubits=5, search=257)
 
 
+def test_plan_kwargs_round_trip(qs):
+    # the options an autotuner returns build a plan again (batch-only fields
+    # such as fuse_min_qubits are left out)
+    o = qs.PlanOpts(mode=qs.PLAN_FUSED, fuse_qubits=6, search=4, fuse_min_qubits=18)
+    kw = qs.plan_kwargs(o)
+    assert "fuse_min_qubits" not in kw and kw["fuse_qubits"] == 6 and kw["search"] == 4
+    circ = W.brick(10, 4, 1)
+    p = qs.Plan(qs.Circuit(circ), 10, "c64", **kw)
+    assert p.stats()["gates"] == len(circ) and p.stats()["passes"] >= 1
+
+
 def test_step_matrix_errors(qs):
     p = qs.Plan(qs.Circuit(W.brick(6, 2, 1)), 6, "c64", mode=qs.PLAN_UNFUSED)
     with pytest.raises(qs.QSError):
