@@ -56,7 +56,7 @@ WORKLOADS = {
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1> (its ncu capture at 26 qubits)
 BLOCK_C64_TRAFFIC_26Q = {  # the block kernels' ncu captures at 26 qubits
-    "k_fused_umma_tma<6,window>": 536.994304e6 + 476.178944e6,
+    "k_fused_umma_tma<6,window>": 536.994048e6 + 476.054528e6,
     "k_fused_umma_tma<6,rows>": 537.023232e6 + 476.058368e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
 }
