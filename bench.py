@@ -292,12 +292,14 @@ def box_runs(q, n):
 
 def step_kernel(plan, i, kind):
     """The kernel a plan step launches: block steps are told apart by their
-    qubits (at least 128 groups: qubits 0..k-1 run the rows form of the TMA
-    kernel; a set without qubit 0 whose qubits form at most 5 runs its box
-    form, reported as "window" for consecutive qubits and "box" otherwise;
-    other sets gather per thread: complex64 k_fused_umma<k>, complex128
-    k_fused_c128<k,gather>); other blocks the SIMT k_dense; other steps keep
-    their kind."""
+    qubits (at least 128 groups and at most 5 runs of block and other
+    qubits: a set starting with the run 0..a-1, a >= 4 for complex64 and 3
+    for complex128, runs the rows form of the TMA kernel, reported as "rows"
+    for qubits 0..k-1 and "lowrun" otherwise; another set with qubit 0
+    outside it or in the run 0, 1 its box form, reported as "window" for
+    consecutive qubits and "box" otherwise; other sets gather per thread:
+    complex64 k_fused_umma<k>, complex128 k_fused_c128<k,gather>); other
+    blocks the SIMT k_dense; other steps keep their kind."""
     if kind != "block":
         return kind
     q = sorted(plan.step_qubits(i))
@@ -306,10 +308,14 @@ def step_kernel(plan, i, kind):
         return "k_dense<%d>" % k
     full = plan.n - k >= 7
     name = "k_fused_c128" if plan.dtype == "c128" else "k_fused_umma_tma"
-    if full and q == list(range(k)):
-        return "%s<%d,rows>" % (name, k)
-    if full and q[0] >= 1 and box_runs(q, plan.n) <= 5:
-        return "%s<%d,%s>" % (name, k, "window" if q == list(range(q[0], q[0] + k)) else "box")
+    a = 0
+    while a < k and q[a] == a:
+        a += 1
+    if full and box_runs(q, plan.n) <= 5:
+        if a >= (3 if plan.dtype == "c128" else 4):
+            return "%s<%d,%s>" % (name, k, "rows" if a == k else "lowrun")
+        if a == 0 or a == 2:
+            return "%s<%d,%s>" % (name, k, "window" if q == list(range(q[0], q[0] + k)) else "box")
     return "k_fused_c128<%d,gather>" % k if plan.dtype == "c128" else "k_fused_umma<%d>" % k
 
 

@@ -44,9 +44,11 @@
 // slices of A, D columns each (two FP16 values per 32-bit column: re, im of
 // one amplitude), then five level accumulators of 2D FP32 columns: 240
 // columns at k = 4 (two CTAs per SM), 480 at k = 5 (one).  Three ways in:
-//   MODE 2: the block is qubits 0 .. k-1: 2^k / 8 two-dimensional TMA boxes
-//           (8 amplitudes x 128 rows, 128-byte swizzle) in, the same boxes
-//           out by TMA stores from a second stage;
+//   MODE 2: the block's qubits start with a run 0 .. a-1 of at least 8
+//           amplitudes (qubits 0 .. k-1, or such a run plus others):
+//           2^a / 8 TMA boxes (8 amplitudes of the low run x 128 rows x
+//           the other block qubits, 128-byte swizzle; make_lowrun_tmap) in,
+//           the same boxes out by TMA stores from a second stage;
 //   MODE 1: any set without qubit 0 forming at most 5 runs with the other
 //           qubits (windows, two-run sets): one TMA box of a view with up
 //           to 5 dimensions per tile in (make_runs_tmap), the same box out
@@ -84,6 +86,7 @@ struct C128Args {
   Ins ins;         // zero insertion at the k qubits
   u64 spread[32];  // spread[r]: OR of 2^qubits[i] over the set bits i of r
   RunBox rb;       // MODE 1: the tile's box (make_runs_tmap)
+  LowBox lb;       // MODE 2: the tile's pieces (make_lowrun_tmap)
 };
 
 template <int K, int MODE>
@@ -95,7 +98,6 @@ struct CShape {
   static constexpr uint32_t TCOLS = SET <= 256 ? 256 : 512;
   static constexpr int NSTAGE = MODE ? 1 : 0;               // TMA input stage
   static constexpr uint32_t OUT = MODE ? TILE : 0;     // output stage (TMA stores)
-  static constexpr uint32_t BOX = kUT * 128;                // MODE 2: 8 amplitudes x 128 rows
   static constexpr uint32_t DIG_BYTES = KR * KR * 2;        // one FP16 digit matrix of B
   static constexpr int NBLK = 2 * kDig - 1;                 // e_0 .. e_4, then e_4 .. e_1 scaled by 2^-9
   static constexpr uint32_t NB = NBLK * KR;                 // columns of the digit matrices side by side
@@ -213,12 +215,13 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   const int row = t & (kUT - 1), h = t / kUT;
   const uint32_t mb0 = smem_u32(mbar);
   const u64 gstep = (u64)gridDim.x * kUT;
+  // MODE 2: piece b of the low run (8 amplitudes), for every line, at box b
+  const uint32_t boxb = MODE == 2 ? S::TILE / (uint32_t)args.lb.nslice : 0;
   auto tile_load = [&](u64 gt, int st) {  // one thread
     const uint32_t mb = mb0 + 8 * st, dst = smem_u32(stage) + st * S::TILE;
     mbar_expect_tx(mb, S::TILE);
     if (MODE == 2) {
-#pragma unroll
-      for (int b = 0; b < D / 8; ++b) tma_load_2d(dst + b * S::BOX, &tmap, 16 * b, (int)gt, mb);
+      lowrun_load(dst, boxb, &tmap, gt, args.lb, mb);
     } else {
       run_load(dst, &tmap, gt, args.rb, 2, mb);
     }
@@ -258,8 +261,13 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       if (((APT * h) >> j) & 1) pbase += args.rb.multe[j];
   }
   const int pm[2] = {args.rb.multe[0], args.rb.multe[1]};
-  // MODE 2: this thread's amplitudes are units u0 .. u0 + APT - 1 of box h / BPR
+  // MODE 2: this thread's amplitudes are units u0 .. u0 + APT - 1 of the
+  // 8-amplitude piece h / BPR: piece (h / BPR) mod nslice of the low run, in
+  // line row + 128 ((h / BPR) / nslice) of its box
   const int u0 = (h % S::BPR) * APT;
+  const uint32_t rowoff = MODE == 2 ? (uint32_t)((h / S::BPR) % args.lb.nslice) * boxb +
+                                          (uint32_t)(row + kUT * ((h / S::BPR) / args.lb.nslice)) * 128u
+                                    : 0u;
   const __half2 k1280 = __floats2half2_rn(1280.f, 1280.f);
   uint32_t ph_full = 0, ph_mma = 0;  // phase bits (bit b: stage / TMEM set b)
 
@@ -281,8 +289,8 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       ph_full ^= 1u << buf;
       const unsigned char* stg = stage + buf * S::TILE;
       if (MODE == 2) {
-        // amplitude APT h + i is unit u0 + i of box h / BPR, stored at unit (u0 + i) ^ (row mod 8)
-        const unsigned char* rb = stg + (h / S::BPR) * S::BOX + row * 128;
+        // amplitude APT h + i is unit u0 + i of this thread's line, stored at unit (u0 + i) ^ (row mod 8)
+        const unsigned char* rb = stg + rowoff;
 #pragma unroll
         for (int i = 0; i < APT; ++i)
           v[i] = *reinterpret_cast<const ulonglong2*>(rb + (((u0 + i) ^ (row & 7)) << 4));
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
         o = scaled_pairs(vr, vi, delta);
       }
       if (MODE == 2) {
-        *reinterpret_cast<double2*>(outst + (h / S::BPR) * S::BOX + row * 128 + (((u0 + p) ^ (row & 7)) << 4)) = o;
+        *reinterpret_cast<double2*>(outst + rowoff + (((u0 + p) ^ (row & 7)) << 4)) = o;
       } else if (MODE == 1) {
         reinterpret_cast<double2*>(outst)[run_elem_pos<2>(pbase, pm, p)] = o;  // the input stage's layout
       } else if (valid) {
@@ -437,8 +445,7 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
       __syncthreads();
       if (t == 0) {
         if (MODE == 2) {
-#pragma unroll
-          for (int b = 0; b < D / 8; ++b) tma_store_2d(&tmap, 16 * b, (int)gt, smem_u32(outst) + b * S::BOX);
+          lowrun_store(&tmap, gt, args.lb, smem_u32(outst), boxb);
         } else {
           run_store(&tmap, gt, args.rb, 2, smem_u32(outst));
         }
@@ -469,23 +476,6 @@ __global__ void __launch_bounds__(CShape<K, MODE>::NT, CShape<K, MODE>::MINB)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
-}
-
-// The 2-D tensor map (64-bit words, group) of a complex128 state for a
-// block on qubits 0 .. k-1: box = 8 amplitudes x 128 groups, 128-byte swizzle.
-qs_status make_rows_tmap128(qs_state* st, int k, CUtensorMap* map) {
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  qs_status s0 = tmap_encoder(&encode);
-  if (s0 != QS_OK) return s0;
-  const cuuint64_t dims[2] = {cuuint64_t(2) << k, cuuint64_t(1) << (st->n - k)};
-  const cuuint64_t strides[1] = {(cuuint64_t(1) << k) * 16};
-  const cuuint32_t box[2] = {16, (cuuint32_t)kUT};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, st->amp, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_c128: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return QS_OK;
 }
 
 // CTAs per SM from shared memory, registers and TMEM columns, times the SMs.
@@ -540,12 +530,9 @@ qs_status launch_c128(qs_state* s, const int* q, const uint4* Bdig, int F, bool 
   const bool full = s->n - K >= 7;  // whole tiles of 128 groups
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  if (full && q[K - 1] == K - 1) {
-    qs_status st = make_rows_tmap128(s, K, &map);
-    if (st != QS_OK) return st;
-    return launch_mode<K, 2>(s, A, Bdig, F, map, dfl);
-  }
   qs_status est = QS_OK;
+  if (full && make_lowrun_tmap(s->amp, s->n, K, q, 2, 8, &map, &A.lb, &est)) return launch_mode<K, 2>(s, A, Bdig, F, map, dfl);
+  if (est != QS_OK) return est;
   if (full && make_runs_tmap(s->amp, s->n, K, q, 2, &map, &A.rb, &est)) return launch_mode<K, 1>(s, A, Bdig, F, map, dfl);
   if (est != QS_OK) return est;
   return launch_mode<K, 0>(s, A, Bdig, F, map, dfl);

@@ -17,8 +17,9 @@
 // for the complex64 path.
 //
 // Two kernels, by the block's qubits (sorted ascending):
-//   k_fused_umma_tma   a set without qubit 0 forming at most 5 runs with the
-//                      other qubits, or qubits 0 .. k-1: each tile moves by
+//   k_fused_umma_tma   a set forming at most 5 runs with the other qubits
+//                      (qubit 0 outside it or in the run 0, 1), or
+//                      qubits 0 .. k-1: each tile moves by
 //                      TMA (one box of up to 5 dimensions, or 2^k / 16
 //                      swizzled 2-D boxes in and out); FP16 parts.
 //   k_fused_umma       any other set: per-thread gathers; TF32 parts.
@@ -63,6 +64,7 @@ struct FusedArgs {
   Ins ins;         // zero insertion at the k qubits (amplitude index space)
   u64 spread[64];  // spread[r]: OR of 2^qubits[i] over the set bits i of r
   RunBox rb;       // k_fused_umma_tma, ROWS = false: the tile's box (make_runs_tmap)
+  LowBox lb;       // k_fused_umma_tma, ROWS = true: the tile's pieces (make_lowrun_tmap)
 };
 
 // ---------------------------------------------------------------------------
@@ -391,8 +393,9 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
   lo = h2bits(__floats2half2_rn(a - hf.x, b - hf.y));
 }
 // ---------------------------------------------------------------------------
-// Blocks on any qubit set without qubit 0 whose qubits, with the tile's,
-// form at most 5 runs (windows, two-run sets; full tiles):
+// Blocks on any qubit set whose qubits, with the others, form at most 5
+// runs, qubit 0 outside the set or in the run 0, 1 (windows, two-run sets;
+// full tiles):
 // k_fused_umma_tma.  A tile of 128 consecutive groups is then one box of a
 // view of the state with up to 5 dimensions (make_runs_tmap): a single TMA
 // copy (cp.async.bulk.tensor, completion counted on an mbarrier) moves it
@@ -411,14 +414,15 @@ __device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint
 // ---------------------------------------------------------------------------
 // ROWS = false: the run box above; the outputs go out by one TMA store from
 // a second stage at k = 6, by 8-byte stores at k = 4, 5.  ROWS = true: the
-// block is qubits 0 .. k-1, so a tile is 128
-// contiguous rows of 2^k amplitudes: 2^k / 16 boxes of 16 amplitudes x 128
-// rows each, in 128-byte-swizzled layout (16-byte unit c of row r stored at
-// unit c ^ (r mod 8)), one per 16-amplitude slice, which is exactly one
-// thread's share of a row: the row reads and the output writes are then
-// conflict-free 16-byte accesses, and the outputs leave through a second
-// stage with TMA stores (a row per lane would touch 32 cache lines per
-// warp store).
+// block's qubits start with a run 0 .. a-1 of at least 16 amplitudes
+// (qubits 0 .. k-1, or such a run plus others, as QFT blocks are): the tile
+// moves as 2^a / 16 boxes (make_lowrun_tmap), box b holding amplitudes
+// 16 b .. 16 b + 15 of the low run for every row and every value of the
+// other block qubits, in 128-byte-swizzled layout (16-byte unit c of smem
+// line L stored at unit c ^ (L mod 8)); a thread's 16 amplitudes are one
+// line of one box, so the reads and the output writes are conflict-free
+// 16-byte accesses, and the outputs leave through a second stage with TMA
+// stores (a row per lane would touch 32 cache lines per warp store).
 template <int K, bool ROWS>
 struct TShape {
   static constexpr int D = 1 << K, KR = 2 * D, H = KR / 32, NT = kUT * H;
@@ -428,7 +432,6 @@ struct TShape {
   // scatter's store issue was the longest phase)
   static constexpr bool TSTORE = ROWS || K == 6;
   static constexpr uint32_t OUT = TSTORE ? STAGE : 0;
-  static constexpr uint32_t BOX = kUT * 16 * 8;  // ROWS: one 16-amplitude slice of the tile
   static constexpr uint32_t B_BYTES = KR * KR * 2, LBO_B = (KR / 8) * 128, SBO = 128;
   static constexpr uint32_t SETCOLS = 2 * KR;  // one tile's TMEM: A hi, A lo (KR / 2 each), accumulator
   static constexpr uint32_t TCOLS = 2 * SETCOLS;  // two tiles in flight
@@ -458,11 +461,12 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   const uint32_t mb_full = smem_u32(mbar), mb_mma0 = smem_u32(mbar + 1);
   const u64 gstep = (u64)gridDim.x * kUT;
   u64 g = (u64)blockIdx.x * kUT;
+  // ROWS: piece b of the low run, for every line, at box b (STAGE / nslice bytes)
+  const uint32_t boxb = ROWS ? S::STAGE / (uint32_t)args.lb.nslice : 0;
   auto tile_load = [&](u64 gt) {  // one thread
     mbar_expect_tx(mb_full, S::STAGE);
     if (ROWS) {
-#pragma unroll
-      for (int b = 0; b < D / 16; ++b) tma_load_2d(smem_u32(stage) + b * S::BOX, &tmap, 16 * b, (int)gt, mb_full);
+      lowrun_load(smem_u32(stage), boxb, &tmap, gt, args.lb, mb_full);
     } else {
       run_load(smem_u32(stage), &tmap, gt, args.rb, 1, mb_full);
     }
@@ -511,6 +515,11 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
   constexpr uint32_t idesc = umma_idesc_f16(kUT, KR);
+  // ROWS: this thread's 16 amplitudes are piece h mod nslice of the low run
+  // in line row + 128 (h / nslice) of its box
+  const uint32_t rowoff = ROWS ? (uint32_t)(h % args.lb.nslice) * boxb +
+                                     (uint32_t)(row + kUT * (h / args.lb.nslice)) * 128u
+                               : 0u;
   // ROWS = false: element 16 h + i of this row at pbase + (multipliers of i's bits)
   const int pbase = ROWS ? 0
                          : run_row_pos(args.rb, row) + ((h & 1) ? args.rb.multe[4] : 0) + ((h & 2) ? args.rb.multe[5] : 0);
@@ -527,13 +536,20 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
     ph_full ^= 1u;
     float2 v[16];
     if (ROWS) {
-      // this thread's slice is box h; its row's 16-byte unit c sits at c ^ (row mod 8)
-      const float4* rowp = reinterpret_cast<const float4*>(sm + h * S::BOX + row * 128);
+      // 16-byte unit c of this thread's line sits at c ^ (row mod 8)
+      const float4* rowp = reinterpret_cast<const float4*>(sm + rowoff);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const float4 q = rowp[c ^ (row & 7)];
         v[2 * c] = make_float2(q.x, q.y);
         v[2 * c + 1] = make_float2(q.z, q.w);
+      }
+    } else if (pm[0] == 1) {  // qubits 0, 1 in the block: elements 2j, 2j + 1 adjacent
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(stage + run_elem_pos<4>(pbase, pm, i));
+        v[i] = make_float2(q.x, q.y);
+        v[i + 1] = make_float2(q.z, q.w);
       }
     } else {
 #pragma unroll
@@ -611,7 +627,7 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
       gsc = norm_correction(nin, nout);
     }
     if (ROWS) {
-      float4* rowo = reinterpret_cast<float4*>(outst + h * S::BOX + row * 128);
+      float4* rowo = reinterpret_cast<float4*>(outst + rowoff);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
         rowo[c ^ (row & 7)] = make_float4(fmaf(o[4 * c], gsc, o[4 * c]), fmaf(o[4 * c + 1], gsc, o[4 * c + 1]),
@@ -619,17 +635,26 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
       if (t == 0) {
-#pragma unroll
-        for (int bx = 0; bx < D / 16; ++bx) tma_store_2d(&tmap, 16 * bx, (int)gt, smem_u32(outst) + bx * S::BOX);
+        lowrun_store(&tmap, gt, args.lb, smem_u32(outst), boxb);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     } else if (S::TSTORE) {
       // the output tile in the input stage's layout, then one TMA store
       float2* outw = reinterpret_cast<float2*>(outst);
+      if (pm[0] == 1) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int j = 2 * i;
-        outw[run_elem_pos<4>(pbase, pm, i)] = make_float2(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]));
+        for (int i = 0; i < 16; i += 2) {
+          const int j = 2 * i;
+          *reinterpret_cast<float4*>(outw + run_elem_pos<4>(pbase, pm, i)) =
+              make_float4(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]), fmaf(o[j + 2], gsc, o[j + 2]),
+                          fmaf(o[j + 3], gsc, o[j + 3]));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = 2 * i;
+          outw[run_elem_pos<4>(pbase, pm, i)] = make_float2(fmaf(o[j], gsc, o[j]), fmaf(o[j + 1], gsc, o[j + 1]));
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
@@ -674,23 +699,6 @@ __global__ void __launch_bounds__(TShape<K, ROWS>::NT, TShape<K, ROWS>::MINB)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
-// The 2-D tensor map (e, group) of a state for a block on qubits 0 .. k-1:
-// box = 16 amplitudes x 128 groups, 128-byte swizzle.
-qs_status make_rows_tmap(qs_state* st, int k, CUtensorMap* map) {
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  qs_status s0 = tmap_encoder(&encode);
-  if (s0 != QS_OK) return s0;
-  const cuuint64_t dims[2] = {cuuint64_t(1) << k, cuuint64_t(1) << (st->n - k)};
-  const cuuint64_t strides[1] = {(cuuint64_t(1) << k) * 8};
-  const cuuint32_t box[2] = {16, (cuuint32_t)kUT};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, st->amp, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(QS_ECUDA, "fused_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return QS_OK;
-}
-
 // Grid for a block kernel: CTAs per SM from shared memory, registers and TMEM
 // columns (the occupancy query does not know about TMEM), times the SMs.
 template <int K, typename Kern>
@@ -719,20 +727,24 @@ qs_status launch_umma(qs_state* s, const FusedArgs& A, const float* B, int renor
   const u64 ngroups = u64(1) << (s->n - K);
   const bool full = ngroups >= (u64)kUT;
   unsigned grid = 0;
-  // qubits ascending: the block is qubits 0 .. K-1 exactly when the last is K-1
-  if (full && qubits[K - 1] == K - 1) {
-    typedef TShape<K, true> ST;
+  // a low run 0 .. a-1 of at least 16 amplitudes (qubits 0 .. K-1 among
+  // them): 128-byte swizzled pieces
+  {
+    FusedArgs AL = A;
     CUtensorMap map;
-    qs_status st = make_rows_tmap(s, K, &map);
-    if (st != QS_OK) return st;
-    st = block_grid<K>(s, k_fused_umma_tma<K, true>, ST::NT, ST::SMEM, ST::TCOLS, grid);
-    if (st != QS_OK) return st;
-    k_fused_umma_tma<K, true><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B, A,
-                                                                       map, renorm);
-    return launch_ok("k_fused_umma_tma");
+    qs_status est = QS_OK;
+    if (full && make_lowrun_tmap(s->amp, s->n, K, qubits, 1, 16, &map, &AL.lb, &est)) {
+      typedef TShape<K, true> ST;
+      qs_status st = block_grid<K>(s, k_fused_umma_tma<K, true>, ST::NT, ST::SMEM, ST::TCOLS, grid);
+      if (st != QS_OK) return st;
+      k_fused_umma_tma<K, true><<<grid, ST::NT, ST::SMEM, s->stream>>>(static_cast<float2*>(s->amp), ngroups, B,
+                                                                         AL, map, renorm);
+      return launch_ok("k_fused_umma_tma");
+    }
+    if (est != QS_OK) return est;
   }
-  // any set without qubit 0 whose qubits (with the tile's) form at most 5
-  // runs: one TMA box per tile
+  // any other set whose qubits form at most 5 runs (qubit 0 outside it or
+  // in the run 0, 1): one TMA box per tile
   {
     FusedArgs AR = A;
     CUtensorMap map;

@@ -305,15 +305,16 @@ std::vector<char> touched(const std::vector<const qs_gate_rec*>& gates, int n) {
 // Tensor-core blocks (both dtypes): the qubits a block runs on, given those its
 // gates touch.  Idle qubits cost nothing there (a block is one HBM pass
 // whatever its width), but the kernel depends on the set's shape: with at
-// least 128 groups, qubits 0 .. k-1 move as contiguous rows and any set
-// without qubit 0 whose qubits form at most 5 runs (with the others') as
-// one TMA box per tile; other sets gather per thread and run at about 0.7
-// of the speed.  The touched qubits are widened to the narrowest window of
+// least 128 groups and at most 5 runs of block and other qubits, a set
+// starting with the run 0 .. a-1 (a >= 4; 3 for complex128) moves as
+// 128-byte swizzled pieces, any other set with qubit 0 outside it or in the
+// run 0, 1 as one TMA box per tile; other sets gather per thread and run at
+// about 0.7 of the speed.  The touched qubits are widened to the narrowest window of
 // consecutive qubits that holds them (at least 4 qubits, at most kmax;
 // starting at 2 or above if possible, else at 0, else at 1); when none
 // exists, to at
-// least 4 qubits by idle ones next to the touched ones (not qubit 0, which
-// would make the set a gather), so no run is added.
+// least 4 qubits by idle ones next to the touched ones (not qubit 0), so no
+// run is added.
 uint64_t tc_block_mask(uint64_t used, int n, int kmax) {
   if (!used) return 0;
   const int lo = __builtin_ctzll(used), hi = 63 - __builtin_clzll(used);
@@ -335,17 +336,20 @@ uint64_t tc_block_mask(uint64_t used, int n, int kmax) {
 }
 
 // Whether a tensor-core block on `mask` runs near HBM speed: its tiles move
-// by TMA (see above), and the box's innermost run holds at least two of
-// the tile's qubits (a block on qubit 1 leaves 16-byte pieces, 0.6 of the
-// speed).
+// by TMA (see above) in pieces of at least 64 bytes: a low run 0 .. a-1
+// with a >= 4 as 128-byte swizzled pieces, or a set without qubits 0 and 1
+// (one holding qubit 1 leaves 16- or 32-byte pieces, 0.6-0.8 of the speed;
+// one holding qubit 0 in a run of 1 or 3 gathers).
 bool tc_mask_fast(uint64_t mask, int n) {
   const int k = __builtin_popcountll(mask);
   if (n - k < 7) return false;
-  if (mask == (uint64_t(1) << k) - 1) return true;  // qubits 0 .. k-1
-  if (mask & 3) return false;
   int runs = 1;
   for (int q = 1; q < n; ++q) runs += ((mask >> q) & 1) != ((mask >> (q - 1)) & 1);
-  return runs <= 5;
+  if (runs > 5) return false;
+  int a = 0;  // the run 0 .. a-1
+  while (a < n && ((mask >> a) & 1)) ++a;
+  if (a >= 4) return true;    // 128-byte swizzled pieces (qubits 0 .. k-1 among these)
+  return (mask & 3) == 0;     // qubit 0 or 1 in the set: gathered, or boxes of 16- or 32-byte pieces
 }
 
 std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax, bool* fast) {

@@ -174,9 +174,12 @@ inline qs_status tmap_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
 // holds at least 5 of the tile's qubits, else 2^(5 - t)-way bank conflicts
 // for a first run of t tile qubits) when that run holds at least
 // kNaturalMinTile of them, else the runs holding tile qubits first (rows
-// r at r + 128 e, free of bank conflicts, shorter bursts).  Needs qubit 0
-// outside the block (dimension 0 is the contiguous one), 2^(n-k) >= 128 and
-// at most 5 runs; false otherwise.  words: 64-bit words per amplitude (1:
+// r at r + 128 e, free of bank conflicts, shorter bursts).  When qubit 0 is
+// in the block, its run must be qubits 0 and 1 exactly: that run is
+// dimension 0, the contiguous one (32-byte pieces; a run of 1 leaves 16-byte
+// pieces and measured slower than gathering), and an element and its
+// neighbour in it are adjacent: complex64 reads them as one 16-byte word.
+// Needs 2^(n-k) >= 128 and at most 5 runs; false otherwise.  words: 64-bit words per amplitude (1:
 // complex64, 2: complex128).  A non-block run's qubits are consecutive
 // bits of the group index, so tile g's coordinate along it is
 // (g >> gb) & (2^len - 1) (times `words` for d = 0); along block runs 0.
@@ -191,7 +194,9 @@ struct RunBox {
 inline bool make_runs_tmap(void* amp, int n, int k, const int* q_sorted, int words, CUtensorMap* map, RunBox* rb,
                            qs_status* st) {
   *st = QS_OK;
-  if (n - k < 7 || q_sorted[0] == 0 || k > 6) return false;
+  if (n - k < 7 || k > 6) return false;
+  if (q_sorted[k - 1] == k - 1) return false;  // qubits 0 .. k-1: the rows form
+  if (q_sorted[0] == 0 && !(q_sorted[1] == 1 && q_sorted[2] > 2)) return false;  // qubit 0 in a run other than 2
   uint64_t inb = 0;
   for (int i = 0; i < k; ++i) inb |= uint64_t(1) << q_sorted[i];
   int tilebit[64] = {0};  // 1: one of the 7 lowest non-block qubits
@@ -210,7 +215,14 @@ inline bool make_runs_tmap(void* amp, int n, int k, const int* q_sorted, int wor
   }
   if (runs.size() > 5) return false;
   std::vector<Run> ord;
-  if (runs[0].tile >= kNaturalMinTile) {
+  if (runs[0].block) {
+    // qubits 0, 1 in the block: that run stays innermost, then
+    // the tile's runs, the other block runs and the rest
+    ord.push_back(runs[0]);
+    for (const Run& r : runs) if (!r.block && r.tile) ord.push_back(r);
+    for (size_t i = 1; i < runs.size(); ++i) if (runs[i].block) ord.push_back(runs[i]);
+    for (const Run& r : runs) if (!r.block && !r.tile) ord.push_back(r);
+  } else if (runs[0].tile >= kNaturalMinTile) {
     ord = runs;
   } else {
     for (const Run& r : runs) if (!r.block && r.tile) ord.push_back(r);
@@ -255,6 +267,134 @@ inline bool make_runs_tmap(void* amp, int n, int k, const int* q_sorted, int wor
     return false;
   }
   return true;
+}
+// Blocks whose qubits start with a run 0 .. a-1 long enough for 128-byte
+// row pieces (2^a amplitudes >= slice_amps: 16 for complex64, 8 for
+// complex128), plus any other runs (at most 5 runs in all): the tile moves
+// as 2^a / slice_amps boxes, box b holding piece b of the low run (slice_amps
+// amplitudes = 128 bytes) for the tile's 128 rows and every value of the
+// other block qubits, 128-byte swizzled (16-byte unit c of smem line L at
+// c ^ (L mod 8)).  Dimensions: the low run (extent slice_amps), the runs
+// holding the tile's qubits, the other block runs, the rest; line
+// L = r + 128 e_hi, e_hi the block index above the low run.  Qubits
+// 0 .. k-1 are the case without other runs.
+struct LowBox {
+  int8_t gb[5];   // dimension d's coordinate: group-index bits gb .. gb + len - 1 (gb < 0: none)
+  int8_t len[5];
+  int rank;
+  int nslice;     // boxes per tile (2^a / slice_amps)
+  int slice_words;  // 64-bit words of one piece (16)
+};
+inline bool make_lowrun_tmap(void* amp, int n, int k, const int* q_sorted, int words, int slice_amps,
+                             CUtensorMap* map, LowBox* lb, qs_status* st) {
+  *st = QS_OK;
+  if (n - k < 7 || k > 6) return false;
+  int a = 0;
+  while (a < k && q_sorted[a] == a) ++a;
+  if ((1 << a) < slice_amps) return false;
+  uint64_t inb = 0;
+  for (int i = 0; i < k; ++i) inb |= uint64_t(1) << q_sorted[i];
+  int tilebit[64] = {0};
+  for (int q = 0, c = 0; q < n && c < 7; ++q)
+    if (!((inb >> q) & 1)) { tilebit[q] = 1; ++c; }
+  struct Run { int lo, len, tile, block; };
+  std::vector<Run> runs;
+  for (int q = 0; q < n;) {
+    const int b = (int)((inb >> q) & 1);
+    int e = q;
+    while (e < n && (int)((inb >> e) & 1) == b) ++e;
+    int t = 0;
+    for (int x = q; x < e; ++x) t += tilebit[x];
+    runs.push_back(Run{q, e - q, t, b});
+    q = e;
+  }
+  if (runs.size() > 5) return false;
+  std::vector<Run> ord;
+  ord.push_back(runs[0]);  // the low run 0 .. a-1
+  for (const Run& r : runs) if (!r.block && r.tile) ord.push_back(r);
+  for (size_t i = 1; i < runs.size(); ++i) if (runs[i].block) ord.push_back(runs[i]);
+  for (const Run& r : runs) if (!r.block && !r.tile) ord.push_back(r);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  *st = tmap_encoder(&encode);
+  if (*st != QS_OK) return false;
+  const int rank = (int)ord.size();
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int d = 0; d < 5; ++d) {
+    lb->gb[d] = -1;
+    lb->len[d] = 0;
+    if (d >= rank) continue;
+    const Run& r = ord[d];
+    dims[d] = (cuuint64_t(1) << r.len) * (d == 0 ? words : 1);
+    box[d] = d == 0 ? (cuuint32_t)(slice_amps * words) : (cuuint32_t)(r.block ? (1u << r.len) : (1u << r.tile));
+    if (d > 0) strides[d - 1] = (cuuint64_t(1) << r.lo) * 8 * words;
+    if (d > 0 && !r.block) {
+      int below = 0;
+      for (int x = 0; x < r.lo; ++x) below += !((inb >> x) & 1);
+      lb->gb[d] = (int8_t)below;
+      lb->len[d] = (int8_t)r.len;
+    }
+  }
+  lb->rank = rank;
+  lb->nslice = (1 << a) / slice_amps;  // at most 4: 2^6 / 16 (complex64), 2^5 / 8 (complex128)
+  lb->slice_words = slice_amps * words;
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, amp, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *st = fail(QS_ECUDA, "cuTensorMapEncodeTiled (low-run box) failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+// Every piece of tile g: box b (b < nslice <= 4) at dst0 + b * boxb, its
+// coordinates computed once (one thread).
+__device__ __forceinline__ void lowrun_coords(uint64_t g, const LowBox& lb, int (&c)[5]) {
+  c[0] = 0;
+#pragma unroll
+  for (int d = 1; d < 5; ++d) c[d] = lb.gb[d] < 0 ? 0 : (int)((g >> lb.gb[d]) & ((uint64_t(1) << lb.len[d]) - 1));
+}
+__device__ __forceinline__ void lowrun_load(uint32_t dst0, uint32_t boxb, const CUtensorMap* map, uint64_t g,
+                                            const LowBox& lb, uint32_t mbar) {
+  int c[5];
+  lowrun_coords(g, lb, c);
+  if (lb.rank == 2) {  // qubits 0 .. k-1
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (b < lb.nslice) tma_load_2d(dst0 + b * boxb, map, b * lb.slice_words, c[1], mbar);
+    return;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (b >= lb.nslice) break;
+    c[0] = b * lb.slice_words;
+    switch (lb.rank) {
+      case 3: tma_load_3d(dst0 + b * boxb, map, c[0], c[1], c[2], mbar); break;
+      case 4: tma_load_4d(dst0 + b * boxb, map, c, mbar); break;
+      default: tma_load_5d(dst0 + b * boxb, map, c, mbar); break;
+    }
+  }
+}
+__device__ __forceinline__ void lowrun_store(const CUtensorMap* map, uint64_t g, const LowBox& lb, uint32_t src0,
+                                             uint32_t boxb) {
+  int c[5];
+  lowrun_coords(g, lb, c);
+  if (lb.rank == 2) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (b < lb.nslice) tma_store_2d(map, b * lb.slice_words, c[1], src0 + b * boxb);
+    return;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (b >= lb.nslice) break;
+    c[0] = b * lb.slice_words;
+    switch (lb.rank) {
+      case 3: tma_store_3d(map, c[0], c[1], c[2], src0 + b * boxb); break;
+      case 4: tma_store_4d(map, c, src0 + b * boxb); break;
+      default: tma_store_5d(map, c, src0 + b * boxb); break;
+    }
+  }
 }
 // The tile's box coordinates (see make_runs_tmap).
 __device__ __forceinline__ void run_coords(uint64_t g, const RunBox& rb, int words, int (&c)[5]) {

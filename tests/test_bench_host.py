@@ -19,11 +19,13 @@ def _runs(q, n):
 
 def test_step_kernel_labels(qs):
     import bench
-    # complex64: qubits 0..k-1 take the rows form of the TMA kernel; sets
-    # without qubit 0 forming at most 5 runs its box form ("window" when
-    # consecutive); other sets, and blocks with fewer than 128 groups, the
-    # per-thread gather kernel.  complex128 k = 4, 5 alike (k_fused_c128),
-    # 6-qubit requests narrowed to 5.
+    # with at most 5 runs of block and other qubits: sets starting with the
+    # run 0..a-1 (a >= 4; 3 for complex128) take the rows form of the TMA
+    # kernel ("rows" for 0..k-1, "lowrun" otherwise), other sets with qubit 0
+    # outside or in the run 0, 1 its box form ("window" when consecutive);
+    # other sets, and blocks with fewer than 128 groups, the per-thread
+    # gather kernel.  complex128 k = 4, 5 alike (k_fused_c128), 6-qubit
+    # requests narrowed to 5.
     seen = set()
     for dtype, n, fq, circ in (("c64", 14, 6, W.brick(14, 12, 3)), ("c64", 14, 6, W.qft(14)),
                                ("c64", 15, 5, W.qv_like(15, 6, 2)), ("c64", 9, 4, W.brick(9, 6, 1)),
@@ -40,13 +42,14 @@ def test_step_kernel_labels(qs):
             q = sorted(p.step_qubits(i))
             k = len(q)
             assert k <= (5 if dtype == "c128" else 6)
+            low = len([j for j in range(k) if q[j] == j and all(q[x] == x for x in range(j))])
             if k < 4:
                 want = "k_dense<%d>" % k
-            elif n - k < 7:
+            elif n - k < 7 or _runs(q, n) > 5:
                 want = gather % k
-            elif q == list(range(k)):
-                want = "%s<%d,rows>" % (name, k)
-            elif q[0] >= 1 and _runs(q, n) <= 5:
+            elif low >= (3 if dtype == "c128" else 4):
+                want = "%s<%d,%s>" % (name, k, "rows" if low == k else "lowrun")
+            elif low in (0, 2):
                 want = "%s<%d,%s>" % (name, k, "window" if q[-1] - q[0] + 1 == k else "box")
             else:
                 want = gather % k

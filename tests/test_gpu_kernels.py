@@ -246,11 +246,20 @@ def test_invalid_arguments_leave_state_unchanged(qs):
     (14, "window1"),      # ... from 1 (the tile's qubit 0, then the block, then the rest)
     (15, "tworuns"),      # two runs of block qubits: a 5-D box
     (16, "tworunsup"),    # ... the upper run ending at the top qubit (4 runs)
+    (15, "zero1"),        # qubit 0 in the block alone: gathered
+    (16, "zero2"),        # qubits 0, 1 in the block: the innermost box dimension, 16-byte pairs
+    (16, "lowrun"),       # qubits 0..3 plus high ones: 128-byte swizzled pieces per line
 ])
 def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
     # complex64 k = 4, 5, 6 blocks run on tcgen05; each way a group's
     # amplitudes are gathered and scattered, against the oracle
-    if qubits == "tworuns":
+    if qubits == "lowrun":
+        qsel = [12, 0, 2, 1, 3, 13][:k]
+    elif qubits == "zero1":
+        qsel = [6, 0, 5, 7, 8, 9][:k]
+    elif qubits == "zero2":
+        qsel = [10, 1, 0, 9, 11, 12][:k]
+    elif qubits == "tworuns":
         qsel = [9, 1, 10, 2, 11, 3][:k]
     elif qubits == "tworunsup":
         qsel = [15, 2, 14, 3, 13, 4][:k]
@@ -359,6 +368,9 @@ def test_apply_fused_c64_dynamic_range(qs, k, mode):
     (17, "window8"),      # ... from 8 (runs of 128 rows)
     (16, "high"),         # the block on the highest qubits
     (15, "tworuns"),      # two runs of block qubits: a 5-D box
+    (15, "zero1"),        # qubit 0 in the block alone: gathered
+    (16, "zero2"),        # qubits 0, 1 in the block: the innermost box dimension
+    (15, "lowrun"),       # qubits 0..2 plus high ones: 128-byte swizzled pieces per line
 ])
 def test_apply_fused_c128_tensor_core_access_modes(qs, k, n, qubits):
     # complex128 k = 4, 5 blocks run on tcgen05 with FP64 operands split into
@@ -366,6 +378,12 @@ def test_apply_fused_c128_tensor_core_access_modes(qs, k, n, qubits):
     # within 2^-36 of its group's norm
     if qubits == "tworuns":
         qsel = [9, 1, 10, 2, 11][:k]
+    elif qubits == "lowrun":
+        qsel = [11, 0, 2, 1, 12][:k]
+    elif qubits == "zero1":
+        qsel = [6, 0, 5, 7, 8][:k]
+    elif qubits == "zero2":
+        qsel = [10, 1, 0, 9, 11][:k]
     elif qubits is None:
         qsel = [1, 3, 4, 6, 8][:k]
     elif qubits == "gathered":
