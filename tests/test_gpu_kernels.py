@@ -285,6 +285,58 @@ def test_apply_fused_tensor_core_access_modes(qs, k, n, qubits):
     check(s.to_numpy(), want, "c64")
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_apply_fused_random_sets(qs, dtype):
+    # random qubit sets of 4..6 (complex128: 4, 5) qubits on 11..16 qubits:
+    # every way a tile can move (rows, low-run pieces, windows, run boxes,
+    # boxes with qubits 0 and 1, gathers) picked by the set's shape, against
+    # the oracle; the sets are drawn so that each shape class occurs
+    import bench
+    rng = np.random.default_rng(424242)
+    seen = set()
+
+    class _P:  # step_kernel's view of a one-block plan
+        def __init__(self, n, q):
+            self.n, self.dtype, self._q = n, dtype, q
+
+        def step_qubits(self, i):
+            return self._q
+
+    for trial in range(36):
+        n = int(rng.integers(11, 17))
+        k = int(rng.choice([4, 5, 6] if dtype == "c64" else [4, 5]))
+        shape = trial % 6
+        if shape == 0:    # low run plus high qubits
+            a = int(rng.integers(3, k + 1))
+            q = list(range(a)) + sorted(rng.choice(np.arange(a + 1, n), size=k - a, replace=False).tolist())
+        elif shape == 1:  # a window
+            s0 = int(rng.integers(0, n - k + 1))
+            q = list(range(s0, s0 + k))
+        elif shape == 2:  # qubits 0, 1 and others
+            q = [0, 1] + sorted(rng.choice(np.arange(3, n), size=k - 2, replace=False).tolist())
+        elif shape == 3:  # two runs
+            s1 = int(rng.integers(1, n - k))
+            a = int(rng.integers(1, k))
+            s2 = int(rng.integers(s1 + a + 1, n - (k - a) + 1)) if s1 + a + 1 <= n - (k - a) else None
+            q = list(range(s1, s1 + a)) + (list(range(s2, s2 + k - a)) if s2 is not None else
+                                           sorted(rng.choice(np.arange(s1 + a + 1, n), size=k - a, replace=False).tolist()))
+        else:             # scattered
+            q = sorted(rng.choice(np.arange(n), size=k, replace=False).tolist())
+        lab = bench.step_kernel(_P(n, sorted(q)), 0, "block")
+        seen.add(lab.split("<")[0] + "," + (lab.split(",")[1] if "," in lab else "gather>"))
+        psi = W.random_state(n, 9100 + trial)
+        M = W.random_unitary(1 << k, 9200 + trial)
+        perm = rng.permutation(k)
+        qsel = [q[i] for i in perm]
+        s = gpu_state(qs, psi, dtype)
+        s.apply_fused(qsel, M)
+        want = start(psi, dtype)
+        oracle.apply_dense(want, qsel, M)
+        check(s.to_numpy(), want, dtype)
+    name = "k_fused_c128" if dtype == "c128" else "k_fused_umma_tma"
+    assert {name + ",rows>", name + ",lowrun>", name + ",window>", name + ",box>"} <= seen, seen
+
+
 def _block_sets(k, mode):
     # one qubit set per tensor-core access path: a window of consecutive
     # qubits (TMA boxes), qubits 0..k-1 (TMA rows), a gathered set
