@@ -168,7 +168,14 @@ qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
 
 /* out = sum_t coeff[t] <psi|P_t|psi> for Pauli strings P_t with X on the
  * qubits set only in xmask[t], Z on those set only in zmask[t], Y on those
- * set in both.  1 <= nterms <= 65536. */
+ * set in both.  1 <= nterms <= 65536.  Terms sharing an X/Y mask form a
+ * group; groups whose X/Y bits fit a tile share tile passes over the
+ * state.  Arithmetic: complex128, and complex64 groups of several terms,
+ * exact products in double-float summed in FP64 (about 2^-46 of the sum of
+ * the term magnitudes); complex64 groups of one term and two-Z-bit classes
+ * in tile passes, FP32 products summed in FP32 per thread and tile, then in
+ * double-float and FP64 (within about 2^-20 of sum_t |coeff[t]| for a
+ * unit-norm state: the complex64 state's own precision). */
 qs_status qs_expect_pauli(qs_state* st, int nterms, const uint64_t* xmask,
                           const uint64_t* zmask, const double* coeff, double* out);
 

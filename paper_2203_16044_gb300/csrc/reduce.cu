@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "kcommon.cuh"
 #include "pauli.cuh"
@@ -297,6 +299,14 @@ struct PTilePass {
   int gi[kPassGroups];         // groups of this pass (indices into the group array)
   int hloc[kPassGroups];       // highest tile-local bit of the group's mask (-1: diagonal group)
   unsigned mloc[kPassGroups];  // the group's X/Y mask in tile-local bits
+  // complex64 register stages: single-term groups on one tile-local bit
+  // with no Z bit outside it, up to 3 bits per stage, evaluated from 2^nb
+  // amplitudes held in registers (the other groups loop over the tile)
+  int nst;
+  int8_t snb[kPassGroups];
+  int8_t sbit[kPassGroups][3];  // ascending local bits
+  int8_t sgg[kPassGroups][3];   // the group slot of each bit
+  unsigned staged;              // bit gg: group slot gg is evaluated in a stage
 };
 
 // h + l renormalised (the accumulators' low parts gather unnormalised error terms)
@@ -317,6 +327,9 @@ __device__ __forceinline__ u64 ptile_global(u64 F, const u64* spreadH, int L, un
 template <typename R> struct TileAmp;
 template <> struct TileAmp<float> {
   typedef float2 T;
+  // XOR swizzle of the tile's 16-amplitude (128-byte) rows: strided reads
+  // of the register stages stay free of bank conflicts
+  __device__ static unsigned sw(unsigned e) { return e ^ ((e >> 4) & 15u); }
   __device__ static T from(float2 v) { return v; }
   __device__ static void get(const T& v, dfl& re, dfl& im) {
     re = dfl{v.x, 0.f};
@@ -325,6 +338,7 @@ template <> struct TileAmp<float> {
 };
 template <> struct TileAmp<double> {
   typedef float4 T;
+  __device__ static unsigned sw(unsigned e) { return e; }
   __device__ static T from(double2 v) {
     const dfl r = d2df(v.x), i = d2df(v.y);
     return make_float4(r.h, r.l, i.h, i.l);
@@ -335,6 +349,50 @@ template <> struct TileAmp<double> {
   }
 };
 
+__device__ __forceinline__ float2 t_as_f2(float2 v) { return v; }
+
+// Stage si of a complex64 tile pass: every 2^NB amplitudes spanning the
+// stage's bits from the (swizzled) tile into registers, then for each
+// bit's group, over the pairs x, x ^ 2^b of the block, Re (or Im) of
+// conj(a_y) a_x in FP32, summed per thread; acc[j] receives bit j's sum.
+template <int NB>
+__device__ __forceinline__ void x_stage(const float2* t, unsigned tile, const PTilePass& P, int si, const bool (&odd)[3],
+                                        float (&acc)[3]) {
+  // the swizzle is linear over the index bits, so the swizzled offset of
+  // base | c's bits is sw(base) ^ sw(c's bits)
+  unsigned sp[1 << NB];
+  unsigned b[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) b[j] = j < NB ? (unsigned)P.sbit[si][j] : 0u;
+#pragma unroll
+  for (int c = 0; c < (1 << NB); ++c) {
+    unsigned o = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if ((c >> j) & 1) o |= 1u << b[j];
+    sp[c] = TileAmp<float>::sw(o);
+  }
+  for (unsigned i = threadIdx.x; i < (tile >> NB); i += kThreads) {
+    unsigned base = i;
+#pragma unroll
+    for (int j = 0; j < NB; ++j)  // a zero at each stage bit (ascending)
+      base = ((base >> b[j]) << (b[j] + 1)) | (base & ((1u << b[j]) - 1u));
+    const unsigned sb = TileAmp<float>::sw(base);
+    float2 v[1 << NB];
+#pragma unroll
+    for (int c = 0; c < (1 << NB); ++c) v[c] = t[sb ^ sp[c]];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+      for (int c = 0; c < (1 << NB); ++c) {
+        if ((c >> j) & 1) continue;
+        const float2 X = v[c], Y = v[c | (1 << j)];
+        acc[j] += !odd[j] ? fmaf(Y.x, X.x, Y.y * X.y) : fmaf(Y.x, X.y, -(Y.y * X.x));
+      }
+  }
+}
+__device__ __forceinline__ float2 t_as_f2(float4 v) { return make_float2(v.x, v.z); }  // unused (complex128)
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict__ a, int n,
                                                           const __grid_constant__ PTilePass P,
@@ -342,6 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
   typedef typename AmpV<R>::T A;
   typedef TileAmp<R> TA;
   typedef typename TA::T E;
+  // complex64 single-term and Z-class groups: FP32 products and per-tile
+  // FP32 sums (see qs_expect_pauli); complex128 and the other group kinds:
+  // exact products in double-float
+  constexpr bool kF32 = std::is_same<R, float>::value;
   extern __shared__ __align__(16) unsigned char psm[];
   u64* spreadH = reinterpret_cast<u64*>(psm);             // [2^r]
   E* t = reinterpret_cast<E*>(psm + sizeof(u64) * (1u << kTH));  // [2^(L + r)]
@@ -371,11 +433,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const unsigned e = e0 + u * kThreads;
-        if (e < tile) t[e] = TA::from(v[u]);
+        if (e < tile) t[TA::sw(e)] = TA::from(v[u]);
       }
     }
     __syncthreads();
+    if constexpr (kF32) {
+      for (int si = 0; si < P.nst; ++si) {
+        const int nb = P.snb[si];
+        bool odd[3] = {false, false, false};
+        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (j >= nb) break;
+          const PauliGroup& g = groups[P.gi[P.sgg[si][j]]];
+          odd[j] = __popcll(g.m & g.z[0]) & 1;
+        }
+        const float2* tf = reinterpret_cast<const float2*>(t);
+        if (nb == 3) x_stage<3>(tf, tile, P, si, odd, acc);
+        else if (nb == 2) x_stage<2>(tf, tile, P, si, odd, acc);
+        else x_stage<1>(tf, tile, P, si, odd, acc);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (j >= nb) break;
+          const PauliGroup& g = groups[P.gi[P.sgg[si][j]]];
+          const dfl c{acc[j], 0.f};
+          const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
+          if (!odd[j]) {
+            df_acc(ar, df_mul(w_r, c));
+            df_acc(ai, df_mul(w_i, c));
+          } else {
+            df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
+            df_acc(ai, df_mul(w_r, c));
+          }
+        }
+      }
+    }
     for (int gg = 0; gg < P.ng; ++gg) {
+      if (kF32 && ((P.staged >> gg) & 1u)) continue;
       const PauliGroup& g = groups[P.gi[gg]];
       const int h = P.hloc[gg];
       if (h < 0 && g.ncls > 0) {
@@ -386,17 +480,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
         dfl sc[kMaxClasses];
 #pragma unroll
         for (int c = 0; c < kMaxClasses; ++c) sc[c] = dfl{0.f, 0.f};
-        for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
-          dfl xr, xi;
-          TA::get(t[l], xr, xi);
-          dfl pw = df_mul(xr, xr);
-          df_acc(pw, df_mul(xi, xi));
-          const u64 x = ptile_global(F, spreadH, L, l);
+        if constexpr (kF32) {
+          // complex64: p_x and the class sums in FP32 over this thread's
+          // amplitudes of the tile (two chains per class), then one
+          // double-float step per class
+          float s2[kMaxClasses][2];
 #pragma unroll
-          for (int c = 0; c < kMaxClasses; ++c) {
-            if (c >= nc) break;
-            const float k = (float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c]));
-            df_acc(sc[c], df_mul(pw, dfl{k, 0.f}));
+          for (int c = 0; c < kMaxClasses; ++c) s2[c][0] = s2[c][1] = 0.f;
+          int par = 0;
+          for (unsigned l = threadIdx.x; l < tile; l += kThreads, par ^= 1) {
+            const float2 v = t_as_f2(t[TA::sw(l)]);
+            const float pw = fmaf(v.x, v.x, v.y * v.y);
+            const u64 x = ptile_global(F, spreadH, L, l);
+#pragma unroll
+            for (int c = 0; c < kMaxClasses; ++c) {
+              if (c >= nc) break;
+              const float k = (float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c]));
+              if (par) s2[c][1] = fmaf(k, pw, s2[c][1]);
+              else s2[c][0] = fmaf(k, pw, s2[c][0]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < kMaxClasses; ++c) sc[c] = dfl{s2[c][0] + s2[c][1], 0.f};
+        } else {
+          for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
+            dfl xr, xi;
+            TA::get(t[TA::sw(l)], xr, xi);
+            dfl pw = df_mul(xr, xr);
+            df_acc(pw, df_mul(xi, xi));
+            const u64 x = ptile_global(F, spreadH, L, l);
+#pragma unroll
+            for (int c = 0; c < kMaxClasses; ++c) {
+              if (c >= nc) break;
+              const float k = (float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c]));
+              df_acc(sc[c], df_mul(pw, dfl{k, 0.f}));
+            }
           }
         }
 #pragma unroll
@@ -410,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
         int since = 0;  // flush the double-float sums into FP64 every kU terms
         for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
           dfl xr, xi;
-          TA::get(t[l], xr, xi);
+          TA::get(t[TA::sw(l)], xr, xi);
           dfl fr, fi;
           fval_df(g, ptile_global(F, spreadH, L, l), fr, fi);
           dfl w = df_mul(xr, xr);
@@ -431,29 +549,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
         const unsigned mloc = P.mloc[gg], lo_mask = (1u << h) - 1u;
         const u64 z0 = g.z[0];
         const bool sm_odd = __popcll(g.m & z0) & 1;
-        dfl c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
+        dfl c;
+        if constexpr (kF32) {
+          // complex64: each pair's Re / Im p in FP32 (one FMA), summed in
+          // FP32 over this thread's pairs of the tile in four chains
+          float c4[4] = {0.f, 0.f, 0.f, 0.f};
+          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const unsigned k = k0 + u * kThreads;
-            if (k >= tile / 2) break;
-            const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
-            dfl xr, xi, yr, yi;
-            TA::get(t[l], xr, xi);
-            TA::get(t[l ^ mloc], yr, yi);
-            dfl c;
-            if (!sm_odd) {
-              c = df_mul(yr, xr);
-              df_acc(c, df_mul(yi, xi));
-            } else {
-              c = df_mul(yr, xi);
-              df_acc(c, df_mul(dfl{-yi.h, -yi.l}, xr));
+            for (int u = 0; u < 4; ++u) {
+              const unsigned k = k0 + u * kThreads;
+              if (k >= tile / 2) break;
+              const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
+              const float2 X = t_as_f2(t[TA::sw(l)]), Y = t_as_f2(t[TA::sw(l ^ mloc)]);
+              float cv = !sm_odd ? fmaf(Y.x, X.x, Y.y * X.y) : fmaf(Y.x, X.y, -(Y.y * X.x));
+              if (z0 && (__popcll(ptile_global(F, spreadH, L, l) & z0) & 1)) cv = -cv;
+              c4[u] += cv;
             }
-            if (z0 && (__popcll(ptile_global(F, spreadH, L, l) & z0) & 1)) c = dfl{-c.h, -c.l};
-            df_acc(c4[u], c);
           }
+          c = dfl{(c4[0] + c4[1]) + (c4[2] + c4[3]), 0.f};
+        } else {
+          dfl c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const unsigned k = k0 + u * kThreads;
+              if (k >= tile / 2) break;
+              const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
+              dfl xr, xi, yr, yi;
+              TA::get(t[TA::sw(l)], xr, xi);
+              TA::get(t[TA::sw(l ^ mloc)], yr, yi);
+              dfl cc;
+              if (!sm_odd) {
+                cc = df_mul(yr, xr);
+                df_acc(cc, df_mul(yi, xi));
+              } else {
+                cc = df_mul(yr, xi);
+                df_acc(cc, df_mul(dfl{-yi.h, -yi.l}, xr));
+              }
+              if (z0 && (__popcll(ptile_global(F, spreadH, L, l) & z0) & 1)) cc = dfl{-cc.h, -cc.l};
+              df_acc(c4[u], cc);
+            }
+          }
+          c = df_add(df_add(df_norm2(c4[0]), df_norm2(c4[1])), df_add(df_norm2(c4[2]), df_norm2(c4[3])));
         }
-        const dfl c = df_add(df_add(df_norm2(c4[0]), df_norm2(c4[1])), df_add(df_norm2(c4[2]), df_norm2(c4[3])));
         const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
         if (!sm_odd) {
           df_acc(ar, df_mul(w_r, c));
@@ -468,8 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
         for (unsigned k = threadIdx.x; k < tile / 2; k += kThreads) {
           const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
           dfl xr, xi, yr, yi;
-          TA::get(t[l], xr, xi);
-          TA::get(t[l ^ mloc], yr, yi);
+          TA::get(t[TA::sw(l)], xr, xi);
+          TA::get(t[TA::sw(l ^ mloc)], yr, yi);
           const u64 x = ptile_global(F, spreadH, L, l);
           dfl pr = df_mul(yr, xr), pi = df_mul(yr, xi);
           df_acc(pr, df_mul(yi, xi));
@@ -606,6 +744,29 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
         if ((mg >> q.H[j]) & 1) ml |= 1u << (kTL + j);
       q.mloc[gg] = ml;
       q.hloc[gg] = ml ? 31 - __builtin_clz(ml) : -1;
+    }
+    // complex64: single-term groups on one local bit with no Z bit outside
+    // it go to register stages of up to 3 bits
+    q.nst = 0;
+    q.staged = 0;
+    if (s->dtype == QS_C64) {
+      std::vector<std::pair<int, int>> one;  // (local bit, group slot)
+      for (int gg = 0; gg < q.ng; ++gg) {
+        const PauliGroup& G = groups[q.gi[gg]];
+        if (G.nt == 1 && __builtin_popcount(q.mloc[gg]) == 1 && (G.z[0] & ~G.m) == 0)
+          one.push_back({q.hloc[gg], gg});
+      }
+      std::sort(one.begin(), one.end());
+      for (size_t i = 0; i < one.size(); i += 3) {
+        const int nb = (int)std::min<size_t>(3, one.size() - i);
+        q.snb[q.nst] = (int8_t)nb;
+        for (int j = 0; j < nb; ++j) {
+          q.sbit[q.nst][j] = (int8_t)one[i + j].first;
+          q.sgg[q.nst][j] = (int8_t)one[i + j].second;
+          q.staged |= 1u << one[i + j].second;
+        }
+        ++q.nst;
+      }
     }
   }
   const unsigned gsz = red_grid(N / 2);
