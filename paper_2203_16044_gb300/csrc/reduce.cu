@@ -21,6 +21,7 @@
 // 30 qubits (one Z-only group and 30 single-X groups) takes three such
 // passes instead of 31.  Groups that fit no tile get a pass of their own.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include <type_traits>
@@ -28,6 +29,7 @@
 #include "dfloat.cuh"
 #include "kcommon.cuh"
 #include "pauli.cuh"
+#include "umma.cuh"
 
 namespace qs {
 namespace {
@@ -40,9 +42,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of up to two values; result valid in thread 0.
+// Block sum of up to two values over NT threads; result valid in thread 0.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kThreads / 32], sb[kThreads / 32];
+  __shared__ double sa[NT / 32], sb[NT / 32];
   a = warp_sum(a);
   b = warp_sum(b);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -50,8 +53,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   if (l == 0) { sa[w] = a; sb[w] = b; }
   __syncthreads();
   if (w == 0) {
-    a = l < kThreads / 32 ? sa[l] : 0.0;
-    b = l < kThreads / 32 ? sb[l] : 0.0;
+    a = l < NT / 32 ? sa[l] : 0.0;
+    b = l < NT / 32 ? sb[l] : 0.0;
     a = warp_sum(a);
     b = warp_sum(b);
   }
@@ -291,6 +294,28 @@ constexpr int kTL = 4;          // low qubits of every expectation tile (runs of
 constexpr int kTH = 9;          // at most this many chosen higher qubits per tile (8 for complex128)
 constexpr int kPassGroups = 16; // groups per tile pass
 
+constexpr int kTileThreads64 = 512;  // complex64 tile passes: CTA size
+constexpr int kStageThreads = 256;   // ... in two warp groups, each running its own register stages
+constexpr int kStageBits = 5;        // at most this many bits per register stage
+
+// A register stage of a complex64 tile pass: single-term groups on up to
+// kStageBits tile-local bits (X or Y on one qubit, Z only on that qubit).
+// Thread t holds the 2^nb amplitudes e | c, c over the stage bits, for e =
+// t's index bits placed at the tile bits tb[] plus each subset of the tile
+// bits dhi.  The lane bits tb[0..3] give the 16 lanes of a half warp
+// (8-byte reads) or the 8 lanes of a quarter warp (16-byte pair reads, in
+// stages holding bit 0) distinct banks of the swizzled tile.
+struct XStage {
+  int8_t nb, pair, gen, ntb;  // bits; bit 0 among them; some Y term; thread-index bits used
+  int8_t grp;                 // the warp group that runs the stage
+  int8_t odd;                 // bit j: bit j's term is Y (Im of the pair products)
+  int8_t slot0;               // first accumulator slot of the stage's bits
+  int8_t bit[kStageBits];     // ascending tile-local bits
+  int8_t gg[kStageBits];      // the group slot of each bit
+  int8_t tb[10];              // tile bit of thread-index bit i
+  unsigned dhi;               // the tile bits each thread enumerates
+};
+
 struct PTilePass {
   int L, r;                    // tile = L low qubits + r high qubits H[0..r)
   int H[kTH];
@@ -300,14 +325,23 @@ struct PTilePass {
   int hloc[kPassGroups];       // highest tile-local bit of the group's mask (-1: diagonal group)
   unsigned mloc[kPassGroups];  // the group's X/Y mask in tile-local bits
   // complex64 register stages: single-term groups on one tile-local bit
-  // with no Z bit outside it, up to 3 bits per stage, evaluated from 2^nb
-  // amplitudes held in registers (the other groups loop over the tile)
-  int nst;
-  int8_t snb[kPassGroups];
-  int8_t sbit[kPassGroups][3];  // ascending local bits
-  int8_t sgg[kPassGroups][3];   // the group slot of each bit
-  unsigned staged;              // bit gg: group slot gg is evaluated in a stage
+  // with no Z bit outside it, evaluated from 2^nb amplitudes held in
+  // registers (the other groups loop over the tile)
+  int nst, nsg;     // stages; staged groups (accumulator slots)
+  XStage st[kPassGroups];
+  unsigned staged;  // bit gg: group slot gg is evaluated in a stage
+  int allst;        // every group staged: no per-amplitude group loop
+  int clsg;         // complex64: slot of the Z-class group (-1: none), summed across tiles
+  int noflush;      // complex64: only staged and Z-class groups (no per-tile FP64 flush)
+  // complex64 tiles by TMA (tma != 0): dimension d of the tensor map is a
+  // run of qubits; tgb[d] >= 0: a run outside the tile, coordinate = bits
+  // tgb[d] .. tgb[d] + tlen[d] - 1 of the tile number
+  int tma, trank;
+  int8_t tgb[5], tlen[5];
 };
+
+// A TMA tile wait that gave up (about 1 s): reported by qs_expect_pauli.
+__device__ int g_expect_timeout;
 
 // h + l renormalised (the accumulators' low parts gather unnormalised error terms)
 __device__ __forceinline__ dfl df_norm2(dfl a) {
@@ -327,9 +361,10 @@ __device__ __forceinline__ u64 ptile_global(u64 F, const u64* spreadH, int L, un
 template <typename R> struct TileAmp;
 template <> struct TileAmp<float> {
   typedef float2 T;
-  // XOR swizzle of the tile's 16-amplitude (128-byte) rows: strided reads
-  // of the register stages stay free of bank conflicts
-  __device__ static unsigned sw(unsigned e) { return e ^ ((e >> 4) & 15u); }
+  // XOR swizzle of the 16-byte pieces (amplitude pairs) of the tile's
+  // 16-amplitude (128-byte) rows: strided reads of the register stages stay
+  // free of bank conflicts, and a pair stays whole for 16-byte copies
+  __device__ static unsigned sw(unsigned e) { return e ^ (((e >> 4) & 7u) << 1); }
   __device__ static T from(float2 v) { return v; }
   __device__ static void get(const T& v, dfl& re, dfl& im) {
     re = dfl{v.x, 0.f};
@@ -351,52 +386,100 @@ template <> struct TileAmp<double> {
 
 __device__ __forceinline__ float2 t_as_f2(float2 v) { return v; }
 
-// Stage si of a complex64 tile pass: every 2^NB amplitudes spanning the
-// stage's bits from the (swizzled) tile into registers, then for each
-// bit's group, over the pairs x, x ^ 2^b of the block, Re (or Im) of
-// conj(a_y) a_x in FP32, summed per thread; acc[j] receives bit j's sum.
-template <int NB>
-__device__ __forceinline__ void x_stage(const float2* t, unsigned tile, const PTilePass& P, int si, const bool (&odd)[3],
-                                        float (&acc)[3]) {
-  // the swizzle is linear over the index bits, so the swizzled offset of
-  // base | c's bits is sw(base) ^ sw(c's bits)
-  unsigned sp[1 << NB];
-  unsigned b[3];
+// Stage S of a complex64 tile pass over the (swizzled) tile t: for each
+// stage bit j's group, over the pairs x, x ^ 2^b_j of the tile, Re (and,
+// for stages with a Y term, Im) of conj(a_y) a_x in FP32, summed per thread
+// into re[j] (im[j]).  swt is the swizzled position of this thread's base
+// amplitude.  Positions: the swizzle is linear over XOR, and the enumerated
+// bits dhi lie above bit 6, where it is the identity, so the amplitude at
+// base | c | cur sits at (swt ^ sw(c)) + cur.
+template <int NB, bool PAIR, bool GEN>
+__device__ __forceinline__ void x_stage(const float2* __restrict__ t, unsigned swt, const XStage& S,
+                                        float (&re)[kStageBits], float (&im)[kStageBits]) {
+  const char* tb = reinterpret_cast<const char*>(t);
+  unsigned off[1 << NB];  // byte offsets
+  off[0] = swt * 8u;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) b[j] = j < NB ? (unsigned)P.sbit[si][j] : 0u;
-#pragma unroll
-  for (int c = 0; c < (1 << NB); ++c) {
-    unsigned o = 0;
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-      if ((c >> j) & 1) o |= 1u << b[j];
-    sp[c] = TileAmp<float>::sw(o);
+  for (int c = 1; c < (1 << NB); ++c) {
+    int j = 0;
+    while (!((c >> j) & 1)) ++j;
+    off[c] = off[c & (c - 1)] ^ (TileAmp<float>::sw(1u << S.bit[j]) * 8u);
   }
-  for (unsigned i = threadIdx.x; i < (tile >> NB); i += kThreads) {
-    unsigned base = i;
+  float r0[NB], r1[NB], i0[NB], i1[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j)  // a zero at each stage bit (ascending)
-      base = ((base >> b[j]) << (b[j] + 1)) | (base & ((1u << b[j]) - 1u));
-    const unsigned sb = TileAmp<float>::sw(base);
+  for (int j = 0; j < NB; ++j) r0[j] = r1[j] = i0[j] = i1[j] = 0.f;
+  const unsigned dhi = S.dhi;
+  unsigned cur = 0;
+  do {
     float2 v[1 << NB];
+    if constexpr (PAIR) {
 #pragma unroll
-    for (int c = 0; c < (1 << NB); ++c) v[c] = t[sb ^ sp[c]];
+      for (int c = 0; c < (1 << NB); c += 2) {
+        const float4 w = *reinterpret_cast<const float4*>(tb + off[c] + cur * 8u);
+        v[c] = make_float2(w.x, w.y);
+        v[c + 1] = make_float2(w.z, w.w);
+      }
+    } else {
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
+      for (int c = 0; c < (1 << NB); ++c) v[c] = *reinterpret_cast<const float2*>(tb + off[c] + cur * 8u);
+    }
+    // products in pair-major order: consecutive FMAs feed different bits'
+    // accumulators (Re: x parts into r0, y parts into r1)
 #pragma unroll
-      for (int c = 0; c < (1 << NB); ++c) {
+    for (int c = 0; c < (1 << NB); ++c) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
         if ((c >> j) & 1) continue;
         const float2 X = v[c], Y = v[c | (1 << j)];
-        acc[j] += !odd[j] ? fmaf(Y.x, X.x, Y.y * X.y) : fmaf(Y.x, X.y, -(Y.y * X.x));
+        r0[j] = fmaf(Y.x, X.x, r0[j]);
+        if constexpr (GEN) i0[j] = fmaf(Y.x, X.y, i0[j]);
       }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if ((c >> j) & 1) continue;
+        const float2 X = v[c], Y = v[c | (1 << j)];
+        r1[j] = fmaf(Y.y, X.y, r1[j]);
+        if constexpr (GEN) i1[j] = fmaf(-Y.y, X.x, i1[j]);
+      }
+    }
+    cur = ((cur | ~dhi) + 1u) & dhi;  // the next subset of dhi
+  } while (cur != 0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    re[j] = r0[j] + r1[j];
+    im[j] = i0[j] + i1[j];
   }
 }
-__device__ __forceinline__ float2 t_as_f2(float4 v) { return make_float2(v.x, v.z); }  // unused (complex128)
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict__ a, int n,
-                                                          const __grid_constant__ PTilePass P,
-                                                          const PauliGroup* __restrict__ groups, double2* part) {
+template <int NB>
+__device__ __forceinline__ void x_stage_any(const float2* t, unsigned swt, const XStage& S, float (&re)[kStageBits],
+                                            float (&im)[kStageBits]) {
+  if (S.pair) {
+    if (S.gen) x_stage<NB, true, true>(t, swt, S, re, im);
+    else x_stage<NB, true, false>(t, swt, S, re, im);
+  } else {
+    if (S.gen) x_stage<NB, false, true>(t, swt, S, re, im);
+    else x_stage<NB, false, false>(t, swt, S, re, im);
+  }
+}
+
+// Shared memory of a tile pass: spreadH, then (complex64) the threads'
+// stage positions and their double-float stage sums, then the tile
+// buffer(s).
+__host__ __device__ constexpr size_t ptile_stage_off() { return sizeof(u64) * (size_t(1) << kTH); }
+__host__ __device__ constexpr size_t ptile_acc_off(int nst, int nt) {
+  return ptile_stage_off() + ((sizeof(uint16_t) * (size_t)nst * (size_t)nt + 15) / 16) * 16;
+}
+__host__ __device__ constexpr size_t ptile_buf_off(int nst, int nsg, int nt) {
+  return ptile_acc_off(nst, nt) + sizeof(float2) * (size_t)nsg * (size_t)nt;
+}
+constexpr size_t kPtileAlign = 1024;  // the tile buffers' alignment (128-byte swizzle period)
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, int n,
+                                                    const __grid_constant__ PTilePass P,
+                                                    const __grid_constant__ CUtensorMap tmap,
+                                                    const PauliGroup* __restrict__ groups, double2* part) {
   typedef typename AmpV<R>::T A;
   typedef TileAmp<R> TA;
   typedef typename TA::T E;
@@ -406,69 +489,153 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
   constexpr bool kF32 = std::is_same<R, float>::value;
   extern __shared__ __align__(16) unsigned char psm[];
   u64* spreadH = reinterpret_cast<u64*>(psm);             // [2^r]
-  E* t = reinterpret_cast<E*>(psm + sizeof(u64) * (1u << kTH));  // [2^(L + r)]
+  constexpr int ST = kStageThreads;
+  const unsigned lt = threadIdx.x % ST, grp = threadIdx.x / ST;  // complex64 stages: thread within its warp group
+  uint16_t* swt = reinterpret_cast<uint16_t*>(psm + ptile_stage_off());  // [nst][ST]
+  float2* sacc = reinterpret_cast<float2*>(psm + ptile_acc_off(P.nst, ST));  // [nsg][ST] (hi, lo)
+  __shared__ __align__(8) uint64_t pmbar[2];  // TMA tiles: buffer b filled
+  const size_t boff = ptile_buf_off(kF32 ? P.nst : 0, kF32 ? P.nsg : 0, ST);
+  const uint32_t sbase = smem_u32(psm);
+  // (complex64 only: its launch adds kPtileAlign bytes for this pad)
+  const size_t bpad = kF32 ? (kPtileAlign - ((sbase + boff) & (kPtileAlign - 1))) & (kPtileAlign - 1) : 0;
+  E* const t0 = reinterpret_cast<E*>(psm + boff + bpad);  // [2^(L + r)] (complex64: two)
+  E* t = t0;
+  const bool use_tma = kF32 && P.tma;
+  if (use_tma && threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&pmbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&pmbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
   const A* av = reinterpret_cast<const A*>(a);
   const int L = P.L, r = P.r, m = L + r;
   const unsigned tile = 1u << m;
-  for (unsigned i = threadIdx.x; i < (1u << r); i += kThreads) {
+  for (unsigned i = threadIdx.x; i < (1u << r); i += NT) {
     u64 sp = 0;
     for (int j = 0; j < r; ++j)
       if ((i >> j) & 1u) sp |= u64(1) << P.H[j];
     spreadH[i] = sp;
   }
+  if constexpr (kF32)
+    for (int si = 0; si < P.nst; ++si) {  // this thread's swizzled base position in its group's stages
+      if (P.st[si].grp != (int)grp) continue;
+      unsigned d = 0;
+      for (int i = 0; i < P.st[si].ntb; ++i)
+        if ((lt >> i) & 1u) d |= 1u << P.st[si].tb[i];
+      swt[si * ST + lt] = (uint16_t)TA::sw(d);
+      for (int j = 0; j < P.st[si].nb; ++j) sacc[(P.st[si].slot0 + j) * ST + lt] = make_float2(0.f, 0.f);
+    }
   const u64 ntiles = u64(1) << (n - m);
   double sr = 0.0, si = 0.0;
   dfl ar{0.f, 0.f}, ai{0.f, 0.f};
-  __syncthreads();
-  for (u64 ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+  // complex64: two tile buffers, the next tile's 16-byte pieces copied
+  // asynchronously (cp.async) while the current one is evaluated
+  auto copy_tile = [&](u64 ti, int buf) {
     const u64 F = expand(ti << L, P.tins);
-    // the tile into shared memory, 4 loads in flight per thread
-    for (unsigned e0 = threadIdx.x; e0 < tile; e0 += 4 * kThreads) {
-      A v[4];
+    const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(t0) + (uint32_t)buf * tile * (uint32_t)sizeof(E);
+    for (unsigned c2 = threadIdx.x; c2 < tile / 2; c2 += NT) {
+      const unsigned e = 2 * c2;
+      const A* src = av + ptile_global(F, spreadH, L, e);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + TA::sw(e) * (uint32_t)sizeof(E)), "l"(src)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // ... or (thread 0) one TMA box: the tile's rows of 16 amplitudes with the
+  // 128-byte swizzle, which is TileAmp<float>::sw
+  auto tma_tile = [&](u64 ti, int buf) {
+    int c[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned e = e0 + u * kThreads;
-        if (e < tile) v[u] = av[ptile_global(F, spreadH, L, e)];
+    for (int d = 0; d < 5; ++d)
+      if (d < P.trank && P.tgb[d] >= 0) c[d] = (int)((ti >> P.tgb[d]) & ((u64(1) << P.tlen[d]) - 1));
+    const uint32_t mb = smem_u32(&pmbar[buf]);
+    const uint32_t dst = smem_u32(t0) + (uint32_t)buf * tile * (uint32_t)sizeof(E);
+    mbar_expect_tx(mb, tile * (uint32_t)sizeof(E));
+    if (P.trank == 3) tma_load_3d(dst, &tmap, c[0], c[1], c[2], mb);
+    else if (P.trank == 4) tma_load_4d(dst, &tmap, c, mb);
+    else if (P.trank == 5) tma_load_5d(dst, &tmap, c, mb);
+    else tma_load_2d(dst, &tmap, c[0], c[1], mb);
+  };
+  __syncthreads();
+  if constexpr (kF32) {
+    if ((u64)blockIdx.x < ntiles) {
+      if (!use_tma) copy_tile(blockIdx.x, 0);
+      else if (threadIdx.x == 0) tma_tile(blockIdx.x, 0);
+    }
+  }
+  // complex64 Z-class sums over the thread's tiles (there is one diagonal
+  // group, so at most one class group per pass)
+  dfl csum[kMaxClasses];
+#pragma unroll
+  for (int c = 0; c < kMaxClasses; ++c) csum[c] = dfl{0.f, 0.f};
+  int it = 0;
+  for (u64 ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+    const bool need_F = !(kF32 && P.allst);
+    const u64 F = need_F ? expand(ti << L, P.tins) : 0;
+    if (use_tma) {
+      if (threadIdx.x == 0 && ti + gridDim.x < ntiles) tma_tile(ti + gridDim.x, (it + 1) & 1);
+      const bool bad = !mbar_wait(smem_u32(&pmbar[it & 1]), (it >> 1) & 1);
+      if (__syncthreads_or(bad)) {
+        // a copy that never arrived: flag it, give the next tile's copy a
+        // bounded wait, and leave without a partial sum
+        if (threadIdx.x == 0) {
+          atomicExch(&g_expect_timeout, 1);
+          if (ti + gridDim.x < ntiles) mbar_wait(smem_u32(&pmbar[(it + 1) & 1]), ((it + 1) >> 1) & 1);
+        }
+        return;
       }
+      t = t0 + (size_t)(it & 1) * tile;
+    } else if constexpr (kF32) {
+      if (ti + gridDim.x < ntiles) {
+        copy_tile(ti + gridDim.x, (it + 1) & 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      t = t0 + (size_t)(it & 1) * tile;
+    } else {
+      // the tile into shared memory, 4 loads in flight per thread
+      for (unsigned e0 = threadIdx.x; e0 < tile; e0 += 4 * NT) {
+        A v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned e = e0 + u * kThreads;
-        if (e < tile) t[TA::sw(e)] = TA::from(v[u]);
+        for (int u = 0; u < 4; ++u) {
+          const unsigned e = e0 + u * NT;
+          if (e < tile) v[u] = av[ptile_global(F, spreadH, L, e)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned e = e0 + u * NT;
+          if (e < tile) t[TA::sw(e)] = TA::from(v[u]);
+        }
       }
     }
-    __syncthreads();
+    if (!use_tma) __syncthreads();
     if constexpr (kF32) {
-      for (int si = 0; si < P.nst; ++si) {
-        const int nb = P.snb[si];
-        bool odd[3] = {false, false, false};
-        float acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (j >= nb) break;
-          const PauliGroup& g = groups[P.gi[P.sgg[si][j]]];
-          odd[j] = __popcll(g.m & g.z[0]) & 1;
-        }
+      for (int sx = 0; sx < P.nst; ++sx) {
+        const XStage& S = P.st[sx];
+        if (S.grp != (int)grp || (lt >> S.ntb)) continue;  // another group's; or small tiles: fewer sets than threads
+        const int nb = S.nb;
+        float re[kStageBits], im[kStageBits];
         const float2* tf = reinterpret_cast<const float2*>(t);
-        if (nb == 3) x_stage<3>(tf, tile, P, si, odd, acc);
-        else if (nb == 2) x_stage<2>(tf, tile, P, si, odd, acc);
-        else x_stage<1>(tf, tile, P, si, odd, acc);
+        const unsigned sb = swt[sx * ST + lt];
+        if (nb == 5) x_stage_any<5>(tf, sb, S, re, im);
+        else if (nb == 4) x_stage_any<4>(tf, sb, S, re, im);
+        else if (nb == 3) x_stage_any<3>(tf, sb, S, re, im);
+        else if (nb == 2) x_stage_any<2>(tf, sb, S, re, im);
+        else x_stage_any<1>(tf, sb, S, re, im);
+        // this tile's FP32 sums into the thread's double-float slots
+        // (exact: TwoSum), weighted once at the end
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < kStageBits; ++j) {
           if (j >= nb) break;
-          const PauliGroup& g = groups[P.gi[P.sgg[si][j]]];
-          const dfl c{acc[j], 0.f};
-          const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
-          if (!odd[j]) {
-            df_acc(ar, df_mul(w_r, c));
-            df_acc(ai, df_mul(w_i, c));
-          } else {
-            df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
-            df_acc(ai, df_mul(w_r, c));
-          }
+          float2& a = sacc[(S.slot0 + j) * ST + lt];
+          float2 v = a, e;
+          v.x = two_sum(v.x, ((S.odd >> j) & 1) ? im[j] : re[j], e.x);
+          v.y += e.x;
+          a = v;
         }
       }
     }
-    for (int gg = 0; gg < P.ng; ++gg) {
+    for (int gg = 0; need_F && gg < P.ng; ++gg) {
       if (kF32 && ((P.staged >> gg) & 1u)) continue;
       const PauliGroup& g = groups[P.gi[gg]];
       const int h = P.hloc[gg];
@@ -481,29 +648,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
 #pragma unroll
         for (int c = 0; c < kMaxClasses; ++c) sc[c] = dfl{0.f, 0.f};
         if constexpr (kF32) {
-          // complex64: p_x and the class sums in FP32 over this thread's
-          // amplitudes of the tile (two chains per class), then one
-          // double-float step per class
-          float s2[kMaxClasses][2];
+          // complex64, by rows of 16 amplitudes, in FP32 per thread and
+          // tile, then one double-float step per class.  V(x) = (x ^ x >> d)
+          // & mask is linear over GF(2), so for a row base xr (bits 0..3
+          // clear) and j < 16, V(xr | j) = V(xr) ^ V(j) with V(j) inside
+          // bits 0..3: k = base - 2 popc(u_j), base = len - 2 popc(V(xr)
+          // above bit 3), u_j = (V(xr) ^ V(j)) & 15, and the row adds
+          // base * sum_j p_j - 2 sum_j p_j popc(u_j)
+          float s2[kMaxClasses];
 #pragma unroll
-          for (int c = 0; c < kMaxClasses; ++c) s2[c][0] = s2[c][1] = 0.f;
-          int par = 0;
-          for (unsigned l = threadIdx.x; l < tile; l += kThreads, par ^= 1) {
-            const float2 v = t_as_f2(t[TA::sw(l)]);
-            const float pw = fmaf(v.x, v.x, v.y * v.y);
-            const u64 x = ptile_global(F, spreadH, L, l);
+          for (int c = 0; c < kMaxClasses; ++c) s2[c] = 0.f;
+          const float4* t4 = reinterpret_cast<const float4*>(t);
+          for (unsigned rho = threadIdx.x; rho < (tile >> kTL); rho += NT) {
+            const u64 xr = F | spreadH[rho];
+            float pj[16];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // the row's 16-byte pieces, unswizzled
+              const float4 w = t4[rho * 8 + (q ^ (rho & 7))];
+              pj[2 * q] = fmaf(w.x, w.x, w.y * w.y);
+              pj[2 * q + 1] = fmaf(w.z, w.z, w.w * w.w);
+            }
+            float pr[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pr[q] = pj[2 * q] + pj[2 * q + 1];
+            const float prow = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
 #pragma unroll
             for (int c = 0; c < kMaxClasses; ++c) {
               if (c >= nc) break;
-              const float k = (float)(g.cls_len[c] - 2 * __popcll((x ^ (x >> g.cls_d[c])) & g.cls_mask[c]));
-              if (par) s2[c][1] = fmaf(k, pw, s2[c][1]);
-              else s2[c][0] = fmaf(k, pw, s2[c][0]);
+              const int d = g.cls_d[c];
+              const u64 mk = g.cls_mask[c];
+              const u64 V = (xr ^ (xr >> d)) & mk;
+              const float base = (float)(g.cls_len[c] - 2 * __popcll(V & ~u64(15)));
+              unsigned bv[4];  // V(2^b), b < 4
+#pragma unroll
+              for (int b = 0; b < 4; ++b) bv[b] = ((1u << b) ^ (d < 4 ? (1u << b) >> d : 0u)) & (unsigned)mk & 15u;
+              unsigned u[16];
+              u[0] = (unsigned)V & 15u;
+              float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (j) {
+                  int b = 0;
+                  while (!((j >> b) & 1)) ++b;
+                  u[j] = u[j & (j - 1)] ^ bv[b];
+                }
+                if (j & 1) a1 = fmaf(pj[j], (float)__popc(u[j]), a1);
+                else a0 = fmaf(pj[j], (float)__popc(u[j]), a0);
+              }
+              s2[c] = fmaf(base, prow, fmaf(-2.f, a0 + a1, s2[c]));
             }
           }
 #pragma unroll
-          for (int c = 0; c < kMaxClasses; ++c) sc[c] = dfl{s2[c][0] + s2[c][1], 0.f};
+          for (int c = 0; c < kMaxClasses; ++c) {
+            // the pass's first class group: into the thread's double-float
+            // class sums (exact: TwoSum), weighted once at the end; any
+            // other (a diagonal group split for its size): weighted per tile
+            if (c >= nc) break;
+            if (gg == P.clsg) {
+              float e;
+              csum[c].h = two_sum(csum[c].h, s2[c], e);
+              csum[c].l += e;
+            } else {
+              sc[c] = dfl{s2[c], 0.f};
+            }
+          }
         } else {
-          for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
+          for (unsigned l = threadIdx.x; l < tile; l += NT) {
             dfl xr, xi;
             TA::get(t[TA::sw(l)], xr, xi);
             dfl pw = df_mul(xr, xr);
@@ -519,14 +729,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
         }
 #pragma unroll
         for (int c = 0; c < kMaxClasses; ++c) {
-          if (c >= nc) break;
+          if ((kF32 && gg == P.clsg) || c >= nc) break;
           const dfl v = df_norm2(sc[c]);
           df_acc(ar, df_mul(dfl{g.cwrh[c], g.cwrl[c]}, v));
           df_acc(ai, df_mul(dfl{g.cwih[c], g.cwil[c]}, v));
         }
       } else if (h < 0) {  // diagonal group: sum_x |a_x|^2 f(x)
         int since = 0;  // flush the double-float sums into FP64 every kU terms
-        for (unsigned l = threadIdx.x; l < tile; l += kThreads) {
+        for (unsigned l = threadIdx.x; l < tile; l += NT) {
           dfl xr, xi;
           TA::get(t[TA::sw(l)], xr, xi);
           dfl fr, fi;
@@ -554,10 +764,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
           // complex64: each pair's Re / Im p in FP32 (one FMA), summed in
           // FP32 over this thread's pairs of the tile in four chains
           float c4[4] = {0.f, 0.f, 0.f, 0.f};
-          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
+          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * NT) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const unsigned k = k0 + u * kThreads;
+              const unsigned k = k0 + u * NT;
               if (k >= tile / 2) break;
               const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
               const float2 X = t_as_f2(t[TA::sw(l)]), Y = t_as_f2(t[TA::sw(l ^ mloc)]);
@@ -569,10 +779,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
           c = dfl{(c4[0] + c4[1]) + (c4[2] + c4[3]), 0.f};
         } else {
           dfl c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * kThreads) {
+          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * NT) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const unsigned k = k0 + u * kThreads;
+              const unsigned k = k0 + u * NT;
               if (k >= tile / 2) break;
               const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
               dfl xr, xi, yr, yi;
@@ -603,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
       } else {
         const unsigned mloc = P.mloc[gg], lo_mask = (1u << h) - 1u;
         int since = 0;
-        for (unsigned k = threadIdx.x; k < tile / 2; k += kThreads) {
+        for (unsigned k = threadIdx.x; k < tile / 2; k += NT) {
           const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
           dfl xr, xi, yr, yi;
           TA::get(t[TA::sw(l)], xr, xi);
@@ -626,11 +836,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_pauli_tiles(const R* __restrict
       }
     }
     // into FP64 once per tile (the FP64 pipe is about 1/64 of FP32 on GB300)
-    df_flush(sr, ar);
-    df_flush(si, ai);
+    if (!(kF32 && P.noflush)) {
+      df_flush(sr, ar);
+      df_flush(si, ai);
+    }
     __syncthreads();
   }
-  block_sum2(sr, si);
+  if constexpr (kF32) {
+    // the stage sums, weighted: 2 w Re p for X-type terms, 2 i w Im p for Y-type
+    for (int sx = 0; sx < P.nst; ++sx) {
+      const XStage& S = P.st[sx];
+      if (S.grp != (int)grp) continue;
+      for (int j = 0; j < S.nb; ++j) {
+        const float2 a = sacc[(S.slot0 + j) * ST + lt];
+        const PauliGroup& g = groups[P.gi[S.gg[j]]];
+        const dfl c = df_norm2(dfl{a.x, a.y});
+        const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
+        if (!((S.odd >> j) & 1)) {
+          df_acc(ar, df_mul(w_r, c));
+          df_acc(ai, df_mul(w_i, c));
+        } else {
+          df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
+          df_acc(ai, df_mul(w_r, c));
+        }
+      }
+    }
+    if (P.clsg >= 0) {  // the class sums, weighted
+      const PauliGroup& g = groups[P.gi[P.clsg]];
+#pragma unroll
+      for (int c = 0; c < kMaxClasses; ++c) {
+        if (c >= g.ncls) break;
+        const dfl v = df_norm2(csum[c]);
+        df_acc(ar, df_mul(dfl{g.cwrh[c], g.cwrl[c]}, v));
+        df_acc(ai, df_mul(dfl{g.cwih[c], g.cwil[c]}, v));
+      }
+    }
+    df_flush(sr, ar);
+    df_flush(si, ai);
+  }
+  block_sum2<NT>(sr, si);
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sr, si);
 }
 
@@ -692,6 +936,146 @@ qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
   return QS_OK;
 }
 
+// Register stages of a complex64 tile pass.  The single-term groups on one
+// tile-local bit (X or Y, Z on that bit only) are placed first fit, in
+// ascending bit order, into stages of at most kStageBits bits; a stage never
+// holds both bits j and j + 3 (j = 1..3), which the swizzle folds onto the
+// same bank position.  Lane bits: bit 0 (unless a stage bit: then pairs are
+// read as 16 bytes) and, for j = 1..3, bit j or else bit j + 3; then the
+// other tile bits ascending.
+void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt) {
+  const int m = q.L + q.r;
+  int lg_nt = 0;
+  while ((1 << lg_nt) < nt) ++lg_nt;
+  std::vector<std::pair<int, int>> one;  // (local bit, group slot)
+  for (int gg = 0; gg < q.ng; ++gg) {
+    const PauliGroup& G = groups[q.gi[gg]];
+    if (G.nt == 1 && __builtin_popcount(q.mloc[gg]) == 1 && (G.z[0] & ~G.m) == 0) one.push_back({q.hloc[gg], gg});
+  }
+  std::sort(one.begin(), one.end());
+  std::vector<unsigned> smask;
+  for (const auto& bg : one) {
+    const int b = bg.first;
+    size_t si = 0;
+    for (; si < smask.size(); ++si) {
+      if (q.st[si].nb >= kStageBits) continue;
+      bool clash = false;
+      for (int j = 1; j <= 3; ++j)
+        if ((b == j && ((smask[si] >> (j + 3)) & 1)) || (b == j + 3 && ((smask[si] >> j) & 1))) clash = true;
+      if (!clash) break;
+    }
+    if (si == smask.size()) {
+      smask.push_back(0);
+      q.st[si] = XStage{};
+    }
+    XStage& S = q.st[si];
+    const PauliGroup& G = groups[q.gi[bg.second]];
+    if (__builtin_popcountll(G.m & G.z[0]) & 1) {
+      S.gen = 1;
+      S.odd |= (int8_t)(1 << S.nb);
+    }
+    S.bit[S.nb] = (int8_t)b;
+    S.gg[S.nb] = (int8_t)bg.second;
+    ++S.nb;
+    smask[si] |= 1u << b;
+    q.staged |= 1u << bg.second;
+  }
+  q.nst = (int)smask.size();
+  // the warp groups: longest stage first to the less loaded group (cost per
+  // amplitude about nb FMAs plus a load and its address)
+  {
+    std::vector<int> ord(q.nst);
+    for (int i = 0; i < q.nst; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return q.st[a].nb > q.st[b].nb; });
+    int load[2] = {0, 0};
+    for (int i : ord) {
+      const int g = load[1] < load[0] ? 1 : 0;
+      q.st[i].grp = (int8_t)g;
+      load[g] += q.st[i].nb + 3;
+    }
+  }
+  q.nsg = 0;
+  for (int si = 0; si < q.nst; ++si) {
+    XStage& S = q.st[si];
+    S.slot0 = (int8_t)q.nsg;
+    q.nsg += S.nb;
+    const unsigned sm = smask[si];
+    S.pair = (int8_t)(sm & 1u);
+    std::vector<int> order;
+    if (!S.pair) order.push_back(0);
+    for (int j = 1; j <= 3; ++j) {
+      if (j < m && !((sm >> j) & 1)) order.push_back(j);
+      else if (j + 3 < m && !((sm >> (j + 3)) & 1)) order.push_back(j + 3);
+    }
+    for (int b = 0; b < m; ++b)
+      if (!((sm >> b) & 1) && std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
+    S.ntb = (int8_t)std::min<int>(lg_nt, (int)order.size());
+    for (int i = 0; i < S.ntb; ++i) S.tb[i] = (int8_t)order[i];
+    S.dhi = 0;
+    for (size_t i = S.ntb; i < order.size(); ++i) S.dhi |= 1u << order[i];
+  }
+}
+
+// Tensor map of a complex64 tile pass: the state as UINT64 amplitudes in
+// dimensions that are runs of qubits -- qubits 0..3 (the tile's 128-byte
+// rows), then ascending runs of tile qubits (split into pieces of at most 8,
+// the box limit) and of the qubits outside the tile (box 1, coordinate from
+// the tile number), at most 5 in all, 128-byte swizzled.  The box's row
+// order is the tile-local order (high tile qubits ascending).  False: more
+// than 5 runs (the pass copies with cp.async).
+bool make_ptile_tmap(void* amp, int n, PTilePass& q, CUtensorMap* map, qs_status* st) {
+  *st = QS_OK;
+  q.tma = 0;
+  if (kTL + q.r < 7) return false;  // both buffers 1024-byte aligned: tiles of 128 amplitudes or more
+  u64 tmask = (u64(1) << kTL) - 1;
+  for (int j = 0; j < q.r; ++j) tmask |= u64(1) << q.H[j];
+  struct Dim { int lo, len, tile; };
+  std::vector<Dim> dims;
+  dims.push_back(Dim{0, kTL, 1});
+  for (int b = kTL; b < n;) {
+    const int t = (int)((tmask >> b) & 1);
+    int e = b;
+    while (e < n && (int)((tmask >> e) & 1) == t) ++e;
+    if (t)
+      for (int x = b; x < e; x += 8) dims.push_back(Dim{x, std::min(8, e - x), 1});
+    else
+      dims.push_back(Dim{b, e - b, 0});
+    b = e;
+  }
+  if (dims.size() > 5) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  *st = tmap_encoder(&encode);
+  if (*st != QS_OK) return false;
+  const int rank = (int)dims.size();
+  cuuint64_t gdim[5], gstr[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int d = 0; d < 5; ++d) {
+    q.tgb[d] = -1;
+    q.tlen[d] = 0;
+    if (d >= rank) continue;
+    const Dim& D = dims[d];
+    gdim[d] = cuuint64_t(1) << D.len;
+    box[d] = D.tile ? (1u << D.len) : 1u;
+    if (d > 0) gstr[d - 1] = (cuuint64_t(1) << D.lo) * 8;
+    if (!D.tile) {
+      int below = 0;  // qubits outside the tile under the run: its first tile-number bit
+      for (int x = kTL; x < D.lo; ++x) below += !((tmask >> x) & 1);
+      q.tgb[d] = (int8_t)below;
+      q.tlen[d] = (int8_t)D.len;
+    }
+  }
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, amp, gdim, gstr, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *st = fail(QS_ECUDA, "cuTensorMapEncodeTiled (expectation tile) failed (%d)", (int)r);
+    return false;
+  }
+  q.trank = rank;
+  q.tma = 1;
+  return true;
+}
+
 qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask, const double* coeff,
                      double* out) {
   const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
@@ -702,7 +1086,9 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
   // small for a tile) get a pass of their own
   std::vector<PTilePass> tp;
   std::vector<int> alone;
-  const bool tiles = s->n >= kTL + 1 && ng > 1;
+  // (complex64: one group too -- the tile pass's row and stage paths beat
+  // the per-amplitude kernel)
+  const bool tiles = s->n >= kTL + 1 && (ng > 1 || (s->dtype == QS_C64 && s->n >= kTL + 3));
   const int rmax = s->dtype == QS_C64 ? kTH : kTH - 1;  // tiles of 64 KB
   for (size_t i = 0; i < ng; ++i) {
     const u64 hi = groups[i].m >> kTL;
@@ -733,7 +1119,17 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
   }
   // each pass's tile-local masks, and its tiles at least 2^(kTL + 1) amplitudes
   for (PTilePass& q : tp) {
-    for (int b = kTL; b < s->n && q.r == 0; ++b) q.H[q.r++] = b;
+    // tiles of up to 2^(kTL + rmax) amplitudes: fewer, larger tiles for
+    // passes that need few high qubits (the extra qubits are the lowest free)
+    {
+      u64 used = 0;
+      for (int j = 0; j < q.r; ++j) used |= u64(1) << q.H[j];
+      for (int b = kTL; b < s->n && q.r < rmax; ++b)
+        if (!((used >> b) & 1)) used |= u64(1) << b, ++q.r;
+      q.r = 0;
+      for (int b = kTL; b < s->n; ++b)
+        if ((used >> b) & 1) q.H[q.r++] = b;
+    }
     q.tins.k = q.r;
     q.tins.set = 0;
     for (int j = 0; j < q.r; ++j) q.tins.pos[j] = q.H[j];
@@ -746,28 +1142,19 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       q.hloc[gg] = ml ? 31 - __builtin_clz(ml) : -1;
     }
     // complex64: single-term groups on one local bit with no Z bit outside
-    // it go to register stages of up to 3 bits
-    q.nst = 0;
+    // it go to register stages
+    q.nst = q.nsg = 0;
     q.staged = 0;
-    if (s->dtype == QS_C64) {
-      std::vector<std::pair<int, int>> one;  // (local bit, group slot)
-      for (int gg = 0; gg < q.ng; ++gg) {
-        const PauliGroup& G = groups[q.gi[gg]];
-        if (G.nt == 1 && __builtin_popcount(q.mloc[gg]) == 1 && (G.z[0] & ~G.m) == 0)
-          one.push_back({q.hloc[gg], gg});
-      }
-      std::sort(one.begin(), one.end());
-      for (size_t i = 0; i < one.size(); i += 3) {
-        const int nb = (int)std::min<size_t>(3, one.size() - i);
-        q.snb[q.nst] = (int8_t)nb;
-        for (int j = 0; j < nb; ++j) {
-          q.sbit[q.nst][j] = (int8_t)one[i + j].first;
-          q.sgg[q.nst][j] = (int8_t)one[i + j].second;
-          q.staged |= 1u << one[i + j].second;
-        }
-        ++q.nst;
-      }
+    if (s->dtype == QS_C64) build_stages(q, groups, kStageThreads);
+    q.allst = q.ng > 0 && q.staged == (q.ng >= 32 ? ~0u : (1u << q.ng) - 1u);
+    q.clsg = -1;
+    q.noflush = 1;
+    for (int gg = 0; gg < q.ng; ++gg) {
+      if ((q.staged >> gg) & 1u) continue;
+      if (q.hloc[gg] < 0 && groups[q.gi[gg]].ncls > 0 && q.clsg < 0) q.clsg = gg;
+      else q.noflush = 0;
     }
+    if (s->dtype != QS_C64) q.clsg = -1, q.noflush = 0;
   }
   const unsigned gsz = red_grid(N / 2);
   const size_t npart = gsz * (tp.size() + alone.size());
@@ -783,22 +1170,40 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     cudaError_t e = cudaMemcpyAsync(dgroups, groups.data(), gbytes, cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "expectation: group upload");
   }
-  for (const PTilePass& q : tp) {
+  bool any_tma = false;
+  for (PTilePass& q : tp) {
     const size_t asz = s->dtype == QS_C64 ? sizeof(float2) : sizeof(double2);
-    const size_t smem = sizeof(u64) * (1u << kTH) + asz * (size_t(1) << (q.L + q.r));
+    const bool c64 = s->dtype == QS_C64;
+    const size_t smem = ptile_buf_off(c64 ? q.nst : 0, c64 ? q.nsg : 0, c64 ? kStageThreads : kThreads) +
+                        (c64 ? kPtileAlign : 0) + asz * (size_t(1) << (q.L + q.r)) * (c64 ? 2 : 1);
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    q.tma = 0;
+    if (c64) {
+      make_ptile_tmap(s->amp, s->n, q, &tmap, &st);
+      if (st != QS_OK) return st;
+      any_tma |= q.tma != 0;
+    }
     const u64 ntiles = u64(1) << (s->n - q.L - q.r);
-    const unsigned g = (unsigned)std::min<u64>(ntiles, (u64)gsz);
+    unsigned g = (unsigned)std::min<u64>(ntiles, (u64)gsz);
     cudaError_t e;
     if (s->dtype == QS_C64) {
-      e = cudaFuncSetAttribute(k_pauli_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      auto kern = k_pauli_tiles<float, kTileThreads64>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
-      k_pauli_tiles<float><<<g, kThreads, smem, s->stream>>>(static_cast<const float*>(s->amp), s->n, q, dgroups,
-                                                             part + gsz * pi);
+      // one wave of resident CTAs: each runs its tiles' copy/evaluate pipeline
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads64, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "expectation: occupancy");
+      g = std::min<unsigned>(g, (unsigned)std::max(1, occ) * (unsigned)sm_count());
+      kern<<<g, kTileThreads64, smem, s->stream>>>(static_cast<const float*>(s->amp), s->n, q, tmap, dgroups,
+                                                   part + gsz * pi);
     } else {
-      e = cudaFuncSetAttribute(k_pauli_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      auto kern = k_pauli_tiles<double, kThreads>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
-      k_pauli_tiles<double><<<g, kThreads, smem, s->stream>>>(static_cast<const double*>(s->amp), s->n, q, dgroups,
-                                                              part + gsz * pi);
+      kern<<<g, kThreads, smem, s->stream>>>(static_cast<const double*>(s->amp), s->n, q, tmap, dgroups,
+                                             part + gsz * pi);
     }
     if ((st = launch_ok("k_pauli_tiles")) != QS_OK) return st;
     // CTAs beyond the tiles write no partial: zero their slots
@@ -820,6 +1225,16 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
   if ((st = launch_ok("k_final")) != QS_OK) return st;
   double2 h;
   if ((st = read_result(s, res, &h)) != QS_OK) return st;
+  if (any_tma) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&flag, g_expect_timeout, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "expectation: status read");
+    if (flag) {
+      const int zero = 0;
+      cudaMemcpyToSymbol(g_expect_timeout, &zero, sizeof(int));
+      return fail(QS_ETIMEOUT, "expectation: a tile copy wait gave up");
+    }
+  }
   *out = h.x;
   return QS_OK;
 }

@@ -567,6 +567,46 @@ def test_expect_pauli_tile_passes(qs, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [6, 7, 13, 20])
+@pytest.mark.parametrize("kind", ["zz_classes", "zz_split", "xy_stages", "scattered"])
+def test_expect_pauli_stage_and_class_layouts(qs, dtype, n, kind):
+    # complex64 tile passes in their several layouts: a one-group
+    # Hamiltonian of Z-Z classes at distances 1..7 with their own weights
+    # (row evaluation), single-qubit X and Y terms on every qubit (register
+    # stages, 16-byte pair reads where qubit 0 is a stage bit), and X terms
+    # on high qubits far enough apart that the tile is no single TMA box
+    # (per-thread copies); 6 qubits: tiles below the TMA size.  zz_split:
+    # more two-Z terms than one group holds (64), so the diagonal terms form
+    # several class groups in one pass, plus single-X terms
+    rng = np.random.default_rng(1000 * n + len(kind))
+    terms = []
+    if kind == "zz_split":
+        for d in range(1, 9):
+            for i in range(n - d):
+                terms.append(W.PauliTerm(0.1 * d - 0.35, 0, (1 << i) | (1 << (i + d))))
+        terms += [W.PauliTerm(float(rng.normal()), 1 << q, 0) for q in range(0, n, 3)]
+    elif kind == "zz_classes":
+        for d in (1, 2, 3, 5, 7):
+            w = float(rng.normal())
+            for i in range(n - d):
+                if rng.random() < 0.7:
+                    terms.append(W.PauliTerm(w, 0, (1 << i) | (1 << (i + d))))
+    elif kind == "xy_stages":
+        for q in range(n):
+            x = 1 << q
+            terms.append(W.PauliTerm(float(rng.normal()), x, x if rng.random() < 0.4 else 0))
+    else:
+        for q in range(5, n, 2):
+            terms.append(W.PauliTerm(float(rng.normal()), 1 << q, 0))
+        terms.append(W.PauliTerm(0.25, 0, (1 << n) - 1))
+    psi = W.random_state(n, 12000 + 10 * n + len(kind))
+    s = gpu_state(qs, psi, dtype)
+    want = oracle.expect_pauli(start(psi, dtype), terms)
+    got = s.expect_pauli(terms)
+    assert abs(got - want) <= EXPECT_TOL[dtype] * sum(abs(t.coeff) for t in terms), (got, want)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_copy_from_host_async_then_plan(qs, dtype):
     # the queued copy lands before work queued behind it on the state's
     # stream: a plan run right after the call sees the copied state, bit for
