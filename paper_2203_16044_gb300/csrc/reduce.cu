@@ -332,6 +332,8 @@ struct PTilePass {
   unsigned staged;  // bit gg: group slot gg is evaluated in a stage
   int allst;        // every group staged: no per-amplitude group loop
   int clsg;         // complex64: slot of the Z-class group (-1: none), summed across tiles
+  int ggrp;         // complex64: the warp group running the non-staged groups (-1: all threads)
+  u64 fmask;        // the qubits outside the tile (the tile base's bits)
   int noflush;      // complex64: only staged and Z-class groups (no per-tile FP64 flush)
   // complex64 tiles by TMA (tma != 0): dimension d of the tensor map is a
   // run of qubits; tgb[d] >= 0: a run outside the tile, coordinate = bits
@@ -475,7 +477,9 @@ __host__ __device__ constexpr size_t ptile_buf_off(int nst, int nsg, int nt) {
 }
 constexpr size_t kPtileAlign = 1024;  // the tile buffers' alignment (128-byte swizzle period)
 
-template <typename R, int NT>
+// ALLST: a complex64 pass whose groups are all in register stages (no
+// per-amplitude group code in that instance).
+template <typename R, int NT, bool ALLST = false>
 __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, int n,
                                                     const __grid_constant__ PTilePass P,
                                                     const __grid_constant__ CUtensorMap tmap,
@@ -567,10 +571,19 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
   dfl csum[kMaxClasses];
 #pragma unroll
   for (int c = 0; c < kMaxClasses; ++c) csum[c] = dfl{0.f, 0.f};
+  // the non-staged groups: all threads, or (complex64 passes with stages)
+  // one warp group while the other runs its stages
+  const bool gsplit = kF32 && P.ggrp >= 0;
+  const unsigned gt = gsplit ? lt : threadIdx.x, gN = gsplit ? (unsigned)ST : (unsigned)NT;
+  const bool gmine = !gsplit || (int)grp == P.ggrp;
+  const bool need_F = !(kF32 && (ALLST || P.allst));
+  // tile base: the tile number's bits at the qubits outside the tile,
+  // advanced by gridDim.x tiles with a masked add (carries skip the tile's
+  // qubits)
+  u64 F = need_F ? expand((u64)blockIdx.x << L, P.tins) : 0;
+  const u64 Fstep = need_F ? expand((u64)gridDim.x << L, P.tins) : 0;
   int it = 0;
-  for (u64 ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
-    const bool need_F = !(kF32 && P.allst);
-    const u64 F = need_F ? expand(ti << L, P.tins) : 0;
+  for (u64 ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it, F = ((F | ~P.fmask) + Fstep) & P.fmask) {
     if (use_tma) {
       if (threadIdx.x == 0 && ti + gridDim.x < ntiles) tma_tile(ti + gridDim.x, (it + 1) & 1);
       const bool bad = !mbar_wait(smem_u32(&pmbar[it & 1]), (it >> 1) & 1);
@@ -635,7 +648,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
         }
       }
     }
-    for (int gg = 0; need_F && gg < P.ng; ++gg) {
+    for (int gg = 0; !ALLST && need_F && gmine && gg < P.ng; ++gg) {
       if (kF32 && ((P.staged >> gg) & 1u)) continue;
       const PauliGroup& g = groups[P.gi[gg]];
       const int h = P.hloc[gg];
@@ -659,7 +672,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
 #pragma unroll
           for (int c = 0; c < kMaxClasses; ++c) s2[c] = 0.f;
           const float4* t4 = reinterpret_cast<const float4*>(t);
-          for (unsigned rho = threadIdx.x; rho < (tile >> kTL); rho += NT) {
+          for (unsigned rho = gt; rho < (tile >> kTL); rho += gN) {
             const u64 xr = F | spreadH[rho];
             float pj[16];
 #pragma unroll
@@ -713,7 +726,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
             }
           }
         } else {
-          for (unsigned l = threadIdx.x; l < tile; l += NT) {
+          for (unsigned l = gt; l < tile; l += gN) {
             dfl xr, xi;
             TA::get(t[TA::sw(l)], xr, xi);
             dfl pw = df_mul(xr, xr);
@@ -736,7 +749,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
         }
       } else if (h < 0) {  // diagonal group: sum_x |a_x|^2 f(x)
         int since = 0;  // flush the double-float sums into FP64 every kU terms
-        for (unsigned l = threadIdx.x; l < tile; l += NT) {
+        for (unsigned l = gt; l < tile; l += gN) {
           dfl xr, xi;
           TA::get(t[TA::sw(l)], xr, xi);
           dfl fr, fi;
@@ -764,10 +777,10 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
           // complex64: each pair's Re / Im p in FP32 (one FMA), summed in
           // FP32 over this thread's pairs of the tile in four chains
           float c4[4] = {0.f, 0.f, 0.f, 0.f};
-          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * NT) {
+          for (unsigned k0 = gt; k0 < tile / 2; k0 += 4 * gN) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const unsigned k = k0 + u * NT;
+              const unsigned k = k0 + u * gN;
               if (k >= tile / 2) break;
               const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
               const float2 X = t_as_f2(t[TA::sw(l)]), Y = t_as_f2(t[TA::sw(l ^ mloc)]);
@@ -779,10 +792,10 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
           c = dfl{(c4[0] + c4[1]) + (c4[2] + c4[3]), 0.f};
         } else {
           dfl c4[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-          for (unsigned k0 = threadIdx.x; k0 < tile / 2; k0 += 4 * NT) {
+          for (unsigned k0 = gt; k0 < tile / 2; k0 += 4 * gN) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const unsigned k = k0 + u * NT;
+              const unsigned k = k0 + u * gN;
               if (k >= tile / 2) break;
               const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
               dfl xr, xi, yr, yi;
@@ -813,7 +826,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
       } else {
         const unsigned mloc = P.mloc[gg], lo_mask = (1u << h) - 1u;
         int since = 0;
-        for (unsigned k = threadIdx.x; k < tile / 2; k += NT) {
+        for (unsigned k = gt; k < tile / 2; k += gN) {
           const unsigned l = ((k & ~lo_mask) << 1) | (k & lo_mask);  // bit h clear
           dfl xr, xi, yr, yi;
           TA::get(t[TA::sw(l)], xr, xi);
@@ -836,7 +849,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
       }
     }
     // into FP64 once per tile (the FP64 pipe is about 1/64 of FP32 on GB300)
-    if (!(kF32 && P.noflush)) {
+    if (!ALLST && !(kF32 && P.noflush)) {
       df_flush(sr, ar);
       df_flush(si, ai);
     }
@@ -861,7 +874,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
         }
       }
     }
-    if (P.clsg >= 0) {  // the class sums, weighted
+    if (!ALLST && P.clsg >= 0) {  // the class sums, weighted
       const PauliGroup& g = groups[P.gi[P.clsg]];
 #pragma unroll
       for (int c = 0; c < kMaxClasses; ++c) {
@@ -1130,6 +1143,8 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       for (int b = kTL; b < s->n; ++b)
         if ((used >> b) & 1) q.H[q.r++] = b;
     }
+    q.fmask = (s->n >= 64 ? ~u64(0) : (u64(1) << s->n) - 1) & ~((u64(1) << kTL) - 1);
+    for (int j = 0; j < q.r; ++j) q.fmask &= ~(u64(1) << q.H[j]);
     q.tins.k = q.r;
     q.tins.set = 0;
     for (int j = 0; j < q.r; ++j) q.tins.pos[j] = q.H[j];
@@ -1155,6 +1170,15 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       else q.noflush = 0;
     }
     if (s->dtype != QS_C64) q.clsg = -1, q.noflush = 0;
+    // complex64 with stages: the non-staged groups to the warp group with
+    // the smaller stage load (cost per amplitude: a stage about nb + 3, a
+    // Z-class group about 6, another group about 20)
+    q.ggrp = -1;
+    if (s->dtype == QS_C64 && q.nst > 0 && !q.allst) {
+      int load[2] = {0, 0};
+      for (int si = 0; si < q.nst; ++si) load[(int)q.st[si].grp] += q.st[si].nb + 3;
+      q.ggrp = load[1] < load[0] ? 1 : 0;
+    }
   }
   const unsigned gsz = red_grid(N / 2);
   const size_t npart = gsz * (tp.size() + alone.size());
@@ -1188,7 +1212,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     unsigned g = (unsigned)std::min<u64>(ntiles, (u64)gsz);
     cudaError_t e;
     if (s->dtype == QS_C64) {
-      auto kern = k_pauli_tiles<float, kTileThreads64>;
+      auto kern = q.allst ? k_pauli_tiles<float, kTileThreads64, true> : k_pauli_tiles<float, kTileThreads64, false>;
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
       // one wave of resident CTAs: each runs its tiles' copy/evaluate pipeline
