@@ -686,30 +686,35 @@ def planner_policies(qs, torch, device, n):
 
 def reductions(qs, torch, states, n, reps=5):
     """FP64-accumulated reductions on the headline states (a7): norm, inner
-    product with itself, and the TFIM expectation (one pass per X/Y-mask
-    group: the ZZ terms together, each X_i alone).  Each call returns its
-    value to the host, so the host clock around the calls includes the
-    device-to-host read; GB/s counts the state bytes each call reads."""
+    product with itself, and the TFIM expectation (its X-mask groups share
+    tile passes: qs_expect_pauli_passes reads of the state).  Each call
+    returns its value to the host, so the host clock around the calls
+    includes the device-to-host read; GB/s counts the state bytes each call
+    reads, hbm_frac divides that by the measured copy bandwidth."""
     out = {}
     terms = W.tfim(n)
     groups = len({t.xmask for t in terms})
+    peak = measured_peaks()[0]
     for dt, s in states.items():
         S = S_BYTES[dt]
         N = float(1 << n)
+        passes = qs.expect_pauli_passes(n, dt, terms)
         r = {}
         # the inner product of the state with itself reads each byte from
         # DRAM once (the second operand's loads hit L1): counted once
         for name, fn, nbytes in (("norm2", lambda: s.norm2(), N * S),
                                  ("inner_self", lambda: s.inner(s), N * S),
-                                 ("expect_tfim", lambda: s.expect_pauli(terms), groups * N * S)):
+                                 ("expect_tfim", lambda: s.expect_pauli(terms), passes * N * S)):
             fn()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
                 v = fn()
             t = (time.perf_counter() - t0) / reps
-            r[name] = {"ms": 1e3 * t, "GBps": nbytes / t / 1e9, "value": v.real if isinstance(v, complex) else v}
+            r[name] = {"ms": 1e3 * t, "GBps": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / peak,
+                       "value": v.real if isinstance(v, complex) else v}
         r["tfim_groups"] = groups
+        r["tfim_passes"] = passes
         out[dt] = r
     return out
 

@@ -179,6 +179,16 @@ qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status qs_expect_pauli(qs_state* st, int nterms, const uint64_t* xmask,
                           const uint64_t* zmask, const double* coeff, double* out);
 
+/* *passes = the number of reads of the whole state that qs_expect_pauli
+ * makes for these terms on an n-qubit state of this dtype: one per tile
+ * pass (groups sharing a tile of the 4 lowest qubits plus up to 9, or 8
+ * for complex128, higher ones) plus one per group with more X/Y bits above
+ * the 4 lowest qubits than a tile holds.  Host only (no device work; no
+ * state needed).  QS_EINVAL for n outside 1..34, an unknown dtype, nterms
+ * outside 1..65536, NULL arrays, or a term on a qubit >= n. */
+qs_status qs_expect_pauli_passes(int n, qs_dtype dtype, int nterms, const uint64_t* xmask,
+                                 const uint64_t* zmask, int* passes);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement in the computational basis (§II-A: a circuit is a sequence  */
 /* of gates, measurements and resets).  Probabilities follow the Born rule, */

@@ -77,6 +77,7 @@ _SIGS = {
     "qs_norm2": ([_vp, _dp], _int),
     "qs_inner": ([_vp, _vp, _dp], _int),
     "qs_expect_pauli": ([_vp, _int, _up, _up, _dp, _dp], _int),
+    "qs_expect_pauli_passes": ([_int, _int, _int, _up, _up, ctypes.POINTER(ctypes.c_int)], _int),
     "qs_inner_noalloc": ([_vp, _vp, _int, _int, _vp, _dp], _int),
     "qs_plan_autotune": ([_vp, _vp, ctypes.POINTER(PlanOpts), _dp], _int),
     "qs_tune_cache_file": ([ctypes.c_char_p], _int),
@@ -494,6 +495,17 @@ def _terms(terms):
     zm = np.ascontiguousarray([t.zmask for t in terms], dtype=np.uint64)
     cf = np.ascontiguousarray([t.coeff for t in terms], dtype=np.float64)
     return xm, zm, cf
+
+
+def expect_pauli_passes(n: int, dtype: str, terms) -> int:
+    """Reads of the whole state that State.expect_pauli makes for these
+    terms on an n-qubit state (host only; qs_expect_pauli_passes)."""
+    xm, zm, _ = _terms(terms)
+    out = ctypes.c_int()
+    code = C64 if dtype == "c64" else C128 if dtype == "c128" else -1
+    _check(_lib.qs_expect_pauli_passes(n, code, len(xm), xm.ctypes.data_as(_up), zm.ctypes.data_as(_up),
+                                       ctypes.byref(out)), "qs_expect_pauli_passes")
+    return out.value
 
 
 def adjoint_grad(state: State, circuit: Circuit, theta, terms):

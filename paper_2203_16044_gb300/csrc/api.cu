@@ -303,4 +303,17 @@ qs_status qs_expect_pauli(qs_state* s, int nterms, const uint64_t* xmask, const 
   return run_expect(s, nterms, xmask, zmask, coeff, out);
 }
 
+qs_status qs_expect_pauli_passes(int n, qs_dtype dtype, int nterms, const uint64_t* xmask, const uint64_t* zmask,
+                                 int* passes) {
+  if (n < 1 || n > 34 || (dtype != QS_C64 && dtype != QS_C128))
+    return fail(QS_EINVAL, "qs_expect_pauli_passes: need 1 <= n <= 34 and a known dtype");
+  if (nterms < 1 || nterms > 65536 || !xmask || !zmask || !passes)
+    return fail(QS_EINVAL, "qs_expect_pauli_passes: need 1 <= nterms <= 65536 and non-NULL arrays");
+  const uint64_t lim = (1ull << n) - 1;
+  for (int t = 0; t < nterms; ++t)
+    if ((xmask[t] & ~lim) || (zmask[t] & ~lim))
+      return fail(QS_EINVAL, "qs_expect_pauli_passes: term %d acts on a qubit >= n", t);
+  return expect_pauli_passes(n, (int)dtype, nterms, xmask, zmask, passes);
+}
+
 }  // extern "C"

@@ -85,6 +85,7 @@ qs_status run_norm2(qs_state* s, double* out);
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]);
 qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask,
                      const double* coeff, double* out);
+qs_status expect_pauli_passes(int n, int dtype, int nterms, const u64* xmask, const u64* zmask, int* passes);
 
 }  // namespace qs
 

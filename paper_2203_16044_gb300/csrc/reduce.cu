@@ -1089,20 +1089,17 @@ bool make_ptile_tmap(void* amp, int n, PTilePass& q, CUtensorMap* map, qs_status
   return true;
 }
 
-qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask, const double* coeff,
-                     double* out) {
-  const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
-  const u64 N = u64(1) << s->n;
+// The passes of an expectation over an n-qubit state: tile passes (first
+// fit of every group whose mask bits above the kTL low qubits number at most
+// kTH, or kTH - 1 for complex128) and the groups that get a pass of their
+// own (more high bits, or a state too small for a tile).
+static void plan_pauli_passes(int n, qs_dtype dt, const std::vector<PauliGroup>& groups, std::vector<PTilePass>& tp,
+                       std::vector<int>& alone) {
   const size_t ng = groups.size();
-  // tile passes: first fit of every group whose mask bits above the kTL low
-  // qubits number at most kTH; the others (and every group of a state too
-  // small for a tile) get a pass of their own
-  std::vector<PTilePass> tp;
-  std::vector<int> alone;
   // (complex64: one group too -- the tile pass's row and stage paths beat
   // the per-amplitude kernel)
-  const bool tiles = s->n >= kTL + 1 && (ng > 1 || (s->dtype == QS_C64 && s->n >= kTL + 3));
-  const int rmax = s->dtype == QS_C64 ? kTH : kTH - 1;  // tiles of 64 KB
+  const bool tiles = n >= kTL + 1 && (ng > 1 || (dt == QS_C64 && n >= kTL + 3));
+  const int rmax = dt == QS_C64 ? kTH : kTH - 1;  // tiles of 64 KB
   for (size_t i = 0; i < ng; ++i) {
     const u64 hi = groups[i].m >> kTL;
     if (!tiles || __builtin_popcountll(hi) > rmax) {
@@ -1114,7 +1111,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       u64 cur = 0;
       for (int j = 0; j < tp[p].r; ++j) cur |= u64(1) << tp[p].H[j];
       const u64 need = (groups[i].m & ~((u64(1) << kTL) - 1)) | cur;
-      if (tp[p].ng < kPassGroups && __builtin_popcountll(need) <= rmax && kTL + __builtin_popcountll(need) <= s->n)
+      if (tp[p].ng < kPassGroups && __builtin_popcountll(need) <= rmax && kTL + __builtin_popcountll(need) <= n)
         break;
     }
     if (p == tp.size()) {
@@ -1126,7 +1123,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     u64 need = groups[i].m & ~((u64(1) << kTL) - 1);
     for (int j = 0; j < q.r; ++j) need |= u64(1) << q.H[j];
     q.r = 0;
-    for (int b = kTL; b < s->n; ++b)
+    for (int b = kTL; b < n; ++b)
       if ((need >> b) & 1) q.H[q.r++] = b;
     q.gi[q.ng++] = (int)i;
   }
@@ -1137,13 +1134,13 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     {
       u64 used = 0;
       for (int j = 0; j < q.r; ++j) used |= u64(1) << q.H[j];
-      for (int b = kTL; b < s->n && q.r < rmax; ++b)
+      for (int b = kTL; b < n && q.r < rmax; ++b)
         if (!((used >> b) & 1)) used |= u64(1) << b, ++q.r;
       q.r = 0;
-      for (int b = kTL; b < s->n; ++b)
+      for (int b = kTL; b < n; ++b)
         if ((used >> b) & 1) q.H[q.r++] = b;
     }
-    q.fmask = (s->n >= 64 ? ~u64(0) : (u64(1) << s->n) - 1) & ~((u64(1) << kTL) - 1);
+    q.fmask = (n >= 64 ? ~u64(0) : (u64(1) << n) - 1) & ~((u64(1) << kTL) - 1);
     for (int j = 0; j < q.r; ++j) q.fmask &= ~(u64(1) << q.H[j]);
     q.tins.k = q.r;
     q.tins.set = 0;
@@ -1160,7 +1157,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     // it go to register stages
     q.nst = q.nsg = 0;
     q.staged = 0;
-    if (s->dtype == QS_C64) build_stages(q, groups, kStageThreads);
+    if (dt == QS_C64) build_stages(q, groups, kStageThreads);
     q.allst = q.ng > 0 && q.staged == (q.ng >= 32 ? ~0u : (1u << q.ng) - 1u);
     q.clsg = -1;
     q.noflush = 1;
@@ -1169,17 +1166,27 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       if (q.hloc[gg] < 0 && groups[q.gi[gg]].ncls > 0 && q.clsg < 0) q.clsg = gg;
       else q.noflush = 0;
     }
-    if (s->dtype != QS_C64) q.clsg = -1, q.noflush = 0;
+    if (dt != QS_C64) q.clsg = -1, q.noflush = 0;
     // complex64 with stages: the non-staged groups to the warp group with
     // the smaller stage load (cost per amplitude: a stage about nb + 3, a
     // Z-class group about 6, another group about 20)
     q.ggrp = -1;
-    if (s->dtype == QS_C64 && q.nst > 0 && !q.allst) {
+    if (dt == QS_C64 && q.nst > 0 && !q.allst) {
       int load[2] = {0, 0};
       for (int si = 0; si < q.nst; ++si) load[(int)q.st[si].grp] += q.st[si].nb + 3;
       q.ggrp = load[1] < load[0] ? 1 : 0;
     }
   }
+}
+
+qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask, const double* coeff,
+                     double* out) {
+  const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff);
+  const u64 N = u64(1) << s->n;
+  const size_t ng = groups.size();
+  std::vector<PTilePass> tp;
+  std::vector<int> alone;
+  plan_pauli_passes(s->n, (qs_dtype)s->dtype, groups, tp, alone);
   const unsigned gsz = red_grid(N / 2);
   const size_t npart = gsz * (tp.size() + alone.size());
   const size_t gbytes = sizeof(PauliGroup) * ng;
@@ -1260,6 +1267,16 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
     }
   }
   *out = h.x;
+  return QS_OK;
+}
+
+qs_status expect_pauli_passes(int n, int dtype, int nterms, const u64* xmask, const u64* zmask, int* passes) {
+  std::vector<double> coeff((size_t)nterms, 1.0);
+  const std::vector<PauliGroup> groups = build_pauli_groups(nterms, xmask, zmask, coeff.data());
+  std::vector<PTilePass> tp;
+  std::vector<int> alone;
+  plan_pauli_passes(n, (qs_dtype)dtype, groups, tp, alone);
+  *passes = (int)(tp.size() + alone.size());
   return QS_OK;
 }
 
