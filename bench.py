@@ -56,7 +56,7 @@ WORKLOADS = {
 # is re-captured.
 TILE_C64_TRAFFIC_26Q = 536.910848e6 + 475.749632e6       # k_tile<0,3,1,1> (its ncu capture at 26 qubits)
 BLOCK_C64_TRAFFIC_26Q = {  # the block kernels' ncu captures at 26 qubits
-    "k_fused_umma_tma<6,window>": 536.994048e6 + 476.054528e6,
+    "k_fused_umma_tma<6,window>": 536.997376e6 + 476.200192e6,
     "k_fused_umma_tma<6,rows>": 537.023232e6 + 476.058368e6,
     "k_fused_umma<6>": 537.065216e6 + 475.915776e6,
 }
@@ -534,20 +534,31 @@ def run_ours(args):
     if "c64" in states and "c128" in states:
         infid = fidelity_vs_c128(torch, states["c64"].tensor, states["c128"].tensor)
     extras = {}
-    if not args.no_extras:
+    want = set() if args.no_extras else (
+        {"plans", "reductions", "measure", "brick33", "c128_unfused", "classes", "c128_config2", "policies", "batch",
+         "adjoint"} if args.extras == "all" else set(args.extras.split(",")))
+    if "plans" in want:
         extras["c64_plans_%dq" % n] = dtype_plans(qs, torch, device, n, circuit, "c64", states.get("c128"))
         extras["c128_plans_%dq" % n] = dtype_plans(qs, torch, device, n, circuit, "c128", None)
+    if "reductions" in want:
         extras["reductions_%dq" % n] = reductions(qs, torch, states, n)
-        if "c64" in states:
-            extras["measure_%dq" % n] = measurement(qs, torch, states["c64"], n)
+    if "measure" in want and "c64" in states:
+        extras["measure_%dq" % n] = measurement(qs, torch, states["c64"], n)
+    if "brick33" in want:
         extras["c64_brick33_d20"] = c64_33q(qs, torch, device, args.fuse_qubits)
+    if "c128_unfused" in want:
         base = c128_unfused(qs, torch, device, n, circuit)
         base["speedup_of_headline"] = base["ms"] / results[args.dtype]["ms_per_step"]
         extras["c128_unfused_%dq" % n] = base
+    if "classes" in want:
         extras["unfused_classes_28q"] = unfused_classes(qs, torch, device, 28)
+    if "c128_config2" in want:
         extras["c128_brick_qft_28q"] = c128_config2(qs, torch, device, 28)
+    if "policies" in want:
         extras["planner_policies_30q"] = planner_policies(qs, torch, device, 30)
+    if "batch" in want:
         extras["batch_512_hea"] = batch_workload(qs, torch, device)
+    if "adjoint" in want:
         extras["adjoint_20q_400p"] = adjoint_workload(qs, torch, device)
     head = results[args.dtype]
     line = {
@@ -896,6 +907,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the class sweep, batch and adjoint workloads")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated extra workloads to run (plans, reductions, measure, brick33, c128_unfused, "
+                         "classes, c128_config2, policies, batch, adjoint), or all")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=8.0)
     args = ap.parse_args()
