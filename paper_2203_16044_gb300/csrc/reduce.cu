@@ -297,6 +297,7 @@ constexpr int kPassGroups = 16; // groups per tile pass
 constexpr int kTileThreads64 = 512;  // complex64 tile passes: CTA size
 constexpr int kStageThreads = 256;   // ... in two warp groups, each running its own register stages
 constexpr int kStageBits = 5;        // at most this many bits per register stage
+constexpr int kStageBits128 = 4;     // ... for complex128 (16-byte amplitudes)
 
 // A register stage of a complex64 tile pass: single-term groups on up to
 // kStageBits tile-local bits (X or Y on one qubit, Z only on that qubit).
@@ -366,7 +367,7 @@ template <> struct TileAmp<float> {
   // XOR swizzle of the 16-byte pieces (amplitude pairs) of the tile's
   // 16-amplitude (128-byte) rows: strided reads of the register stages stay
   // free of bank conflicts, and a pair stays whole for 16-byte copies
-  __device__ static unsigned sw(unsigned e) { return e ^ (((e >> 4) & 7u) << 1); }
+  __host__ __device__ static unsigned sw(unsigned e) { return e ^ (((e >> 4) & 7u) << 1); }
   __device__ static T from(float2 v) { return v; }
   __device__ static void get(const T& v, dfl& re, dfl& im) {
     re = dfl{v.x, 0.f};
@@ -375,7 +376,10 @@ template <> struct TileAmp<float> {
 };
 template <> struct TileAmp<double> {
   typedef float4 T;
-  __device__ static unsigned sw(unsigned e) { return e; }
+  // XOR swizzle of the 16-byte amplitudes of the tile's 8-amplitude
+  // (128-byte) rows: strided reads of the register stages stay free of bank
+  // conflicts
+  __host__ __device__ static unsigned sw(unsigned e) { return e ^ ((e >> 3) & 7u); }
   __device__ static T from(double2 v) {
     const dfl r = d2df(v.x), i = d2df(v.y);
     return make_float4(r.h, r.l, i.h, i.l);
@@ -465,6 +469,80 @@ __device__ __forceinline__ void x_stage_any(const float2* t, unsigned swt, const
   }
 }
 
+// acc += a b + c d for double-float a, b, c, d (given as high and low
+// floats): the high products exact (two-product), the four cross products
+// and the two product errors in FP32 into the low part, the high products
+// added exactly (TwoSum)
+__device__ __forceinline__ void df_dot2_acc(dfl& acc, float ah, float al, float bh, float bl, float ch, float cl,
+                                            float dh, float dl) {
+  const float p1 = ah * bh, e1 = fmaf(ah, bh, -p1);
+  const float p2 = ch * dh, e2 = fmaf(ch, dh, -p2);
+  const float lo = fmaf(ah, bl, fmaf(al, bh, fmaf(ch, dl, fmaf(cl, dh, e1 + e2))));
+  float t1, t2;
+  float h = two_sum(acc.h, p1, t1);
+  h = two_sum(h, p2, t2);
+  acc.h = h;
+  acc.l += lo + (t1 + t2);
+}
+
+// Stage S of a complex128 tile pass (amplitudes as double-float (re h, re l,
+// im h, im l), swizzled by TileAmp<double>::sw): for each stage qubit j,
+// Re (and, with a Y term, Im) of conj(a_y) a_x over this thread's pairs
+// x, x ^ 2^b_j, in double-float, two accumulators per qubit.  Positions as
+// in x_stage: the swizzle is linear over XOR and the identity above bit 5,
+// where the enumerated bits lie.
+template <int NB, bool GEN>
+__device__ __forceinline__ void x_stage128(const float4* __restrict__ t, unsigned swt, const XStage& S,
+                                           dfl (&re)[kStageBits], dfl (&im)[kStageBits]) {
+  unsigned off[1 << NB];
+  off[0] = swt;
+#pragma unroll
+  for (int c = 1; c < (1 << NB); ++c) {
+    int j = 0;
+    while (!((c >> j) & 1)) ++j;
+    off[c] = off[c & (c - 1)] ^ TileAmp<double>::sw(1u << S.bit[j]);
+  }
+  dfl r0[NB], r1[NB], i0[NB], i1[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) r0[j] = r1[j] = i0[j] = i1[j] = dfl{0.f, 0.f};
+  const unsigned dhi = S.dhi;
+  unsigned cur = 0;
+  do {
+    float4 v[1 << NB];
+#pragma unroll
+    for (int c = 0; c < (1 << NB); ++c) v[c] = t[off[c] + cur];
+#pragma unroll
+    for (int c = 0; c < (1 << NB); ++c) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if ((c >> j) & 1) continue;
+        const float4 X = v[c], Y = v[c | (1 << j)];
+        // the pairs of bit j alternate between two accumulators
+        const bool second = ((c >> (j == 0 ? 1 : 0)) & 1) != 0;
+        dfl& r = second ? r1[j] : r0[j];
+        df_dot2_acc(r, Y.x, Y.y, X.x, X.y, Y.z, Y.w, X.z, X.w);  // Re: yr xr + yi xi
+        if constexpr (GEN) {
+          dfl& q = second ? i1[j] : i0[j];
+          df_dot2_acc(q, Y.x, Y.y, X.z, X.w, -Y.z, -Y.w, X.x, X.y);  // Im: yr xi - yi xr
+        }
+      }
+    }
+    cur = ((cur | ~dhi) + 1u) & dhi;
+  } while (cur != 0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    re[j] = df_add(r0[j], r1[j]);
+    im[j] = df_add(i0[j], i1[j]);
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void x_stage128_any(const float4* t, unsigned swt, const XStage& S, dfl (&re)[kStageBits],
+                                               dfl (&im)[kStageBits]) {
+  if (S.gen) x_stage128<NB, true>(t, swt, S, re, im);
+  else x_stage128<NB, false>(t, swt, S, re, im);
+}
+
 // Shared memory of a tile pass: spreadH, then (complex64) the threads'
 // stage positions and their double-float stage sums, then the tile
 // buffer(s).
@@ -476,11 +554,15 @@ __host__ __device__ constexpr size_t ptile_buf_off(int nst, int nsg, int nt) {
   return ptile_acc_off(nst, nt) + sizeof(float2) * (size_t)nsg * (size_t)nt;
 }
 constexpr size_t kPtileAlign = 1024;  // the tile buffers' alignment (128-byte swizzle period)
+// complex128 stage slots go to FP64 every kSlotTiles tiles: the low float of
+// a slot then rounds at most kSlotTiles times its own size, ~2^-44 of the
+// summed term magnitudes
+constexpr int kSlotTiles = 16;
 
 // ALLST: a complex64 pass whose groups are all in register stages (no
 // per-amplitude group code in that instance).
 template <typename R, int NT, bool ALLST = false>
-__global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, int n,
+__global__ void __launch_bounds__(NT, (std::is_same<R, float>::value ? 1 : 2)) k_pauli_tiles(const R* __restrict__ a, int n,
                                                     const __grid_constant__ PTilePass P,
                                                     const __grid_constant__ CUtensorMap tmap,
                                                     const PauliGroup* __restrict__ groups, double2* part) {
@@ -498,7 +580,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
   uint16_t* swt = reinterpret_cast<uint16_t*>(psm + ptile_stage_off());  // [nst][ST]
   float2* sacc = reinterpret_cast<float2*>(psm + ptile_acc_off(P.nst, ST));  // [nsg][ST] (hi, lo)
   __shared__ __align__(8) uint64_t pmbar[2];  // TMA tiles: buffer b filled
-  const size_t boff = ptile_buf_off(kF32 ? P.nst : 0, kF32 ? P.nsg : 0, ST);
+  const size_t boff = ptile_buf_off(P.nst, P.nsg, ST);
   const uint32_t sbase = smem_u32(psm);
   // (complex64 only: its launch adds kPtileAlign bytes for this pad)
   const size_t bpad = kF32 ? (kPtileAlign - ((sbase + boff) & (kPtileAlign - 1))) & (kPtileAlign - 1) : 0;
@@ -519,15 +601,14 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
       if ((i >> j) & 1u) sp |= u64(1) << P.H[j];
     spreadH[i] = sp;
   }
-  if constexpr (kF32)
-    for (int si = 0; si < P.nst; ++si) {  // this thread's swizzled base position in its group's stages
-      if (P.st[si].grp != (int)grp) continue;
-      unsigned d = 0;
-      for (int i = 0; i < P.st[si].ntb; ++i)
-        if ((lt >> i) & 1u) d |= 1u << P.st[si].tb[i];
-      swt[si * ST + lt] = (uint16_t)TA::sw(d);
-      for (int j = 0; j < P.st[si].nb; ++j) sacc[(P.st[si].slot0 + j) * ST + lt] = make_float2(0.f, 0.f);
-    }
+  for (int si = 0; si < P.nst; ++si) {  // this thread's swizzled base position in its group's stages
+    if (P.st[si].grp != (int)grp) continue;
+    unsigned d = 0;
+    for (int i = 0; i < P.st[si].ntb; ++i)
+      if ((lt >> i) & 1u) d |= 1u << P.st[si].tb[i];
+    swt[si * ST + lt] = (uint16_t)TA::sw(d);
+    for (int j = 0; j < P.st[si].nb; ++j) sacc[(P.st[si].slot0 + j) * ST + lt] = make_float2(0.f, 0.f);
+  }
   const u64 ntiles = u64(1) << (n - m);
   double sr = 0.0, si = 0.0;
   dfl ar{0.f, 0.f}, ai{0.f, 0.f};
@@ -566,6 +647,30 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
       else if (threadIdx.x == 0) tma_tile(blockIdx.x, 0);
     }
   }
+  // the stage sums, weighted, into the FP64 accumulators: 2 w Re p for
+  // X-type terms, 2 i w Im p for Y-type; the slots restart from zero
+  auto flush_slots = [&]() {
+    for (int sx = 0; sx < P.nst; ++sx) {
+      const XStage& S = P.st[sx];
+      if (S.grp != (int)grp) continue;
+      for (int j = 0; j < S.nb; ++j) {
+        float2& a = sacc[(S.slot0 + j) * ST + lt];
+        const PauliGroup& g = groups[P.gi[S.gg[j]]];
+        const dfl c = df_norm2(dfl{a.x, a.y});
+        a = make_float2(0.f, 0.f);
+        const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
+        if (!((S.odd >> j) & 1)) {
+          df_acc(ar, df_mul(w_r, c));
+          df_acc(ai, df_mul(w_i, c));
+        } else {
+          df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
+          df_acc(ai, df_mul(w_r, c));
+        }
+      }
+    }
+    df_flush(sr, ar);
+    df_flush(si, ai);
+  };
   // complex64 Z-class sums over the thread's tiles (there is one diagonal
   // group, so at most one class group per pass)
   dfl csum[kMaxClasses];
@@ -622,14 +727,14 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
       }
     }
     if (!use_tma) __syncthreads();
-    if constexpr (kF32) {
-      for (int sx = 0; sx < P.nst; ++sx) {
-        const XStage& S = P.st[sx];
-        if (S.grp != (int)grp || (lt >> S.ntb)) continue;  // another group's; or small tiles: fewer sets than threads
-        const int nb = S.nb;
+    for (int sx = 0; sx < P.nst; ++sx) {
+      const XStage& S = P.st[sx];
+      if (S.grp != (int)grp || (lt >> S.ntb)) continue;  // another group's; or small tiles: fewer sets than threads
+      const int nb = S.nb;
+      const unsigned sb = swt[sx * ST + lt];
+      if constexpr (kF32) {
         float re[kStageBits], im[kStageBits];
         const float2* tf = reinterpret_cast<const float2*>(t);
-        const unsigned sb = swt[sx * ST + lt];
         if (nb == 5) x_stage_any<5>(tf, sb, S, re, im);
         else if (nb == 4) x_stage_any<4>(tf, sb, S, re, im);
         else if (nb == 3) x_stage_any<3>(tf, sb, S, re, im);
@@ -646,10 +751,31 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
           v.y += e.x;
           a = v;
         }
+      } else {
+        dfl re[kStageBits], im[kStageBits];
+        const float4* tf = reinterpret_cast<const float4*>(t);
+        if (nb == 4) x_stage128_any<4>(tf, sb, S, re, im);
+        else if (nb == 3) x_stage128_any<3>(tf, sb, S, re, im);
+        else if (nb == 2) x_stage128_any<2>(tf, sb, S, re, im);
+        else x_stage128_any<1>(tf, sb, S, re, im);
+        // this tile's double-float sums into the thread's slots (high parts
+        // exactly, TwoSum), weighted and flushed to FP64 every kSlotTiles
+        // tiles
+#pragma unroll
+        for (int j = 0; j < kStageBits128; ++j) {
+          if (j >= nb) break;
+          float2& a = sacc[(S.slot0 + j) * ST + lt];
+          const dfl c = ((S.odd >> j) & 1) ? im[j] : re[j];
+          float2 v = a;
+          float e;
+          v.x = two_sum(v.x, c.h, e);
+          v.y += c.l + e;
+          a = v;
+        }
       }
     }
     for (int gg = 0; !ALLST && need_F && gmine && gg < P.ng; ++gg) {
-      if (kF32 && ((P.staged >> gg) & 1u)) continue;
+      if ((P.staged >> gg) & 1u) continue;
       const PauliGroup& g = groups[P.gi[gg]];
       const int h = P.hloc[gg];
       if (h < 0 && g.ncls > 0) {
@@ -848,6 +974,7 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
         }
       }
     }
+    if (!kF32 && P.nst > 0 && (it % kSlotTiles) == kSlotTiles - 1) flush_slots();
     // into FP64 once per tile (the FP64 pipe is about 1/64 of FP32 on GB300)
     if (!ALLST && !(kF32 && P.noflush)) {
       df_flush(sr, ar);
@@ -855,25 +982,8 @@ __global__ void __launch_bounds__(NT, 1) k_pauli_tiles(const R* __restrict__ a, 
     }
     __syncthreads();
   }
+  flush_slots();
   if constexpr (kF32) {
-    // the stage sums, weighted: 2 w Re p for X-type terms, 2 i w Im p for Y-type
-    for (int sx = 0; sx < P.nst; ++sx) {
-      const XStage& S = P.st[sx];
-      if (S.grp != (int)grp) continue;
-      for (int j = 0; j < S.nb; ++j) {
-        const float2 a = sacc[(S.slot0 + j) * ST + lt];
-        const PauliGroup& g = groups[P.gi[S.gg[j]]];
-        const dfl c = df_norm2(dfl{a.x, a.y});
-        const dfl w_r{2.f * g.wrh[0], 2.f * g.wrl[0]}, w_i{2.f * g.wih[0], 2.f * g.wil[0]};
-        if (!((S.odd >> j) & 1)) {
-          df_acc(ar, df_mul(w_r, c));
-          df_acc(ai, df_mul(w_i, c));
-        } else {
-          df_acc(ar, df_mul(dfl{-w_i.h, -w_i.l}, c));
-          df_acc(ai, df_mul(w_r, c));
-        }
-      }
-    }
     if (!ALLST && P.clsg >= 0) {  // the class sums, weighted
       const PauliGroup& g = groups[P.gi[P.clsg]];
 #pragma unroll
@@ -956,8 +1066,12 @@ qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
 // same bank position.  Lane bits: bit 0 (unless a stage bit: then pairs are
 // read as 16 bytes) and, for j = 1..3, bit j or else bit j + 3; then the
 // other tile bits ascending.
-void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt) {
+// Complex128 (c128): 16-byte amplitudes, swizzle e ^ ((e >> 3) & 7): the
+// clash pairs are j, j + 3 for j = 0..2, the lanes of a quarter warp take
+// qubit j or j + 3, stages hold at most kStageBits128 qubits, one warp group.
+void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt, bool c128) {
   const int m = q.L + q.r;
+  const int jlo = c128 ? 0 : 1, jhi = c128 ? 2 : 3, maxnb = c128 ? kStageBits128 : kStageBits;
   int lg_nt = 0;
   while ((1 << lg_nt) < nt) ++lg_nt;
   std::vector<std::pair<int, int>> one;  // (local bit, group slot)
@@ -971,9 +1085,9 @@ void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt) {
     const int b = bg.first;
     size_t si = 0;
     for (; si < smask.size(); ++si) {
-      if (q.st[si].nb >= kStageBits) continue;
+      if (q.st[si].nb >= maxnb) continue;
       bool clash = false;
-      for (int j = 1; j <= 3; ++j)
+      for (int j = jlo; j <= jhi; ++j)
         if ((b == j && ((smask[si] >> (j + 3)) & 1)) || (b == j + 3 && ((smask[si] >> j) & 1))) clash = true;
       if (!clash) break;
     }
@@ -1002,7 +1116,7 @@ void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt) {
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return q.st[a].nb > q.st[b].nb; });
     int load[2] = {0, 0};
     for (int i : ord) {
-      const int g = load[1] < load[0] ? 1 : 0;
+      const int g = !c128 && load[1] < load[0] ? 1 : 0;
       q.st[i].grp = (int8_t)g;
       load[g] += q.st[i].nb + 3;
     }
@@ -1013,10 +1127,10 @@ void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt) {
     S.slot0 = (int8_t)q.nsg;
     q.nsg += S.nb;
     const unsigned sm = smask[si];
-    S.pair = (int8_t)(sm & 1u);
+    S.pair = (int8_t)(!c128 && (sm & 1u));
     std::vector<int> order;
-    if (!S.pair) order.push_back(0);
-    for (int j = 1; j <= 3; ++j) {
+    if (!c128 && !S.pair) order.push_back(0);
+    for (int j = jlo; j <= jhi; ++j) {
       if (j < m && !((sm >> j) & 1)) order.push_back(j);
       else if (j + 3 < m && !((sm >> (j + 3)) & 1)) order.push_back(j + 3);
     }
@@ -1157,7 +1271,7 @@ static void plan_pauli_passes(int n, qs_dtype dt, const std::vector<PauliGroup>&
     // it go to register stages
     q.nst = q.nsg = 0;
     q.staged = 0;
-    if (dt == QS_C64) build_stages(q, groups, kStageThreads);
+    build_stages(q, groups, kStageThreads, dt == QS_C128);
     q.allst = q.ng > 0 && q.staged == (q.ng >= 32 ? ~0u : (1u << q.ng) - 1u);
     q.clsg = -1;
     q.noflush = 1;
@@ -1205,7 +1319,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
   for (PTilePass& q : tp) {
     const size_t asz = s->dtype == QS_C64 ? sizeof(float2) : sizeof(double2);
     const bool c64 = s->dtype == QS_C64;
-    const size_t smem = ptile_buf_off(c64 ? q.nst : 0, c64 ? q.nsg : 0, c64 ? kStageThreads : kThreads) +
+    const size_t smem = ptile_buf_off(q.nst, q.nsg, c64 ? kStageThreads : kThreads) +
                         (c64 ? kPtileAlign : 0) + asz * (size_t(1) << (q.L + q.r)) * (c64 ? 2 : 1);
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
@@ -1230,9 +1344,13 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
       kern<<<g, kTileThreads64, smem, s->stream>>>(static_cast<const float*>(s->amp), s->n, q, tmap, dgroups,
                                                    part + gsz * pi);
     } else {
-      auto kern = k_pauli_tiles<double, kThreads>;
+      auto kern = q.allst ? k_pauli_tiles<double, kThreads, true> : k_pauli_tiles<double, kThreads, false>;
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return cuda_fail(e, "expectation: smem attribute");
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "expectation: occupancy");
+      g = std::min<unsigned>(g, (unsigned)std::max(1, occ) * (unsigned)sm_count());
       kern<<<g, kThreads, smem, s->stream>>>(static_cast<const double*>(s->amp), s->n, q, tmap, dgroups,
                                              part + gsz * pi);
     }
