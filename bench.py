@@ -711,8 +711,8 @@ def reductions(qs, torch, states, n, reps=5):
         N = float(1 << n)
         passes = qs.expect_pauli_passes(n, dt, terms)
         r = {}
-        # the inner product of the state with itself reads each byte from
-        # DRAM once (the second operand's loads hit L1): counted once
+        # the inner product of the state with itself is its norm (the
+        # library recognises the same vector): one read, counted once
         for name, fn, nbytes in (("norm2", lambda: s.norm2(), N * S),
                                  ("inner_self", lambda: s.inner(s), N * S),
                                  ("expect_tfim", lambda: s.expect_pauli(terms), passes * N * S)):

@@ -163,7 +163,9 @@ qs_status qs_fused_swap(qs_state* st, int p, int q, int s);
 /* out = sum_x |a_x|^2. */
 qs_status qs_norm2(qs_state* st, double* out);
 
-/* out[0] + i out[1] = <a|b> = sum_x conj(a_x) b_x.  Same n and dtype. */
+/* out[0] + i out[1] = <a|b> = sum_x conj(a_x) b_x.  Same n and dtype.  When
+ * a and b hold the same device vector this is the norm (qs_norm2, one read
+ * of the state) with out[1] = 0. */
 qs_status qs_inner(qs_state* a, qs_state* b, double out[2]);
 
 /* out = sum_t coeff[t] <psi|P_t|psi> for Pauli strings P_t with X on the

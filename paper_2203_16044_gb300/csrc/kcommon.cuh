@@ -41,7 +41,7 @@ struct Ins {
   u64 set;
 };
 
-__device__ __forceinline__ u64 expand(u64 i, const Ins& ins) {
+__host__ __device__ __forceinline__ u64 expand(u64 i, const Ins& ins) {
 #pragma unroll
   for (int j = 0; j < 12; ++j) {
     if (j < ins.k) {

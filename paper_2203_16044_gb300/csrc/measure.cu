@@ -38,15 +38,36 @@ constexpr int kPrefixThreads = 1024;
 struct MargArgs {
   Ins ins;          // zero insertion at the measured qubits
   u64 spread[64];   // spread[r]: OR of 2^qubits[i] over the set bits i of r
+  u64 free;         // the other qubits' bits (a group base's bits)
+  u64 step1, stepU; // masked-add steps: the bases of the groups stride and kMargU strides on
 };
 
+// p = x^2 into a double-float sum: the FP32 square exactly as p + e
+// (FMA), p added exactly (TwoSum), e and the TwoSum error into the low part
+__device__ __forceinline__ void sq_acc(dfl& acc, float x) {
+  const float p = __fmul_rn(x, x), e = __fmaf_rn(x, x, -p);
+  float t;
+  acc.h = two_sum(acc.h, p, t);
+  acc.l = __fadd_rn(acc.l, __fadd_rn(e, t));
+}
+__device__ __forceinline__ void sq_acc(dfl& acc, double x) {
+  const dfl d = d2df(x);
+  df_acc(acc, df_mul(d, d));
+}
+
 // Outcomes [b0, b0 + NB): each thread sums its groups (the other qubits) in
-// grid-stride order, the squares exact in double-float, flushed into FP64
-// every 4 groups; the CTA reduces every bin into part[blockIdx.x * kBins + j].
+// grid-stride order, kMargU groups at a time (their 8 loads issued first),
+// the squares exact in double-float, flushed into FP64 every kMargFlush
+// groups (the low float then holds at most 2 kMargFlush rounding errors of
+// the TwoSums, ~2^-43 of the sum); the CTA reduces every bin into
+// part[blockIdx.x * kBins + j].
+constexpr int kMargFlush = 16;
+template <int NB> struct MargU { static constexpr int value = NB >= 8 ? 1 : 8 / NB; };
 template <typename A, int NB>
-__global__ void __launch_bounds__(kMT) k_marginal(const A* __restrict__ a, u64 ngroups,
+__global__ void __launch_bounds__(kMT, NB >= 8 ? 2 : 3) k_marginal(const A* __restrict__ a, u64 ngroups,
                                                   const __grid_constant__ MargArgs args, int b0,
                                                   double* __restrict__ part) {
+  constexpr int kMargU = MargU<NB>::value;
   double acc[NB];
   dfl da[NB];
 #pragma unroll
@@ -54,21 +75,43 @@ __global__ void __launch_bounds__(kMT) k_marginal(const A* __restrict__ a, u64 n
     acc[j] = 0.0;
     da[j] = dfl{0.f, 0.f};
   }
+  // bases of groups g, g + stride, ...: the group index's bits at the
+  // other qubits, advanced by masked adds (carries skip the measured qubits)
   const u64 stride = (u64)gridDim.x * kMT;
-  int since = 0;
-  for (u64 g = (u64)blockIdx.x * kMT + threadIdx.x; g < ngroups; g += stride) {
-    const u64 base = expand(g, args.ins);
+  u64 g = (u64)blockIdx.x * kMT + threadIdx.x;
+  u64 base[kMargU];
+  base[0] = expand(g, args.ins);
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const A v = a[base | args.spread[b0 + j]];
-      const dfl x = to_df(v.x), y = to_df(v.y);
-      df_acc(da[j], df_mul(x, x));
-      df_acc(da[j], df_mul(y, y));
+  for (int u = 1; u < kMargU; ++u) base[u] = ((base[u - 1] | ~args.free) + args.step1) & args.free;
+  int since = 0;
+  for (; g + (kMargU - 1) * stride < ngroups; g += kMargU * stride) {
+    A v[kMargU][NB];
+#pragma unroll
+    for (int u = 0; u < kMargU; ++u)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) v[u][j] = a[base[u] | args.spread[b0 + j]];
+#pragma unroll
+    for (int u = 0; u < kMargU; ++u) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        sq_acc(da[j], v[u][j].x);
+        sq_acc(da[j], v[u][j].y);
+      }
+      base[u] = ((base[u] | ~args.free) + args.stepU) & args.free;
     }
-    if (++since == 4) {
+    since += kMargU;
+    if (since >= kMargFlush) {
 #pragma unroll
       for (int j = 0; j < NB; ++j) df_flush(acc[j], da[j]);
       since = 0;
+    }
+  }
+  for (u64 b = base[0]; g < ngroups; g += stride, b = ((b | ~args.free) + args.step1) & args.free) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const A v = a[b | args.spread[b0 + j]];
+      sq_acc(da[j], v.x);
+      sq_acc(da[j], v.y);
     }
   }
 #pragma unroll
@@ -332,22 +375,37 @@ qs_status marginal(qs_state* s, const int* qubits, int k, double* out) {
     args.spread[r] = sp;
   }
   const u64 ngroups = u64(1) << (s->n - k);
-  const unsigned g = grid_for(ngroups, kMT, 4);
-  qs_status st = ensure_scratch(s, sizeof(double) * kBins * g);
+  // one wave of resident CTAs (3 per SM for up to 4 bins a pass, 2 for 8)
+  const unsigned g = grid_for(ngroups, kMT, (1 << k) >= kBins ? 2 : 3);
+  args.free = (u64(1) << s->n) - 1;
+  for (int i = 0; i < k; ++i) args.free &= ~(u64(1) << qubits[i]);
+  const u64 stride = (u64)g * kMT;
+  args.step1 = expand(stride, args.ins);
+  // every pass writes its own partials; one read-back after the last
+  const int npass = ((1 << k) + kBins - 1) / kBins;
+  const size_t per = (size_t)kBins * g;
+  qs_status st = ensure_scratch(s, sizeof(double) * per * npass);
   if (st != QS_OK) return st;
   double* part = static_cast<double*>(s->scratch);
-  std::vector<double> h((size_t)kBins * g);
+  std::vector<double> h(per * npass);
   for (int b0 = 0; b0 < (1 << k); b0 += kBins) {
     const int nb = std::min(kBins, (1 << k) - b0);  // 2, 4 or 8
     const A* amp = static_cast<const A*>(s->amp);
-    if (nb == 2) k_marginal<A, 2><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
-    else if (nb == 4) k_marginal<A, 4><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
-    else k_marginal<A, 8><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, part);
+    const int U = nb == 2 ? MargU<2>::value : nb == 4 ? MargU<4>::value : MargU<8>::value;
+    args.stepU = expand((u64)U * stride, args.ins);
+    double* pp = part + per * (size_t)(b0 / kBins);
+    if (nb == 2) k_marginal<A, 2><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, pp);
+    else if (nb == 4) k_marginal<A, 4><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, pp);
+    else k_marginal<A, 8><<<g, kMT, 0, s->stream>>>(amp, ngroups, args, b0, pp);
     if ((st = launch_ok("k_marginal")) != QS_OK) return st;
-    if ((st = sync_copy(s, h.data(), part, sizeof(double) * kBins * g, cudaMemcpyDeviceToHost)) != QS_OK) return st;
+  }
+  if ((st = sync_copy(s, h.data(), part, sizeof(double) * per * npass, cudaMemcpyDeviceToHost)) != QS_OK) return st;
+  for (int b0 = 0; b0 < (1 << k); b0 += kBins) {
+    const int nb = std::min(kBins, (1 << k) - b0);
+    const double* hp = h.data() + per * (size_t)(b0 / kBins);
     for (int j = 0; j < nb; ++j) {
       double sum = 0.0;
-      for (unsigned c = 0; c < g; ++c) sum += h[(size_t)c * kBins + j];
+      for (unsigned c = 0; c < g; ++c) sum += hp[(size_t)c * kBins + j];
       out[b0 + j] = sum;
     }
   }

@@ -1033,6 +1033,13 @@ qs_status run_norm2(qs_state* s, double* out) {
 }
 
 qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
+  if (a->amp == b->amp) {  // the same vector: <a|a> = the norm, one read of the state
+    double v = 0.0;
+    const qs_status st = run_norm2(a, &v);
+    out[0] = v;
+    out[1] = 0.0;
+    return st;
+  }
   const int LA = a->dtype == QS_C64 ? 1 : 0;
   const u64 npk = u64(1) << (a->n - LA);
   const unsigned g = red_grid(npk);

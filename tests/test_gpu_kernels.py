@@ -184,6 +184,8 @@ def test_norm_and_inner(qs, dtype, n):
     # FP64 accumulation of the same (FP32-exact for c64) inputs
     assert abs(sa.norm2() - want_n) <= 1e-12 * want_n
     assert abs(sa.inner(sb) - want_i) <= 1e-12 * (1 << n)
+    # a state with itself: the norm, exactly
+    assert sa.inner(sa) == complex(sa.norm2(), 0.0)
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
