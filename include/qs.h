@@ -293,7 +293,7 @@ qs_status qs_circuit_size(const qs_circuit* c, int* ngates);
  * block; 1 takes, at every block, the qubit set that absorbs the most
  * gates): a block's set decides which gates later blocks can take, so the
  * greedy order is not the fewest passes (a brick circuit of depth 40 on 30
- * qubits: 67 passes greedy, 64 with the default search).  QS_PLAN_SWAP and
+ * qubits: 67 passes greedy, 64 with a width of 16, 63 with the default 64).  QS_PLAN_SWAP and
  * QS_PLAN_PERMUTE apply the
  * gates in tile passes over the tile_qubits lowest physical qubits only and
  * move every other target there first, by in-place bit-pair exchange
@@ -321,7 +321,7 @@ typedef struct {
   int dense;
   int fuse_qubits;    /* QS_PLAN_FUSED: qubits per dense block, 2..6 (0 = 5) */
   int search;         /* QS_PLAN_FUSED: block-order search width, 1..256
-                         (1 = greedy; 0 = 16)                           */
+                         (1 = greedy; 0 = 64)                           */
   int fuse_min_qubits;/* qs_batch_create: circuits of at least this many
                          qubits run as QS_PLAN_FUSED plans (fuse_qubits,
                          0 = 6 for QS_C64, 5 for QS_C128) on parallel

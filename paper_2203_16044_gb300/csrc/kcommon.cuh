@@ -42,7 +42,9 @@ struct Ins {
 };
 
 __host__ __device__ __forceinline__ u64 expand(u64 i, const Ins& ins) {
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
   for (int j = 0; j < 12; ++j) {
     if (j < ins.k) {
       const u64 lo = i & ((u64(1) << ins.pos[j]) - 1);

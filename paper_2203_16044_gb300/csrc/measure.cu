@@ -351,10 +351,11 @@ Ins ins_for(const int* qubits, int k) {
   Ins ins{};
   ins.k = k;
   ins.set = 0;
-  int s[6];
-  for (int i = 0; i < k; ++i) s[i] = qubits[i];
-  std::sort(s, s + k);
-  for (int i = 0; i < k; ++i) ins.pos[i] = s[i];
+  for (int i = 0; i < k && i < 6; ++i) {  // insertion sort of at most 6 qubits
+    int j = i;
+    for (; j > 0 && ins.pos[j - 1] > qubits[i]; --j) ins.pos[j] = ins.pos[j - 1];
+    ins.pos[j] = qubits[i];
+  }
   return ins;
 }
 

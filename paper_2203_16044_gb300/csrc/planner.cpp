@@ -17,6 +17,11 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "qs_internal.h"
@@ -383,9 +388,10 @@ std::vector<int> tc_block_qubits(const std::vector<char>& used, int n, int kmax,
 namespace {
 typedef unsigned long long u64m;
 constexpr int kBranch = 8;
+constexpr int kPlanThreads = 8;  // host threads of the block-order search
 }  // namespace
 
-constexpr int kDefaultBeam = 16;  // QS_PLAN_FUSED search width when opts.search is 0
+constexpr int kDefaultBeam = 64;  // QS_PLAN_FUSED search width when opts.search is 0
 
 namespace {
 
@@ -466,6 +472,70 @@ u64m key_of_taken(const std::vector<int>& rem, const u64m* gm, u64m S, int nS) {
 }
 }  // namespace
 
+// Host threads for the search's steps, started once per search: run(count,
+// fn) calls fn(0 .. count-1) on the workers and the calling thread (indices
+// taken from a shared counter) and returns when all are done.
+class WorkPool {
+ public:
+  explicit WorkPool(int workers) {
+    for (int w = 0; w < workers; ++w) th_.emplace_back([this]() { loop(); });
+  }
+  ~WorkPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (std::thread& t : th_) t.join();
+  }
+  void run(int count, const std::function<void(int)>& fn) {
+    if (th_.empty() || count <= 1) {
+      for (int i = 0; i < count; ++i) fn(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      fn_ = &fn;
+      count_ = count;
+      next_.store(0);
+      active_ = (int)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_.wait(g, [this]() { return active_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work() {
+    for (int i = next_.fetch_add(1); i < count_; i = next_.fetch_add(1)) (*fn_)(i);
+  }
+  void loop() {
+    long seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&]() { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+      }
+      work();
+      std::lock_guard<std::mutex> g(mu_);
+      if (--active_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int count_ = 0, active_ = 0;
+  long gen_ = 0;
+  std::atomic<int> next_{0};
+  bool stop_ = false;
+};
+
 // Whether a tensor-core block whose gates touch `touched` gets a TMA shape.
 bool tc_fast_shape(u64m touched, int n, int kmax) {
   if (!touched) return true;
@@ -495,6 +565,13 @@ std::vector<std::pair<u64m, int>> search_blocks(const std::vector<qs_gate_rec>& 
     double cost, score;
   };
   const int branch = beam > 1 ? kBranch : 1;
+  // the states of a step are expanded, and the kept children built, on up
+  // to kPlanThreads host threads (each state's work is independent; the
+  // merge below runs in state order, so the result does not depend on the
+  // thread count)
+  const int nthr = beam >= 16 ? std::max(1, std::min<int>(kPlanThreads, (int)std::thread::hardware_concurrency())) : 1;
+  WorkPool pool(nthr - 1);
+  auto parallel = [&](int count, const std::function<void(int)>& fn) { pool.run(count, fn); };
   for (;;) {
     int done = -1;
     for (int s = 0; s < (int)cur.size(); ++s)
@@ -506,10 +583,10 @@ std::vector<std::pair<u64m, int>> search_blocks(const std::vector<qs_gate_rec>& 
       *cost = cur[done].cost;
       return out;
     }
-    std::vector<Child> kids;
-    for (int s = 0; s < (int)cur.size(); ++s) {
+    std::vector<std::vector<Child>> per((size_t)cur.size());
+    parallel((int)cur.size(), [&](int s) {
       const SchedState& S0 = cur[s];
-      std::vector<Child> mine;
+      std::vector<Child>& mine = per[(size_t)s];
       auto consider = [&](u64m set, int nS) {
         u64m touched = 0;
         const int taken = take_count(S0.rem, gm.data(), set, nS, &touched);
@@ -530,28 +607,41 @@ std::vector<std::pair<u64m, int>> search_blocks(const std::vector<qs_gate_rec>& 
       // most gates per unit of cost first; ties keep the candidate order
       std::stable_sort(mine.begin(), mine.end(), [](const Child& a, const Child& b) { return a.score > b.score; });
       if ((int)mine.size() > branch) mine.resize(branch);
-      kids.insert(kids.end(), mine.begin(), mine.end());
-    }
+    });
+    std::vector<Child> kids;
+    for (const std::vector<Child>& mine : per) kids.insert(kids.end(), mine.begin(), mine.end());
     std::stable_sort(kids.begin(), kids.end(), [&](const Child& a, const Child& b) {
       const size_t ra = cur[a.st].rem.size() - a.taken, rb = cur[b.st].rem.size() - b.taken;
       return ra != rb ? ra < rb : a.cost < b.cost;
     });
-    std::vector<SchedState> nxt;
+    // the children's keys (in parallel), then the first `beam` distinct
+    // ones in rank order, then their gate lists (in parallel)
+    std::vector<u64m> keys(kids.size());
+    const size_t nk = std::min(kids.size(), (size_t)beam * (size_t)kBranch);
+    parallel((int)nk, [&](int i) {
+      const SchedState& S0 = cur[kids[(size_t)i].st];
+      keys[(size_t)i] = S0.key ^ key_of_taken(S0.rem, gm.data(), kids[(size_t)i].set, kids[(size_t)i].nS);
+    });
+    std::vector<int> pick;
     std::vector<u64m> seen;
-    for (const Child& c : kids) {
-      if ((int)nxt.size() >= beam) break;
+    for (size_t i = 0; i < nk && (int)pick.size() < beam; ++i) {
+      if (std::find(seen.begin(), seen.end(), keys[i]) != seen.end()) continue;
+      seen.push_back(keys[i]);
+      pick.push_back((int)i);
+    }
+    std::vector<SchedState> nxt(pick.size());
+    parallel((int)pick.size(), [&](int j) {
+      const Child& c = kids[(size_t)pick[(size_t)j]];
       const SchedState& S0 = cur[c.st];
-      const u64m k = S0.key ^ key_of_taken(S0.rem, gm.data(), c.set, c.nS);
-      if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
-      seen.push_back(k);
-      SchedState ns;
       u64m kk = 0;
-      ns.rem = take_rest(S0.rem, gm.data(), c.set, c.nS, &kk);
-      ns.cost = c.cost;
-      ns.key = k;
-      nodes.push_back(SchedNode{S0.node, c.set, c.nS});
-      ns.node = (int)nodes.size() - 1;
-      nxt.push_back(std::move(ns));
+      nxt[(size_t)j].rem = take_rest(S0.rem, gm.data(), c.set, c.nS, &kk);
+      nxt[(size_t)j].cost = c.cost;
+      nxt[(size_t)j].key = keys[(size_t)pick[(size_t)j]];
+    });
+    for (size_t j = 0; j < pick.size(); ++j) {
+      const Child& c = kids[(size_t)pick[j]];
+      nodes.push_back(SchedNode{cur[c.st].node, c.set, c.nS});
+      nxt[j].node = (int)nodes.size() - 1;
     }
     cur.swap(nxt);
   }

@@ -1026,7 +1026,7 @@ qs_status run_norm2(qs_state* s, double* out) {
   if ((st = launch_ok("k_norm2")) != QS_OK) return st;
   k_final<<<1, kThreads, 0, s->stream>>>(part, g, res, 0);
   if ((st = launch_ok("k_final")) != QS_OK) return st;
-  double2 h;
+  double2 h{0.0, 0.0};
   if ((st = read_result(s, res, &h)) != QS_OK) return st;
   *out = h.x;
   return QS_OK;
@@ -1059,7 +1059,7 @@ qs_status run_inner(qs_state* a, qs_state* b, double out[2]) {
   if ((st = launch_ok("k_inner")) != QS_OK) return st;
   k_final<<<1, kThreads, 0, a->stream>>>(part, g, res, 0);
   if ((st = launch_ok("k_final")) != QS_OK) return st;
-  double2 h;
+  double2 h{0.0, 0.0};
   if ((st = read_result(a, res, &h)) != QS_OK) return st;
   out[0] = h.x;
   out[1] = h.y;
@@ -1143,8 +1143,9 @@ void build_stages(PTilePass& q, const std::vector<PauliGroup>& groups, int nt, b
     }
     for (int b = 0; b < m; ++b)
       if (!((sm >> b) & 1) && std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
-    S.ntb = (int8_t)std::min<int>(lg_nt, (int)order.size());
-    for (int i = 0; i < S.ntb; ++i) S.tb[i] = (int8_t)order[i];
+    const int ntb = std::min<int>(std::min<int>(lg_nt, (int)sizeof(S.tb)), (int)order.size());
+    S.ntb = (int8_t)ntb;
+    for (int i = 0; i < ntb && i < (int)sizeof(S.tb); ++i) S.tb[i] = (int8_t)order[i];
     S.dhi = 0;
     for (size_t i = S.ntb; i < order.size(); ++i) S.dhi |= 1u << order[i];
   }
@@ -1379,7 +1380,7 @@ qs_status run_expect(qs_state* s, int nterms, const u64* xmask, const u64* zmask
   }
   k_final<<<1, kThreads, 0, s->stream>>>(part, (int)npart, res, 0);
   if ((st = launch_ok("k_final")) != QS_OK) return st;
-  double2 h;
+  double2 h{0.0, 0.0};
   if ((st = read_result(s, res, &h)) != QS_OK) return st;
   if (any_tma) {
     int flag = 0;
