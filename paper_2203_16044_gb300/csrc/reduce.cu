@@ -331,6 +331,8 @@ struct PTilePass {
   int nst, nsg;     // stages; staged groups (accumulator slots)
   XStage st[kPassGroups];
   unsigned staged;  // bit gg: group slot gg is evaluated in a stage
+  int ngen;         // the other group slots, in order
+  int8_t genl[kPassGroups];
   int allst;        // every group staged: no per-amplitude group loop
   int clsg;         // complex64: slot of the Z-class group (-1: none), summed across tiles
   int ggrp;         // complex64: the warp group running the non-staged groups (-1: all threads)
@@ -580,6 +582,11 @@ __global__ void __launch_bounds__(NT, (std::is_same<R, float>::value ? 1 : 2)) k
   uint16_t* swt = reinterpret_cast<uint16_t*>(psm + ptile_stage_off());  // [nst][ST]
   float2* sacc = reinterpret_cast<float2*>(psm + ptile_acc_off(P.nst, ST));  // [nsg][ST] (hi, lo)
   __shared__ __align__(8) uint64_t pmbar[2];  // TMA tiles: buffer b filled
+  // the Z-class parameters of the pass's class group, read once
+  __shared__ struct {
+    u64 mask[kMaxClasses];
+    int d[kMaxClasses], len[kMaxClasses];
+  } ctab;
   const size_t boff = ptile_buf_off(P.nst, P.nsg, ST);
   const uint32_t sbase = smem_u32(psm);
   // (complex64 only: its launch adds kPtileAlign bytes for this pad)
@@ -608,6 +615,12 @@ __global__ void __launch_bounds__(NT, (std::is_same<R, float>::value ? 1 : 2)) k
       if ((lt >> i) & 1u) d |= 1u << P.st[si].tb[i];
     swt[si * ST + lt] = (uint16_t)TA::sw(d);
     for (int j = 0; j < P.st[si].nb; ++j) sacc[(P.st[si].slot0 + j) * ST + lt] = make_float2(0.f, 0.f);
+  }
+  if (kF32 && P.clsg >= 0 && threadIdx.x < kMaxClasses) {
+    const PauliGroup& cg = groups[P.gi[P.clsg]];
+    ctab.mask[threadIdx.x] = cg.cls_mask[threadIdx.x];
+    ctab.d[threadIdx.x] = cg.cls_d[threadIdx.x];
+    ctab.len[threadIdx.x] = cg.cls_len[threadIdx.x];
   }
   const u64 ntiles = u64(1) << (n - m);
   double sr = 0.0, si = 0.0;
@@ -774,8 +787,8 @@ __global__ void __launch_bounds__(NT, (std::is_same<R, float>::value ? 1 : 2)) k
         }
       }
     }
-    for (int gg = 0; !ALLST && need_F && gmine && gg < P.ng; ++gg) {
-      if ((P.staged >> gg) & 1u) continue;
+    for (int gq = 0; !ALLST && need_F && gmine && gq < P.ngen; ++gq) {
+      const int gg = P.genl[gq];
       const PauliGroup& g = groups[P.gi[gg]];
       const int h = P.hloc[gg];
       if (h < 0 && g.ncls > 0) {
@@ -814,10 +827,13 @@ __global__ void __launch_bounds__(NT, (std::is_same<R, float>::value ? 1 : 2)) k
 #pragma unroll
             for (int c = 0; c < kMaxClasses; ++c) {
               if (c >= nc) break;
-              const int d = g.cls_d[c];
-              const u64 mk = g.cls_mask[c];
+              // (the pass's class group from the shared table; another one,
+              // a diagonal group split for its size, from its own record)
+              const bool tab = gg == P.clsg;
+              const int d = tab ? ctab.d[c] : g.cls_d[c];
+              const u64 mk = tab ? ctab.mask[c] : g.cls_mask[c];
               const u64 V = (xr ^ (xr >> d)) & mk;
-              const float base = (float)(g.cls_len[c] - 2 * __popcll(V & ~u64(15)));
+              const float base = (float)((tab ? ctab.len[c] : g.cls_len[c]) - 2 * __popcll(V & ~u64(15)));
               unsigned bv[4];  // V(2^b), b < 4
 #pragma unroll
               for (int b = 0; b < 4; ++b) bv[b] = ((1u << b) ^ (d < 4 ? (1u << b) >> d : 0u)) & (unsigned)mk & 15u;
@@ -1281,6 +1297,9 @@ static void plan_pauli_passes(int n, qs_dtype dt, const std::vector<PauliGroup>&
     q.staged = 0;
     build_stages(q, groups, kStageThreads, dt == QS_C128);
     q.allst = q.ng > 0 && q.staged == (q.ng >= 32 ? ~0u : (1u << q.ng) - 1u);
+    q.ngen = 0;
+    for (int gg = 0; gg < q.ng; ++gg)
+      if (!((q.staged >> gg) & 1u)) q.genl[q.ngen++] = (int8_t)gg;
     q.clsg = -1;
     q.noflush = 1;
     for (int gg = 0; gg < q.ng; ++gg) {
