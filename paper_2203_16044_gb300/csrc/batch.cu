@@ -36,6 +36,9 @@ namespace {
 
 // Bound of one dependency wait, in SM clock cycles (about 2 s at 2 GHz).
 constexpr long long kSpinCycles = 4000000000LL;
+// fused circuits of a batch: tiles per CTA of their block kernels (their
+// states are small, and eight of them run at once on side streams)
+constexpr int kBatchTilesPerCta = 4;
 
 struct BCircuit {   // device
   void* amp;
@@ -341,6 +344,7 @@ qs_status qs_batch_create(int count, const int* nq, qs_dtype dtype, void* const*
             r = fail(QS_EINVAL, "qs_batch_create: circuit %d: a fused step is not a tensor-core block", i);
       qs_state* s = nullptr;
       if (r == QS_OK) r = qs_wrap(nq[i], dtype, dev_states[i], &s);
+      if (r == QS_OK) s->tiles_per_cta = kBatchTilesPerCta;
       if (r != QS_OK) {
         if (p) qs_plan_destroy(p);
         qs_batch_destroy(b);

@@ -718,7 +718,10 @@ qs_status block_grid(qs_state* s, Kern kern, int nthreads, size_t smem, int tcol
   per_sm = std::min(per_sm, 65536 / (regs * nthreads));
   per_sm = std::min(per_sm, 512 / tcols);
   if (per_sm < 1) per_sm = 1;
-  grid = grid_for(u64(1) << (s->n - K), kUT, per_sm);
+  // (a state in a batch asks for several tiles per CTA: each CTA's set-up --
+  // tensor memory, barriers, the block matrix -- then serves more tiles, and
+  // the batch's concurrent circuits share the SMs)
+  grid = grid_for(u64(1) << (s->n - K), (u64)kUT * (u64)std::max(1, s->tiles_per_cta), per_sm);
   return QS_OK;
 }
 

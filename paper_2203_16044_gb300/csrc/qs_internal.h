@@ -21,6 +21,7 @@ struct qs_state {
   void* scratch = nullptr;      // reduction partials, plan tables
   size_t scratch_bytes = 0;
   double* pinned = nullptr;     // small pinned host buffer for results
+  int tiles_per_cta = 1;        // block kernels: at least this many tiles per CTA (batched small states)
 };
 
 namespace qs {
