@@ -79,6 +79,24 @@ def test_block_order_search(qs, dtype):
         qs.Plan(qs.Circuit(W.brick(8, 2, 1)), 8, dtype, mode=qs.PLAN_FUSED, fuse_qubits=5, search=257)
 
 
+def test_wide_search_is_deterministic(qs):
+    # widths of 16 and more expand the beam's states on host threads; the
+    # merge runs in state order, so repeated builds give the same blocks,
+    # and the width-64 plan of a brick circuit is no longer than width 16's
+    circ = W.brick(20, 30, 6)
+    c = qs.Circuit(circ)
+
+    def blocks(search):
+        p = qs.Plan(c, 20, "c64", mode=qs.PLAN_FUSED, fuse_qubits=6, search=search)
+        return [tuple(sorted(p.step_qubits(i))) for i in range(p.stats()["passes"])]
+
+    first = blocks(64)
+    for _ in range(3):
+        assert blocks(64) == first
+    assert len(first) <= len(blocks(16))
+    assert blocks(0) == first  # the default width is 64
+
+
 def test_plan_kwargs_round_trip(qs):
     # the options an autotuner returns build a plan again (batch-only fields
     # such as fuse_min_qubits are left out)
