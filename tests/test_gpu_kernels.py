@@ -569,7 +569,7 @@ def test_expect_pauli_tile_passes(qs, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n", [6, 7, 13, 20])
+@pytest.mark.parametrize("n", [6, 7, 13, 20, 22])
 @pytest.mark.parametrize("kind", ["zz_classes", "zz_split", "xy_stages", "scattered"])
 def test_expect_pauli_stage_and_class_layouts(qs, dtype, n, kind):
     # complex64 tile passes in their several layouts: a one-group
@@ -579,7 +579,9 @@ def test_expect_pauli_stage_and_class_layouts(qs, dtype, n, kind):
     # on high qubits far enough apart that the tile is no single TMA box
     # (per-thread copies); 6 qubits: tiles below the TMA size.  zz_split:
     # more two-Z terms than one group holds (64), so the diagonal terms form
-    # several class groups in one pass, plus single-X terms
+    # several class groups in one pass, plus single-X terms.  22 qubits:
+    # 512 complex64 tiles of 2^13, so CTAs run several tiles each (the
+    # double-buffered copies reuse their buffers)
     rng = np.random.default_rng(1000 * n + len(kind))
     terms = []
     if kind == "zz_split":
