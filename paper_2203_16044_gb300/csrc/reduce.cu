@@ -3,7 +3,8 @@
 // Each thread accumulates over a grid-stride range of elements in
 // double-float, flushed into FP64 (see kU); warps combine in FP64 with shuffles, CTAs through shared memory, and the
 // per-CTA partials are summed by one CTA in index order.  The grid size
-// depends only on the problem size, so results are bitwise reproducible.
+// depends only on the problem size (and, for tile passes, the device), so
+// results are bitwise reproducible.
 //
 // Expectation of Pauli strings: P|x> = i^{nY} (-1)^{popcount(x & z)} |x ^ m>
 // (m = X/Y positions, z = Z/Y positions), so
@@ -20,6 +21,19 @@
 // and x ^ m then lie in the same tile.  The transverse-field Ising energy at
 // 30 qubits (one Z-only group and 30 single-X groups) takes three such
 // passes instead of 31.  Groups that fit no tile get a pass of their own.
+//
+// Inside a tile pass, single-term groups on one qubit (X or Y) go to
+// register stages: a thread holds the amplitudes spanning a few tile qubits
+// and forms every qubit's pair products from them (complex64: FP32 products
+// and FP32 sums per thread and tile, then exact double-float slots;
+// complex128: double-float products, slots flushed to FP64 every 16 tiles);
+// the lanes of a warp take tile qubits that the XOR swizzle of the tile
+// spreads over distinct banks.  Z-only two-qubit terms go by rows of 16
+// amplitudes (complex64), their parity function being linear over GF(2).
+// Complex64 tiles arrive by TMA (128-byte swizzle) into two buffers, the
+// next tile's copy in flight while the current one is evaluated.  The
+// partial sums follow a fixed order for a given grid, which depends on the
+// problem size and the device, so results repeat on a given GPU.
 #include <algorithm>
 #include <cstring>
 #include <vector>
