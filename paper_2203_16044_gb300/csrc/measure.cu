@@ -64,7 +64,7 @@ __device__ __forceinline__ void sq_acc(dfl& acc, double x) {
 constexpr int kMargFlush = 16;
 template <int NB> struct MargU { static constexpr int value = NB >= 8 ? 1 : 8 / NB; };
 template <typename A, int NB>
-__global__ void __launch_bounds__(kMT, NB >= 8 ? 2 : 3) k_marginal(const A* __restrict__ a, u64 ngroups,
+__global__ void __launch_bounds__(kMT, (NB >= 8 && sizeof(A) > 8) ? 2 : 3) k_marginal(const A* __restrict__ a, u64 ngroups,
                                                   const __grid_constant__ MargArgs args, int b0,
                                                   double* __restrict__ part) {
   constexpr int kMargU = MargU<NB>::value;
@@ -376,8 +376,8 @@ qs_status marginal(qs_state* s, const int* qubits, int k, double* out) {
     args.spread[r] = sp;
   }
   const u64 ngroups = u64(1) << (s->n - k);
-  // one wave of resident CTAs (3 per SM for up to 4 bins a pass, 2 for 8)
-  const unsigned g = grid_for(ngroups, kMT, (1 << k) >= kBins ? 2 : 3);
+  // one wave of resident CTAs (3 per SM; 2 for complex128 passes of 8 bins)
+  const unsigned g = grid_for(ngroups, kMT, ((1 << k) >= kBins && s->dtype == QS_C128) ? 2 : 3);
   args.free = (u64(1) << s->n) - 1;
   for (int i = 0; i < k; ++i) args.free &= ~(u64(1) << qubits[i]);
   const u64 stride = (u64)g * kMT;
