@@ -632,7 +632,7 @@ qs_status launch_layer(const LayerInfo& li, const qs_circuit* c, V* psi, V* lam,
       A.fixed[j] = to_mat(md, typename std::conditional<sizeof(V) == 8, float, double>::type(0));
     }
   }
-  std::sort(qs_sorted, qs_sorted + li.M);
+  small_sort(qs_sorted, li.M, [](int x, int y) { return x < y; });
   A.ins.k = li.M;
   A.ins.set = 0;
   for (int j = 0; j < li.M; ++j) A.ins.pos[j] = qs_sorted[j];

@@ -564,7 +564,7 @@ qs_status tc128_prepare(const int* qubits, int k, const double* M, int* q_sorted
   const int D = 1 << k, KR = 2 * D;
   int ord[6];
   for (int i = 0; i < k; ++i) ord[i] = i;
-  std::sort(ord, ord + k, [&](int x, int y) { return qubits[x] < qubits[y]; });
+  small_sort(ord, k, [&](int x, int y) { return qubits[x] < qubits[y]; });
   for (int p = 0; p < k; ++p) q_sorted[p] = qubits[ord[p]];
   int perm[32];
   for (int rp = 0; rp < D; ++rp) {

@@ -785,7 +785,7 @@ qs_status tc_prepare(const int* qubits, int k, const double* M, int* q_sorted, s
   const int D = 1 << k, KR = 2 * D;
   int ord[6];
   for (int i = 0; i < k; ++i) ord[i] = i;
-  std::sort(ord, ord + k, [&](int x, int y) { return qubits[x] < qubits[y]; });
+  small_sort(ord, k, [&](int x, int y) { return qubits[x] < qubits[y]; });
   for (int p = 0; p < k; ++p) q_sorted[p] = qubits[ord[p]];
   int perm[64];
   for (int rp = 0; rp < D; ++rp) {

@@ -33,6 +33,17 @@ __device__ __forceinline__ void st16(double* p, const double (&v)[2]) {
   *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
 }
 
+// Ascending insertion sort of a few ints under `less` (host; qubit lists).
+template <typename Less>
+inline void small_sort(int* a, int k, Less less) {
+  for (int i = 1; i < k; ++i) {
+    const int v = a[i];
+    int j = i;
+    for (; j > 0 && less(v, a[j - 1]); --j) a[j] = a[j - 1];
+    a[j] = v;
+  }
+}
+
 // Bit insertion: positions sorted ascending, each inserted as a 0 into the
 // compact counter i; `set` then ORs the bits that must be 1.
 struct Ins {
