@@ -12,7 +12,8 @@
   (tiled plan, itself oracle-exact at every size above) <= 1e-5; the circuit
   followed by its inverse returns |0...0>; sampled amplitudes of the QFT of a
   basis state against the closed form e^(2 pi i x0 k / N) / sqrt(N), for both
-  dtypes in the benchmark's plans.
+  dtypes in the benchmark's plans; the Ising energy (plus Y terms) of a
+  30-qubit product state against its closed form, for both dtypes.
 The oracle runs on the host cores (OpenMP); the 28-qubit comparison takes
 about a minute there.
 """
@@ -125,3 +126,34 @@ def test_qft_30q_sampled_closed_form(qs, dtype, mode, fuse):
     err = np.max(np.abs(got - want))
     tol = C128_TOL if dtype == "c128" else 1e-5 / math.sqrt(N)
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation_30q_product_state_closed_form(qs, dtype):
+    # the benchmark's TFIM observable plus a Y term on every qubit, at the
+    # full 30-qubit size (three complex64 tile passes, four complex128 ones,
+    # CTAs running hundreds of tiles each), on the product state
+    # prod_i U3(t_i, p_i, 0)|0>: <Z_i> = cos t_i, <X_i> = sin t_i cos p_i,
+    # <Y_i> = sin t_i sin p_i, and Z_i Z_j factorises, so
+    # E = sum_i cos t_i cos t_i+1 + sum_i sin t_i cos p_i + sum_i g_i sin t_i sin p_i.
+    # Complex128 within 1e-12 of sum |coeff|; complex64 within 1e-5: its
+    # amplitudes are products of 30 FP32-rounded factors (~30 * 2^-24
+    # relative each) and its sums are FP32 per tile (~2^-20)
+    n = 30
+    rng = np.random.default_rng(30)
+    t = rng.uniform(0.0, math.pi, n)
+    p = rng.uniform(-math.pi, math.pi, n)
+    g = rng.uniform(-1.0, 1.0, n)
+    terms = W.tfim(n) + [W.PauliTerm(float(g[i]), 1 << i, 1 << i) for i in range(n)]
+    s = qs.State(n, dtype)
+    for i in range(n):
+        c, sn = math.cos(t[i] / 2), math.sin(t[i] / 2)
+        U = np.array([[c, -sn], [np.exp(1j * p[i]) * sn, np.exp(1j * p[i]) * c]], dtype=np.complex128)
+        s.apply_1q(i, U)
+    want = (sum(math.cos(t[i]) * math.cos(t[i + 1]) for i in range(n - 1))
+            + sum(math.sin(t[i]) * math.cos(p[i]) for i in range(n))
+            + sum(g[i] * math.sin(t[i]) * math.sin(p[i]) for i in range(n)))
+    got = s.expect_pauli(terms)
+    tol = (1e-12 if dtype == "c128" else 1e-5) * sum(abs(x.coeff) for x in terms)
+    assert abs(got - want) <= tol, (got, want)
+    del s
