@@ -62,3 +62,19 @@ def test_argument_checks(qs):
     x[0] = 1 << 9
     assert L.qs_expect_pauli_passes(10, qs.C64, 1, xp, zp, ctypes.byref(out)) == qs.QS_OK
     assert out.value == 1
+
+
+def test_small_states_and_mixed_groups(qs):
+    # n = 5, 6: one tile covers the whole state (4 low qubits plus the rest),
+    # so every group fitting it shares one pass, for both dtypes
+    for n in (5, 6):
+        terms = xs(range(n)) + [W.PauliTerm(1.0, 0, 3), W.PauliTerm(0.5, 0b11, 0b10)]
+        assert qs.expect_pauli_passes(n, "c64", terms) == 1
+        assert qs.expect_pauli_passes(n, "c128", terms) == 1
+    # strings on a low and a high qubit share the tile of their high qubits;
+    # high qubits 10..18 (9 of them) fill a complex64 tile, a tenth opens a
+    # second pass, complex128 tiles hold 8
+    terms = [W.PauliTerm(1.0, (1 << q) | 1, 0) for q in range(10, 19)]
+    assert qs.expect_pauli_passes(24, "c64", terms) == 1
+    assert qs.expect_pauli_passes(24, "c64", terms + [W.PauliTerm(1.0, 1 << 20, 0)]) == 2
+    assert qs.expect_pauli_passes(24, "c128", terms) == 2
